@@ -1,0 +1,164 @@
+/*
+ * hsolve.h -- C-ABI of the GB300 (sm_103a) hierarchical solver with deferred
+ * compression.
+ *
+ * The method: Chen, Cambier, Boman, Rajamanickam, Tuminaro, Darve, "A Robust
+ * Hierarchical Solver for Ill-conditioned Systems with Applications to Ice
+ * Sheet Modeling".  The library solves A x = b for a sparse SPD matrix A
+ * (Sec. 3, Eq. ax=b) with a hierarchical factorization (Algorithm 1) used as
+ * a preconditioner (Algorithm 2) inside PCG or right-preconditioned GMRES
+ * (Sec. 5).
+ *
+ * Conventions for every entry point:
+ *   - CSR input: rowptr[n+1] (int64), col[nnz] (int32), val[nnz] (double);
+ *     both triangles stored, columns of a row in any order, A symmetric
+ *     positive definite.  The library copies what it needs during the call;
+ *     the caller keeps ownership of every pointer it passes.
+ *   - Vectors and CSR arrays live where options.mem says (HS_MEM_HOST: host
+ *     memory, HS_MEM_DEVICE: device memory of the current CUDA device).
+ *     hs_apply and hs_krylov always take device vectors.
+ *   - All device work is ordered on options.stream (a cudaStream_t, NULL =
+ *     legacy default stream); calls return after their work has completed,
+ *     except hs_apply, which is stream-ordered and returns immediately.
+ *   - Every function returns an hs_status; no exception crosses the ABI.
+ *     On error, output handles are set to NULL and nothing is leaked.
+ */
+#ifndef HSOLVE_H
+#define HSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_ARG = 1,         /* invalid argument (sizes, pointers, options)       */
+    HS_ERR_NOT_SPD = 2,     /* a diagonal block lost definiteness (Sec. 2, after
+                               Prop. 1): hs_info.fail_level / fail_cluster      */
+    HS_ERR_NOCONV = 3,      /* Krylov did not reach rtol within maxit            */
+    HS_ERR_CUDA = 4,        /* a CUDA call failed                                */
+    HS_ERR_OOM = 5,         /* device allocation failed                          */
+    HS_ERR_UNSUPPORTED = 6, /* a block is larger than the kernels support        */
+    HS_ERR_TIMEOUT = 7      /* a bounded device wait gave up                     */
+} hs_status;
+
+enum { HS_MEM_HOST = 0, HS_MEM_DEVICE = 1 };
+enum { HS_PREC_FP64 = 0, HS_PREC_MIXED = 1 };
+enum { HS_KRYLOV_PCG = 0, HS_KRYLOV_GMRES = 1 };
+
+/* Partition tree: leaf c owns the DOFs perm[leaf_ptr[c] .. leaf_ptr[c+1]);
+ * siblings 2c, 2c+1 merge at the next level (Sec. 4.2, Sec. 5).  n_leaf must
+ * be divisible by 2^depth. */
+typedef struct {
+    int32_t n_leaf;
+    int32_t* perm;      /* n entries, host memory */
+    int32_t* leaf_ptr;  /* n_leaf + 1 entries, host memory */
+    int32_t depth;      /* elimination levels before the dense top */
+} hs_tree;
+
+typedef struct {
+    double tol;          /* compression tolerance eps (absolute on the scaled
+                            block G^-1 A_sw, Eq. offdiag_new); default 1e-2  */
+    int32_t depth;       /* levels; -1 = log2(n_leaf) - 2 (top of 8 clusters) */
+    int32_t leaf_lines;  /* partitioner: vertical lines per leaf (default 4)   */
+    double theta;        /* partitioner: strong-coupling threshold (0.5)       */
+    int32_t precision;   /* HS_PREC_FP64 or HS_PREC_MIXED                      */
+    int32_t krylov;      /* HS_KRYLOV_PCG or HS_KRYLOV_GMRES                   */
+    int32_t restart;     /* GMRES restart length (default 50)                  */
+    double rtol;         /* Krylov stop: ||b - A x|| / ||b|| (default 1e-8)    */
+    int32_t maxit;       /* Krylov iteration cap (default 1000)                */
+    int32_t mem;         /* HS_MEM_HOST or HS_MEM_DEVICE                       */
+    int32_t profile;     /* nonzero: CUDA-event timing of every kernel class   */
+    void* stream;        /* cudaStream_t for all device work                   */
+    const double* coords; /* host n x 2 horizontal DOF positions for the
+                            partitioner when no tree is given (NULL: BFS)     */
+} hs_options;
+
+typedef struct {
+    int32_t iters;        /* Krylov iterations (PCG steps / GMRES inner steps) */
+    double rel_resid;     /* final true relative residual                      */
+    double setup_s;       /* partition + symbolic + numeric factorization      */
+    double solve_s;       /* Krylov solve                                      */
+    int32_t fail_level;   /* where HS_ERR_NOT_SPD happened, else -1            */
+    int32_t fail_cluster;
+    int64_t factor_bytes; /* device bytes held by the factor                   */
+} hs_info;
+
+typedef struct hs_factor_s* hs_handle;
+
+/* Fill *opt with the defaults listed above. */
+int hs_default_options(hs_options* opt);
+
+/* Column-preserving partition (Sec. 4.2): strongly coupled vertical lines
+ * (|a_ij| >= theta * max_k!=i |a_ik|) stay in one cluster; the line graph is
+ * bisected recursively (coords: n x 2 horizontal positions, or NULL for BFS
+ * graph growing) into 2^L leaves of at most leaf_lines lines.  Host pointers.
+ * out->perm / out->leaf_ptr are allocated by the library; release them with
+ * hs_tree_free. */
+int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col,
+                          const double* val, const double* coords, int32_t leaf_lines,
+                          double theta, hs_tree* out);
+int hs_tree_free(hs_tree* t);
+
+/* Hierarchical_Factor (Algorithm 1): scaled low-rank elimination of every
+ * cluster, level by level, then dense Cholesky of the top.  tree may be NULL
+ * (then hs_partition_extruded runs on options->coords, options->leaf_lines,
+ * options->theta, and options->depth applies).  CSR in options->mem.  On HS_ERR_NOT_SPD the
+ * failing (level, cluster) is written to *info when info is not NULL. */
+int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+             const hs_tree* tree, const hs_options* opt, hs_handle* out, hs_info* info);
+
+/* Hierarchical_Solve (Algorithm 2): z = M^-1 r, device pointers, n doubles
+ * each, stream-ordered on the handle's stream; r and z may not alias. */
+int hs_apply(hs_handle h, const double* r, double* z);
+
+/* Preconditioned Krylov solve with the factored handle (PCG, or GMRES(restart)
+ * with FP64 true-residual restarts): x0 = 0, stops at rel. residual <= rtol.
+ * b, x device pointers. */
+int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info);
+
+/* Partition + setup + Krylov in one call; pointers in opt->mem. */
+int hs_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+             const double* b, double* x, const hs_options* opt, hs_info* info);
+
+/* Release the handle and all device memory it owns (NULL is accepted). */
+int hs_destroy(hs_handle h);
+
+/* Introspection (host outputs): levels, per-cluster start size / final
+ * size (rank, 0 if eliminated) / phase of level l, dense top size. */
+int hs_num_levels(hs_handle h, int32_t* levels);
+int hs_level_clusters(hs_handle h, int32_t level, int32_t* nc);
+int hs_level_info(hs_handle h, int32_t level, int32_t* size0, int32_t* final_size,
+                  int32_t* phase);
+int hs_top_size(hs_handle h, int32_t* ntop);
+
+/* Kernel classes: 0 factor phase (Cholesky + scaling + CPQR + write-back),
+ * 1 Schur update, 2 level assembly, 3 dense top, 4 preconditioner apply,
+ * 5 Krylov SpMV / vector kernels.  For each class k < nclasses (host arrays,
+ * any may be NULL): device milliseconds summed over its launches since setup
+ * (CUDA events on the handle's stream; only when options.profile was set),
+ * the number of launch sites used, and the algorithmic FP64 flops / bytes of
+ * the factorization classes (POTRF s^3/3, scaling s^2 (n+w), CPQR
+ * sum_k 4 (s-k)(w-k) + 4 s r n, Schur n^2 f; assembly 20 bytes per nonzero). */
+int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops,
+                    double* bytes);
+int hs_reset_kernel_stats(hs_handle h);
+
+/* Number of this library's kernels launched by the process so far (a kernel
+ * inside the solve-phase CUDA graph counts once per graph launch). */
+int hs_launch_count(int64_t* count);
+
+/* Measures the FP64 FMA throughput of the current device with a chain of
+ * independent fma() operations (8 per thread, 8 CTAs per SM); TFLOP/s out. */
+int hs_measure_fp64_peak(void* stream, double* tflops);
+
+/* Static string for a status code. */
+const char* hs_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSOLVE_H */

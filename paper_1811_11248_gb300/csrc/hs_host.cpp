@@ -1,0 +1,1412 @@
+// hs_host.cpp -- host side of the hierarchical solver: column-preserving
+// partition (Sec. 4.2), per-level symbolic planning (phases, neighbour / fill
+// lists, block pattern with fill, Schur targets), the level-by-level driver of
+// Algorithm 1, the solve phase of Algorithm 2 (captured once as a CUDA graph),
+// PCG / GMRES (Sec. 5) and the C-ABI of include/hsolve.h.
+//
+// The phase rule (the paper leaves the cluster order of Algorithm 1 open):
+// repeatedly take the greedy maximal independent set, in ascending cluster
+// index, of the unprocessed clusters in the current block graph; that set is
+// one phase.  Clusters of a phase share no block, so eliminating them together
+// equals eliminating them one after another, up to the summation order of
+// their additive Schur updates, which is fixed (ascending cluster index).
+// Structure: the neighbours of a cluster are the blocks present in the level's
+// input; eliminating a cluster's fine part creates a block between every pair
+// of its neighbours; a cluster with no fill block has rank 0 and leaves.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hsolve.h"
+#include "hs_internal.h"
+
+using namespace hs;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// small utilities
+// ---------------------------------------------------------------------------
+struct HsError {
+    int code;
+};
+
+#define CK(x)                                                                        \
+    do {                                                                             \
+        cudaError_t e_ = (x);                                                        \
+        if (e_ != cudaSuccess) {                                                     \
+            if (e_ == cudaErrorMemoryAllocation) throw HsError{HS_ERR_OOM};          \
+            std::fprintf(stderr, "hsolve: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                  \
+            throw HsError{HS_ERR_CUDA};                                              \
+        }                                                                            \
+    } while (0)
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Device buffer owned by a handle.
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void ensure(size_t b) {
+        if (p && bytes >= b) return;
+        alloc(b);
+    }
+    void alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        CK(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+void upload(DBuf& d, const std::vector<T>& h, cudaStream_t st) {
+    d.alloc(sizeof(T) * std::max<size_t>(h.size(), 1));
+    if (!h.empty()) CK(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+}
+
+void sorted_insert(std::vector<int>& v, int x) {
+    auto it = std::lower_bound(v.begin(), v.end(), x);
+    if (it == v.end() || *it != x) v.insert(it, x);
+}
+void sorted_erase(std::vector<int>& v, int x) {
+    auto it = std::lower_bound(v.begin(), v.end(), x);
+    if (it != v.end() && *it == x) v.erase(it);
+}
+bool sorted_has(const std::vector<int>& v, int x) { return std::binary_search(v.begin(), v.end(), x); }
+
+// ---------------------------------------------------------------------------
+// Partition (Sec. 4.2)
+// ---------------------------------------------------------------------------
+struct Partitioner {
+    int nl = 0;
+    std::vector<double> lx, ly;
+    bool have_coords = false;
+    std::vector<int> gptr, gadj;
+    int L = 0;
+    std::vector<int> leaf_of;
+    int next_leaf = 0;
+    std::vector<char> state;
+
+    // BFS inside `set` from `start`; new components start at the lowest unvisited line.
+    std::vector<int> bfs(const std::vector<int>& set, int start) {
+        std::vector<int> out;
+        out.reserve(set.size());
+        for (int x : set) state[x] = 1;
+        std::vector<int> queue;
+        queue.reserve(set.size());
+        int root = start;
+        while (out.size() < set.size()) {
+            if (state[root] != 1) {
+                root = -1;
+                for (int x : set)
+                    if (state[x] == 1 && (root < 0 || x < root)) root = x;
+            }
+            state[root] = 2;
+            queue.clear();
+            queue.push_back(root);
+            for (size_t h = 0; h < queue.size(); h++) {
+                const int u = queue[h];
+                out.push_back(u);
+                for (int e = gptr[u]; e < gptr[u + 1]; e++) {
+                    const int w = gadj[e];
+                    if (state[w] == 1) {
+                        state[w] = 2;
+                        queue.push_back(w);
+                    }
+                }
+            }
+        }
+        for (int x : set) state[x] = 0;
+        return out;
+    }
+
+    void split(std::vector<int> set, int depth) {
+        if (depth == L) {
+            const int leaf = next_leaf++;
+            for (int x : set) leaf_of[x] = leaf;
+            return;
+        }
+        const size_t k = set.size(), left = (k + 1) / 2;
+        if (have_coords) {
+            double x0 = lx[set[0]], x1 = x0, y0 = ly[set[0]], y1 = y0;
+            for (int x : set) {
+                x0 = std::min(x0, lx[x]); x1 = std::max(x1, lx[x]);
+                y0 = std::min(y0, ly[x]); y1 = std::max(y1, ly[x]);
+            }
+            const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? lx : ly;
+            std::sort(set.begin(), set.end(), [&](int a, int b) {
+                return key[a] < key[b] || (key[a] == key[b] && a < b);
+            });
+        } else {
+            const int lo = *std::min_element(set.begin(), set.end());
+            std::vector<int> first = bfs(set, lo);
+            set = bfs(set, first.back());
+        }
+        std::vector<int> a(set.begin(), set.begin() + left), b(set.begin() + left, set.end());
+        std::sort(a.begin(), a.end());
+        std::sort(b.begin(), b.end());
+        split(std::move(a), depth + 1);
+        split(std::move(b), depth + 1);
+    }
+};
+
+int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const double* val, const double* coords,
+                   int leaf_lines, double theta, std::vector<int32_t>& perm, std::vector<int32_t>& leaf_ptr) {
+    const int n = (int)n64;
+    // strongly coupled lines: union-find over |a_ij| >= theta * max_{k != i} |a_ik|
+    std::vector<int> root(n);
+    for (int i = 0; i < n; i++) root[i] = i;
+    auto find = [&](int x) {
+        while (root[x] != x) { root[x] = root[root[x]]; x = root[x]; }
+        return x;
+    };
+    for (int i = 0; i < n; i++) {
+        double m = 0.0;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++)
+            if (col[e] != i) m = std::max(m, std::fabs(val[e]));
+        if (m <= 0.0) continue;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+            const int j = col[e];
+            if (j != i && std::fabs(val[e]) >= theta * m) {
+                const int a = find(i), b = find(j);
+                if (a != b) root[std::max(a, b)] = std::min(a, b);
+            }
+        }
+    }
+    Partitioner P;
+    std::vector<int> line_of(n), first;
+    {
+        std::vector<int> id(n, -1);
+        for (int i = 0; i < n; i++) {
+            const int r = find(i);
+            if (id[r] < 0) { id[r] = (int)first.size(); first.push_back(i); }
+            line_of[i] = id[r];
+        }
+    }
+    P.nl = (int)first.size();
+    {
+        std::vector<std::vector<int>> nb(P.nl);
+        for (int i = 0; i < n; i++)
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                const int lj = line_of[col[e]];
+                if (lj != line_of[i]) nb[line_of[i]].push_back(lj);
+            }
+        P.gptr.assign(P.nl + 1, 0);
+        for (int l = 0; l < P.nl; l++) {
+            std::sort(nb[l].begin(), nb[l].end());
+            nb[l].erase(std::unique(nb[l].begin(), nb[l].end()), nb[l].end());
+            P.gptr[l + 1] = P.gptr[l] + (int)nb[l].size();
+        }
+        P.gadj.reserve(P.gptr[P.nl]);
+        for (int l = 0; l < P.nl; l++) P.gadj.insert(P.gadj.end(), nb[l].begin(), nb[l].end());
+    }
+    if (coords) {
+        P.have_coords = true;
+        P.lx.resize(P.nl);
+        P.ly.resize(P.nl);
+        for (int l = 0; l < P.nl; l++) {
+            P.lx[l] = coords[2 * (int64_t)first[l]];
+            P.ly[l] = coords[2 * (int64_t)first[l] + 1];
+        }
+    }
+    int L = 0;
+    while (((int64_t)P.nl + (1LL << L) - 1) / (1LL << L) > leaf_lines && (1LL << (L + 1)) <= P.nl) L++;
+    P.L = L;
+    P.leaf_of.assign(P.nl, -1);
+    P.state.assign(P.nl, 0);
+    std::vector<int> all(P.nl);
+    for (int l = 0; l < P.nl; l++) all[l] = l;
+    P.split(std::move(all), 0);
+    const int nleaf = P.next_leaf;
+    leaf_ptr.assign(nleaf + 1, 0);
+    for (int i = 0; i < n; i++) leaf_ptr[P.leaf_of[line_of[i]] + 1]++;
+    for (int c = 0; c < nleaf; c++) leaf_ptr[c + 1] += leaf_ptr[c];
+    std::vector<int32_t> pos(leaf_ptr.begin(), leaf_ptr.end() - 1);
+    perm.assign(n, 0);
+    for (int i = 0; i < n; i++) perm[pos[P.leaf_of[line_of[i]]]++] = i;
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Symbolic plan of one level
+// ---------------------------------------------------------------------------
+struct LevelPlan {
+    int nc = 0;
+    std::vector<int> size0;
+    std::vector<std::vector<int>> adj0;  // level input pattern (no diagonal)
+    std::vector<int> phase;              // -1: empty cluster
+    std::vector<std::vector<int>> phases;
+    std::vector<std::vector<int>> nl, wl;
+    std::vector<std::vector<int>> all;   // every block that exists during the level (with diagonal)
+    std::vector<std::vector<int>> endp;  // blocks at level end (with diagonal of kept clusters)
+    std::vector<char> vanished;
+};
+
+void plan_level(LevelPlan& P) {
+    const int nc = P.nc;
+    std::vector<std::vector<int>> cur = P.adj0;
+    P.all = P.adj0;
+    for (int c = 0; c < nc; c++)
+        if (P.size0[c] > 0) sorted_insert(P.all[c], c);
+    P.phase.assign(nc, -1);
+    P.nl.assign(nc, {});
+    P.wl.assign(nc, {});
+    P.vanished.assign(nc, 0);
+    std::vector<char> done(nc, 0), insel(nc, 0);
+    int remaining = 0;
+    for (int c = 0; c < nc; c++) {
+        if (P.size0[c] > 0) remaining++;
+        else done[c] = 1;
+    }
+    while (remaining > 0) {
+        std::vector<int> sel;
+        for (int c = 0; c < nc; c++) {
+            if (done[c]) continue;
+            bool ok = true;
+            for (int q : cur[c])
+                if (insel[q]) { ok = false; break; }
+            if (ok) { insel[c] = 1; sel.push_back(c); }
+        }
+        const int ph = (int)P.phases.size();
+        for (int c : sel) {
+            auto& nlc = P.nl[c];
+            auto& wlc = P.wl[c];
+            for (int q : cur[c]) (sorted_has(P.adj0[c], q) ? nlc : wlc).push_back(q);
+            for (int p : nlc)
+                for (int q : nlc)
+                    if (p != q) {
+                        sorted_insert(cur[p], q);
+                        sorted_insert(P.all[p], q);
+                    }
+            if (wlc.empty()) {
+                P.vanished[c] = 1;
+                for (int q : cur[c]) sorted_erase(cur[q], c);
+                cur[c].clear();
+            }
+            done[c] = 1;
+            insel[c] = 0;
+            P.phase[c] = ph;
+            remaining--;
+        }
+        P.phases.push_back(std::move(sel));
+    }
+    P.endp = cur;
+    for (int c = 0; c < nc; c++)
+        if (P.size0[c] > 0 && !P.vanished[c]) sorted_insert(P.endp[c], c);
+}
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+enum { KC_FACTOR = 0, KC_SCHUR = 1, KC_ASSEMBLY = 2, KC_TOP = 3, KC_APPLY = 4, KC_KRYLOV = 5, KC_N = 6 };
+
+struct Level {
+    int nc = 0;
+    std::vector<int> size0, fin, phase;
+    std::vector<int64_t> slot;  // vector slot offsets (size nc + 1)
+    int nphases = 0;
+    std::vector<int> ph_task, ph_target, ph_nbt;  // per-phase ranges (size nphases + 1)
+    int smax = 0, wmax = 0, lmax = 0;
+    std::vector<TaskDev> tasks;
+    std::vector<ListDev> lists;
+    std::vector<int> task_rank;  // filled after the level
+    DBuf d_tasks, d_lists, d_nbt, d_nbc, d_meta, d_fac, d_slot, d_vcopy, d_y;
+    int nvcopy = 0;
+    int64_t fac_doubles = 0;
+    // algorithmic work of the level (filled after it ran)
+    double flops_factor = 0, flops_schur = 0;
+};
+
+struct Prof {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[KC_N];
+    size_t used[KC_N] = {0};
+    int64_t launches[KC_N] = {0};
+    double ms[KC_N] = {0};
+    void begin(int k, cudaStream_t st) {
+        launches[k]++;
+        if (!on) return;
+        if (used[k] == ev[k].size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            ev[k].push_back({a, b});
+        }
+        cudaEventRecord(ev[k][used[k]].first, st);
+    }
+    void end(int k, cudaStream_t st) {
+        if (!on) return;
+        cudaEventRecord(ev[k][used[k]].second, st);
+        used[k]++;
+    }
+    void collect() {
+        if (!on) return;
+        for (int k = 0; k < KC_N; k++) {
+            for (size_t i = 0; i < used[k]; i++) {
+                float t = 0.f;
+                cudaEventSynchronize(ev[k][i].second);
+                cudaEventElapsedTime(&t, ev[k][i].first, ev[k][i].second);
+                ms[k] += t;
+            }
+            used[k] = 0;
+        }
+    }
+    void reset() {
+        for (int k = 0; k < KC_N; k++) { ms[k] = 0; launches[k] = 0; used[k] = 0; }
+    }
+    ~Prof() {
+        for (int k = 0; k < KC_N; k++)
+            for (auto& e : ev[k]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
+};
+
+}  // namespace
+
+struct hs_factor_s {
+    int64_t n = 0;
+    int device = 0;
+    cudaStream_t st = nullptr;
+    hs_options opt{};
+    std::vector<int32_t> perm;
+    int depth = 0;
+    std::vector<std::unique_ptr<Level>> lev;
+    int ntop = 0;
+    DBuf d_perm, d_rowptr, d_col, d_val, d_top, d_ytop;
+    // Krylov workspace
+    DBuf d_kv, d_part, d_scal, d_V, d_Z, d_h;
+    int64_t factor_bytes = 0;
+    cudaGraphExec_t apply_graph = nullptr;
+    int64_t graph_kernels = 0;
+    Prof prof;
+    double work_flops[KC_N] = {0};
+    double work_bytes[KC_N] = {0};
+    ~hs_factor_s() {
+        if (apply_graph) cudaGraphExecDestroy(apply_graph);
+    }
+};
+
+namespace {
+
+void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
+    int32_t st[3];
+    CK(cudaMemcpyAsync(st, d_status.p, sizeof(st), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (st[0] == ST_NOT_SPD) {
+        if (info) { info->fail_level = st[1] < 0 ? h->depth : st[1]; info->fail_cluster = st[2]; }
+        throw HsError{HS_ERR_NOT_SPD};
+    }
+    if (st[0] != ST_OK) throw HsError{HS_ERR_UNSUPPORTED};
+}
+
+// Block table of a level: CSR over clusters of the blocks in `all`.
+struct BlockTable {
+    std::vector<int32_t> ptr, col, ld;
+    std::vector<int64_t> off;
+    int64_t total = 0;
+    int find(int p, int q) const {
+        auto b = col.begin() + ptr[p], e = col.begin() + ptr[p + 1];
+        auto it = std::lower_bound(b, e, q);
+        if (it == e || *it != q) throw HsError{HS_ERR_ARG};  // planner invariant broken
+        return (int)(it - col.begin());
+    }
+};
+
+BlockTable make_table(const LevelPlan& P) {
+    BlockTable T;
+    T.ptr.assign(P.nc + 1, 0);
+    for (int c = 0; c < P.nc; c++) T.ptr[c + 1] = T.ptr[c] + (int)P.all[c].size();
+    T.col.reserve(T.ptr[P.nc]);
+    T.off.reserve(T.ptr[P.nc]);
+    T.ld.reserve(T.ptr[P.nc]);
+    int64_t o = 0;
+    for (int c = 0; c < P.nc; c++)
+        for (int q : P.all[c]) {
+            T.col.push_back(q);
+            T.off.push_back(o);
+            T.ld.push_back(P.size0[q]);
+            o += (int64_t)P.size0[c] * P.size0[q];
+        }
+    T.total = o;
+    return T;
+}
+
+// Factor one level: plan, device records, phases.  `blocks` holds the level's
+// assembled matrix (layout T).  Returns the final sizes.
+void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf& blocks, DBuf& d_cur,
+                  DBuf& d_status, hs_info* info) {
+    Level& L = *h->lev[l];
+    cudaStream_t st = h->st;
+    L.nc = P.nc;
+    L.size0 = P.size0;
+    L.phase = P.phase;
+    L.nphases = (int)P.phases.size();
+    L.slot.assign(P.nc + 1, 0);
+    for (int c = 0; c < P.nc; c++) L.slot[c + 1] = L.slot[c] + P.size0[c];
+
+    // tasks in phase order
+    std::vector<int> task_of(P.nc, -1);
+    int64_t fac = 0, ws_phase_max = 0;
+    int32_t meta = 0;
+    L.ph_task.assign(1, 0);
+    L.ph_target.assign(1, 0);
+    L.ph_nbt.assign(1, 0);
+    std::vector<TargetDev> targets;
+    std::vector<ContribDev> contribs;
+    std::vector<NbTargetDev> nbts;
+    std::vector<NbContribDev> nbcs;
+    L.smax = 1; L.wmax = 1; L.lmax = 1;
+    for (int ph = 0; ph < L.nphases; ph++) {
+        int64_t ws = 0;
+        for (int c : P.phases[ph]) {
+            TaskDev t{};
+            t.c = c;
+            t.s = P.size0[c];
+            t.nn = (int)P.nl[c].size();
+            t.nw = (int)P.wl[c].size();
+            t.list = (int)L.lists.size();
+            t.diag_blk = T.find(c, c);
+            int ncap = 0, wcap = 0;
+            for (int k = 0; k < t.nn + t.nw; k++) {
+                const int q = k < t.nn ? P.nl[c][k] : P.wl[c][k - t.nn];
+                ListDev le{};
+                le.q = q;
+                le.blk_cq = T.find(c, q);
+                le.blk_qc = T.find(q, c);
+                L.lists.push_back(le);
+                wcap += P.size0[q];
+                if (k < t.nn) ncap += P.size0[q];
+            }
+            t.ncap = ncap;
+            t.wcap = wcap;
+            t.meta = meta;
+            meta += 1 + 2 * t.nn;
+            t.g_off = fac; fac += (int64_t)t.s * t.s;
+            t.v_off = fac; fac += (int64_t)t.s * t.s;
+            t.tau_off = fac; fac += t.s;
+            t.c_off = fac; fac += (int64_t)t.s * std::max(ncap, 1);
+            t.m_off = ws; ws += (int64_t)t.s * std::max(wcap, 1);
+            L.smax = std::max(L.smax, t.s);
+            L.wmax = std::max(L.wmax, wcap);
+            L.lmax = std::max(L.lmax, t.nn + t.nw);
+            task_of[c] = (int)L.tasks.size();
+            L.tasks.push_back(t);
+        }
+        ws_phase_max = std::max(ws_phase_max, ws);
+        // Schur targets of the phase: (p, q), p <= q, contributions ascending
+        std::map<std::pair<int, int>, std::vector<ContribDev>> tg;
+        std::map<int, std::vector<NbContribDev>> nb;
+        for (int c : P.phases[ph]) {
+            const int ti = task_of[c];
+            const auto& nlc = P.nl[c];
+            for (int a = 0; a < (int)nlc.size(); a++) {
+                nb[nlc[a]].push_back(NbContribDev{ti, a});
+                for (int b = 0; b < (int)nlc.size(); b++)
+                    if (nlc[a] <= nlc[b]) tg[{nlc[a], nlc[b]}].push_back(ContribDev{ti, a, b});
+            }
+        }
+        for (auto& kv : tg) {
+            TargetDev g{};
+            g.p = kv.first.first;
+            g.q = kv.first.second;
+            g.blk_pq = T.find(g.p, g.q);
+            g.blk_qp = T.find(g.q, g.p);
+            g.c_begin = (int)contribs.size();
+            contribs.insert(contribs.end(), kv.second.begin(), kv.second.end());
+            g.c_end = (int)contribs.size();
+            targets.push_back(g);
+        }
+        for (auto& kv : nb) {
+            NbTargetDev g{};
+            g.q = kv.first;
+            g.c_begin = (int)nbcs.size();
+            nbcs.insert(nbcs.end(), kv.second.begin(), kv.second.end());
+            g.c_end = (int)nbcs.size();
+            nbts.push_back(g);
+        }
+        L.ph_task.push_back((int)L.tasks.size());
+        L.ph_target.push_back((int)targets.size());
+        L.ph_nbt.push_back((int)nbts.size());
+    }
+    if (factor_smem_bytes(L.smax, L.wmax, L.lmax) > (size_t)kFactorMaxSmem) throw HsError{HS_ERR_UNSUPPORTED};
+
+    upload(L.d_tasks, L.tasks, st);
+    upload(L.d_lists, L.lists, st);
+    DBuf d_targets, d_contribs, d_ws;
+    upload(d_targets, targets, st);
+    upload(d_contribs, contribs, st);
+    upload(L.d_nbt, nbts, st);
+    upload(L.d_nbc, nbcs, st);
+    L.d_meta.alloc(sizeof(int32_t) * std::max<int32_t>(meta, 1));
+    L.d_fac.alloc(sizeof(double) * std::max<int64_t>(fac, 1));
+    L.fac_doubles = fac;
+    d_ws.alloc(sizeof(double) * std::max<int64_t>(ws_phase_max, 1));
+    upload(L.d_slot, L.slot, st);
+
+    std::vector<int32_t> ld(T.ld.begin(), T.ld.end());
+    DBuf d_off, d_ld;
+    upload(d_off, T.off, st);
+    upload(d_ld, ld, st);
+    const double eps2 = h->opt.tol * h->opt.tol;
+    for (int ph = 0; ph < L.nphases; ph++) {
+        const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
+        h->prof.begin(KC_FACTOR, st);
+        CK(launch_factor_phase(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.wmax, L.lmax,
+                               L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
+                               d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.as<double>(),
+                               L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l));
+        h->prof.end(KC_FACTOR, st);
+        const int g0 = L.ph_target[ph], ng = L.ph_target[ph + 1] - g0;
+        if (ng > 0) {
+            h->prof.begin(KC_SCHUR, st);
+            CK(launch_schur_phase(st, d_targets.as<TargetDev>(), g0, ng, d_contribs.as<ContribDev>(),
+                                  L.d_tasks.as<TaskDev>(), L.d_fac.as<double>(), L.d_meta.as<int32_t>(),
+                                  blocks.as<double>(), d_off.as<int64_t>(), d_ld.as<int32_t>(),
+                                  d_cur.as<int32_t>(), h->opt.precision));
+            h->prof.end(KC_SCHUR, st);
+        }
+    }
+    check_status(h, d_status, info);
+    L.fin.assign(P.nc, 0);
+    CK(cudaMemcpyAsync(L.fin.data(), d_cur.p, sizeof(int32_t) * P.nc, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> hmeta(meta);
+    if (meta) CK(cudaMemcpyAsync(hmeta.data(), L.d_meta.p, sizeof(int32_t) * meta, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // algorithmic work: POTRF s^3/3, TRSM s^2 (n + w), CPQR sum_k 4 (s-k)(w-k) + 4 s r n, Schur n^2 f
+    L.task_rank.resize(L.tasks.size());
+    for (size_t ti = 0; ti < L.tasks.size(); ti++) {
+        const TaskDev& t = L.tasks[ti];
+        const int r = hmeta[t.meta];
+        L.task_rank[ti] = r;
+        double ncol = 0, wcol = 0;
+        for (int k = 0; k < t.nn + t.nw; k++) {
+            const int q = L.lists[t.list + k].q;
+            const int w = (P.phase[q] >= 0 && P.phase[q] < P.phase[t.c]) ? L.fin[q] : P.size0[q];
+            (k < t.nn ? ncol : wcol) += w;
+        }
+        const double s = t.s;
+        double f = s * s * s / 3.0 + s * s * (ncol + wcol) + 4.0 * s * r * ncol;
+        for (int k = 0; k < r; k++) f += 4.0 * (s - k) * (wcol - k);
+        L.flops_factor += f;
+        L.flops_schur += ncol * ncol * (s - r);  // symmetric half, FMA = 2
+    }
+    h->work_flops[KC_FACTOR] += L.flops_factor;
+    h->work_flops[KC_SCHUR] += L.flops_schur;
+}
+
+// Coarse-vector copies from level l to the next level / the top.
+void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& next_slot) {
+    std::vector<VCopyDev> v;
+    for (int c = 0; c < L.nc; c++) {
+        if (L.fin[c] <= 0) continue;
+        VCopyDev x{};
+        x.src = L.slot[c];
+        x.dst = next_slot[c / 2] + ((c & 1) ? L.fin[c - 1] : 0);
+        x.len = L.fin[c];
+        v.push_back(x);
+    }
+    L.nvcopy = (int)v.size();
+    upload(L.d_vcopy, v, h->st);
+}
+
+// Block copies from level-l blocks (table T, final sizes fin, end pattern endp)
+// into the next level (table Tn) or, if Tn == nullptr, into the dense top
+// (row offsets top_off, leading dimension ntop).
+std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& fin, const BlockTable& T,
+                                   const BlockTable* Tn, const std::vector<int>& nsize,
+                                   const std::vector<int64_t>& top_off, int ntop) {
+    std::vector<CopyDev> cps;
+    for (int a = 0; a < P.nc; a++) {
+        if (fin[a] <= 0) continue;
+        const int A2 = a / 2, oa = (a & 1) ? fin[a - 1] : 0;
+        for (int b : P.endp[a]) {
+            if (fin[b] <= 0) continue;
+            const int B2 = b / 2, ob = (b & 1) ? fin[b - 1] : 0;
+            CopyDev c{};
+            const int sb = T.find(a, b);
+            c.src = T.off[sb];
+            c.src_ld = T.ld[sb];
+            if (Tn) {
+                const int db = Tn->find(A2, B2);
+                c.dst = Tn->off[db] + (int64_t)oa * nsize[B2] + ob;
+                c.dst_ld = nsize[B2];
+            } else {
+                c.dst = (top_off[A2] + oa) * (int64_t)ntop + top_off[B2] + ob;
+                c.dst_ld = ntop;
+            }
+            c.rows = fin[a];
+            c.cols = fin[b];
+            cps.push_back(c);
+        }
+    }
+    return cps;
+}
+
+void build_apply_graph(hs_factor_s* h);
+
+void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const double* val,
+                const hs_tree* tree_in, hs_info* info) {
+    cudaStream_t st = h->st;
+    const int64_t n = h->n;
+    // host copy of the pattern (the symbolic analysis runs on the host)
+    std::vector<int64_t> hrp;
+    std::vector<int32_t> hcol;
+    std::vector<double> hval;
+    const int64_t* rp = rowptr;
+    const int32_t* cl = col;
+    const double* vl = val;
+    if (h->opt.mem == HS_MEM_DEVICE) {
+        hrp.resize(n + 1);
+        CK(cudaMemcpyAsync(hrp.data(), rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int64_t nnz = hrp[n];
+        hcol.resize(nnz);
+        CK(cudaMemcpyAsync(hcol.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st));
+        if (!tree_in) {
+            hval.resize(nnz);
+            CK(cudaMemcpyAsync(hval.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        rp = hrp.data();
+        cl = hcol.data();
+        vl = hval.empty() ? nullptr : hval.data();
+    }
+    const int64_t nnz = rp[n];
+    for (int64_t i = 0; i < n; i++)
+        if (rp[i + 1] < rp[i]) throw HsError{HS_ERR_ARG};
+    for (int64_t e = 0; e < nnz; e++)
+        if (cl[e] < 0 || cl[e] >= n) throw HsError{HS_ERR_ARG};
+
+    // partition tree
+    std::vector<int32_t> leaf_ptr;
+    int depth;
+    if (tree_in) {
+        if (!tree_in->perm || !tree_in->leaf_ptr || tree_in->n_leaf <= 0) throw HsError{HS_ERR_ARG};
+        h->perm.assign(tree_in->perm, tree_in->perm + n);
+        leaf_ptr.assign(tree_in->leaf_ptr, tree_in->leaf_ptr + tree_in->n_leaf + 1);
+        depth = tree_in->depth;
+    } else {
+        partition_impl(n, rp, cl, vl, h->opt.coords, h->opt.leaf_lines, h->opt.theta, h->perm, leaf_ptr);
+        depth = h->opt.depth;
+    }
+    const int nleaf = (int)leaf_ptr.size() - 1;
+    if (depth < 0) {
+        int Lg = 0;
+        while ((1 << (Lg + 1)) <= nleaf) Lg++;
+        depth = std::max(nleaf >= 2 ? 1 : 0, Lg - 2);
+    }
+    if (leaf_ptr[0] != 0 || leaf_ptr[nleaf] != n) throw HsError{HS_ERR_ARG};
+    if (depth > 0 && (depth > 30 || nleaf % (1 << depth) != 0)) throw HsError{HS_ERR_ARG};
+    {
+        std::vector<char> seen(n, 0);
+        for (int64_t i = 0; i < n; i++) {
+            const int32_t p = h->perm[i];
+            if (p < 0 || p >= n || seen[p]) throw HsError{HS_ERR_ARG};
+            seen[p] = 1;
+        }
+    }
+    h->depth = depth;
+
+    // device copies of A (SpMV) and of the permutation
+    h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));
+    h->d_col.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    h->d_val.alloc(sizeof(double) * std::max<int64_t>(nnz, 1));
+    const cudaMemcpyKind kind = h->opt.mem == HS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(h->d_rowptr.p, rowptr, sizeof(int64_t) * (n + 1), kind, st));
+    if (nnz) {
+        CK(cudaMemcpyAsync(h->d_col.p, col, sizeof(int32_t) * nnz, kind, st));
+        CK(cudaMemcpyAsync(h->d_val.p, val, sizeof(double) * nnz, kind, st));
+    }
+    upload(h->d_perm, h->perm, st);
+
+    // level 0 pattern
+    std::vector<int32_t> dof_cluster(n), dof_local(n);
+    for (int c = 0; c < nleaf; c++)
+        for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
+            dof_cluster[h->perm[k]] = c;
+            dof_local[h->perm[k]] = k - leaf_ptr[c];
+        }
+    LevelPlan P;
+    P.nc = nleaf;
+    P.size0.resize(nleaf);
+    for (int c = 0; c < nleaf; c++) P.size0[c] = leaf_ptr[c + 1] - leaf_ptr[c];
+    P.adj0.assign(nleaf, {});
+    for (int64_t i = 0; i < n; i++) {
+        const int p = dof_cluster[i];
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+            const int q = dof_cluster[cl[e]];
+            if (q != p) {  // block pattern kept symmetric even if the CSR pattern is not
+                P.adj0[p].push_back(q);
+                P.adj0[q].push_back(p);
+            }
+        }
+    }
+    for (auto& v : P.adj0) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+
+    DBuf d_status;
+    d_status.alloc(sizeof(int32_t) * 4);
+    CK(cudaMemsetAsync(d_status.p, 0, sizeof(int32_t) * 4, st));
+
+    plan_level(P);
+    BlockTable T = make_table(P);
+    DBuf blocks;
+    blocks.alloc(sizeof(double) * std::max<int64_t>(T.total, 1));
+    CK(cudaMemsetAsync(blocks.p, 0, sizeof(double) * std::max<int64_t>(T.total, 1), st));
+    {
+        DBuf d_dc, d_dl, d_bp, d_bc, d_bo, d_bl;
+        upload(d_dc, dof_cluster, st);
+        upload(d_dl, dof_local, st);
+        upload(d_bp, T.ptr, st);
+        upload(d_bc, T.col, st);
+        upload(d_bo, T.off, st);
+        upload(d_bl, T.ld, st);
+        h->prof.begin(KC_ASSEMBLY, st);
+        CK(launch_scatter_csr(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(),
+                              d_dc.as<int32_t>(), d_dl.as<int32_t>(), d_bp.as<int32_t>(), d_bc.as<int32_t>(),
+                              d_bo.as<int64_t>(), d_bl.as<int32_t>(), blocks.as<double>()));
+        h->prof.end(KC_ASSEMBLY, st);
+        CK(cudaStreamSynchronize(st));
+    }
+    h->work_bytes[KC_ASSEMBLY] += 20.0 * nnz;
+
+    h->lev.clear();
+    std::vector<int> fin = P.size0;  // depth 0: every cluster goes to the top as is
+    for (int l = 0; l < depth; l++) {
+        h->lev.emplace_back(new Level());
+        DBuf d_cur;
+        upload(d_cur, P.size0, st);
+        factor_level(h, l, P, T, blocks, d_cur, d_status, info);
+        Level& L = *h->lev[l];
+        fin = L.fin;
+        // next level (or the top)
+        const int nn = P.nc / 2;
+        std::vector<int> nsize(nn);
+        for (int c = 0; c < nn; c++) nsize[c] = fin[2 * c] + fin[2 * c + 1];
+        std::vector<int64_t> nslot(nn + 1, 0);
+        for (int c = 0; c < nn; c++) nslot[c + 1] = nslot[c] + nsize[c];
+        make_vcopies(h, L, nslot);
+        if (l + 1 < depth) {
+            LevelPlan Pn;
+            Pn.nc = nn;
+            Pn.size0 = nsize;
+            Pn.adj0.assign(nn, {});
+            for (int a = 0; a < P.nc; a++) {
+                if (fin[a] <= 0) continue;
+                for (int b : P.endp[a])
+                    if (fin[b] > 0 && a / 2 != b / 2) Pn.adj0[a / 2].push_back(b / 2);
+            }
+            for (auto& v : Pn.adj0) {
+                std::sort(v.begin(), v.end());
+                v.erase(std::unique(v.begin(), v.end()), v.end());
+            }
+            plan_level(Pn);
+            BlockTable Tn = make_table(Pn);
+            DBuf nblocks;
+            nblocks.alloc(sizeof(double) * std::max<int64_t>(Tn.total, 1));
+            CK(cudaMemsetAsync(nblocks.p, 0, sizeof(double) * std::max<int64_t>(Tn.total, 1), st));
+            std::vector<CopyDev> cps = make_assembly(P, fin, T, &Tn, nsize, {}, 0);
+            DBuf d_cps;
+            upload(d_cps, cps, st);
+            h->prof.begin(KC_ASSEMBLY, st);
+            CK(launch_copy_blocks(st, d_cps.as<CopyDev>(), (int)cps.size(), blocks.as<double>(),
+                                  nblocks.as<double>()));
+            h->prof.end(KC_ASSEMBLY, st);
+            CK(cudaStreamSynchronize(st));
+            blocks = std::move(nblocks);
+            P = std::move(Pn);
+            T = std::move(Tn);
+        }
+    }
+    // dense top
+    {
+        std::vector<int> tsize;
+        const bool merge = depth > 0;
+        const int ntc = merge ? P.nc / 2 : P.nc;
+        tsize.resize(ntc);
+        for (int c = 0; c < ntc; c++) tsize[c] = merge ? fin[2 * c] + fin[2 * c + 1] : fin[c];
+        std::vector<int64_t> toff(ntc + 1, 0);
+        for (int c = 0; c < ntc; c++) toff[c + 1] = toff[c] + tsize[c];
+        h->ntop = (int)toff[ntc];
+        h->d_top.alloc(sizeof(double) * std::max<int64_t>((int64_t)h->ntop * h->ntop, 1));
+        h->d_ytop.alloc(sizeof(double) * std::max(h->ntop, 1));
+        if (h->ntop > 0) {
+            CK(cudaMemsetAsync(h->d_top.p, 0, sizeof(double) * (int64_t)h->ntop * h->ntop, st));
+            std::vector<CopyDev> cps;
+            if (merge) {
+                cps = make_assembly(P, fin, T, nullptr, tsize, toff, h->ntop);
+            } else {
+                for (int a = 0; a < P.nc; a++)
+                    for (int b : P.all[a]) {
+                        CopyDev c{};
+                        const int sb = T.find(a, b);
+                        c.src = T.off[sb];
+                        c.src_ld = T.ld[sb];
+                        c.dst = toff[a] * (int64_t)h->ntop + toff[b];
+                        c.dst_ld = h->ntop;
+                        c.rows = fin[a];
+                        c.cols = fin[b];
+                        cps.push_back(c);
+                    }
+            }
+            DBuf d_cps;
+            upload(d_cps, cps, st);
+            h->prof.begin(KC_TOP, st);
+            CK(launch_copy_blocks(st, d_cps.as<CopyDev>(), (int)cps.size(), blocks.as<double>(),
+                                  h->d_top.as<double>()));
+            CK(launch_dense_cholesky(st, h->ntop, h->d_top.as<double>(), d_status.as<int32_t>()));
+            h->prof.end(KC_TOP, st);
+            check_status(h, d_status, info);
+        }
+    }
+    blocks.release();
+    // level vectors for the solve phase
+    int64_t fb = (int64_t)h->ntop * h->ntop * 8;
+    for (auto& Lp : h->lev) {
+        Lp->d_y.alloc(sizeof(double) * std::max<int64_t>(Lp->slot[Lp->nc], 1));
+        fb += Lp->fac_doubles * 8;
+    }
+    h->factor_bytes = fb;
+    CK(cudaStreamSynchronize(st));
+    build_apply_graph(h);
+}
+
+// Algorithm 2 on the internal level vectors (y0 holds r in partition order).
+void enqueue_apply(hs_factor_s* h) {
+    cudaStream_t st = h->st;
+    const int D = (int)h->lev.size();
+    for (int l = 0; l < D; l++) {
+        Level& L = *h->lev[l];
+        for (int ph = 0; ph < L.nphases; ph++) {
+            const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
+            CK(launch_apply_fwd_diag(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.d_fac.as<double>(),
+                                     L.d_meta.as<int32_t>(), L.d_slot.as<int64_t>(), L.d_y.as<double>()));
+            const int g0 = L.ph_nbt[ph], ng = L.ph_nbt[ph + 1] - g0;
+            CK(launch_apply_fwd_nb(st, L.d_nbt.as<NbTargetDev>(), g0, ng, L.d_nbc.as<NbContribDev>(),
+                                   L.d_tasks.as<TaskDev>(), L.d_fac.as<double>(), L.d_meta.as<int32_t>(),
+                                   L.d_slot.as<int64_t>(), L.d_y.as<double>()));
+        }
+        double* next = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
+        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, L.d_y.as<double>(), next, 0));
+    }
+    CK(launch_top_solve(st, h->ntop, h->d_top.as<double>(), h->d_ytop.as<double>()));
+    for (int l = D - 1; l >= 0; l--) {
+        Level& L = *h->lev[l];
+        double* next = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
+        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, next, L.d_y.as<double>(), 1));
+        for (int ph = L.nphases - 1; ph >= 0; ph--) {
+            const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
+            CK(launch_apply_bwd(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.d_lists.as<ListDev>(),
+                                L.d_fac.as<double>(), L.d_meta.as<int32_t>(), L.d_slot.as<int64_t>(),
+                                L.d_y.as<double>()));
+        }
+    }
+}
+
+void build_apply_graph(hs_factor_s* h) {
+    if (h->apply_graph) { cudaGraphExecDestroy(h->apply_graph); h->apply_graph = nullptr; }
+    if (h->lev.empty() && h->ntop == 0) return;
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = h->st;
+    h->st = cap;
+    cudaGraph_t g = nullptr;
+    try {
+        const int64_t before = launch_count();
+        CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_apply(h);
+        CK(cudaStreamEndCapture(cap, &g));
+        h->graph_kernels = launch_count() - before;
+        launch_count_add(-h->graph_kernels);  // captured, not executed
+        CK(cudaGraphInstantiate(&h->apply_graph, g, 0));
+    } catch (...) {
+        h->st = saved;
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        throw;
+    }
+    h->st = saved;
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+}
+
+// z = M^-1 r (device vectors, original ordering)
+void apply_impl(hs_factor_s* h, const double* r, double* z) {
+    cudaStream_t st = h->st;
+    double* y0 = h->lev.empty() ? h->d_ytop.as<double>() : h->lev[0]->d_y.as<double>();
+    h->prof.begin(KC_APPLY, st);
+    CK(launch_permute(st, h->n, h->d_perm.as<int32_t>(), r, y0, 0));
+    if (h->apply_graph) {
+        CK(cudaGraphLaunch(h->apply_graph, st));
+        launch_count_add(h->graph_kernels);
+    }
+    CK(launch_permute(st, h->n, h->d_perm.as<int32_t>(), y0, z, 1));
+    h->prof.end(KC_APPLY, st);
+}
+
+double read_scalar(hs_factor_s* h, const double* d) {
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return v;
+}
+
+int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
+    cudaStream_t st = h->st;
+    const int64_t n = h->n;
+    h->d_kv.ensure(sizeof(double) * 4 * n);
+    double* r = h->d_kv.as<double>();
+    double* z = r + n;
+    double* p = z + n;
+    double* q = p + n;
+    h->d_part.ensure(sizeof(double) * kDotParts);
+    h->d_scal.ensure(sizeof(double) * 8);
+    double* part = h->d_part.as<double>();
+    double* sc = h->d_scal.as<double>();  // 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb
+    auto spmv = [&](const double* xx, double* yy) {
+        h->prof.begin(KC_KRYLOV, st);
+        CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), xx, yy));
+        h->prof.end(KC_KRYLOV, st);
+    };
+    auto dot = [&](const double* a, const double* bb, double* out) {
+        h->prof.begin(KC_KRYLOV, st);
+        CK(launch_dot(st, n, a, bb, part, out));
+        h->prof.end(KC_KRYLOV, st);
+    };
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    dot(b, b, sc + 4);
+    const double bn = std::sqrt(read_scalar(h, sc + 4));
+    if (bn == 0.0) {
+        info->iters = 0;
+        info->rel_resid = 0.0;
+        return HS_OK;
+    }
+    apply_impl(h, r, z);
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    dot(r, z, sc + 0);
+    int it = 0;
+    double rn = bn;
+    int rc = HS_ERR_NOCONV;
+    while (it < h->opt.maxit) {
+        spmv(p, q);
+        dot(p, q, sc + 1);
+        h->prof.begin(KC_KRYLOV, st);
+        CK(launch_pcg_update_xr(st, n, sc + 0, sc + 1, p, q, x, r));
+        h->prof.end(KC_KRYLOV, st);
+        it++;
+        dot(r, r, sc + 3);
+        rn = std::sqrt(read_scalar(h, sc + 3));
+        if (rn / bn <= h->opt.rtol) {
+            spmv(x, q);
+            h->prof.begin(KC_KRYLOV, st);
+            CK(launch_axpby(st, n, 1.0, b, -1.0, q));
+            h->prof.end(KC_KRYLOV, st);
+            dot(q, q, sc + 3);
+            rn = std::sqrt(read_scalar(h, sc + 3));
+            if (rn / bn <= h->opt.rtol) { rc = HS_OK; break; }
+            CK(cudaMemcpyAsync(r, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            apply_impl(h, r, z);
+            CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            dot(r, z, sc + 0);
+            continue;
+        }
+        apply_impl(h, r, z);
+        dot(r, z, sc + 2);
+        h->prof.begin(KC_KRYLOV, st);
+        CK(launch_pcg_update_p(st, n, sc + 2, sc + 0, z, p));
+        h->prof.end(KC_KRYLOV, st);
+        CK(cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    info->iters = it;
+    info->rel_resid = rn / bn;
+    return rc;
+}
+
+int gmres_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
+    cudaStream_t st = h->st;
+    const int64_t n = h->n;
+    const int m = std::max(1, h->opt.restart);
+    h->d_V.ensure(sizeof(double) * (size_t)(m + 1) * n);
+    h->d_Z.ensure(sizeof(double) * (size_t)m * n);
+    h->d_kv.ensure(sizeof(double) * n);
+    h->d_part.ensure(sizeof(double) * 256 * (m + 2));
+    h->d_h.ensure(sizeof(double) * 2 * (m + 2));
+    h->d_scal.ensure(sizeof(double) * 8);
+    double* V = h->d_V.as<double>();
+    double* Z = h->d_Z.as<double>();
+    double* w = h->d_kv.as<double>();
+    double* part = h->d_part.as<double>();
+    double* dh = h->d_h.as<double>();
+    double* sc = h->d_scal.as<double>();
+    CK(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)(m + 1) * n, st));
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    auto norm = [&](const double* a) {
+        h->prof.begin(KC_KRYLOV, st);
+        CK(launch_dot(st, n, a, a, part, sc));
+        h->prof.end(KC_KRYLOV, st);
+        return std::sqrt(read_scalar(h, sc));
+    };
+    const double bn = norm(b);
+    if (bn == 0.0) {
+        info->iters = 0;
+        info->rel_resid = 0.0;
+        return HS_OK;
+    }
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m), hh(m + 1), hh2(m + 1);
+    int it = 0, rc = HS_ERR_NOCONV;
+    double rn = bn;
+    for (;;) {
+        // true residual (iterative refinement restart)
+        CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), x, w));
+        CK(launch_axpby(st, n, 1.0, b, -1.0, w));
+        const double beta = norm(w);
+        rn = beta;
+        if (beta / bn <= h->opt.rtol) { rc = HS_OK; break; }
+        if (it >= h->opt.maxit) break;
+        CK(launch_axpby(st, n, 1.0 / beta, w, 0.0, V));
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int kk = 0;
+        for (int j = 0; j < m && it < h->opt.maxit; j++) {
+            apply_impl(h, V + (size_t)j * n, Z + (size_t)j * n);
+            h->prof.begin(KC_KRYLOV, st);
+            CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(),
+                           Z + (size_t)j * n, w));
+            // classical Gram-Schmidt, twice
+            CK(launch_gemv_t(st, n, j + 1, V, n, w, part, dh));
+            CK(launch_gmres_update(st, n, j + 1, dh, V, n, w, -1.0));
+            CK(launch_gemv_t(st, n, j + 1, V, n, w, part, dh + m + 1));
+            CK(launch_gmres_update(st, n, j + 1, dh + m + 1, V, n, w, -1.0));
+            h->prof.end(KC_KRYLOV, st);
+            CK(cudaMemcpyAsync(hh.data(), dh, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hh2.data(), dh + m + 1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+            const double hn = norm(w);
+            for (int k = 0; k <= j; k++) H[(size_t)k * m + j] = hh[k] + hh2[k];
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0) CK(launch_axpby(st, n, 1.0 / hn, w, 0.0, V + (size_t)(j + 1) * n));
+            for (int k = 0; k < j; k++) {
+                const double a = H[(size_t)k * m + j], c2 = H[(size_t)(k + 1) * m + j];
+                H[(size_t)k * m + j] = cs[k] * a + sn[k] * c2;
+                H[(size_t)(k + 1) * m + j] = -sn[k] * a + cs[k] * c2;
+            }
+            const double a = H[(size_t)j * m + j], c2 = H[(size_t)(j + 1) * m + j];
+            const double d = std::sqrt(a * a + c2 * c2);
+            cs[j] = d > 0 ? a / d : 1.0;
+            sn[j] = d > 0 ? c2 / d : 0.0;
+            H[(size_t)j * m + j] = d;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            const double t = g[j];
+            g[j] = cs[j] * t;
+            g[j + 1] = -sn[j] * t;
+            it++;
+            kk = j + 1;
+            if (std::fabs(g[j + 1]) / bn <= h->opt.rtol || hn == 0.0) break;
+        }
+        for (int k = kk - 1; k >= 0; k--) {
+            double t = g[k];
+            for (int j = k + 1; j < kk; j++) t -= H[(size_t)k * m + j] * yv[j];
+            yv[k] = t / H[(size_t)k * m + k];
+        }
+        CK(cudaMemcpyAsync(dh, yv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
+        CK(launch_gmres_update(st, n, kk, dh, Z, n, x, 1.0));
+    }
+    info->iters = it;
+    info->rel_resid = rn / bn;
+    return rc;
+}
+
+template <class F>
+int run_guarded(F&& f) {
+    try {
+        f();
+        return HS_OK;
+    } catch (const HsError& e) {
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        return HS_ERR_OOM;
+    } catch (...) {
+        return HS_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+int hs_default_options(hs_options* opt) {
+    if (!opt) return HS_ERR_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->tol = 1e-2;
+    opt->depth = -1;
+    opt->leaf_lines = 4;
+    opt->theta = 0.5;
+    opt->precision = HS_PREC_FP64;
+    opt->krylov = HS_KRYLOV_PCG;
+    opt->restart = 50;
+    opt->rtol = 1e-8;
+    opt->maxit = 1000;
+    opt->mem = HS_MEM_HOST;
+    opt->stream = nullptr;
+    opt->coords = nullptr;
+    return HS_OK;
+}
+
+int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                          const double* coords, int32_t leaf_lines, double theta, hs_tree* out) {
+    if (!out) return HS_ERR_ARG;
+    out->n_leaf = 0;
+    out->perm = nullptr;
+    out->leaf_ptr = nullptr;
+    out->depth = 0;
+    if (n <= 0 || n > INT32_MAX || !rowptr || !col || !val || leaf_lines <= 0) return HS_ERR_ARG;
+    return run_guarded([&] {
+        std::vector<int32_t> perm, lp;
+        partition_impl(n, rowptr, col, val, coords, leaf_lines, theta, perm, lp);
+        const int nleaf = (int)lp.size() - 1;
+        out->perm = static_cast<int32_t*>(std::malloc(sizeof(int32_t) * n));
+        out->leaf_ptr = static_cast<int32_t*>(std::malloc(sizeof(int32_t) * (nleaf + 1)));
+        if (!out->perm || !out->leaf_ptr) {
+            std::free(out->perm);
+            std::free(out->leaf_ptr);
+            out->perm = nullptr;
+            out->leaf_ptr = nullptr;
+            throw HsError{HS_ERR_OOM};
+        }
+        std::memcpy(out->perm, perm.data(), sizeof(int32_t) * n);
+        std::memcpy(out->leaf_ptr, lp.data(), sizeof(int32_t) * (nleaf + 1));
+        out->n_leaf = nleaf;
+        int Lg = 0;
+        while ((1 << (Lg + 1)) <= nleaf) Lg++;
+        out->depth = std::max(nleaf >= 2 ? 1 : 0, Lg - 2);
+    });
+}
+
+int hs_tree_free(hs_tree* t) {
+    if (!t) return HS_ERR_ARG;
+    std::free(t->perm);
+    std::free(t->leaf_ptr);
+    t->perm = nullptr;
+    t->leaf_ptr = nullptr;
+    t->n_leaf = 0;
+    return HS_OK;
+}
+
+int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const hs_tree* tree,
+             const hs_options* opt, hs_handle* out, hs_info* info) {
+    if (!out) return HS_ERR_ARG;
+    *out = nullptr;
+    if (info) { std::memset(info, 0, sizeof(*info)); info->fail_level = -1; info->fail_cluster = -1; }
+    if (n <= 0 || n > INT32_MAX || !rowptr || !col || !val || !opt) return HS_ERR_ARG;
+    if (!(opt->tol >= 0.0) || opt->leaf_lines <= 0 || (opt->mem != HS_MEM_HOST && opt->mem != HS_MEM_DEVICE))
+        return HS_ERR_ARG;
+    hs_factor_s* h = new (std::nothrow) hs_factor_s();
+    if (!h) return HS_ERR_OOM;
+    h->n = n;
+    h->opt = *opt;
+    h->st = static_cast<cudaStream_t>(opt->stream);
+    h->prof.on = opt->profile != 0;
+    const double t0 = now_s();
+    const int rc = run_guarded([&] {
+        CK(cudaGetDevice(&h->device));
+        setup_impl(h, rowptr, col, val, tree, info);
+        h->prof.collect();
+    });
+    if (rc != HS_OK) {
+        delete h;
+        return rc;
+    }
+    if (info) {
+        info->setup_s = now_s() - t0;
+        info->factor_bytes = h->factor_bytes;
+    }
+    *out = h;
+    return HS_OK;
+}
+
+int hs_apply(hs_handle h, const double* r, double* z) {
+    if (!h || !r || !z || r == z) return HS_ERR_ARG;
+    return run_guarded([&] { apply_impl(h, r, z); });
+}
+
+int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info) {
+    if (!h || !b || !x) return HS_ERR_ARG;
+    hs_info tmp{};
+    hs_info* inf = info ? info : &tmp;
+    const double t0 = now_s();
+    int krc = HS_OK;
+    const int rc = run_guarded([&] {
+        krc = h->opt.krylov == HS_KRYLOV_GMRES ? gmres_impl(h, b, x, inf) : pcg_impl(h, b, x, inf);
+        CK(cudaStreamSynchronize(h->st));
+        h->prof.collect();
+    });
+    inf->solve_s = now_s() - t0;
+    return rc != HS_OK ? rc : krc;
+}
+
+int hs_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* b, double* x,
+             const hs_options* opt, hs_info* info) {
+    if (!opt || !b || !x) return HS_ERR_ARG;
+    hs_info tmp{};
+    hs_info* inf = info ? info : &tmp;
+    hs_handle h = nullptr;
+    int rc = hs_setup(n, rowptr, col, val, nullptr, opt, &h, inf);
+    if (rc != HS_OK) return rc;
+    const double t0 = now_s();
+    rc = run_guarded([&] {
+        cudaStream_t st = h->st;
+        if (opt->mem == HS_MEM_DEVICE) {
+            const int krc = hs_krylov(h, b, x, inf);
+            if (krc != HS_OK) throw HsError{krc};
+        } else {
+            DBuf db, dx;
+            db.alloc(sizeof(double) * n);
+            dx.alloc(sizeof(double) * n);
+            CK(cudaMemcpyAsync(db.p, b, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+            const int krc = hs_krylov(h, db.as<double>(), dx.as<double>(), inf);
+            CK(cudaMemcpyAsync(x, dx.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (krc != HS_OK) throw HsError{krc};
+        }
+    });
+    inf->solve_s = now_s() - t0;
+    hs_destroy(h);
+    return rc;
+}
+
+int hs_destroy(hs_handle h) {
+    if (!h) return HS_OK;
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    delete h;
+    return HS_OK;
+}
+
+int hs_num_levels(hs_handle h, int32_t* levels) {
+    if (!h || !levels) return HS_ERR_ARG;
+    *levels = (int32_t)h->lev.size();
+    return HS_OK;
+}
+
+int hs_level_clusters(hs_handle h, int32_t level, int32_t* nc) {
+    if (!h || !nc || level < 0 || level >= (int32_t)h->lev.size()) return HS_ERR_ARG;
+    *nc = h->lev[level]->nc;
+    return HS_OK;
+}
+
+int hs_level_info(hs_handle h, int32_t level, int32_t* size0, int32_t* final_size, int32_t* phase) {
+    if (!h || level < 0 || level >= (int32_t)h->lev.size()) return HS_ERR_ARG;
+    const Level& L = *h->lev[level];
+    for (int c = 0; c < L.nc; c++) {
+        if (size0) size0[c] = L.size0[c];
+        if (final_size) final_size[c] = L.fin[c];
+        if (phase) phase[c] = L.phase[c];
+    }
+    return HS_OK;
+}
+
+int hs_top_size(hs_handle h, int32_t* ntop) {
+    if (!h || !ntop) return HS_ERR_ARG;
+    *ntop = h->ntop;
+    return HS_OK;
+}
+
+int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops,
+                    double* bytes) {
+    if (!h || nclasses < 0) return HS_ERR_ARG;
+    for (int k = 0; k < nclasses; k++) {
+        const bool ok = k < KC_N;
+        if (times_ms) times_ms[k] = ok ? h->prof.ms[k] : 0.0;
+        if (launches) launches[k] = ok ? h->prof.launches[k] : 0;
+        if (flops) flops[k] = ok ? h->work_flops[k] : 0.0;
+        if (bytes) bytes[k] = ok ? h->work_bytes[k] : 0.0;
+    }
+    return HS_OK;
+}
+
+int hs_reset_kernel_stats(hs_handle h) {
+    if (!h) return HS_ERR_ARG;
+    h->prof.reset();
+    return HS_OK;
+}
+
+int hs_launch_count(int64_t* count) {
+    if (!count) return HS_ERR_ARG;
+    *count = launch_count();
+    return HS_OK;
+}
+
+int hs_measure_fp64_peak(void* stream, double* tflops) {
+    if (!tflops) return HS_ERR_ARG;
+    return run_guarded([&] {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DBuf sink;
+        sink.alloc(64);
+        const int blocks = sms * 8, iters = 1 << 14;
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(launch_fp64_peak(st, blocks, 256, sink.as<double>()));  // warm-up
+        CK(cudaEventRecord(a, st));
+        CK(launch_fp64_peak(st, blocks, iters, sink.as<double>()));
+        CK(cudaEventRecord(b, st));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        *tflops = 2.0 * 8.0 * (double)iters * blocks * 256 / (ms * 1e-3) / 1e12;
+    });
+}
+
+const char* hs_status_str(int status) {
+    switch (status) {
+        case HS_OK: return "ok";
+        case HS_ERR_ARG: return "invalid argument";
+        case HS_ERR_NOT_SPD: return "diagonal block not positive definite";
+        case HS_ERR_NOCONV: return "Krylov solver did not converge";
+        case HS_ERR_CUDA: return "CUDA error";
+        case HS_ERR_OOM: return "out of device memory";
+        case HS_ERR_UNSUPPORTED: return "block size beyond kernel limits";
+        case HS_ERR_TIMEOUT: return "bounded device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// hs_internal.h -- records shared by the host planner (hs_host.cpp) and the
+// sm_103a kernels (hs_kernels.cu).  All records are plain int32/int64 so the
+// host builds them once per level and uploads them with one copy.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hs {
+
+// One cluster elimination ("scaled low-rank elimination", Sec. 3.1) of a
+// phase.  Column blocks of the cluster's row are listed n-neighbours first,
+// then fill ("w") blocks, each with its current width read on the device.
+struct TaskDev {
+    int32_t c;         // cluster id at this level
+    int32_t s;         // its size when processed (= size at level start)
+    int32_t nn, nw;    // neighbour / fill block counts
+    int32_t list;      // first ListDev entry
+    int32_t diag_blk;  // block index of (c, c)
+    int32_t ncap;      // sum of level-start sizes of the n-neighbours (ld of C)
+    int32_t wcap;      // same over n and w (capacity of the block row)
+    int32_t meta;      // first int of: rank, then (col offset, width) per n-neighbour
+    int32_t pad;
+    int64_t g_off;     // G (s x s, lower, row-major) in the factor array
+    int64_t v_off;     // Householder vectors (s x s, column k = reflector k)
+    int64_t tau_off;   // tau (s)
+    int64_t c_off;     // C = fine rows of U^T G^-1 A_sn ((s - r) x ncap)
+    int64_t m_off;     // block-row workspace (s x wcap) in the workspace array
+};
+
+struct ListDev {
+    int32_t q;       // neighbour / fill cluster
+    int32_t blk_cq;  // block index of (c, q)
+    int32_t blk_qc;  // block index of (q, c)
+    int32_t pad;
+};
+
+// Schur target: block (p, q), p <= q, of one phase; contributions from the
+// phase's tasks that have both p and q as n-neighbours, in ascending task order.
+struct TargetDev {
+    int32_t p, q, blk_pq, blk_qp, c_begin, c_end;
+};
+
+struct ContribDev {
+    int32_t task, kp, kq;  // task index (in the level's task array), positions of p, q in its n-list
+};
+
+// Forward-substitution neighbour update: y_q -= sum_t C_t(:, q)^T y_t(fine).
+struct NbTargetDev {
+    int32_t q, c_begin, c_end;
+};
+
+struct NbContribDev {
+    int32_t task, k;  // task index, position of q in its n-list
+};
+
+// Dense copy of a rows x cols sub-block (level assembly, top assembly).
+struct CopyDev {
+    int64_t src, dst;   // element offsets
+    int32_t src_ld, dst_ld, rows, cols;
+};
+
+// Vector slice copy (coarse parts between levels).
+struct VCopyDev {
+    int64_t src, dst;
+    int32_t len, pad;
+};
+
+// status word written by kernels (0 = ok)
+enum : int32_t { ST_OK = 0, ST_NOT_SPD = 1, ST_TOO_BIG = 2 };
+
+// ---- kernel launchers (hs_kernels.cu) -------------------------------------
+cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col,
+                               const double* val, const int32_t* dof_cluster, const int32_t* dof_local,
+                               const int32_t* blk_ptr, const int32_t* blk_col, const int64_t* blk_off,
+                               const int32_t* blk_ld, double* blocks);
+cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
+                                int wmax, int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
+                                const int32_t* blk_ld, int32_t* cur, double* fac, int32_t* meta,
+                                double* ws, double eps2, int32_t* status, int32_t level);
+cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
+                               const ContribDev* contribs, const TaskDev* tasks, const double* fac,
+                               const int32_t* meta, double* blocks, const int64_t* blk_off,
+                               const int32_t* blk_ld, const int32_t* cur, int precision);
+cudaError_t launch_copy_blocks(cudaStream_t st, const CopyDev* cps, int ncps, const double* src,
+                               double* dst);
+cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* status);
+cudaError_t launch_apply_fwd_diag(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
+                                  const double* fac, const int32_t* meta, const int64_t* slot, double* y);
+cudaError_t launch_apply_fwd_nb(cudaStream_t st, const NbTargetDev* nbt, int g0, int ntargets,
+                                const NbContribDev* nbc, const TaskDev* tasks, const double* fac,
+                                const int32_t* meta, const int64_t* slot, double* y);
+cudaError_t launch_apply_bwd(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
+                             const ListDev* lists, const double* fac, const int32_t* meta,
+                             const int64_t* slot, double* y);
+cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
+                         int reverse);
+cudaError_t launch_top_solve(cudaStream_t st, int n, const double* L, double* y);
+cudaError_t launch_permute(cudaStream_t st, int64_t n, const int32_t* perm, const double* src, double* dst,
+                           int inverse);
+cudaError_t launch_spmv(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col,
+                        const double* val, const double* x, double* y);
+// partial sums for dot products: out[k] for k < nparts, then a final pass
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const double* a, const double* b, double* partial,
+                       double* out);
+// y = a*x + y with device scalar alpha = num/den (sign), etc.
+cudaError_t launch_pcg_update_xr(cudaStream_t st, int64_t n, const double* rz, const double* pq,
+                                 const double* p, const double* q, double* x, double* r);
+cudaError_t launch_pcg_update_p(cudaStream_t st, int64_t n, const double* rz_new, const double* rz_old,
+                                const double* z, double* p);
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y);
+cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double* coef, const double* V,
+                                int64_t ldv, double* y, double sign);
+cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv,
+                          const double* w, double* partial, double* out);
+
+size_t factor_smem_bytes(int smax, int wmax, int lmax);
+// process-wide count of this library's kernel launches
+int64_t launch_count();
+void launch_count_add(int64_t k);
+cudaError_t launch_fp64_peak(cudaStream_t st, int nblocks, int iters, double* sink);
+
+constexpr int kDotParts = 1024;
+constexpr int kFactorMaxSmem = 226 * 1024;  // dynamic part; static shared adds a few bytes
+
+}  // namespace hs

@@ -1,0 +1,847 @@
+// hs_kernels.cu -- sm_103a kernels of the hierarchical solver.
+//
+// Factorization (Algorithm 1), per phase of independent clusters:
+//   k_factor_phase : one CTA per cluster: Cholesky of A_ss (Sec. 2), scaling
+//                    G^-1 [A_sn A_sw] (Eq. scaling), column-pivoted QR of the
+//                    scaled fill block with every reflector applied to the
+//                    whole row (Eq. offdiag_new, Eq. sparse), write-back of the
+//                    coarse row (Eq. perm) and of the factor {G, U, C, r}.
+//   k_schur_phase  : one CTA per target block: X_nn = A_nn - C^T C (Eq. elim),
+//                    contributions summed in ascending cluster order.
+// Solve (Algorithm 2): k_apply_fwd_diag / k_apply_fwd_nb / k_apply_bwd per
+// phase, k_vcopy between levels, k_top_solve for the dense top.
+// Krylov: CSR SpMV, deterministic two-stage dot products, vector updates.
+//
+// Decisions that must agree with any other implementation of the method:
+// rank = smallest k with sum of squared trailing column norms <= eps^2;
+// pivot = lowest unpivoted column index with squared norm >= (1 - 1e-10) *
+// the largest; Householder beta = -sign(alpha) * norm, v_k = 1,
+// tau = (beta - alpha) / beta.
+#include <atomic>
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+namespace {
+
+constexpr double kPivotTie = 1e-10;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_min_int(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reductions; scratch holds >= 32 doubles.  Every thread returns
+// the same value.  Fixed reduction tree => deterministic.
+__device__ double block_sum(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double t = (lane < nw) ? scratch[lane] : 0.0;
+    t = warp_sum(t);
+    return t;
+}
+__device__ double block_max(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double t = (lane < nw) ? scratch[lane] : -DBL_MAX;
+    return warp_max(t);
+}
+__device__ int block_min_int(int v, int* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_min_int(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    int t = (lane < nw) ? scratch[lane] : INT_MAX;
+    return warp_min_int(t);
+}
+
+// ---------------------------------------------------------------------------
+// Level-0 assembly: scatter CSR entries into the dense blocks.
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_csr(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const int32_t* __restrict__ dof_cluster,
+                              const int32_t* __restrict__ dof_local, const int32_t* __restrict__ blk_ptr,
+                              const int32_t* __restrict__ blk_col, const int64_t* __restrict__ blk_off,
+                              const int32_t* __restrict__ blk_ld, double* __restrict__ blocks) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = dof_cluster[i], li = dof_local[i];
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+        const int j = col[e];
+        const int q = dof_cluster[j], lj = dof_local[j];
+        int lo = blk_ptr[p], hi = blk_ptr[p + 1] - 1, b = -1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1, cm = blk_col[mid];
+            if (cm == q) { b = mid; break; }
+            if (cm < q) lo = mid + 1; else hi = mid - 1;
+        }
+        if (b >= 0) blocks[blk_off[b] + (int64_t)li * blk_ld[b] + lj] += val[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Factor one phase: one CTA per cluster.
+// Shared memory: G (s*s) | rdiag (s) | v (s) | cn (wmax) | red (64) | ioff (lmax+1 ints) | flags
+// ---------------------------------------------------------------------------
+constexpr int kFactorThreads = 256;
+
+__global__ void __launch_bounds__(kFactorThreads)
+k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
+               double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+               const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, double* __restrict__ fac,
+               int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
+               int32_t level, int smax, int wmax) {
+    extern __shared__ double sm[];
+    const TaskDev T = tasks[t0 + blockIdx.x];
+    const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
+    const int L = T.nn + T.nw;
+    double* G = sm;
+    double* rdiag = G + (size_t)smax * smax;
+    double* v = rdiag + smax;
+    double* cn = v + smax;
+    double* red = cn + wmax;
+    int* ioff = reinterpret_cast<int*>(red + 64);
+    __shared__ int s_flag;
+    __shared__ double s_hh[3];
+
+    // column offsets of the row blocks (compact, current widths)
+    if (tid == 0) {
+        int o = 0;
+        for (int e = 0; e < L; e++) {
+            ioff[e] = o;
+            o += cur[lists[T.list + e].q];
+        }
+        ioff[L] = o;
+        s_flag = 0;
+    }
+    // A_ss -> shared memory
+    {
+        const double* A = blocks + blk_off[T.diag_blk];
+        const int ld = blk_ld[T.diag_blk];
+        for (int idx = tid; idx < s * s; idx += NT) G[idx] = A[(int64_t)(idx / s) * ld + idx % s];
+    }
+    __syncthreads();
+    const int W = ioff[L], ncols = ioff[T.nn], Wn = W - ncols;
+
+    // Cholesky A_ss = G G^T (right-looking, in shared memory)
+    for (int j = 0; j < s; j++) {
+        if (tid == 0) {
+            const double d = G[j * s + j];
+            if (!(d > 0.0)) {
+                s_flag = 1;
+            } else {
+                const double g = sqrt(d);
+                G[j * s + j] = g;
+                rdiag[j] = 1.0 / g;
+            }
+        }
+        __syncthreads();
+        if (s_flag) {
+            if (tid == 0 && atomicCAS(status, 0, ST_NOT_SPD) == 0) {
+                status[1] = level;
+                status[2] = T.c;
+            }
+            return;
+        }
+        const double rj = rdiag[j];
+        for (int i = j + 1 + tid; i < s; i += NT) G[i * s + j] *= rj;
+        __syncthreads();
+        const int m = s - j - 1;
+        for (int idx = tid; idx < m * m; idx += NT) {
+            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
+            if (k <= i) G[i * s + k] -= G[i * s + j] * G[k * s + j];
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < s * s; idx += NT)
+        if (idx % s > idx / s) G[idx] = 0.0;
+    __syncthreads();
+
+    // gather the block row [A_sn | A_sw] into the workspace (row-major, ld W)
+    double* M = ws + T.m_off;
+    for (int e = 0; e < L; e++) {
+        const ListDev le = lists[T.list + e];
+        const int wq = ioff[e + 1] - ioff[e];
+        const double* src = blocks + blk_off[le.blk_cq];
+        const int ld = blk_ld[le.blk_cq];
+        const int o = ioff[e];
+        for (int idx = tid; idx < s * wq; idx += NT) {
+            const int i = idx / wq, j = idx % wq;
+            M[(int64_t)i * W + o + j] = src[(int64_t)i * ld + j];
+        }
+    }
+    __syncthreads();
+
+    // scaling: M <- G^-1 M (forward substitution, one thread per column)
+    for (int j = tid; j < W; j += NT) {
+        for (int i = 0; i < s; i++) {
+            double acc = M[(int64_t)i * W + j];
+            for (int k = 0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * W + j];
+            M[(int64_t)i * W + j] = acc * rdiag[i];
+        }
+    }
+    __syncthreads();
+
+    // column-pivoted QR of the fill columns, reflectors applied to the whole row
+    double* Vf = fac + T.v_off;
+    double* tauf = fac + T.tau_off;
+    for (int j = tid; j < Wn; j += NT) {
+        double c = 0.0;
+        for (int i = 0; i < s; i++) {
+            const double x = M[(int64_t)i * W + ncols + j];
+            c += x * x;
+        }
+        cn[j] = c;
+    }
+    __syncthreads();
+    int k = 0;
+    while (k < s) {
+        double lt = 0.0, lm = 0.0;
+        for (int j = tid; j < Wn; j += NT) {
+            const double c = cn[j];
+            if (c >= 0.0) {
+                lt += c;
+                lm = fmax(lm, c);
+            }
+        }
+        const double total = block_sum(lt, red);
+        const double cmax = block_max(lm, red);
+        if (total <= eps2) break;
+        const double thr = (1.0 - kPivotTie) * cmax;
+        int lp = INT_MAX;
+        for (int j = tid; j < Wn; j += NT)
+            if (cn[j] >= 0.0 && cn[j] >= thr) {
+                lp = j;
+                break;  // lowest of this thread's columns
+            }
+        const int p = block_min_int(lp, reinterpret_cast<int*>(red));
+        const int pc = ncols + p;
+        double ls = 0.0;
+        for (int i = k + 1 + tid; i < s; i += NT) {
+            const double x = M[(int64_t)i * W + pc];
+            ls += x * x;
+        }
+        const double sig = block_sum(ls, red);
+        if (tid == 0) {
+            const double alpha = M[(int64_t)k * W + pc];
+            const double nrm = sqrt(alpha * alpha + sig);
+            const double beta = alpha >= 0.0 ? -nrm : nrm;
+            s_hh[0] = beta;
+            s_hh[1] = (beta - alpha) / beta;
+            s_hh[2] = 1.0 / (alpha - beta);
+            cn[p] = -1.0;
+        }
+        __syncthreads();
+        const double beta = s_hh[0], tau = s_hh[1], scal = s_hh[2];
+        for (int i = tid; i < s; i += NT) {
+            double vi = 0.0;
+            if (i == k) vi = 1.0;
+            else if (i > k) vi = M[(int64_t)i * W + pc] * scal;
+            v[i] = vi;
+            Vf[(int64_t)i * s + k] = vi;
+        }
+        if (tid == 0) tauf[k] = tau;
+        __syncthreads();
+        for (int i = k + tid; i < s; i += NT) M[(int64_t)i * W + pc] = (i == k) ? beta : 0.0;
+        for (int j = tid; j < W; j += NT) {
+            if (j == pc) continue;
+            if (j >= ncols && cn[j - ncols] < 0.0) continue;
+            double t = M[(int64_t)k * W + j];
+            for (int i = k + 1; i < s; i++) t += v[i] * M[(int64_t)i * W + j];
+            t *= tau;
+            M[(int64_t)k * W + j] -= t;
+            double c = 0.0;
+            for (int i = k + 1; i < s; i++) {
+                const double x = M[(int64_t)i * W + j] - t * v[i];
+                M[(int64_t)i * W + j] = x;
+                c += x * x;
+            }
+            if (j >= ncols) cn[j - ncols] = c;
+        }
+        __syncthreads();
+        k++;
+    }
+    const int r = k;
+
+    // factor: rank and n-column layout, G, C = rows r.. of the n columns
+    int32_t* mt = meta + T.meta;
+    if (tid == 0) mt[0] = r;
+    for (int e = tid; e < T.nn; e += NT) {
+        mt[1 + 2 * e] = ioff[e];
+        mt[2 + 2 * e] = ioff[e + 1] - ioff[e];
+    }
+    {
+        double* Gf = fac + T.g_off;
+        for (int idx = tid; idx < s * s; idx += NT) Gf[idx] = G[idx];
+        double* Cf = fac + T.c_off;
+        const int f = s - r;
+        for (int idx = tid; idx < f * ncols; idx += NT) {
+            const int i = idx / ncols, j = idx % ncols;
+            Cf[(int64_t)i * T.ncap + j] = M[(int64_t)(r + i) * W + j];
+        }
+    }
+    // write back the coarse row (identity diagonal, U^T G^-1 A_sn, V1^T)
+    if (T.nw > 0 && r > 0) {
+        for (int e = 0; e < L; e++) {
+            const ListDev le = lists[T.list + e];
+            const int wq = ioff[e + 1] - ioff[e], o = ioff[e];
+            double* dcq = blocks + blk_off[le.blk_cq];
+            const int ldcq = blk_ld[le.blk_cq];
+            double* dqc = blocks + blk_off[le.blk_qc];
+            const int ldqc = blk_ld[le.blk_qc];
+            for (int idx = tid; idx < r * wq; idx += NT) {
+                const int i = idx / wq, j = idx % wq;
+                const double x = M[(int64_t)i * W + o + j];
+                dcq[(int64_t)i * ldcq + j] = x;
+                dqc[(int64_t)j * ldqc + i] = x;
+            }
+        }
+        double* dcc = blocks + blk_off[T.diag_blk];
+        const int ld = blk_ld[T.diag_blk];
+        for (int idx = tid; idx < r * r; idx += NT) {
+            const int i = idx / r, j = idx % r;
+            dcc[(int64_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
+        }
+    }
+    if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Schur update of one phase: one CTA per target block (p, q), p <= q.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_schur_phase(const TargetDev* __restrict__ targets, int g0, const ContribDev* __restrict__ contribs,
+              const TaskDev* __restrict__ tasks, const double* __restrict__ fac,
+              const int32_t* __restrict__ meta, double* __restrict__ blocks,
+              const int64_t* __restrict__ blk_off, const int32_t* __restrict__ blk_ld,
+              const int32_t* __restrict__ cur) {
+    const TargetDev g = targets[g0 + blockIdx.x];
+    const int mp = cur[g.p], mq = cur[g.q];
+    double* A = blocks + blk_off[g.blk_pq];
+    const int lda = blk_ld[g.blk_pq];
+    double* At = blocks + blk_off[g.blk_qp];
+    const int ldt = blk_ld[g.blk_qp];
+    for (int idx = threadIdx.x; idx < mp * mq; idx += blockDim.x) {
+        const int i = idx / mq, j = idx % mq;
+        double acc = A[(int64_t)i * lda + j];
+        for (int c = g.c_begin; c < g.c_end; c++) {
+            const ContribDev cb = contribs[c];
+            const TaskDev T = tasks[cb.task];
+            const int32_t* mt = meta + T.meta;
+            const int r = mt[0], f = T.s - r;
+            const int op = mt[1 + 2 * cb.kp], oq = mt[1 + 2 * cb.kq];
+            const double* C = fac + T.c_off;
+            double sub = 0.0;
+            for (int k = 0; k < f; k++) sub += C[(int64_t)k * T.ncap + op + i] * C[(int64_t)k * T.ncap + oq + j];
+            acc -= sub;
+        }
+        A[(int64_t)i * lda + j] = acc;
+        if (g.p != g.q) At[(int64_t)j * ldt + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block copies (level assembly and dense top assembly).
+// ---------------------------------------------------------------------------
+__global__ void k_copy_blocks(const CopyDev* __restrict__ cps, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+    const CopyDev c = cps[blockIdx.x];
+    for (int idx = threadIdx.x; idx < c.rows * c.cols; idx += blockDim.x) {
+        const int i = idx / c.cols, j = idx % c.cols;
+        dst[c.dst + (int64_t)i * c.dst_ld + j] = src[c.src + (int64_t)i * c.src_ld + j];
+    }
+}
+
+// Dense Cholesky of the top (lower, row-major, in place), one CTA.
+__global__ void __launch_bounds__(1024) k_dense_cholesky(int n, double* a, int32_t* status) {
+    __shared__ int flag;
+    __shared__ double rd;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    if (tid == 0) flag = 0;
+    for (int j = 0; j < n; j++) {
+        __syncthreads();
+        if (tid == 0) {
+            const double d = a[(int64_t)j * n + j];
+            if (!(d > 0.0)) flag = 1;
+            else {
+                a[(int64_t)j * n + j] = sqrt(d);
+                rd = 1.0 / sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (flag) {
+            if (tid == 0 && atomicCAS(status, 0, ST_NOT_SPD) == 0) {
+                status[1] = -1;
+                status[2] = j;
+            }
+            return;
+        }
+        for (int i = j + 1 + tid; i < n; i += NT) a[(int64_t)i * n + j] *= rd;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int idx = tid; idx < m * m; idx += NT) {
+            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
+            if (k <= i) a[(int64_t)i * n + k] -= a[(int64_t)i * n + j] * a[(int64_t)k * n + j];
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += NT)
+        if (idx % n > idx / n) a[idx] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Solve phase (Algorithm 2)
+// ---------------------------------------------------------------------------
+constexpr int kApplyThreads = 128;
+
+// y_s <- U^T G^-1 y_s for each task of a phase.
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_fwd_diag(const TaskDev* __restrict__ tasks, int t0, const double* __restrict__ fac,
+                 const int32_t* __restrict__ meta, const int64_t* __restrict__ slot, double* __restrict__ y) {
+    extern __shared__ double ys[];
+    __shared__ double red[32];
+    const TaskDev T = tasks[t0 + blockIdx.x];
+    const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
+    double* yg = y + slot[T.c];
+    const double* G = fac + T.g_off;
+    for (int i = tid; i < s; i += NT) ys[i] = yg[i];
+    __syncthreads();
+    for (int k = 0; k < s; k++) {
+        const double yk = ys[k] / G[(int64_t)k * s + k];
+        __syncthreads();
+        if (tid == 0) ys[k] = yk;
+        for (int i = k + 1 + tid; i < s; i += NT) ys[i] -= G[(int64_t)i * s + k] * yk;
+        __syncthreads();
+    }
+    const int r = meta[T.meta];
+    const double* V = fac + T.v_off;
+    const double* tau = fac + T.tau_off;
+    for (int k = 0; k < r; k++) {
+        double part = 0.0;
+        for (int i = k + tid; i < s; i += NT) part += V[(int64_t)i * s + k] * ys[i];
+        const double t = block_sum(part, red) * tau[k];
+        for (int i = k + tid; i < s; i += NT) ys[i] -= t * V[(int64_t)i * s + k];
+        __syncthreads();
+    }
+    for (int i = tid; i < s; i += NT) yg[i] = ys[i];
+}
+
+// y_q -= sum over tasks of C_t(:, q)^T y_t(r:), one CTA per neighbour q.
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_fwd_nb(const NbTargetDev* __restrict__ nbt, int g0, const NbContribDev* __restrict__ nbc,
+               const TaskDev* __restrict__ tasks, const double* __restrict__ fac,
+               const int32_t* __restrict__ meta, const int64_t* __restrict__ slot, double* __restrict__ y) {
+    const NbTargetDev g = nbt[g0 + blockIdx.x];
+    double* yq = y + slot[g.q];
+    int m = 0;
+    if (g.c_end > g.c_begin) {
+        const NbContribDev c0 = nbc[g.c_begin];
+        m = meta[tasks[c0.task].meta + 2 + 2 * c0.k];
+    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double acc = yq[j];
+        for (int c = g.c_begin; c < g.c_end; c++) {
+            const NbContribDev cb = nbc[c];
+            const TaskDev T = tasks[cb.task];
+            const int32_t* mt = meta + T.meta;
+            const int r = mt[0], f = T.s - r, o = mt[1 + 2 * cb.k];
+            const double* C = fac + T.c_off;
+            const double* yt = y + slot[T.c] + r;
+            double sub = 0.0;
+            for (int i = 0; i < f; i++) sub += C[(int64_t)i * T.ncap + o + j] * yt[i];
+            acc -= sub;
+        }
+        yq[j] = acc;
+    }
+}
+
+// x_s(r:) -= C x_n;  x_s <- U x_s;  x_s <- G^-T x_s   (one CTA per task)
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_bwd(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
+            const double* __restrict__ fac, const int32_t* __restrict__ meta,
+            const int64_t* __restrict__ slot, double* __restrict__ y) {
+    extern __shared__ double ys[];
+    __shared__ double red[32];
+    const TaskDev T = tasks[t0 + blockIdx.x];
+    const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
+    double* yg = y + slot[T.c];
+    const int32_t* mt = meta + T.meta;
+    const int r = mt[0], f = s - r;
+    const double* C = fac + T.c_off;
+    for (int i = tid; i < s; i += NT) ys[i] = yg[i];
+    __syncthreads();
+    for (int i = tid; i < f; i += NT) {
+        double acc = 0.0;
+        for (int e = 0; e < T.nn; e++) {
+            const int o = mt[1 + 2 * e], m = mt[2 + 2 * e];
+            const double* xq = y + slot[lists[T.list + e].q];
+            for (int j = 0; j < m; j++) acc += C[(int64_t)i * T.ncap + o + j] * xq[j];
+        }
+        ys[r + i] -= acc;
+    }
+    __syncthreads();
+    const double* V = fac + T.v_off;
+    const double* tau = fac + T.tau_off;
+    for (int k = r - 1; k >= 0; k--) {
+        double part = 0.0;
+        for (int i = k + tid; i < s; i += NT) part += V[(int64_t)i * s + k] * ys[i];
+        const double t = block_sum(part, red) * tau[k];
+        for (int i = k + tid; i < s; i += NT) ys[i] -= t * V[(int64_t)i * s + k];
+        __syncthreads();
+    }
+    const double* G = fac + T.g_off;
+    for (int k = s - 1; k >= 0; k--) {
+        const double yk = ys[k] / G[(int64_t)k * s + k];
+        __syncthreads();
+        if (tid == 0) ys[k] = yk;
+        for (int i = tid; i < k; i += NT) ys[i] -= G[(int64_t)k * s + i] * yk;
+        __syncthreads();
+    }
+    for (int i = tid; i < s; i += NT) yg[i] = ys[i];
+}
+
+__global__ void k_vcopy(const VCopyDev* __restrict__ cps, int ncps, const double* __restrict__ src,
+                        double* __restrict__ dst, int reverse) {
+    const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (c >= ncps) return;
+    const VCopyDev v = cps[c];
+    for (int i = threadIdx.x & 31; i < v.len; i += 32) {
+        if (reverse) dst[v.src + i] = src[v.dst + i];
+        else dst[v.dst + i] = src[v.src + i];
+    }
+}
+
+// y <- L^-T L^-1 y for the dense top (one CTA).
+__global__ void __launch_bounds__(1024) k_top_solve(int n, const double* __restrict__ L, double* __restrict__ y) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    for (int k = 0; k < n; k++) {
+        __syncthreads();
+        const double yk = y[k] / L[(int64_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) y[k] = yk;
+        for (int i = k + 1 + tid; i < n; i += NT) y[i] -= L[(int64_t)i * n + k] * yk;
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        __syncthreads();
+        const double yk = y[k] / L[(int64_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) y[k] = yk;
+        for (int i = tid; i < k; i += NT) y[i] -= L[(int64_t)k * n + i] * yk;
+    }
+}
+
+__global__ void k_permute(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                          double* __restrict__ dst, int inverse) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (inverse) dst[perm[i]] = src[i];
+    else dst[i] = src[perm[i]];
+}
+
+// ---------------------------------------------------------------------------
+// Krylov pieces
+// ---------------------------------------------------------------------------
+__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double t = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) t += val[e] * x[col[e]];
+    y[i] = t;
+}
+
+__global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, double* __restrict__ partial) {
+    __shared__ double red[32];
+    double t = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t += a[i] * b[i];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partial, int np,
+                                                       double* __restrict__ out) {
+    __shared__ double red[32];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) t += partial[i];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) *out = t;
+}
+
+__global__ void k_pcg_xr(int64_t n, const double* __restrict__ rz, const double* __restrict__ pq,
+                         const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                         double* __restrict__ r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double alpha = *rz / *pq;
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+}
+
+__global__ void k_pcg_p(int64_t n, const double* __restrict__ rzn, const double* __restrict__ rzo,
+                        const double* __restrict__ z, double* __restrict__ p) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double beta = *rzn / *rzo;
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    y[i] = a * x[i] + b * y[i];
+}
+
+// y += sign * sum_k coef[k] * V[k*ldv + i]
+__global__ void k_gmres_update(int64_t n, int k, const double* __restrict__ coef, const double* __restrict__ V,
+                               int64_t ldv, double* __restrict__ y, double sign) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double t = 0.0;
+    for (int j = 0; j < k; j++) t += coef[j] * V[(int64_t)j * ldv + i];
+    y[i] += sign * t;
+}
+
+// partial[j * nb + blk] = sum over the block's rows of V[j] . w  (j < k)
+__global__ void __launch_bounds__(256) k_gemv_t_partial(int64_t n, int k, const double* __restrict__ V,
+                                                        int64_t ldv, const double* __restrict__ w,
+                                                        double* __restrict__ partial) {
+    __shared__ double red[32];
+    for (int j = 0; j < k; j++) {
+        double t = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            t += V[(int64_t)j * ldv + i] * w[i];
+        t = block_sum(t, red);
+        if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gemv_t_final(int k, int np, const double* __restrict__ partial,
+                                                      double* __restrict__ out) {
+    __shared__ double red[32];
+    const int j = blockIdx.x;
+    if (j >= k) return;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) t += partial[(int64_t)j * np + i];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) out[j] = t;
+}
+
+// FP64 FMA throughput probe: 8 independent chains per thread.
+__global__ void __launch_bounds__(256) k_fp64_peak(int iters, double* sink) {
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) a[u] = 1.0 + 1e-9 * (threadIdx.x + u);
+    const double b = 0.999999999, c = 1e-12;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) a[u] = fma(a[u], b, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; u++) t += a[u];
+    if (t == 12345.0) sink[0] = t;  // keeps the chains alive
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+std::atomic<int64_t> g_launches{0};
+inline void counted(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+}  // namespace
+
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void launch_count_add(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col,
+                               const double* val, const int32_t* dof_cluster, const int32_t* dof_local,
+                               const int32_t* blk_ptr, const int32_t* blk_col, const int64_t* blk_off,
+                               const int32_t* blk_ld, double* blocks) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    k_scatter_csr<<<blocks_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, dof_cluster, dof_local, blk_ptr,
+                                                      blk_col, blk_off, blk_ld, blocks);
+    return cudaGetLastError();
+}
+
+size_t factor_smem_bytes(int smax, int wmax, int lmax) {
+    return sizeof(double) * ((size_t)smax * smax + 2 * (size_t)smax + (size_t)wmax + 64) +
+           sizeof(int) * ((size_t)lmax + 1);
+}
+
+cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax, int wmax,
+                                int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
+                                const int32_t* blk_ld, int32_t* cur, double* fac, int32_t* meta, double* ws,
+                                double eps2, int32_t* status, int32_t level) {
+    if (ntasks <= 0) return cudaSuccess;
+    const size_t smem = factor_smem_bytes(smax, wmax, lmax);
+    cudaError_t e = cudaFuncSetAttribute(k_factor_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    counted();
+    k_factor_phase<<<ntasks, kFactorThreads, smem, st>>>(tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta,
+                                                         ws, eps2, status, level, smax, wmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
+                               const ContribDev* contribs, const TaskDev* tasks, const double* fac,
+                               const int32_t* meta, double* blocks, const int64_t* blk_off, const int32_t* blk_ld,
+                               const int32_t* cur, int precision) {
+    (void)precision;
+    if (ntargets <= 0) return cudaSuccess;
+    counted();
+    k_schur_phase<<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_blocks(cudaStream_t st, const CopyDev* cps, int ncps, const double* src, double* dst) {
+    if (ncps <= 0) return cudaSuccess;
+    counted();
+    k_copy_blocks<<<ncps, 128, 0, st>>>(cps, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* status) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    k_dense_cholesky<<<1, 1024, 0, st>>>(n, a, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_fwd_diag(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
+                                  const double* fac, const int32_t* meta, const int64_t* slot, double* y) {
+    if (ntasks <= 0) return cudaSuccess;
+    counted();
+    k_apply_fwd_diag<<<ntasks, kApplyThreads, sizeof(double) * smax, st>>>(tasks, t0, fac, meta, slot, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_fwd_nb(cudaStream_t st, const NbTargetDev* nbt, int g0, int ntargets,
+                                const NbContribDev* nbc, const TaskDev* tasks, const double* fac,
+                                const int32_t* meta, const int64_t* slot, double* y) {
+    if (ntargets <= 0) return cudaSuccess;
+    counted();
+    k_apply_fwd_nb<<<ntargets, kApplyThreads, 0, st>>>(nbt, g0, nbc, tasks, fac, meta, slot, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_bwd(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
+                             const ListDev* lists, const double* fac, const int32_t* meta, const int64_t* slot,
+                             double* y) {
+    if (ntasks <= 0) return cudaSuccess;
+    counted();
+    k_apply_bwd<<<ntasks, kApplyThreads, sizeof(double) * smax, st>>>(tasks, t0, lists, fac, meta, slot, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
+                         int reverse) {
+    if (ncps <= 0) return cudaSuccess;
+    counted();
+    k_vcopy<<<blocks_for(ncps, 8), 256, 0, st>>>(cps, ncps, src, dst, reverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_top_solve(cudaStream_t st, int n, const double* L, double* y) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    k_top_solve<<<1, 1024, 0, st>>>(n, L, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(cudaStream_t st, int64_t n, const int32_t* perm, const double* src, double* dst,
+                           int inverse) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    k_permute<<<blocks_for(n, 256), 256, 0, st>>>(n, perm, src, dst, inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                        const double* x, double* y) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    k_spmv<<<blocks_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const double* a, const double* b, double* partial, double* out) {
+    counted();
+    k_dot_partial<<<kDotParts, 256, 0, st>>>(n, a, b, partial);
+    counted();
+    k_sum_partials<<<1, 1024, 0, st>>>(partial, kDotParts, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update_xr(cudaStream_t st, int64_t n, const double* rz, const double* pq, const double* p,
+                                 const double* q, double* x, double* r) {
+    counted();
+    k_pcg_xr<<<blocks_for(n, 256), 256, 0, st>>>(n, rz, pq, p, q, x, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update_p(cudaStream_t st, int64_t n, const double* rz_new, const double* rz_old,
+                                const double* z, double* p) {
+    counted();
+    k_pcg_p<<<blocks_for(n, 256), 256, 0, st>>>(n, rz_new, rz_old, z, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y) {
+    counted();
+    k_axpby<<<blocks_for(n, 256), 256, 0, st>>>(n, a, x, b, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double* coef, const double* V,
+                                int64_t ldv, double* y, double sign) {
+    if (k <= 0) return cudaSuccess;
+    counted();
+    k_gmres_update<<<blocks_for(n, 256), 256, 0, st>>>(n, k, coef, V, ldv, y, sign);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_peak(cudaStream_t st, int nblocks, int iters, double* sink) {
+    counted();
+    k_fp64_peak<<<nblocks, 256, 0, st>>>(iters, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv, const double* w,
+                          double* partial, double* out) {
+    if (k <= 0) return cudaSuccess;
+    const int nb = 256;
+    counted();
+    k_gemv_t_partial<<<nb, 256, 0, st>>>(n, k, V, ldv, w, partial);
+    counted();
+    k_gemv_t_final<<<k, 256, 0, st>>>(k, nb, partial, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

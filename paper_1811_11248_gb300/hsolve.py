@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C-ABI in include/hsolve.h (argument marshalling only).
+
+Every step of the solver runs in the compiled library
+(paper_1811_11248_gb300/_build/libhsolve.so: sm_103a kernels + host planner).
+There is no fallback: if the library is missing or fails to load, ``lib()``
+raises.  Pointers: numpy arrays are passed as host pointers, torch tensors as
+their ``data_ptr()`` (host or device, as the call expects).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhsolve.so")
+
+HS_OK, HS_ERR_ARG, HS_ERR_NOT_SPD, HS_ERR_NOCONV = 0, 1, 2, 3
+HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_UNSUPPORTED, HS_ERR_TIMEOUT = 4, 5, 6, 7
+HS_MEM_HOST, HS_MEM_DEVICE = 0, 1
+HS_PREC_FP64, HS_PREC_MIXED = 0, 1
+HS_KRYLOV_PCG, HS_KRYLOV_GMRES = 0, 1
+KERNEL_CLASSES = ("factor", "schur", "assembly", "top", "apply", "krylov")
+
+P = ctypes.c_void_p
+I32, I64, F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class hs_tree(ctypes.Structure):
+    _fields_ = [("n_leaf", I32), ("perm", ctypes.POINTER(I32)),
+                ("leaf_ptr", ctypes.POINTER(I32)), ("depth", I32)]
+
+
+class hs_options(ctypes.Structure):
+    _fields_ = [("tol", F64), ("depth", I32), ("leaf_lines", I32), ("theta", F64),
+                ("precision", I32), ("krylov", I32), ("restart", I32), ("rtol", F64),
+                ("maxit", I32), ("mem", I32), ("profile", I32), ("stream", P), ("coords", P)]
+
+
+class hs_info(ctypes.Structure):
+    _fields_ = [("iters", I32), ("rel_resid", F64), ("setup_s", F64), ("solve_s", F64),
+                ("fail_level", I32), ("fail_cluster", I32), ("factor_bytes", I64)]
+
+
+class HsError(RuntimeError):
+    def __init__(self, code, where, info=None):
+        self.code = code
+        self.info = info
+        msg = lib().hs_status_str(code).decode()
+        if info is not None and code == HS_ERR_NOT_SPD:
+            msg += f" (level {info.fail_level}, cluster {info.fail_cluster})"
+        super().__init__(f"{where}: {msg} [{code}]")
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"hsolve library not built ({LIB_PATH} missing); run "
+                           "python -c 'import __graft_entry__ as g; g.build()'")
+    L = ctypes.CDLL(LIB_PATH)
+    L.hs_default_options.argtypes = [ctypes.POINTER(hs_options)]
+    L.hs_partition_extruded.argtypes = [I64, P, P, P, P, I32, F64, ctypes.POINTER(hs_tree)]
+    L.hs_tree_free.argtypes = [ctypes.POINTER(hs_tree)]
+    L.hs_setup.argtypes = [I64, P, P, P, ctypes.POINTER(hs_tree), ctypes.POINTER(hs_options),
+                           ctypes.POINTER(P), ctypes.POINTER(hs_info)]
+    L.hs_apply.argtypes = [P, P, P]
+    L.hs_krylov.argtypes = [P, P, P, ctypes.POINTER(hs_info)]
+    L.hs_solve.argtypes = [I64, P, P, P, P, P, ctypes.POINTER(hs_options), ctypes.POINTER(hs_info)]
+    L.hs_destroy.argtypes = [P]
+    L.hs_num_levels.argtypes = [P, ctypes.POINTER(I32)]
+    L.hs_level_clusters.argtypes = [P, I32, ctypes.POINTER(I32)]
+    L.hs_level_info.argtypes = [P, I32, P, P, P]
+    L.hs_top_size.argtypes = [P, ctypes.POINTER(I32)]
+    L.hs_kernel_stats.argtypes = [P, I32, P, P, P, P]
+    L.hs_reset_kernel_stats.argtypes = [P]
+    L.hs_measure_fp64_peak.argtypes = [P, ctypes.POINTER(F64)]
+    L.hs_launch_count.argtypes = [ctypes.POINTER(I64)]
+    L.hs_status_str.argtypes = [ctypes.c_int]
+    L.hs_status_str.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+# names the C-ABI exports (tests check that every one is present)
+EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_setup", "hs_apply",
+            "hs_krylov", "hs_solve", "hs_destroy", "hs_num_levels", "hs_level_clusters",
+            "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
+            "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str")
+
+
+def _ptr(x):
+    """Host pointer of a numpy array or data_ptr() of a torch tensor (or None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data_as(P)
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return P(x.data_ptr())
+    if isinstance(x, int):
+        return P(x)
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(rc, where, info=None):
+    if rc != HS_OK:
+        raise HsError(rc, where, info)
+
+
+def hs_default_options(**kw):
+    o = hs_options()
+    _check(lib().hs_default_options(ctypes.byref(o)), "hs_default_options")
+    for k, v in kw.items():
+        if k == "stream":
+            v = P(v) if v is not None else None
+        elif k == "coords":
+            o._coords_keep = v  # the caller's array must outlive the call
+            v = _ptr(v)
+        setattr(o, k, v)
+    return o
+
+
+def hs_partition_extruded(n, rowptr, col, val, coords=None, leaf_lines=4, theta=0.5):
+    """-> (perm int32[n], leaf_ptr int32[n_leaf+1], default depth); host arrays."""
+    t = hs_tree()
+    _check(lib().hs_partition_extruded(int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(coords),
+                                       int(leaf_lines), float(theta), ctypes.byref(t)),
+           "hs_partition_extruded")
+    try:
+        perm = np.ctypeslib.as_array(t.perm, shape=(int(n),)).copy()
+        lp = np.ctypeslib.as_array(t.leaf_ptr, shape=(t.n_leaf + 1,)).copy()
+        depth = int(t.depth)
+    finally:
+        lib().hs_tree_free(ctypes.byref(t))
+    return perm, lp, depth
+
+
+class Handle:
+    """Factor handle returned by hs_setup (owns the device factor)."""
+
+    def __init__(self, h, n, info):
+        self._h = h
+        self.n = n
+        self.setup_info = info
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().hs_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def hs_apply(self, r, z):
+        _check(lib().hs_apply(self._h, _ptr(r), _ptr(z)), "hs_apply")
+
+    def hs_krylov(self, b, x, check=True):
+        info = hs_info()
+        rc = lib().hs_krylov(self._h, _ptr(b), _ptr(x), ctypes.byref(info))
+        if check:
+            _check(rc, "hs_krylov", info)
+        return info, rc
+
+    def num_levels(self):
+        v = I32()
+        _check(lib().hs_num_levels(self._h, ctypes.byref(v)), "hs_num_levels")
+        return int(v.value)
+
+    def level_info(self, level):
+        nc = I32()
+        _check(lib().hs_level_clusters(self._h, int(level), ctypes.byref(nc)), "hs_level_clusters")
+        s0, fi, ph = (np.zeros(nc.value, np.int32) for _ in range(3))
+        _check(lib().hs_level_info(self._h, int(level), _ptr(s0), _ptr(fi), _ptr(ph)), "hs_level_info")
+        return s0, fi, ph
+
+    def top_size(self):
+        v = I32()
+        _check(lib().hs_top_size(self._h, ctypes.byref(v)), "hs_top_size")
+        return int(v.value)
+
+    def kernel_stats(self):
+        k = len(KERNEL_CLASSES)
+        t = np.zeros(k)
+        n = np.zeros(k, np.int64)
+        f = np.zeros(k)
+        b = np.zeros(k)
+        _check(lib().hs_kernel_stats(self._h, k, _ptr(t), _ptr(n), _ptr(f), _ptr(b)), "hs_kernel_stats")
+        return {name: dict(ms=float(t[i]), launches=int(n[i]), flops=float(f[i]), bytes=float(b[i]))
+                for i, name in enumerate(KERNEL_CLASSES)}
+
+    def reset_kernel_stats(self):
+        _check(lib().hs_reset_kernel_stats(self._h), "hs_reset_kernel_stats")
+
+
+def hs_setup(n, rowptr, col, val, tree=None, opt=None, **kw):
+    """tree: None or (perm, leaf_ptr, depth) host arrays."""
+    opt = opt if opt is not None else hs_default_options(**kw)
+    info = hs_info()
+    h = P()
+    tp = None
+    keep = None
+    if tree is not None:
+        perm, lp, depth = tree
+        perm = np.ascontiguousarray(perm, dtype=np.int32)
+        lp = np.ascontiguousarray(lp, dtype=np.int32)
+        keep = (perm, lp)
+        tp = hs_tree(len(lp) - 1, perm.ctypes.data_as(ctypes.POINTER(I32)),
+                     lp.ctypes.data_as(ctypes.POINTER(I32)), int(depth))
+    rc = lib().hs_setup(int(n), _ptr(rowptr), _ptr(col), _ptr(val),
+                        ctypes.byref(tp) if tp is not None else None, ctypes.byref(opt),
+                        ctypes.byref(h), ctypes.byref(info))
+    del keep
+    _check(rc, "hs_setup", info)
+    return Handle(h, int(n), info)
+
+
+def hs_solve(n, rowptr, col, val, b, x, opt=None, check=True, **kw):
+    opt = opt if opt is not None else hs_default_options(**kw)
+    info = hs_info()
+    rc = lib().hs_solve(int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
+                        ctypes.byref(opt), ctypes.byref(info))
+    if check:
+        _check(rc, "hs_solve", info)
+    return info, rc
+
+
+def hs_launch_count():
+    v = I64()
+    _check(lib().hs_launch_count(ctypes.byref(v)), "hs_launch_count")
+    return int(v.value)
+
+
+def hs_measure_fp64_peak(stream=None):
+    v = F64()
+    _check(lib().hs_measure_fp64_peak(P(stream) if stream else None, ctypes.byref(v)),
+           "hs_measure_fp64_peak")
+    return float(v.value)

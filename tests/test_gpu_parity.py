@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle on the
+same seeded inputs and the same partition tree.
+
+Bars: identical phases and ranks per cluster (integer decisions), operator
+parity max_r ||M_gpu^-1 r - M_or^-1 r|| / ||M_or^-1 r|| <= tol over 8 random r,
+PCG iterations within 1, both true residuals <= 1e-8, and
+||x_gpu - x_or|| / ||x_or|| <= 1e-6.  tol = max(1e-10, 100 u kappa(A)) where
+kappa is computed densely for the small cases (the two implementations round
+differently; their difference is bounded by the forward-error bound of either).
+"""
+import numpy as np
+import pytest
+
+from paper_1811_11248_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = np.finfo(float).eps
+
+
+@pytest.fixture(scope="module")
+def hs():
+    from paper_1811_11248_gb300 import build, hsolve
+    build.build()
+    hsolve.lib()
+    assert torch.cuda.is_available()
+    return hsolve
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def setup_both(hs, oracle_lib, p, depth, tol, leaf=4, mem="device", **kw):
+    perm, lp = oracle_lib.partition(p, leaf)
+    if depth is None:
+        depth = oracle_lib.default_depth(len(lp) - 1)
+    ref = oracle_lib.Factor(p, perm, lp, depth, tol)
+    if mem == "device":
+        opt = hs.hs_default_options(tol=tol, mem=hs.HS_MEM_DEVICE,
+                                    stream=torch.cuda.current_stream().cuda_stream, **kw)
+        h = hs.hs_setup(p.n, dev(p.rowptr), dev(p.col), dev(p.val), tree=(perm, lp, depth), opt=opt)
+    else:
+        opt = hs.hs_default_options(tol=tol, mem=hs.HS_MEM_HOST,
+                                    stream=torch.cuda.current_stream().cuda_stream, **kw)
+        h = hs.hs_setup(p.n, p.rowptr, p.col, p.val, tree=(perm, lp, depth), opt=opt)
+    return h, ref, depth
+
+
+def check_structure(h, ref, depth):
+    assert h.num_levels() == depth
+    for l in range(depth):
+        s0, fi, ph = h.level_info(l)
+        o0, of, oph = ref.level_info(l)
+        assert np.array_equal(s0, o0), f"level {l} sizes"
+        assert np.array_equal(ph, oph), f"level {l} phases"
+        bad = np.flatnonzero(fi != of)
+        assert bad.size == 0, f"level {l} ranks differ at clusters {bad[:10]}: {fi[bad[:10]]} vs {of[bad[:10]]}"
+    assert h.top_size() == ref.top_n
+
+
+def operator_diff(h, ref, n, nvec=8, seed=0):
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(nvec):
+        r = rng.uniform(-1, 1, n)
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        h.hs_apply(dev(r), z)
+        torch.cuda.synchronize()
+        zo = ref.apply(r)
+        worst = max(worst, np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo))
+    return worst
+
+
+def krylov_check(h, ref, p, gmres=False):
+    x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    info, rc = h.hs_krylov(dev(p.b), x)
+    xg = x.cpu().numpy()
+    xo, ito, rro, rco = (ref.gmres(rtol=1e-8, restart=50) if gmres else ref.pcg(rtol=1e-8))
+    assert rco == 0
+    assert abs(info.iters - ito) <= 1, (info.iters, ito)
+    res = np.linalg.norm(p.b - p.matvec(xg)) / np.linalg.norm(p.b)
+    assert res <= 1e-8 and info.rel_resid <= 1e-8
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+    return info, ito
+
+
+def kappa(p):
+    ev = np.linalg.eigvalsh(p.dense())
+    return ev[-1] / ev[0]
+
+
+SMALL = [
+    ("dirichlet-8x8x4", lambda: inputs.grid_operator(8, 8, 4, ratio=1e4), 2, 1e-2),
+    ("ice-16x16x8-1e-2", lambda: inputs.grid_operator(16, 16, 8, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5), 4, 1e-2),
+    ("ice-16x16x8-1e-4", lambda: inputs.grid_operator(16, 16, 8, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5), 4, 1e-4),
+    ("shelf-16x16x8-1e-1", lambda: inputs.grid_operator(16, 16, 8, ratio=1e6, sigma=1.0, seed=3, bc="ice", shelf=1.0), 4, 1e-1),
+    ("ragged-12x10x5", lambda: inputs.grid_operator(12, 10, 5, ratio=1e3, sigma=1.0, seed=2, bc="ice", shelf=0.5), 2, 1e-2),
+    ("vector-8x8x4", lambda: inputs.vector_operator(8, 8, 4, ratio=1e4, bc="ice", shelf=0.5), 2, 1e-2),
+    ("exact-8x8x4", lambda: inputs.grid_operator(8, 8, 4, ratio=1e3, sigma=1.0, seed=4, bc="ice", shelf=0.5), 2, 0.0),
+    ("depth0-4x4x3", lambda: inputs.grid_operator(4, 4, 3, ratio=1e2), 0, 1e-2),
+]
+
+
+@pytest.mark.parametrize("name,make,depth,tol", SMALL, ids=[c[0] for c in SMALL])
+def test_small_parity(hs, oracle_lib, name, make, depth, tol):
+    p = make()
+    h, ref, depth = setup_both(hs, oracle_lib, p, depth, tol)
+    check_structure(h, ref, depth)
+    bound = max(1e-10, 100 * U * kappa(p))
+    d = operator_diff(h, ref, p.n)
+    assert d <= bound, (d, bound)
+    krylov_check(h, ref, p)
+    h.close()
+
+
+def test_dirichlet_16x16x8_workload(hs, oracle_lib):
+    p = inputs.anisotropic_16x16x8()
+    h, ref, depth = setup_both(hs, oracle_lib, p, 4, 1e-2)
+    check_structure(h, ref, depth)
+    assert operator_diff(h, ref, p.n) <= 1e-10
+    krylov_check(h, ref, p)
+
+
+def test_host_and_device_inputs_agree(hs, oracle_lib):
+    p = inputs.grid_operator(16, 16, 8, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
+    hd, ref, depth = setup_both(hs, oracle_lib, p, 4, 1e-2, mem="device")
+    hh, _, _ = setup_both(hs, oracle_lib, p, 4, 1e-2, mem="host")
+    r = dev(np.random.default_rng(5).uniform(-1, 1, p.n))
+    z1 = torch.empty_like(r)
+    z2 = torch.empty_like(r)
+    hd.hs_apply(r, z1)
+    hh.hs_apply(r, z2)
+    torch.cuda.synchronize()
+    assert torch.equal(z1, z2)  # same kernels, same inputs: bitwise
+
+
+def test_gmres_parity(hs, oracle_lib):
+    p = inputs.vector_operator(12, 12, 5, ratio=1e6, bc="ice", shelf=0.5)
+    h, ref, depth = setup_both(hs, oracle_lib, p, None, 1e-2, krylov=hs.HS_KRYLOV_GMRES, restart=50)
+    check_structure(h, ref, depth)
+    krylov_check(h, ref, p, gmres=True)
+
+
+def test_hs_solve_host_pointers(hs, oracle_lib):
+    """Partition + setup + Krylov in one C-ABI call on host buffers."""
+    p = inputs.grid_operator(16, 16, 8, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
+    x = np.zeros(p.n)
+    info, rc = hs.hs_solve(p.n, p.rowptr, p.col, p.val, p.b, x, mem=hs.HS_MEM_HOST, tol=1e-2)
+    assert rc == 0 and info.rel_resid <= 1e-8
+    assert np.linalg.norm(p.b - p.matvec(x)) <= 1e-8 * np.linalg.norm(p.b)
+
+
+def test_not_spd_reported(hs, oracle_lib):
+    p = inputs.grid_operator(8, 8, 4, ratio=1e2)
+    perm, lp = oracle_lib.partition(p, 4)
+    i0 = perm[0]
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    k = np.flatnonzero((rows == i0) & (p.col == i0))[0]
+    p.val = p.val.copy()
+    p.val[k] = -1.0
+    opt = hs.hs_default_options(tol=1e-2, mem=hs.HS_MEM_HOST)
+    with pytest.raises(hs.HsError) as e:
+        hs.hs_setup(p.n, p.rowptr, p.col, p.val, tree=(perm, lp, 2), opt=opt)
+    assert e.value.code == hs.HS_ERR_NOT_SPD
+    assert e.value.info.fail_level == 0 and e.value.info.fail_cluster == 0
+    # the context stays usable
+    q = inputs.grid_operator(8, 8, 4, ratio=1e2)
+    h, ref, depth = setup_both(hs, oracle_lib, q, 2, 1e-2)
+    assert operator_diff(h, ref, q.n, nvec=2) <= 1e-10
+
+
+def test_single_dof(hs):
+    rp = np.array([0, 1], np.int64)
+    ci = np.array([0], np.int32)
+    va = np.array([4.0])
+    x = np.zeros(1)
+    info, rc = hs.hs_solve(1, rp, ci, va, np.array([2.0]), x, mem=hs.HS_MEM_HOST)
+    assert rc == 0 and abs(x[0] - 0.5) < 1e-15
+
+
+@pytest.mark.slow
+def test_full_size_64x64x16_parity(hs, oracle_lib):
+    """The benchmark workload at full size, same launch configuration as the
+    benchmark's FP64 leg: whole-operator parity (the oracle runs it fully)."""
+    p = inputs.anisotropic_64x64x16()
+    h, ref, depth = setup_both(hs, oracle_lib, p, 8, 1e-2)
+    check_structure(h, ref, depth)
+    d = operator_diff(h, ref, p.n, nvec=4)
+    assert d <= 1e-8, d
+    krylov_check(h, ref, p)
