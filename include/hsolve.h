@@ -119,6 +119,25 @@ int hs_apply(hs_handle h, const double* r, double* z);
  * b, x device pointers. */
 int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info);
 
+/* Allocation-free PCG solve with an existing handle.  No counterpart in the
+ * paper: it is for callers that cannot allocate device memory when they
+ * solve, for example a time-stepping loop inside a host application whose own
+ * allocator owns all device memory, or code that must not call
+ * cudaMalloc/cudaFree (which synchronise the device) after initialisation.
+ * It runs the same PCG as hs_krylov, but the four work vectors and the
+ * dot-product partial sums live in a fixed array compiled into the library
+ * (static __device__, 256-byte aligned, 4 * 262144 + 1040 doubles, about
+ * 8.4 MB, held on every GPU that loads the library until the process exits).
+ * Limits: n <= 262144 (else HS_ERR_ARG) and a handle set up with
+ * HS_KRYLOV_PCG (else HS_ERR_UNSUPPORTED).  The first call on a device looks
+ * up the array's device address and caches it; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (this call zeroes or writes everything it reads): calls
+ * whose device work overlaps in time (several streams, threads or handles at
+ * once) race and return wrong results.  b, x: device pointers, n doubles.
+ * Allocates nothing: no cudaMalloc / cudaFree and no allocating library call. */
+int hs_krylov_noalloc(hs_handle h, const double* b, double* x, hs_info* info);
+
 /* Partition + setup + Krylov in one call; pointers in opt->mem. */
 int hs_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
              const double* b, double* x, const hs_options* opt, hs_info* info);

@@ -1146,6 +1146,77 @@ int gmres_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
     return rc;
 }
 
+// PCG of hs_krylov_noalloc: the same iteration as pcg_impl, with every work
+// vector in the library's static device scratch and no profiling, so that no
+// device memory is allocated.
+int pcg_noalloc(hs_factor_s* h, const double* b, double* x, double* scratch, hs_info* info) {
+    cudaStream_t st = h->st;
+    const int64_t n = h->n;
+    double* r = scratch;
+    double* z = r + kNoAllocMaxN;
+    double* p = z + kNoAllocMaxN;
+    double* q = p + kNoAllocMaxN;
+    double* part = q + kNoAllocMaxN;
+    double* sc = part + kDotParts;  // 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb
+    double* y0 = h->lev.empty() ? h->d_ytop.as<double>() : h->lev[0]->d_y.as<double>();
+    auto apply = [&](const double* rr, double* zz) {
+        CK(launch_permute(st, n, h->d_perm.as<int32_t>(), rr, y0, 0));
+        if (h->apply_graph) {
+            CK(cudaGraphLaunch(h->apply_graph, st));
+            launch_count_add(h->graph_kernels);
+        }
+        CK(launch_permute(st, n, h->d_perm.as<int32_t>(), y0, zz, 1));
+    };
+    auto spmv = [&](const double* xx, double* yy) {
+        CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), xx, yy));
+    };
+    auto dot = [&](const double* a, const double* bb, double* out) { CK(launch_dot(st, n, a, bb, part, out)); };
+    // the scratch keeps the previous call's contents: everything read below is
+    // written first in this call (x is zeroed, r copied from b, scalars set by dot)
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    dot(b, b, sc + 4);
+    const double bn = std::sqrt(read_scalar(h, sc + 4));
+    if (bn == 0.0) {
+        info->iters = 0;
+        info->rel_resid = 0.0;
+        return HS_OK;
+    }
+    apply(r, z);
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    dot(r, z, sc + 0);
+    int it = 0;
+    double rn = bn;
+    int rc = HS_ERR_NOCONV;
+    while (it < h->opt.maxit) {
+        spmv(p, q);
+        dot(p, q, sc + 1);
+        CK(launch_pcg_update_xr(st, n, sc + 0, sc + 1, p, q, x, r));
+        it++;
+        dot(r, r, sc + 3);
+        rn = std::sqrt(read_scalar(h, sc + 3));
+        if (rn / bn <= h->opt.rtol) {
+            spmv(x, q);
+            CK(launch_axpby(st, n, 1.0, b, -1.0, q));
+            dot(q, q, sc + 3);
+            rn = std::sqrt(read_scalar(h, sc + 3));
+            if (rn / bn <= h->opt.rtol) { rc = HS_OK; break; }
+            CK(cudaMemcpyAsync(r, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            apply(r, z);
+            CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            dot(r, z, sc + 0);
+            continue;
+        }
+        apply(r, z);
+        dot(r, z, sc + 2);
+        CK(launch_pcg_update_p(st, n, sc + 2, sc + 0, z, p));
+        CK(cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    info->iters = it;
+    info->rel_resid = rn / bn;
+    return rc;
+}
+
 template <class F>
 int run_guarded(F&& f) {
     try {
@@ -1272,6 +1343,24 @@ int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info) {
         krc = h->opt.krylov == HS_KRYLOV_GMRES ? gmres_impl(h, b, x, inf) : pcg_impl(h, b, x, inf);
         CK(cudaStreamSynchronize(h->st));
         h->prof.collect();
+    });
+    inf->solve_s = now_s() - t0;
+    return rc != HS_OK ? rc : krc;
+}
+
+int hs_krylov_noalloc(hs_handle h, const double* b, double* x, hs_info* info) {
+    if (!h || !b || !x) return HS_ERR_ARG;
+    if (h->n > kNoAllocMaxN) return HS_ERR_ARG;               // beyond the fixed scratch
+    if (h->opt.krylov != HS_KRYLOV_PCG) return HS_ERR_UNSUPPORTED;
+    hs_info tmp{};
+    hs_info* inf = info ? info : &tmp;
+    const double t0 = now_s();
+    int krc = HS_OK;
+    const int rc = run_guarded([&] {
+        double* scratch = nullptr;
+        CK(noalloc_scratch(&scratch));
+        krc = pcg_noalloc(h, b, x, scratch, inf);
+        CK(cudaStreamSynchronize(h->st));
     });
     inf->solve_s = now_s() - t0;
     return rc != HS_OK ? rc : krc;

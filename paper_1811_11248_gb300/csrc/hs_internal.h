@@ -122,6 +122,12 @@ void launch_count_add(int64_t k);
 cudaError_t launch_fp64_peak(cudaStream_t st, int nblocks, int iters, double* sink);
 
 constexpr int kDotParts = 1024;
+// allocation-free PCG: largest n, scratch layout r | z | p | q | partials | scalars
+constexpr int64_t kNoAllocMaxN = 262144;
+constexpr int64_t kNoAllocDoubles = 4 * kNoAllocMaxN + kDotParts + 16;
+constexpr int kNoAllocMaxDevices = 64;
+// device address of the static scratch on the current device (looked up once per device)
+cudaError_t noalloc_scratch(double** ptr);
 constexpr int kFactorMaxSmem = 226 * 1024;  // dynamic part; static shared adds a few bytes
 
 }  // namespace hs

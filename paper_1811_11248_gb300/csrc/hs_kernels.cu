@@ -21,6 +21,7 @@
 #include <cfloat>
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include "hs_internal.h"
 
@@ -672,6 +673,32 @@ std::atomic<int64_t> g_launches{0};
 inline void counted(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 }  // namespace
+
+// Fixed device scratch of the allocation-free PCG (hs_krylov_noalloc): four
+// work vectors of at most kNoAllocMaxN doubles, the dot-product partial sums
+// and a few scalars.  Compiled into the library; every device that loads it
+// holds the array until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+cudaError_t noalloc_scratch(double** ptr) {
+    static std::mutex mu;
+    static double* addr[kNoAllocMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        // the symbol names a host-side stand-in; only this call yields the
+        // array's address on the current device
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<double*>(p);
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
+}
 
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void launch_count_add(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }

@@ -72,6 +72,7 @@ def lib():
                            ctypes.POINTER(P), ctypes.POINTER(hs_info)]
     L.hs_apply.argtypes = [P, P, P]
     L.hs_krylov.argtypes = [P, P, P, ctypes.POINTER(hs_info)]
+    L.hs_krylov_noalloc.argtypes = [P, P, P, ctypes.POINTER(hs_info)]
     L.hs_solve.argtypes = [I64, P, P, P, P, P, ctypes.POINTER(hs_options), ctypes.POINTER(hs_info)]
     L.hs_destroy.argtypes = [P]
     L.hs_num_levels.argtypes = [P, ctypes.POINTER(I32)]
@@ -90,7 +91,7 @@ def lib():
 
 # names the C-ABI exports (tests check that every one is present)
 EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_setup", "hs_apply",
-            "hs_krylov", "hs_solve", "hs_destroy", "hs_num_levels", "hs_level_clusters",
+            "hs_krylov", "hs_krylov_noalloc", "hs_solve", "hs_destroy", "hs_num_levels", "hs_level_clusters",
             "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
             "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str")
 
@@ -172,6 +173,14 @@ class Handle:
         rc = lib().hs_krylov(self._h, _ptr(b), _ptr(x), ctypes.byref(info))
         if check:
             _check(rc, "hs_krylov", info)
+        return info, rc
+
+    def hs_krylov_noalloc(self, b, x, check=True):
+        """PCG with the library's fixed device scratch (allocates nothing)."""
+        info = hs_info()
+        rc = lib().hs_krylov_noalloc(self._h, _ptr(b), _ptr(x), ctypes.byref(info))
+        if check:
+            _check(rc, "hs_krylov_noalloc", info)
         return info, rc
 
     def num_levels(self):
