@@ -55,6 +55,34 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Stream on which DBuf allocations and frees are ordered (set by every C-ABI
+// entry point that allocates).  Allocations come from the device's default
+// memory pool, which keeps freed blocks for reuse by the next setup.
+thread_local cudaStream_t g_alloc_stream = nullptr;
+
+void prepare_pool() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+struct Trace {
+    bool on = std::getenv("HS_TRACE") != nullptr;
+    double t = now_s();
+    void mark(const char* what) {
+        if (!on) return;
+        const double n = now_s();
+        std::fprintf(stderr, "hs_trace %-28s %8.3f ms\n", what, (n - t) * 1e3);
+        t = n;
+    }
+};
+
 // Device buffer owned by a handle.
 struct DBuf {
     void* p = nullptr;
@@ -69,7 +97,7 @@ struct DBuf {
     }
     ~DBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, g_alloc_stream);
         p = nullptr;
         bytes = 0;
     }
@@ -80,7 +108,7 @@ struct DBuf {
     void alloc(size_t b) {
         release();
         if (b == 0) b = 16;
-        CK(cudaMalloc(&p, b));
+        CK(cudaMallocAsync(&p, b, g_alloc_stream));
         bytes = b;
     }
     template <class T>
@@ -334,13 +362,21 @@ struct Level {
     std::vector<int> size0, fin, phase;
     std::vector<int64_t> slot;  // vector slot offsets (size nc + 1)
     int nphases = 0;
-    std::vector<int> ph_task, ph_target, ph_nbt;  // per-phase ranges (size nphases + 1)
-    int smax = 0, wmax = 0, lmax = 0;
+    std::vector<int> ph_task, ph_target;  // per-phase ranges (size nphases + 1)
+    int smax = 0, wmax = 0, lmax = 0, nmax = 0;
     std::vector<TaskDev> tasks;
     std::vector<ListDev> lists;
-    std::vector<int> task_rank;  // filled after the level
-    DBuf d_tasks, d_lists, d_nbt, d_nbc, d_meta, d_fac, d_slot, d_vcopy, d_y;
-    int nvcopy = 0;
+    // solve phase: (task, k) lists of the updates each cluster receives from
+    // tasks of earlier phases (early) / later phases (late)
+    std::vector<std::vector<std::pair<int, int>>> early, late;
+    std::vector<int64_t> stg;          // stage offset of every task
+    std::vector<int32_t> hmeta;        // rank and n-column layout of every task
+    std::vector<int> task_rank;        // filled after the level
+    std::vector<ApPull> ap_pulls;      // early pulls of the tasks, then the late pulls
+    int64_t work_max_phase = 0;        // largest sum over a phase of s^2 + f * ncols
+    DBuf d_tasks, d_lists, d_meta, d_fac, d_slot, d_vcopy, d_y, d_stage;
+    DBuf d_ap_tasks, d_ap_pulls, d_ap_nbs, d_ap_fins, d_ph;
+    int nvcopy = 0, nfin = 0;
     int64_t fac_doubles = 0;
     // algorithmic work of the level (filled after it ran)
     double flops_factor = 0, flops_schur = 0;
@@ -406,6 +442,8 @@ struct hs_factor_s {
     int64_t factor_bytes = 0;
     cudaGraphExec_t apply_graph = nullptr;
     int64_t graph_kernels = 0;
+    int first_coarse = 0;
+    DBuf d_aplevels;
     Prof prof;
     double work_flops[KC_N] = {0};
     double work_bytes[KC_N] = {0};
@@ -474,16 +512,13 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
 
     // tasks in phase order
     std::vector<int> task_of(P.nc, -1);
-    int64_t fac = 0, ws_phase_max = 0;
+    int64_t fac = 0, ws_phase_max = 0, stage = 0;
     int32_t meta = 0;
     L.ph_task.assign(1, 0);
     L.ph_target.assign(1, 0);
-    L.ph_nbt.assign(1, 0);
     std::vector<TargetDev> targets;
     std::vector<ContribDev> contribs;
-    std::vector<NbTargetDev> nbts;
-    std::vector<NbContribDev> nbcs;
-    L.smax = 1; L.wmax = 1; L.lmax = 1;
+    L.smax = 1; L.wmax = 1; L.lmax = 1; L.nmax = 1;
     for (int ph = 0; ph < L.nphases; ph++) {
         int64_t ws = 0;
         for (int c : P.phases[ph]) {
@@ -509,29 +544,27 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             t.wcap = wcap;
             t.meta = meta;
             meta += 1 + 2 * t.nn;
-            t.g_off = fac; fac += (int64_t)t.s * t.s;
-            t.v_off = fac; fac += (int64_t)t.s * t.s;
-            t.tau_off = fac; fac += t.s;
+            L.stg.push_back(stage);
+            stage += std::max(ncap, 1);
+            t.w_off = fac; fac += (int64_t)t.s * t.s;
             t.c_off = fac; fac += (int64_t)t.s * std::max(ncap, 1);
-            t.m_off = ws; ws += (int64_t)t.s * std::max(wcap, 1);
+            t.m_off = ws; ws += (int64_t)t.s * (wcap + t.s);
             L.smax = std::max(L.smax, t.s);
             L.wmax = std::max(L.wmax, wcap);
             L.lmax = std::max(L.lmax, t.nn + t.nw);
+            L.nmax = std::max(L.nmax, ncap);
             task_of[c] = (int)L.tasks.size();
             L.tasks.push_back(t);
         }
         ws_phase_max = std::max(ws_phase_max, ws);
         // Schur targets of the phase: (p, q), p <= q, contributions ascending
         std::map<std::pair<int, int>, std::vector<ContribDev>> tg;
-        std::map<int, std::vector<NbContribDev>> nb;
         for (int c : P.phases[ph]) {
             const int ti = task_of[c];
             const auto& nlc = P.nl[c];
-            for (int a = 0; a < (int)nlc.size(); a++) {
-                nb[nlc[a]].push_back(NbContribDev{ti, a});
+            for (int a = 0; a < (int)nlc.size(); a++)
                 for (int b = 0; b < (int)nlc.size(); b++)
                     if (nlc[a] <= nlc[b]) tg[{nlc[a], nlc[b]}].push_back(ContribDev{ti, a, b});
-            }
         }
         for (auto& kv : tg) {
             TargetDev g{};
@@ -544,30 +577,33 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             g.c_end = (int)contribs.size();
             targets.push_back(g);
         }
-        for (auto& kv : nb) {
-            NbTargetDev g{};
-            g.q = kv.first;
-            g.c_begin = (int)nbcs.size();
-            nbcs.insert(nbcs.end(), kv.second.begin(), kv.second.end());
-            g.c_end = (int)nbcs.size();
-            nbts.push_back(g);
-        }
         L.ph_task.push_back((int)L.tasks.size());
         L.ph_target.push_back((int)targets.size());
-        L.ph_nbt.push_back((int)nbts.size());
+    }
+    // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
+    // before its own transform (q in a later phase) or at level end (earlier)
+    L.early.assign(P.nc, {});
+    L.late.assign(P.nc, {});
+    for (int ti = 0; ti < (int)L.tasks.size(); ti++) {
+        const TaskDev& t = L.tasks[ti];
+        for (int k = 0; k < t.nn; k++) {
+            const int q = L.lists[t.list + k].q;
+            (P.phase[q] > P.phase[t.c] ? L.early[q] : L.late[q]).push_back({ti, k});
+        }
     }
     if (factor_smem_bytes(L.smax, L.wmax, L.lmax) > (size_t)kFactorMaxSmem) throw HsError{HS_ERR_UNSUPPORTED};
+    Trace tr;
+    tr.mark("  records");
 
     upload(L.d_tasks, L.tasks, st);
     upload(L.d_lists, L.lists, st);
     DBuf d_targets, d_contribs, d_ws;
     upload(d_targets, targets, st);
     upload(d_contribs, contribs, st);
-    upload(L.d_nbt, nbts, st);
-    upload(L.d_nbc, nbcs, st);
     L.d_meta.alloc(sizeof(int32_t) * std::max<int32_t>(meta, 1));
     L.d_fac.alloc(sizeof(double) * std::max<int64_t>(fac, 1));
     L.fac_doubles = fac;
+    L.d_stage.alloc(sizeof(double) * std::max<int64_t>(stage, 1));
     d_ws.alloc(sizeof(double) * std::max<int64_t>(ws_phase_max, 1));
     upload(L.d_slot, L.slot, st);
 
@@ -576,6 +612,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     upload(d_off, T.off, st);
     upload(d_ld, ld, st);
     const double eps2 = h->opt.tol * h->opt.tol;
+    tr.mark("  uploads");
     for (int ph = 0; ph < L.nphases; ph++) {
         const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
         h->prof.begin(KC_FACTOR, st);
@@ -594,17 +631,62 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             h->prof.end(KC_SCHUR, st);
         }
     }
+    tr.mark("  launches");
     check_status(h, d_status, info);
+    tr.mark("  kernels (sync)");
     L.fin.assign(P.nc, 0);
     CK(cudaMemcpyAsync(L.fin.data(), d_cur.p, sizeof(int32_t) * P.nc, cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> hmeta(meta);
     if (meta) CK(cudaMemcpyAsync(hmeta.data(), L.d_meta.p, sizeof(int32_t) * meta, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    // solve-phase records with resolved offsets
+    {
+        std::vector<ApTask> at(L.tasks.size());
+        std::vector<ApNb> nbs;
+        std::vector<int> ph_of(L.tasks.size());
+        for (int ph = 0; ph < L.nphases; ph++)
+            for (int ti = L.ph_task[ph]; ti < L.ph_task[ph + 1]; ti++) ph_of[ti] = ph;
+        std::vector<int64_t> work(L.nphases, 0);
+        for (size_t ti = 0; ti < L.tasks.size(); ti++) {
+            const TaskDev& t = L.tasks[ti];
+            const int32_t* mt = hmeta.data() + t.meta;
+            ApTask a{};
+            a.y = L.slot[t.c];
+            a.w = t.w_off;
+            a.cm = t.c_off;
+            a.stg = L.stg[ti];
+            a.s = t.s;
+            a.r = mt[0];
+            a.ncols = t.nn > 0 ? mt[1 + 2 * (t.nn - 1)] + mt[2 + 2 * (t.nn - 1)] : 0;
+            a.ncap = t.ncap;
+            a.pull0 = (int)L.ap_pulls.size();
+            for (auto& pk : L.early[t.c])
+                L.ap_pulls.push_back(ApPull{L.stg[pk.first] + hmeta[L.tasks[pk.first].meta + 1 + 2 * pk.second]});
+            a.pull1 = (int)L.ap_pulls.size();
+            a.nb0 = (int)nbs.size();
+            for (int e = 0; e < t.nn; e++) {
+                ApNb nb{};
+                nb.y = L.slot[L.lists[t.list + e].q];
+                nb.col = mt[1 + 2 * e];
+                nb.m = mt[2 + 2 * e];
+                nbs.push_back(nb);
+            }
+            a.nb1 = (int)nbs.size();
+            at[ti] = a;
+            work[ph_of[ti]] += (int64_t)a.s * a.s + (int64_t)(a.s - a.r) * a.ncols;
+        }
+        for (auto w : work) L.work_max_phase = std::max(L.work_max_phase, w);
+        upload(L.d_ap_tasks, at, st);
+        upload(L.d_ap_nbs, nbs, st);
+        upload(L.d_ph, L.ph_task, st);
+        L.hmeta = std::move(hmeta);
+        L.early.clear();
+    }
     // algorithmic work: POTRF s^3/3, TRSM s^2 (n + w), CPQR sum_k 4 (s-k)(w-k) + 4 s r n, Schur n^2 f
     L.task_rank.resize(L.tasks.size());
     for (size_t ti = 0; ti < L.tasks.size(); ti++) {
         const TaskDev& t = L.tasks[ti];
-        const int r = hmeta[t.meta];
+        const int r = L.hmeta[t.meta];
         L.task_rank[ti] = r;
         double ncol = 0, wcol = 0;
         for (int k = 0; k < t.nn + t.nw; k++) {
@@ -622,9 +704,12 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     h->work_flops[KC_SCHUR] += L.flops_schur;
 }
 
-// Coarse-vector copies from level l to the next level / the top.
+// Coarse-vector copies from level l to the next level / the top: the
+// backward scatter (vcopy) and the forward end-of-level records (late
+// updates + gather); uploads the level's update list.
 void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& next_slot) {
     std::vector<VCopyDev> v;
+    std::vector<ApFin> fins;
     for (int c = 0; c < L.nc; c++) {
         if (L.fin[c] <= 0) continue;
         VCopyDev x{};
@@ -632,9 +717,23 @@ void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& next_slo
         x.dst = next_slot[c / 2] + ((c & 1) ? L.fin[c - 1] : 0);
         x.len = L.fin[c];
         v.push_back(x);
+        ApFin f{};
+        f.y = L.slot[c];
+        f.dst = x.dst;
+        f.len = L.fin[c];
+        f.pull0 = (int)L.ap_pulls.size();
+        for (auto& pk : L.late[c])
+            L.ap_pulls.push_back(ApPull{L.stg[pk.first] + L.hmeta[L.tasks[pk.first].meta + 1 + 2 * pk.second]});
+        f.pull1 = (int)L.ap_pulls.size();
+        fins.push_back(f);
     }
     L.nvcopy = (int)v.size();
+    L.nfin = (int)fins.size();
     upload(L.d_vcopy, v, h->st);
+    upload(L.d_ap_fins, fins, h->st);
+    upload(L.d_ap_pulls, L.ap_pulls, h->st);
+    L.late.clear();
+    L.late.shrink_to_fit();
 }
 
 // Block copies from level-l blocks (table T, final sizes fin, end pattern endp)
@@ -676,6 +775,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
                 const hs_tree* tree_in, hs_info* info) {
     cudaStream_t st = h->st;
     const int64_t n = h->n;
+    Trace tr;
     // host copy of the pattern (the symbolic analysis runs on the host)
     std::vector<int64_t> hrp;
     std::vector<int32_t> hcol;
@@ -734,6 +834,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         }
     }
     h->depth = depth;
+    tr.mark("pattern+partition");
 
     // device copies of A (SpMV) and of the permutation
     h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));
@@ -778,8 +879,10 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     d_status.alloc(sizeof(int32_t) * 4);
     CK(cudaMemsetAsync(d_status.p, 0, sizeof(int32_t) * 4, st));
 
+    tr.mark("upload A, level-0 pattern");
     plan_level(P);
     BlockTable T = make_table(P);
+    tr.mark("level-0 plan");
     DBuf blocks;
     blocks.alloc(sizeof(double) * std::max<int64_t>(T.total, 1));
     CK(cudaMemsetAsync(blocks.p, 0, sizeof(double) * std::max<int64_t>(T.total, 1), st));
@@ -799,6 +902,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         CK(cudaStreamSynchronize(st));
     }
     h->work_bytes[KC_ASSEMBLY] += 20.0 * nnz;
+    tr.mark("level-0 scatter");
 
     h->lev.clear();
     std::vector<int> fin = P.size0;  // depth 0: every cluster goes to the top as is
@@ -807,6 +911,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         DBuf d_cur;
         upload(d_cur, P.size0, st);
         factor_level(h, l, P, T, blocks, d_cur, d_status, info);
+        tr.mark("level factor (records+kernels)");
         Level& L = *h->lev[l];
         fin = L.fin;
         // next level (or the top)
@@ -847,6 +952,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             P = std::move(Pn);
             T = std::move(Tn);
         }
+        tr.mark("next-level plan+assembly");
     }
     // dense top
     {
@@ -898,37 +1004,48 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     }
     h->factor_bytes = fb;
     CK(cudaStreamSynchronize(st));
+    tr.mark("top");
     build_apply_graph(h);
+    tr.mark("apply graph");
+}
+
+// First level handled by the single-CTA coarse kernel: every level from there
+// on has clusters of at most kCoarseSmax DOFs and little work per phase.
+int first_coarse_level(const hs_factor_s* h) {
+    int lc = (int)h->lev.size();
+    for (int l = (int)h->lev.size() - 1; l >= 0; l--) {
+        const Level& L = *h->lev[l];
+        if (L.smax > kCoarseSmax || L.work_max_phase > (int64_t)1 << 16) break;
+        lc = l;
+    }
+    return lc;
 }
 
 // Algorithm 2 on the internal level vectors (y0 holds r in partition order).
 void enqueue_apply(hs_factor_s* h) {
     cudaStream_t st = h->st;
     const int D = (int)h->lev.size();
-    for (int l = 0; l < D; l++) {
+    const int lc = h->first_coarse;
+    auto next_of = [&](int l) { return (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>(); };
+    for (int l = 0; l < lc; l++) {
         Level& L = *h->lev[l];
         for (int ph = 0; ph < L.nphases; ph++) {
             const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
-            CK(launch_apply_fwd_diag(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.d_fac.as<double>(),
-                                     L.d_meta.as<int32_t>(), L.d_slot.as<int64_t>(), L.d_y.as<double>()));
-            const int g0 = L.ph_nbt[ph], ng = L.ph_nbt[ph + 1] - g0;
-            CK(launch_apply_fwd_nb(st, L.d_nbt.as<NbTargetDev>(), g0, ng, L.d_nbc.as<NbContribDev>(),
-                                   L.d_tasks.as<TaskDev>(), L.d_fac.as<double>(), L.d_meta.as<int32_t>(),
-                                   L.d_slot.as<int64_t>(), L.d_y.as<double>()));
+            CK(launch_ap_fwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.d_ap_pulls.as<ApPull>(),
+                             L.d_fac.as<double>(), L.d_stage.as<double>(), L.d_y.as<double>()));
         }
-        double* next = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
-        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, L.d_y.as<double>(), next, 0));
+        CK(launch_ap_fin(st, L.d_ap_fins.as<ApFin>(), L.nfin, L.d_ap_pulls.as<ApPull>(), L.d_stage.as<double>(),
+                         L.d_y.as<double>(), next_of(l)));
     }
-    CK(launch_top_solve(st, h->ntop, h->d_top.as<double>(), h->d_ytop.as<double>()));
-    for (int l = D - 1; l >= 0; l--) {
+    CK(launch_ap_coarse(st, h->d_aplevels.as<ApLevel>(), D - lc, h->ntop, h->d_top.as<double>(),
+                        h->d_ytop.as<double>()));
+    for (int l = lc - 1; l >= 0; l--) {
         Level& L = *h->lev[l];
-        double* next = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
-        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, next, L.d_y.as<double>(), 1));
+        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, next_of(l), L.d_y.as<double>(), 1));
         for (int ph = L.nphases - 1; ph >= 0; ph--) {
             const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
-            CK(launch_apply_bwd(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.d_lists.as<ListDev>(),
-                                L.d_fac.as<double>(), L.d_meta.as<int32_t>(), L.d_slot.as<int64_t>(),
-                                L.d_y.as<double>()));
+            CK(launch_ap_bwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.nmax, L.d_ap_nbs.as<ApNb>(),
+                             L.d_fac.as<double>(), L.d_y.as<double>()));
         }
     }
 }
@@ -936,6 +1053,31 @@ void enqueue_apply(hs_factor_s* h) {
 void build_apply_graph(hs_factor_s* h) {
     if (h->apply_graph) { cudaGraphExecDestroy(h->apply_graph); h->apply_graph = nullptr; }
     if (h->lev.empty() && h->ntop == 0) return;
+    h->first_coarse = first_coarse_level(h);
+    {
+        const int D = (int)h->lev.size();
+        std::vector<ApLevel> al;
+        for (int l = h->first_coarse; l < D; l++) {
+            Level& L = *h->lev[l];
+            ApLevel a{};
+            a.tasks = L.d_ap_tasks.as<ApTask>();
+            a.ph = L.d_ph.as<int32_t>();
+            a.pulls = L.d_ap_pulls.as<ApPull>();
+            a.nbs = L.d_ap_nbs.as<ApNb>();
+            a.fins = L.d_ap_fins.as<ApFin>();
+            a.vcopy = L.d_vcopy.as<VCopyDev>();
+            a.fac = L.d_fac.as<double>();
+            a.stage = L.d_stage.as<double>();
+            a.y = L.d_y.as<double>();
+            a.ynext = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
+            a.nph = L.nphases;
+            a.nfin = L.nfin;
+            a.nvcopy = L.nvcopy;
+            al.push_back(a);
+        }
+        upload(h->d_aplevels, al, h->st);
+        CK(cudaStreamSynchronize(h->st));
+    }
     cudaStream_t cap;
     CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaStream_t saved = h->st;
@@ -1311,6 +1453,8 @@ int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
     h->st = static_cast<cudaStream_t>(opt->stream);
     h->prof.on = opt->profile != 0;
     const double t0 = now_s();
+    g_alloc_stream = h->st;
+    prepare_pool();
     const int rc = run_guarded([&] {
         CK(cudaGetDevice(&h->device));
         setup_impl(h, rowptr, col, val, tree, info);
@@ -1339,6 +1483,7 @@ int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info) {
     hs_info* inf = info ? info : &tmp;
     const double t0 = now_s();
     int krc = HS_OK;
+    g_alloc_stream = h->st;
     const int rc = run_guarded([&] {
         krc = h->opt.krylov == HS_KRYLOV_GMRES ? gmres_impl(h, b, x, inf) : pcg_impl(h, b, x, inf);
         CK(cudaStreamSynchronize(h->st));
@@ -1381,6 +1526,7 @@ int hs_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
             const int krc = hs_krylov(h, b, x, inf);
             if (krc != HS_OK) throw HsError{krc};
         } else {
+            g_alloc_stream = h->st;
             DBuf db, dx;
             db.alloc(sizeof(double) * n);
             dx.alloc(sizeof(double) * n);
@@ -1398,9 +1544,9 @@ int hs_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
 
 int hs_destroy(hs_handle h) {
     if (!h) return HS_OK;
-    if (h->st) cudaStreamSynchronize(h->st);
-    else cudaDeviceSynchronize();
-    delete h;
+    g_alloc_stream = h->st;
+    cudaStreamSynchronize(h->st);  // no pending apply may still use the graph
+    delete h;                      // frees are ordered on the handle's stream
     return HS_OK;
 }
 

@@ -12,6 +12,12 @@ namespace hs {
 // One cluster elimination ("scaled low-rank elimination", Sec. 3.1) of a
 // phase.  Column blocks of the cluster's row are listed n-neighbours first,
 // then fill ("w") blocks, each with its current width read on the device.
+// Vector slice copy (coarse parts between levels).
+struct VCopyDev {
+    int64_t src, dst;
+    int32_t len, pad;
+};
+
 struct TaskDev {
     int32_t c;         // cluster id at this level
     int32_t s;         // its size when processed (= size at level start)
@@ -22,11 +28,51 @@ struct TaskDev {
     int32_t wcap;      // same over n and w (capacity of the block row)
     int32_t meta;      // first int of: rank, then (col offset, width) per n-neighbour
     int32_t pad;
-    int64_t g_off;     // G (s x s, lower, row-major) in the factor array
-    int64_t v_off;     // Householder vectors (s x s, column k = reflector k)
-    int64_t tau_off;   // tau (s)
+    int64_t w_off;     // W = U^T G^-1 (s x s, row-major) in the factor array
     int64_t c_off;     // C = fine rows of U^T G^-1 A_sn ((s - r) x ncap)
-    int64_t m_off;     // block-row workspace (s x wcap) in the workspace array
+    int64_t m_off;     // block-row workspace (s x (wcap + s)) in the workspace array
+};
+
+// ---- solve phase (Algorithm 2), records built on the host after a level is
+// factored, with every offset resolved so that a kernel reads each operand in
+// one round of loads.
+struct ApTask {
+    int64_t y;        // slot of the cluster in the level vector
+    int64_t w;        // W = U^T G^-1 (s x s, row-major) in the factor array
+    int64_t cm;       // C ((s - r) x ncap) in the factor array
+    int64_t stg;      // staged update C^T y_fine (ncols) in the stage array
+    int32_t s, r, ncols, ncap;
+    int32_t pull0, pull1;  // staged updates subtracted before the transform
+    int32_t nb0, nb1;      // neighbour slices read by the backward step
+};
+// A staged update y_q -= C_t(:, q)^T y_t(fine) of task t's neighbour q: its
+// offset in the stage array (its length is q's width when t was processed).
+struct ApPull {
+    int64_t off;
+};
+struct ApNb {
+    int64_t y;       // neighbour's slot in the level vector
+    int32_t col, m;  // its first column in C and its width
+};
+// End-of-level forward step of a cluster with a coarse part: subtract the
+// updates of tasks processed after it, copy the coarse part to the parent slot.
+struct ApFin {
+    int64_t y, dst;
+    int32_t len, pull0, pull1, pad;
+};
+// One level of the single-CTA coarse-levels kernel.
+struct ApLevel {
+    const ApTask* tasks;
+    const int32_t* ph;  // phase ranges (nph + 1)
+    const ApPull* pulls;
+    const ApNb* nbs;
+    const ApFin* fins;
+    const VCopyDev* vcopy;
+    const double* fac;
+    double* stage;
+    double* y;
+    double* ynext;
+    int32_t nph, nfin, nvcopy, pad;
 };
 
 struct ListDev {
@@ -46,26 +92,12 @@ struct ContribDev {
     int32_t task, kp, kq;  // task index (in the level's task array), positions of p, q in its n-list
 };
 
-// Forward-substitution neighbour update: y_q -= sum_t C_t(:, q)^T y_t(fine).
-struct NbTargetDev {
-    int32_t q, c_begin, c_end;
-};
-
-struct NbContribDev {
-    int32_t task, k;  // task index, position of q in its n-list
-};
-
 // Dense copy of a rows x cols sub-block (level assembly, top assembly).
 struct CopyDev {
     int64_t src, dst;   // element offsets
     int32_t src_ld, dst_ld, rows, cols;
 };
 
-// Vector slice copy (coarse parts between levels).
-struct VCopyDev {
-    int64_t src, dst;
-    int32_t len, pad;
-};
 
 // status word written by kernels (0 = ok)
 enum : int32_t { ST_OK = 0, ST_NOT_SPD = 1, ST_TOO_BIG = 2 };
@@ -86,14 +118,17 @@ cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0
 cudaError_t launch_copy_blocks(cudaStream_t st, const CopyDev* cps, int ncps, const double* src,
                                double* dst);
 cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* status);
-cudaError_t launch_apply_fwd_diag(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
-                                  const double* fac, const int32_t* meta, const int64_t* slot, double* y);
-cudaError_t launch_apply_fwd_nb(cudaStream_t st, const NbTargetDev* nbt, int g0, int ntargets,
-                                const NbContribDev* nbc, const TaskDev* tasks, const double* fac,
-                                const int32_t* meta, const int64_t* slot, double* y);
-cudaError_t launch_apply_bwd(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
-                             const ListDev* lists, const double* fac, const int32_t* meta,
-                             const int64_t* slot, double* y);
+cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax,
+                          const ApPull* pulls, const double* fac, double* stage, double* y);
+cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const ApPull* pulls, const double* stage,
+                          double* y, double* ynext);
+cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
+                          const ApNb* nbs, const double* fac, double* y);
+// levels lvl[0..nlev) forward, dense top, then backward, in one CTA
+constexpr int kCoarseThreads = 512;
+constexpr int kCoarseSmax = 128;  // largest cluster the coarse kernel handles
+cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
+                             double* ytop);
 cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
                          int reverse);
 cudaError_t launch_top_solve(cudaStream_t st, int n, const double* L, double* y);

@@ -8,8 +8,9 @@
 //                    coarse row (Eq. perm) and of the factor {G, U, C, r}.
 //   k_schur_phase  : one CTA per target block: X_nn = A_nn - C^T C (Eq. elim),
 //                    contributions summed in ascending cluster order.
-// Solve (Algorithm 2): k_apply_fwd_diag / k_apply_fwd_nb / k_apply_bwd per
-// phase, k_vcopy between levels, k_top_solve for the dense top.
+// Solve (Algorithm 2): k_apply_fwd / k_apply_bwd per phase with the explicit
+// per-cluster operator W = U^T G^-1, k_apply_fin / k_vcopy between levels,
+// k_top_solve for the dense top.
 // Krylov: CSR SpMV, deterministic two-stage dot products, vector updates.
 //
 // Decisions that must agree with any other implementation of the method:
@@ -180,7 +181,9 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         if (idx % s > idx / s) G[idx] = 0.0;
     __syncthreads();
 
-    // gather the block row [A_sn | A_sw] into the workspace (row-major, ld W)
+    // gather the block row [A_sn | A_sw | I] into the workspace (row-major, ld Wt);
+    // the identity columns come out as W = U^T G^-1, the solve-phase operator
+    const int Wt = W + s;
     double* M = ws + T.m_off;
     for (int e = 0; e < L; e++) {
         const ListDev le = lists[T.list + e];
@@ -190,28 +193,32 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         const int o = ioff[e];
         for (int idx = tid; idx < s * wq; idx += NT) {
             const int i = idx / wq, j = idx % wq;
-            M[(int64_t)i * W + o + j] = src[(int64_t)i * ld + j];
+            M[(int64_t)i * Wt + o + j] = src[(int64_t)i * ld + j];
         }
+    }
+    for (int idx = tid; idx < s * s; idx += NT) {
+        const int i = idx / s, j = idx % s;
+        M[(int64_t)i * Wt + W + j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
 
-    // scaling: M <- G^-1 M (forward substitution, one thread per column)
-    for (int j = tid; j < W; j += NT) {
-        for (int i = 0; i < s; i++) {
-            double acc = M[(int64_t)i * W + j];
-            for (int k = 0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * W + j];
-            M[(int64_t)i * W + j] = acc * rdiag[i];
+    // scaling: M <- G^-1 M (forward substitution, one thread per column;
+    // identity column j is zero above row j)
+    for (int j = tid; j < Wt; j += NT) {
+        const int i0 = (j >= W) ? j - W : 0;
+        for (int i = i0; i < s; i++) {
+            double acc = M[(int64_t)i * Wt + j];
+            for (int k = i0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * Wt + j];
+            M[(int64_t)i * Wt + j] = acc * rdiag[i];
         }
     }
     __syncthreads();
 
     // column-pivoted QR of the fill columns, reflectors applied to the whole row
-    double* Vf = fac + T.v_off;
-    double* tauf = fac + T.tau_off;
     for (int j = tid; j < Wn; j += NT) {
         double c = 0.0;
         for (int i = 0; i < s; i++) {
-            const double x = M[(int64_t)i * W + ncols + j];
+            const double x = M[(int64_t)i * Wt + ncols + j];
             c += x * x;
         }
         cn[j] = c;
@@ -241,12 +248,12 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         const int pc = ncols + p;
         double ls = 0.0;
         for (int i = k + 1 + tid; i < s; i += NT) {
-            const double x = M[(int64_t)i * W + pc];
+            const double x = M[(int64_t)i * Wt + pc];
             ls += x * x;
         }
         const double sig = block_sum(ls, red);
         if (tid == 0) {
-            const double alpha = M[(int64_t)k * W + pc];
+            const double alpha = M[(int64_t)k * Wt + pc];
             const double nrm = sqrt(alpha * alpha + sig);
             const double beta = alpha >= 0.0 ? -nrm : nrm;
             s_hh[0] = beta;
@@ -259,34 +266,33 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         for (int i = tid; i < s; i += NT) {
             double vi = 0.0;
             if (i == k) vi = 1.0;
-            else if (i > k) vi = M[(int64_t)i * W + pc] * scal;
+            else if (i > k) vi = M[(int64_t)i * Wt + pc] * scal;
             v[i] = vi;
-            Vf[(int64_t)i * s + k] = vi;
         }
-        if (tid == 0) tauf[k] = tau;
         __syncthreads();
-        for (int i = k + tid; i < s; i += NT) M[(int64_t)i * W + pc] = (i == k) ? beta : 0.0;
-        for (int j = tid; j < W; j += NT) {
+        for (int i = k + tid; i < s; i += NT) M[(int64_t)i * Wt + pc] = (i == k) ? beta : 0.0;
+        for (int j = tid; j < Wt; j += NT) {
             if (j == pc) continue;
-            if (j >= ncols && cn[j - ncols] < 0.0) continue;
-            double t = M[(int64_t)k * W + j];
-            for (int i = k + 1; i < s; i++) t += v[i] * M[(int64_t)i * W + j];
+            const bool cand = (j >= ncols && j < W);
+            if (cand && cn[j - ncols] < 0.0) continue;  // pivoted: zero below its row
+            double t = M[(int64_t)k * Wt + j];
+            for (int i = k + 1; i < s; i++) t += v[i] * M[(int64_t)i * Wt + j];
             t *= tau;
-            M[(int64_t)k * W + j] -= t;
+            M[(int64_t)k * Wt + j] -= t;
             double c = 0.0;
             for (int i = k + 1; i < s; i++) {
-                const double x = M[(int64_t)i * W + j] - t * v[i];
-                M[(int64_t)i * W + j] = x;
-                c += x * x;
+                const double x = M[(int64_t)i * Wt + j] - t * v[i];
+                M[(int64_t)i * Wt + j] = x;
+                if (cand) c += x * x;
             }
-            if (j >= ncols) cn[j - ncols] = c;
+            if (cand) cn[j - ncols] = c;
         }
         __syncthreads();
         k++;
     }
     const int r = k;
 
-    // factor: rank and n-column layout, G, C = rows r.. of the n columns
+    // factor: rank and n-column layout, W = U^T G^-1, C = rows r.. of the n columns
     int32_t* mt = meta + T.meta;
     if (tid == 0) mt[0] = r;
     for (int e = tid; e < T.nn; e += NT) {
@@ -294,13 +300,13 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         mt[2 + 2 * e] = ioff[e + 1] - ioff[e];
     }
     {
-        double* Gf = fac + T.g_off;
-        for (int idx = tid; idx < s * s; idx += NT) Gf[idx] = G[idx];
+        double* Wf = fac + T.w_off;
+        for (int idx = tid; idx < s * s; idx += NT) Wf[idx] = M[(int64_t)(idx / s) * Wt + W + idx % s];
         double* Cf = fac + T.c_off;
         const int f = s - r;
         for (int idx = tid; idx < f * ncols; idx += NT) {
             const int i = idx / ncols, j = idx % ncols;
-            Cf[(int64_t)i * T.ncap + j] = M[(int64_t)(r + i) * W + j];
+            Cf[(int64_t)i * T.ncap + j] = M[(int64_t)(r + i) * Wt + j];
         }
     }
     // write back the coarse row (identity diagonal, U^T G^-1 A_sn, V1^T)
@@ -314,7 +320,7 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
             const int ldqc = blk_ld[le.blk_qc];
             for (int idx = tid; idx < r * wq; idx += NT) {
                 const int i = idx / wq, j = idx % wq;
-                const double x = M[(int64_t)i * W + o + j];
+                const double x = M[(int64_t)i * Wt + o + j];
                 dcq[(int64_t)i * ldcq + j] = x;
                 dqc[(int64_t)j * ldqc + i] = x;
             }
@@ -417,110 +423,251 @@ __global__ void __launch_bounds__(1024) k_dense_cholesky(int n, double* a, int32
 // ---------------------------------------------------------------------------
 constexpr int kApplyThreads = 128;
 
-// y_s <- U^T G^-1 y_s for each task of a phase.
+// ----- solve phase, fine levels: one CTA per task, one launch per phase -----
+
+// Forward step of one phase:
+//   y_c -= staged updates of the tasks of earlier phases that have c as a
+//          neighbour (ascending task order);
+//   y_c <- W_c y_c with W_c = U^T G^-1;
+//   stage d_c = C_c^T y_c(r:), the update of every neighbour of c (Eq. elim
+//          applied to the vector), consumed by later tasks or at level end.
 __global__ void __launch_bounds__(kApplyThreads)
-k_apply_fwd_diag(const TaskDev* __restrict__ tasks, int t0, const double* __restrict__ fac,
-                 const int32_t* __restrict__ meta, const int64_t* __restrict__ slot, double* __restrict__ y) {
-    extern __shared__ double ys[];
-    __shared__ double red[32];
-    const TaskDev T = tasks[t0 + blockIdx.x];
+k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pulls,
+         const double* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y, int smax) {
+    extern __shared__ double sh[];
+    double* ys = sh;
+    double* yn = sh + smax;
+    const ApTask T = tasks[t0 + blockIdx.x];
     const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
-    double* yg = y + slot[T.c];
-    const double* G = fac + T.g_off;
-    for (int i = tid; i < s; i += NT) ys[i] = yg[i];
+    double* yg = y + T.y;
+    for (int j = tid; j < s; j += NT) {
+        double v = yg[j];
+        for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
+        ys[j] = v;
+    }
     __syncthreads();
-    for (int k = 0; k < s; k++) {
-        const double yk = ys[k] / G[(int64_t)k * s + k];
-        __syncthreads();
-        if (tid == 0) ys[k] = yk;
-        for (int i = k + 1 + tid; i < s; i += NT) ys[i] -= G[(int64_t)i * s + k] * yk;
-        __syncthreads();
+    const double* Wm = fac + T.w;
+    const int lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
+    for (int i0 = 4 * wid; i0 < s; i0 += 4 * nwarp) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int j = lane; j < s; j += 32) {
+            const double yj = ys[j];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (i0 + u < s) a[u] += Wm[(int64_t)(i0 + u) * s + j] * yj;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const double t = warp_sum(a[u]);
+            if (lane == 0 && i0 + u < s) yn[i0 + u] = t;
+        }
     }
-    const int r = meta[T.meta];
-    const double* V = fac + T.v_off;
-    const double* tau = fac + T.tau_off;
-    for (int k = 0; k < r; k++) {
-        double part = 0.0;
-        for (int i = k + tid; i < s; i += NT) part += V[(int64_t)i * s + k] * ys[i];
-        const double t = block_sum(part, red) * tau[k];
-        for (int i = k + tid; i < s; i += NT) ys[i] -= t * V[(int64_t)i * s + k];
-        __syncthreads();
+    __syncthreads();
+    for (int j = tid; j < s; j += NT) yg[j] = yn[j];
+    const int f = s - T.r;
+    const double* C = fac + T.cm;
+    const double* yf = yn + T.r;
+    for (int j = tid; j < T.ncols; j += NT) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        const double* cj = C + j;
+        int i = 0;
+        for (; i + 3 < f; i += 4) {
+            a0 += cj[(int64_t)i * T.ncap] * yf[i];
+            a1 += cj[(int64_t)(i + 1) * T.ncap] * yf[i + 1];
+            a2 += cj[(int64_t)(i + 2) * T.ncap] * yf[i + 2];
+            a3 += cj[(int64_t)(i + 3) * T.ncap] * yf[i + 3];
+        }
+        for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * yf[i];
+        stage[T.stg + j] = (a0 + a1) + (a2 + a3);
     }
-    for (int i = tid; i < s; i += NT) yg[i] = ys[i];
 }
 
-// y_q -= sum over tasks of C_t(:, q)^T y_t(r:), one CTA per neighbour q.
+// End of a level's forward solve, one CTA per cluster with a coarse part.
 __global__ void __launch_bounds__(kApplyThreads)
-k_apply_fwd_nb(const NbTargetDev* __restrict__ nbt, int g0, const NbContribDev* __restrict__ nbc,
-               const TaskDev* __restrict__ tasks, const double* __restrict__ fac,
-               const int32_t* __restrict__ meta, const int64_t* __restrict__ slot, double* __restrict__ y) {
-    const NbTargetDev g = nbt[g0 + blockIdx.x];
-    double* yq = y + slot[g.q];
-    int m = 0;
-    if (g.c_end > g.c_begin) {
-        const NbContribDev c0 = nbc[g.c_begin];
-        m = meta[tasks[c0.task].meta + 2 + 2 * c0.k];
-    }
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double acc = yq[j];
-        for (int c = g.c_begin; c < g.c_end; c++) {
-            const NbContribDev cb = nbc[c];
-            const TaskDev T = tasks[cb.task];
-            const int32_t* mt = meta + T.meta;
-            const int r = mt[0], f = T.s - r, o = mt[1 + 2 * cb.k];
-            const double* C = fac + T.c_off;
-            const double* yt = y + slot[T.c] + r;
-            double sub = 0.0;
-            for (int i = 0; i < f; i++) sub += C[(int64_t)i * T.ncap + o + j] * yt[i];
-            acc -= sub;
-        }
-        yq[j] = acc;
+k_ap_fin(const ApFin* __restrict__ fins, const ApPull* __restrict__ pulls, const double* __restrict__ stage,
+         double* __restrict__ y, double* __restrict__ ynext) {
+    const ApFin F = fins[blockIdx.x];
+    for (int j = threadIdx.x; j < F.len; j += blockDim.x) {
+        double v = y[F.y + j];
+        for (int pi = F.pull0; pi < F.pull1; pi++) v -= stage[pulls[pi].off + j];
+        y[F.y + j] = v;
+        ynext[F.dst + j] = v;
     }
 }
 
-// x_s(r:) -= C x_n;  x_s <- U x_s;  x_s <- G^-T x_s   (one CTA per task)
+// Backward step of one phase: x_c(r:) -= C x_n, then x_c <- W_c^T x_c.
 __global__ void __launch_bounds__(kApplyThreads)
-k_apply_bwd(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
-            const double* __restrict__ fac, const int32_t* __restrict__ meta,
-            const int64_t* __restrict__ slot, double* __restrict__ y) {
-    extern __shared__ double ys[];
-    __shared__ double red[32];
-    const TaskDev T = tasks[t0 + blockIdx.x];
-    const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
-    double* yg = y + slot[T.c];
-    const int32_t* mt = meta + T.meta;
-    const int r = mt[0], f = s - r;
-    const double* C = fac + T.c_off;
-    for (int i = tid; i < s; i += NT) ys[i] = yg[i];
+k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs, const double* __restrict__ fac,
+         double* __restrict__ y, int smax) {
+    extern __shared__ double sh[];
+    double* xs = sh;
+    double* part = sh + smax;
+    double* xn = part + blockDim.x;
+    const ApTask T = tasks[t0 + blockIdx.x];
+    const int s = T.s, r = T.r, f = s - r, tid = threadIdx.x, NT = blockDim.x;
+    double* yg = y + T.y;
+    for (int i = tid; i < s; i += NT) xs[i] = yg[i];
+    for (int e = T.nb0; e < T.nb1; e++) {
+        const ApNb nb = nbs[e];
+        for (int j = tid; j < nb.m; j += NT) xn[nb.col + j] = y[nb.y + j];
+    }
     __syncthreads();
-    for (int i = tid; i < f; i += NT) {
-        double acc = 0.0;
-        for (int e = 0; e < T.nn; e++) {
-            const int o = mt[1 + 2 * e], m = mt[2 + 2 * e];
-            const double* xq = y + slot[lists[T.list + e].q];
-            for (int j = 0; j < m; j++) acc += C[(int64_t)i * T.ncap + o + j] * xq[j];
+    const double* C = fac + T.cm;
+    const int lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
+    for (int i0 = 2 * wid; i0 < f; i0 += 2 * nwarp) {
+        double a0 = 0.0, a1 = 0.0;
+        const bool two = i0 + 1 < f;
+        for (int j = lane; j < T.ncols; j += 32) {
+            const double xj = xn[j];
+            a0 += C[(int64_t)i0 * T.ncap + j] * xj;
+            if (two) a1 += C[(int64_t)(i0 + 1) * T.ncap + j] * xj;
         }
-        ys[r + i] -= acc;
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane == 0) {
+            xs[r + i0] -= a0;
+            if (two) xs[r + i0 + 1] -= a1;
+        }
     }
     __syncthreads();
-    const double* V = fac + T.v_off;
-    const double* tau = fac + T.tau_off;
-    for (int k = r - 1; k >= 0; k--) {
-        double part = 0.0;
-        for (int i = k + tid; i < s; i += NT) part += V[(int64_t)i * s + k] * ys[i];
-        const double t = block_sum(part, red) * tau[k];
-        for (int i = k + tid; i < s; i += NT) ys[i] -= t * V[(int64_t)i * s + k];
+    const double* Wm = fac + T.w;
+    if (s >= NT) {
+        for (int jj = tid; jj < s; jj += NT) {
+            double a0 = 0.0, a1 = 0.0;
+            int i = 0;
+            for (; i + 1 < s; i += 2) {
+                a0 += Wm[(int64_t)i * s + jj] * xs[i];
+                a1 += Wm[(int64_t)(i + 1) * s + jj] * xs[i + 1];
+            }
+            if (i < s) a0 += Wm[(int64_t)i * s + jj] * xs[i];
+            yg[jj] = a0 + a1;
+        }
+        return;
+    }
+    const int G = NT / s, g = tid / s, j = tid % s;
+    double a0 = 0.0, a1 = 0.0;
+    if (g < G) {
+        int i = g;
+        for (; i + G < s; i += 2 * G) {
+            a0 += Wm[(int64_t)i * s + j] * xs[i];
+            a1 += Wm[(int64_t)(i + G) * s + j] * xs[i + G];
+        }
+        if (i < s) a0 += Wm[(int64_t)i * s + j] * xs[i];
+    }
+    part[tid] = a0 + a1;
+    __syncthreads();
+    if (tid < s) {
+        double t = 0.0;
+        for (int gg = 0; gg < G; gg++) t += part[gg * s + tid];
+        yg[tid] = t;
+    }
+}
+
+// ----- solve phase, coarse levels: one CTA, one warp per task -----
+
+__device__ void warp_fwd(const ApTask& T, const ApPull* __restrict__ pulls, const double* __restrict__ fac,
+                         double* __restrict__ stage, double* __restrict__ y, double* ys, double* yn) {
+    const int lane = threadIdx.x & 31, s = T.s;
+    for (int j = lane; j < s; j += 32) {
+        double v = y[T.y + j];
+        for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
+        ys[j] = v;
+    }
+    __syncwarp();
+    const double* Wm = fac + T.w;
+    for (int i = lane; i < s; i += 32) {
+        double a = 0.0;
+        for (int j = 0; j < s; j++) a += Wm[(int64_t)i * s + j] * ys[j];
+        yn[i] = a;
+    }
+    __syncwarp();
+    for (int j = lane; j < s; j += 32) y[T.y + j] = yn[j];
+    const int f = s - T.r;
+    const double* C = fac + T.cm;
+    for (int j = lane; j < T.ncols; j += 32) {
+        double a = 0.0;
+        for (int i = 0; i < f; i++) a += C[(int64_t)i * T.ncap + j] * yn[T.r + i];
+        stage[T.stg + j] = a;
+    }
+    __syncwarp();
+}
+
+__device__ void warp_bwd(const ApTask& T, const ApNb* __restrict__ nbs, const double* __restrict__ fac,
+                         double* __restrict__ y, double* xs) {
+    const int lane = threadIdx.x & 31, s = T.s, r = T.r, f = s - r;
+    for (int i = lane; i < s; i += 32) xs[i] = y[T.y + i];
+    __syncwarp();
+    const double* C = fac + T.cm;
+    for (int i = lane; i < f; i += 32) {
+        double a = 0.0;
+        for (int e = T.nb0; e < T.nb1; e++) {
+            const ApNb nb = nbs[e];
+            for (int j = 0; j < nb.m; j++) a += C[(int64_t)i * T.ncap + nb.col + j] * y[nb.y + j];
+        }
+        xs[r + i] -= a;
+    }
+    __syncwarp();
+    const double* Wm = fac + T.w;
+    for (int j = lane; j < s; j += 32) {
+        double a = 0.0;
+        for (int i = 0; i < s; i++) a += Wm[(int64_t)i * s + j] * xs[i];
+        y[T.y + j] = a;
+    }
+    __syncwarp();
+}
+
+// Forward over the coarse levels, the dense top (L^-T L^-1), then backward,
+// with __syncthreads between phases instead of kernel boundaries.
+__global__ void __launch_bounds__(kCoarseThreads)
+k_ap_coarse(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
+            double* __restrict__ ytop) {
+    extern __shared__ double sh[];
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
+    double* ys = sh + (size_t)wid * 2 * kCoarseSmax;
+    double* yn = ys + kCoarseSmax;
+    for (int l = 0; l < nlev; l++) {
+        const ApLevel V = lvl[l];
+        for (int ph = 0; ph < V.nph; ph++) {
+            for (int t = V.ph[ph] + wid; t < V.ph[ph + 1]; t += nwarp) warp_fwd(V.tasks[t], V.pulls, V.fac, V.stage, V.y, ys, yn);
+            __syncthreads();
+        }
+        for (int k = wid; k < V.nfin; k += nwarp) {
+            const ApFin F = V.fins[k];
+            for (int j = lane; j < F.len; j += 32) {
+                double v = V.y[F.y + j];
+                for (int pi = F.pull0; pi < F.pull1; pi++) v -= V.stage[V.pulls[pi].off + j];
+                V.y[F.y + j] = v;
+                V.ynext[F.dst + j] = v;
+            }
+        }
         __syncthreads();
     }
-    const double* G = fac + T.g_off;
-    for (int k = s - 1; k >= 0; k--) {
-        const double yk = ys[k] / G[(int64_t)k * s + k];
+    for (int k = 0; k < ntop; k++) {
+        const double yk = ytop[k] / Ltop[(int64_t)k * ntop + k];
         __syncthreads();
-        if (tid == 0) ys[k] = yk;
-        for (int i = tid; i < k; i += NT) ys[i] -= G[(int64_t)k * s + i] * yk;
+        if (tid == 0) ytop[k] = yk;
+        for (int i = k + 1 + tid; i < ntop; i += NT) ytop[i] -= Ltop[(int64_t)i * ntop + k] * yk;
         __syncthreads();
     }
-    for (int i = tid; i < s; i += NT) yg[i] = ys[i];
+    for (int k = ntop - 1; k >= 0; k--) {
+        const double yk = ytop[k] / Ltop[(int64_t)k * ntop + k];
+        __syncthreads();
+        if (tid == 0) ytop[k] = yk;
+        for (int i = tid; i < k; i += NT) ytop[i] -= Ltop[(int64_t)k * ntop + i] * yk;
+        __syncthreads();
+    }
+    for (int l = nlev - 1; l >= 0; l--) {
+        const ApLevel V = lvl[l];
+        for (int k = wid; k < V.nvcopy; k += nwarp) {
+            const VCopyDev c = V.vcopy[k];
+            for (int j = lane; j < c.len; j += 32) V.y[c.src + j] = V.ynext[c.dst + j];
+        }
+        __syncthreads();
+        for (int ph = V.nph - 1; ph >= 0; ph--) {
+            for (int t = V.ph[ph] + wid; t < V.ph[ph + 1]; t += nwarp) warp_bwd(V.tasks[t], V.nbs, V.fac, V.y, ys);
+            __syncthreads();
+        }
+    }
 }
 
 __global__ void k_vcopy(const VCopyDev* __restrict__ cps, int ncps, const double* __restrict__ src,
@@ -761,29 +908,36 @@ cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* st
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_fwd_diag(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
-                                  const double* fac, const int32_t* meta, const int64_t* slot, double* y) {
+cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax,
+                          const ApPull* pulls, const double* fac, double* stage, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
-    k_apply_fwd_diag<<<ntasks, kApplyThreads, sizeof(double) * smax, st>>>(tasks, t0, fac, meta, slot, y);
+    k_ap_fwd<<<ntasks, kApplyThreads, sizeof(double) * 2 * smax, st>>>(tasks, t0, pulls, fac, stage, y, smax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_fwd_nb(cudaStream_t st, const NbTargetDev* nbt, int g0, int ntargets,
-                                const NbContribDev* nbc, const TaskDev* tasks, const double* fac,
-                                const int32_t* meta, const int64_t* slot, double* y) {
-    if (ntargets <= 0) return cudaSuccess;
+cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const ApPull* pulls, const double* stage,
+                          double* y, double* ynext) {
+    if (nfin <= 0) return cudaSuccess;
     counted();
-    k_apply_fwd_nb<<<ntargets, kApplyThreads, 0, st>>>(nbt, g0, nbc, tasks, fac, meta, slot, y);
+    k_ap_fin<<<nfin, kApplyThreads, 0, st>>>(fins, pulls, stage, y, ynext);
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_bwd(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
-                             const ListDev* lists, const double* fac, const int32_t* meta, const int64_t* slot,
-                             double* y) {
+cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
+                          const ApNb* nbs, const double* fac, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
-    k_apply_bwd<<<ntasks, kApplyThreads, sizeof(double) * smax, st>>>(tasks, t0, lists, fac, meta, slot, y);
+    k_ap_bwd<<<ntasks, kApplyThreads, sizeof(double) * (smax + kApplyThreads + nmax), st>>>(tasks, t0, nbs, fac, y,
+                                                                                            smax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L, double* ytop) {
+    if (nlev <= 0 && ntop <= 0) return cudaSuccess;
+    counted();
+    const size_t smem = sizeof(double) * 2 * kCoarseSmax * (kCoarseThreads / 32);
+    k_ap_coarse<<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
     return cudaGetLastError();
 }
 
