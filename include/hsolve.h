@@ -74,6 +74,10 @@ typedef struct {
     void* stream;        /* cudaStream_t for all device work                   */
     const double* coords; /* host n x 2 horizontal DOF positions for the
                             partitioner when no tree is given (NULL: BFS)     */
+    int32_t coarse_dense; /* solve phase: the levels from the first one with at
+                            most this many DOFs (and the top) are applied as
+                            one explicit dense operator formed at setup;
+                            0 = never; default 4096                           */
 } hs_options;
 
 typedef struct {

@@ -373,7 +373,9 @@ struct Level {
     std::vector<int32_t> hmeta;        // rank and n-column layout of every task
     std::vector<int> task_rank;        // filled after the level
     std::vector<ApPull> ap_pulls;      // early pulls of the tasks, then the late pulls
-    int64_t work_max_phase = 0;        // largest sum over a phase of s^2 + f * ncols
+    int64_t work_max_phase = 0;        // largest sum over a stage of s^2 + f * ncols
+    int nstages = 0;                   // solve stages of the level
+    std::vector<int> ap_stage;         // stage ranges in the solve task array
     DBuf d_tasks, d_lists, d_meta, d_fac, d_slot, d_vcopy, d_y, d_stage;
     DBuf d_ap_tasks, d_ap_pulls, d_ap_nbs, d_ap_fins, d_ph;
     int nvcopy = 0, nfin = 0;
@@ -442,8 +444,11 @@ struct hs_factor_s {
     int64_t factor_bytes = 0;
     cudaGraphExec_t apply_graph = nullptr;
     int64_t graph_kernels = 0;
-    int first_coarse = 0;
-    DBuf d_aplevels;
+    int first_coarse = 0;  // first level of the single-CTA chain (or of the dense operator)
+    bool coarse_dense = false;
+    int ncoarse = 0;       // size of the dense coarse operator
+    DBuf d_aplevels, d_coarse, d_ycout;
+    double* apply_out = nullptr;  // level-0 vector holding the result of the graph
     Prof prof;
     double work_flops[KC_N] = {0};
     double work_bytes[KC_N] = {0};
@@ -675,10 +680,34 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             at[ti] = a;
             work[ph_of[ti]] += (int64_t)a.s * a.s + (int64_t)(a.s - a.r) * a.ncols;
         }
-        for (auto w : work) L.work_max_phase = std::max(L.work_max_phase, w);
-        upload(L.d_ap_tasks, at, st);
+        // Solve stages: a task depends only on the tasks whose staged update
+        // it subtracts (fill couplings were compressed away), so stage =
+        // longest chain of such dependencies; the backward runs the stages in
+        // reverse.  Tasks of a stage are independent.
+        std::vector<int> stage_of(L.tasks.size(), 0);
+        for (size_t ti = 0; ti < L.tasks.size(); ti++)
+            for (auto& pk : L.early[L.tasks[ti].c]) stage_of[ti] = std::max(stage_of[ti], stage_of[pk.first] + 1);
+        int nst = 0;
+        for (int v : stage_of) nst = std::max(nst, v + 1);
+        std::vector<int> order(L.tasks.size());
+        for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return stage_of[a] < stage_of[b]; });
+        std::vector<ApTask> ats(at.size());
+        L.ap_stage.assign(1, 0);
+        std::vector<int64_t> swork(nst, 0);
+        for (size_t i = 0; i < order.size(); i++) {
+            ats[i] = at[order[i]];
+            const ApTask& a = ats[i];
+            swork[stage_of[order[i]]] += (int64_t)a.s * a.s + (int64_t)(a.s - a.r) * a.ncols;
+            if (i + 1 == order.size() || stage_of[order[i + 1]] != stage_of[order[i]])
+                L.ap_stage.push_back((int)i + 1);
+        }
+        L.nstages = nst;
+        L.work_max_phase = 0;
+        for (auto w : swork) L.work_max_phase = std::max(L.work_max_phase, w);
+        upload(L.d_ap_tasks, ats, st);
         upload(L.d_ap_nbs, nbs, st);
-        upload(L.d_ph, L.ph_task, st);
+        upload(L.d_ph, L.ap_stage, st);
         L.hmeta = std::move(hmeta);
         L.early.clear();
     }
@@ -1015,7 +1044,7 @@ int first_coarse_level(const hs_factor_s* h) {
     int lc = (int)h->lev.size();
     for (int l = (int)h->lev.size() - 1; l >= 0; l--) {
         const Level& L = *h->lev[l];
-        if (L.smax > kCoarseSmax || L.work_max_phase > (int64_t)1 << 16) break;
+        if (L.smax > kCoarseSmax || L.nmax > kCoarseNmax || L.work_max_phase > (int64_t)1 << 16) break;
         lc = l;
     }
     return lc;
@@ -1026,24 +1055,33 @@ void enqueue_apply(hs_factor_s* h) {
     cudaStream_t st = h->st;
     const int D = (int)h->lev.size();
     const int lc = h->first_coarse;
-    auto next_of = [&](int l) { return (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>(); };
+    auto vec_of = [&](int l) { return l < D ? h->lev[l]->d_y.as<double>() : h->d_ytop.as<double>(); };
+    // forward writes level l+1's vector; in dense mode the backward reads the
+    // dense operator's output for the first coarse level
+    auto next_of = [&](int l) { return vec_of(l + 1); };
+    auto back_of = [&](int l) {
+        return (h->coarse_dense && l + 1 == lc) ? h->d_ycout.as<double>() : vec_of(l + 1);
+    };
     for (int l = 0; l < lc; l++) {
         Level& L = *h->lev[l];
-        for (int ph = 0; ph < L.nphases; ph++) {
-            const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
+        for (int k = 0; k < L.nstages; k++) {
+            const int t0 = L.ap_stage[k], nt = L.ap_stage[k + 1] - t0;
             CK(launch_ap_fwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.d_ap_pulls.as<ApPull>(),
                              L.d_fac.as<double>(), L.d_stage.as<double>(), L.d_y.as<double>()));
         }
         CK(launch_ap_fin(st, L.d_ap_fins.as<ApFin>(), L.nfin, L.d_ap_pulls.as<ApPull>(), L.d_stage.as<double>(),
                          L.d_y.as<double>(), next_of(l)));
     }
-    CK(launch_ap_coarse(st, h->d_aplevels.as<ApLevel>(), D - lc, h->ntop, h->d_top.as<double>(),
-                        h->d_ytop.as<double>()));
+    if (h->coarse_dense)
+        CK(launch_dense_gemv(st, h->ncoarse, h->d_coarse.as<double>(), vec_of(lc), h->d_ycout.as<double>()));
+    else
+        CK(launch_ap_coarse(st, h->d_aplevels.as<ApLevel>(), D - lc, h->ntop, h->d_top.as<double>(),
+                            h->d_ytop.as<double>()));
     for (int l = lc - 1; l >= 0; l--) {
         Level& L = *h->lev[l];
-        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, next_of(l), L.d_y.as<double>(), 1));
-        for (int ph = L.nphases - 1; ph >= 0; ph--) {
-            const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
+        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, back_of(l), L.d_y.as<double>(), 1));
+        for (int k = L.nstages - 1; k >= 0; k--) {
+            const int t0 = L.ap_stage[k], nt = L.ap_stage[k + 1] - t0;
             CK(launch_ap_bwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.nmax, L.d_ap_nbs.as<ApNb>(),
                              L.d_fac.as<double>(), L.d_y.as<double>()));
         }
@@ -1053,12 +1091,44 @@ void enqueue_apply(hs_factor_s* h) {
 void build_apply_graph(hs_factor_s* h) {
     if (h->apply_graph) { cudaGraphExecDestroy(h->apply_graph); h->apply_graph = nullptr; }
     if (h->lev.empty() && h->ntop == 0) return;
-    h->first_coarse = first_coarse_level(h);
-    {
-        const int D = (int)h->lev.size();
+    const int D = (int)h->lev.size();
+    const int lc0 = first_coarse_level(h);
+    auto level_len = [&](int l) -> int64_t { return l < D ? h->lev[l]->slot[h->lev[l]->nc] : h->ntop; };
+    // dense coarse operator from the first level (>= lc0) small enough
+    int ld = -1;
+    if (h->opt.coarse_dense > 0)
+        for (int l = lc0; l <= D; l++)
+            if (level_len(l) <= h->opt.coarse_dense) { ld = l; break; }
+    if (ld >= 0) {  // the batched build needs one workspace per unit vector
+        int64_t stride = 0;
+        for (int l = ld; l <= D; l++) stride += std::max<int64_t>(level_len(l), 1);
+        for (int l = ld; l < D; l++) stride += (int64_t)(h->lev[l]->d_stage.bytes / sizeof(double));
+        if ((double)stride * level_len(ld) * 8.0 > 2e9) ld = -1;
+    }
+    h->coarse_dense = ld >= 0;
+    h->first_coarse = h->coarse_dense ? ld : lc0;
+    if (std::getenv("HS_TRACE")) {
+        for (size_t l = 0; l < h->lev.size(); l++)
+            std::fprintf(stderr, "hs_trace level %zu: %d clusters, %d phases, %d solve stages, smax %d, ncap %d%s\n", l,
+                         h->lev[l]->nc, h->lev[l]->nphases, h->lev[l]->nstages, h->lev[l]->smax, h->lev[l]->nmax,
+                         (int)l >= h->first_coarse ? (h->coarse_dense ? " (dense coarse operator)" : " (coarse kernel)")
+                                                   : "");
+    }
+    // ApLevel records of the coarse levels; in dense mode their vectors and
+    // stage arrays live in a per-right-hand-side workspace (stride apart)
+    auto make_levels = [&](double* ws_base, int64_t* stride_out, double** yin0, double** ytop0) {
         std::vector<ApLevel> al;
+        std::vector<int64_t> yoff, soff;
+        int64_t o = 0;
+        for (int l = h->first_coarse; l <= D; l++) { yoff.push_back(o); o += std::max<int64_t>(level_len(l), 1); }
+        for (int l = h->first_coarse; l < D; l++) {
+            soff.push_back(o);
+            o += std::max<int64_t>(h->lev[l]->d_stage.bytes / sizeof(double), 1);
+        }
+        if (stride_out) *stride_out = o;
         for (int l = h->first_coarse; l < D; l++) {
             Level& L = *h->lev[l];
+            const int k = l - h->first_coarse;
             ApLevel a{};
             a.tasks = L.d_ap_tasks.as<ApTask>();
             a.ph = L.d_ph.as<int32_t>();
@@ -1067,17 +1137,48 @@ void build_apply_graph(hs_factor_s* h) {
             a.fins = L.d_ap_fins.as<ApFin>();
             a.vcopy = L.d_vcopy.as<VCopyDev>();
             a.fac = L.d_fac.as<double>();
-            a.stage = L.d_stage.as<double>();
-            a.y = L.d_y.as<double>();
-            a.ynext = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
-            a.nph = L.nphases;
+            if (ws_base) {
+                a.stage = ws_base + soff[k];
+                a.y = ws_base + yoff[k];
+                a.ynext = ws_base + yoff[k + 1];
+            } else {
+                a.stage = L.d_stage.as<double>();
+                a.y = L.d_y.as<double>();
+                a.ynext = (l + 1 < D) ? h->lev[l + 1]->d_y.as<double>() : h->d_ytop.as<double>();
+            }
+            a.nph = L.nstages;
             a.nfin = L.nfin;
             a.nvcopy = L.nvcopy;
             al.push_back(a);
         }
+        if (yin0) *yin0 = ws_base + yoff[0];
+        if (ytop0) *ytop0 = ws_base + yoff.back();
+        return al;
+    };
+    if (h->coarse_dense) {
+        const int n = (int)level_len(ld);
+        h->ncoarse = n;
+        h->d_coarse.alloc(sizeof(double) * std::max<int64_t>((int64_t)n * n, 1));
+        h->d_ycout.alloc(sizeof(double) * std::max(n, 1));
+        int64_t stride = 0;
+        make_levels(nullptr, &stride, nullptr, nullptr);
+        DBuf ws;
+        ws.alloc(sizeof(double) * std::max<int64_t>(stride * std::max(n, 1), 1));
+        double *yin0 = nullptr, *ytop0 = nullptr;
+        std::vector<ApLevel> al = make_levels(ws.as<double>(), nullptr, &yin0, &ytop0);
+        DBuf d_al;
+        upload(d_al, al, h->st);
+        h->prof.begin(KC_TOP, h->st);
+        CK(launch_ap_coarse_batch(h->st, d_al.as<ApLevel>(), (int)al.size(), h->ntop, h->d_top.as<double>(), ytop0,
+                                  yin0, n, stride, h->d_coarse.as<double>()));
+        h->prof.end(KC_TOP, h->st);
+        CK(cudaStreamSynchronize(h->st));
+    } else {
+        std::vector<ApLevel> al = make_levels(nullptr, nullptr, nullptr, nullptr);
         upload(h->d_aplevels, al, h->st);
         CK(cudaStreamSynchronize(h->st));
     }
+    h->apply_out = (h->coarse_dense && ld == 0) ? h->d_ycout.as<double>() : nullptr;
     cudaStream_t cap;
     CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaStream_t saved = h->st;
@@ -1112,7 +1213,7 @@ void apply_impl(hs_factor_s* h, const double* r, double* z) {
         CK(cudaGraphLaunch(h->apply_graph, st));
         launch_count_add(h->graph_kernels);
     }
-    CK(launch_permute(st, h->n, h->d_perm.as<int32_t>(), y0, z, 1));
+    CK(launch_permute(st, h->n, h->d_perm.as<int32_t>(), h->apply_out ? h->apply_out : y0, z, 1));
     h->prof.end(KC_APPLY, st);
 }
 
@@ -1307,7 +1408,7 @@ int pcg_noalloc(hs_factor_s* h, const double* b, double* x, double* scratch, hs_
             CK(cudaGraphLaunch(h->apply_graph, st));
             launch_count_add(h->graph_kernels);
         }
-        CK(launch_permute(st, n, h->d_perm.as<int32_t>(), y0, zz, 1));
+        CK(launch_permute(st, n, h->d_perm.as<int32_t>(), h->apply_out ? h->apply_out : y0, zz, 1));
     };
     auto spmv = [&](const double* xx, double* yy) {
         CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), xx, yy));
@@ -1395,6 +1496,7 @@ int hs_default_options(hs_options* opt) {
     opt->mem = HS_MEM_HOST;
     opt->stream = nullptr;
     opt->coords = nullptr;
+    opt->coarse_dense = 4096;
     return HS_OK;
 }
 

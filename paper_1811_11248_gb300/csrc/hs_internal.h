@@ -125,10 +125,15 @@ cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const Ap
 cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
                           const ApNb* nbs, const double* fac, double* y);
 // levels lvl[0..nlev) forward, dense top, then backward, in one CTA
-constexpr int kCoarseThreads = 512;
-constexpr int kCoarseSmax = 128;  // largest cluster the coarse kernel handles
+constexpr int kCoarseThreads = 1024;
+constexpr int kCoarseSmax = 64;   // largest cluster the coarse kernel handles
+constexpr int kCoarseNmax = 320;  // largest neighbour width (ncols) it handles
 cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
                              double* ytop);
+// explicit coarse operator (one CTA per unit vector) and its application
+cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
+                                   double* ytop0, double* yin0, int n, int64_t stride, double* Mc);
+cudaError_t launch_dense_gemv(cudaStream_t st, int n, const double* Mc, const double* x, double* y);
 cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
                          int reverse);
 cudaError_t launch_top_solve(cudaStream_t st, int n, const double* L, double* y);

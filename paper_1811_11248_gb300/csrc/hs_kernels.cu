@@ -564,80 +564,132 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
 }
 
 // ----- solve phase, coarse levels: one CTA, one warp per task -----
+// Per-warp shared memory: the cluster's vector (kCoarseSmax doubles) and the
+// transformed vector / gathered neighbour values (kCoarseNmax doubles).
 
-__device__ void warp_fwd(const ApTask& T, const ApPull* __restrict__ pulls, const double* __restrict__ fac,
-                         double* __restrict__ stage, double* __restrict__ y, double* ys, double* yn) {
-    const int lane = threadIdx.x & 31, s = T.s;
-    for (int j = lane; j < s; j += 32) {
+__device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPull* __restrict__ pulls,
+                          const double* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y,
+                          double* ys, double* yn) {
+    const int s = act ? T.s : 0;
+    for (int j = gl; j < s; j += gs) {
         double v = y[T.y + j];
         for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
         ys[j] = v;
     }
     __syncwarp();
-    const double* Wm = fac + T.w;
-    for (int i = lane; i < s; i += 32) {
-        double a = 0.0;
-        for (int j = 0; j < s; j++) a += Wm[(int64_t)i * s + j] * ys[j];
-        yn[i] = a;
+    if (act) {
+        const double* Wm = fac + T.w;
+        for (int i = gl; i < s; i += gs) {
+            const double* wi = Wm + (int64_t)i * s;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int j = 0;
+            for (; j + 3 < s; j += 4) {
+                a0 += wi[j] * ys[j];
+                a1 += wi[j + 1] * ys[j + 1];
+                a2 += wi[j + 2] * ys[j + 2];
+                a3 += wi[j + 3] * ys[j + 3];
+            }
+            for (; j < s; j++) a0 += wi[j] * ys[j];
+            yn[i] = (a0 + a1) + (a2 + a3);
+        }
     }
     __syncwarp();
-    for (int j = lane; j < s; j += 32) y[T.y + j] = yn[j];
-    const int f = s - T.r;
-    const double* C = fac + T.cm;
-    for (int j = lane; j < T.ncols; j += 32) {
-        double a = 0.0;
-        for (int i = 0; i < f; i++) a += C[(int64_t)i * T.ncap + j] * yn[T.r + i];
-        stage[T.stg + j] = a;
+    if (act) {
+        for (int j = gl; j < s; j += gs) y[T.y + j] = yn[j];
+        const int f = s - T.r;
+        const double* C = fac + T.cm;
+        const double* yf = yn + T.r;
+        for (int j = gl; j < T.ncols; j += gs) {
+            const double* cj = C + j;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int i = 0;
+            for (; i + 3 < f; i += 4) {
+                a0 += cj[(int64_t)i * T.ncap] * yf[i];
+                a1 += cj[(int64_t)(i + 1) * T.ncap] * yf[i + 1];
+                a2 += cj[(int64_t)(i + 2) * T.ncap] * yf[i + 2];
+                a3 += cj[(int64_t)(i + 3) * T.ncap] * yf[i + 3];
+            }
+            for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * yf[i];
+            stage[T.stg + j] = (a0 + a1) + (a2 + a3);
+        }
     }
     __syncwarp();
 }
 
-__device__ void warp_bwd(const ApTask& T, const ApNb* __restrict__ nbs, const double* __restrict__ fac,
-                         double* __restrict__ y, double* xs) {
-    const int lane = threadIdx.x & 31, s = T.s, r = T.r, f = s - r;
-    for (int i = lane; i < s; i += 32) xs[i] = y[T.y + i];
-    __syncwarp();
-    const double* C = fac + T.cm;
-    for (int i = lane; i < f; i += 32) {
-        double a = 0.0;
-        for (int e = T.nb0; e < T.nb1; e++) {
-            const ApNb nb = nbs[e];
-            for (int j = 0; j < nb.m; j++) a += C[(int64_t)i * T.ncap + nb.col + j] * y[nb.y + j];
-        }
-        xs[r + i] -= a;
+__device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb* __restrict__ nbs,
+                          const double* __restrict__ fac, double* __restrict__ y, double* xs, double* xn) {
+    const int s = act ? T.s : 0, r = T.r, f = s - r;
+    for (int i = gl; i < s; i += gs) xs[i] = y[T.y + i];
+    const int ncols = act ? T.ncols : 0;
+    for (int e = act ? T.nb0 : 0; e < (act ? T.nb1 : 0); e++) {
+        const ApNb nb = nbs[e];
+        for (int j = gl; j < nb.m; j += gs) xn[nb.col + j] = y[nb.y + j];
     }
     __syncwarp();
-    const double* Wm = fac + T.w;
-    for (int j = lane; j < s; j += 32) {
-        double a = 0.0;
-        for (int i = 0; i < s; i++) a += Wm[(int64_t)i * s + j] * xs[i];
-        y[T.y + j] = a;
+    if (act) {
+        const double* C = fac + T.cm;
+        for (int i = gl; i < f; i += gs) {
+            const double* ci = C + (int64_t)i * T.ncap;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int j = 0;
+            for (; j + 3 < ncols; j += 4) {
+                a0 += ci[j] * xn[j];
+                a1 += ci[j + 1] * xn[j + 1];
+                a2 += ci[j + 2] * xn[j + 2];
+                a3 += ci[j + 3] * xn[j + 3];
+            }
+            for (; j < ncols; j++) a0 += ci[j] * xn[j];
+            xs[r + i] -= (a0 + a1) + (a2 + a3);
+        }
+    }
+    __syncwarp();
+    if (act) {
+        const double* Wm = fac + T.w;
+        for (int j = gl; j < s; j += gs) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int i = 0;
+            for (; i + 3 < s; i += 4) {
+                a0 += Wm[(int64_t)i * s + j] * xs[i];
+                a1 += Wm[(int64_t)(i + 1) * s + j] * xs[i + 1];
+                a2 += Wm[(int64_t)(i + 2) * s + j] * xs[i + 2];
+                a3 += Wm[(int64_t)(i + 3) * s + j] * xs[i + 3];
+            }
+            for (; i < s; i++) a0 += Wm[(int64_t)i * s + j] * xs[i];
+            y[T.y + j] = (a0 + a1) + (a2 + a3);
+        }
     }
     __syncwarp();
 }
 
 // Forward over the coarse levels, the dense top (L^-T L^-1), then backward,
-// with __syncthreads between phases instead of kernel boundaries.
-__global__ void __launch_bounds__(kCoarseThreads)
-k_ap_coarse(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
-            double* __restrict__ ytop) {
+// with __syncthreads between stages instead of kernel boundaries.  `off` is
+// added to every level vector, stage and top-vector address (a private
+// workspace per CTA when the chain is run on many right-hand sides at once).
+__device__ void coarse_chain(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
+                             double* __restrict__ ytop, int64_t off) {
     extern __shared__ double sh[];
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
-    double* ys = sh + (size_t)wid * 2 * kCoarseSmax;
-    double* yn = ys + kCoarseSmax;
+    double* wsh = sh + (size_t)wid * (kCoarseSmax + kCoarseNmax);
+    ytop += off;
     for (int l = 0; l < nlev; l++) {
         const ApLevel V = lvl[l];
+        double* yv = V.y + off;
+        double* ynx = V.ynext + off;
+        double* stg = V.stage + off;
+        double* ys = wsh;
+        double* yn = ys + kCoarseSmax;
         for (int ph = 0; ph < V.nph; ph++) {
-            for (int t = V.ph[ph] + wid; t < V.ph[ph + 1]; t += nwarp) warp_fwd(V.tasks[t], V.pulls, V.fac, V.stage, V.y, ys, yn);
+            const int b = V.ph[ph], e = V.ph[ph + 1];
+            for (int t = b + wid; t < e; t += nwarp) group_fwd(true, V.tasks[t], lane, 32, V.pulls, V.fac, stg, yv, ys, yn);
             __syncthreads();
         }
         for (int k = wid; k < V.nfin; k += nwarp) {
             const ApFin F = V.fins[k];
             for (int j = lane; j < F.len; j += 32) {
-                double v = V.y[F.y + j];
-                for (int pi = F.pull0; pi < F.pull1; pi++) v -= V.stage[V.pulls[pi].off + j];
-                V.y[F.y + j] = v;
-                V.ynext[F.dst + j] = v;
+                double v = yv[F.y + j];
+                for (int pi = F.pull0; pi < F.pull1; pi++) v -= stg[V.pulls[pi].off + j];
+                yv[F.y + j] = v;
+                ynx[F.dst + j] = v;
             }
         }
         __syncthreads();
@@ -658,16 +710,61 @@ k_ap_coarse(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* _
     }
     for (int l = nlev - 1; l >= 0; l--) {
         const ApLevel V = lvl[l];
+        double* yv = V.y + off;
+        const double* ynx = V.ynext + off;
+        double* xs = wsh;
+        double* xn = xs + kCoarseSmax;
         for (int k = wid; k < V.nvcopy; k += nwarp) {
             const VCopyDev c = V.vcopy[k];
-            for (int j = lane; j < c.len; j += 32) V.y[c.src + j] = V.ynext[c.dst + j];
+            for (int j = lane; j < c.len; j += 32) yv[c.src + j] = ynx[c.dst + j];
         }
         __syncthreads();
         for (int ph = V.nph - 1; ph >= 0; ph--) {
-            for (int t = V.ph[ph] + wid; t < V.ph[ph + 1]; t += nwarp) warp_bwd(V.tasks[t], V.nbs, V.fac, V.y, ys);
+            const int b = V.ph[ph], e = V.ph[ph + 1];
+            for (int t = b + wid; t < e; t += nwarp) group_bwd(true, V.tasks[t], lane, 32, V.nbs, V.fac, yv, xs, xn);
             __syncthreads();
         }
     }
+}
+
+__global__ void __launch_bounds__(kCoarseThreads)
+k_ap_coarse(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
+            double* __restrict__ ytop) {
+    coarse_chain(lvl, nlev, ntop, Ltop, ytop, 0);
+}
+
+// Explicit coarse operator: CTA j runs the coarse chain on the unit vector e_j
+// in its own workspace (stride doubles apart) and writes the result as row j
+// of Mc (n x n; symmetric up to rounding).  yin0 is CTA 0's input vector.
+__global__ void __launch_bounds__(kCoarseThreads)
+k_ap_coarse_batch(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
+                  double* __restrict__ ytop, double* __restrict__ yin0, int n, int64_t stride,
+                  double* __restrict__ Mc) {
+    const int64_t off = (int64_t)blockIdx.x * stride;
+    double* yin = yin0 + off;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) yin[i] = (i == (int)blockIdx.x) ? 1.0 : 0.0;
+    __syncthreads();
+    coarse_chain(lvl, nlev, ntop, Ltop, ytop, off);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Mc[(int64_t)blockIdx.x * n + i] = yin[i];
+}
+
+// y = Mc x (n x n, row-major): one warp per row, lanes over columns.
+__global__ void __launch_bounds__(256) k_dense_gemv(int n, const double* __restrict__ Mc,
+                                                    const double* __restrict__ x, double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const double* m = Mc + (int64_t)row * n;
+    double a0 = 0.0, a1 = 0.0;
+    int j = lane;
+    for (; j + 32 < n; j += 64) {
+        a0 += m[j] * x[j];
+        a1 += m[j + 32] * x[j + 32];
+    }
+    if (j < n) a0 += m[j] * x[j];
+    const double t = warp_sum(a0 + a1);
+    if (lane == 0) y[row] = t;
 }
 
 __global__ void k_vcopy(const VCopyDev* __restrict__ cps, int ncps, const double* __restrict__ src,
@@ -933,10 +1030,29 @@ cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntas
     return cudaGetLastError();
 }
 
+cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
+                                   double* ytop0, double* yin0, int n, int64_t stride, double* Mc) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    const int threads = 256;
+    const size_t smem = sizeof(double) * (kCoarseSmax + kCoarseNmax) * (threads / 32);
+    k_ap_coarse_batch<<<n, threads, smem, st>>>(lvl, nlev, ntop, L, ytop0, yin0, n, stride, Mc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_gemv(cudaStream_t st, int n, const double* Mc, const double* x, double* y) {
+    if (n <= 0) return cudaSuccess;
+    counted();
+    k_dense_gemv<<<(n + 7) / 8, 256, 0, st>>>(n, Mc, x, y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L, double* ytop) {
     if (nlev <= 0 && ntop <= 0) return cudaSuccess;
     counted();
-    const size_t smem = sizeof(double) * 2 * kCoarseSmax * (kCoarseThreads / 32);
+    const size_t smem = sizeof(double) * (kCoarseSmax + kCoarseNmax) * (kCoarseThreads / 32);
+    cudaError_t e = cudaFuncSetAttribute(k_ap_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_ap_coarse<<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
     return cudaGetLastError();
 }

@@ -115,6 +115,20 @@ def test_small_parity(hs, oracle_lib, name, make, depth, tol):
     h.close()
 
 
+@pytest.mark.parametrize("coarse_dense", [0, 64, 100000])
+def test_solve_phase_modes(hs, oracle_lib, coarse_dense):
+    """The coarse levels of the solve phase run as a chain of stages in one
+    CTA (coarse_dense = 0), as an explicit dense operator formed at setup
+    (large limit), or split between per-stage kernels and a smaller dense
+    operator: all give the same operator."""
+    p = inputs.grid_operator(24, 16, 6, ratio=1e6, sigma=1.0, seed=6, bc="ice", shelf=0.5)
+    h, ref, depth = setup_both(hs, oracle_lib, p, 3, 1e-3, coarse_dense=coarse_dense)
+    check_structure(h, ref, depth)
+    bound = max(1e-10, 100 * U * kappa(p))
+    assert operator_diff(h, ref, p.n) <= bound
+    krylov_check(h, ref, p)
+
+
 def test_dirichlet_16x16x8_workload(hs, oracle_lib):
     p = inputs.anisotropic_16x16x8()
     h, ref, depth = setup_both(hs, oracle_lib, p, 4, 1e-2)
