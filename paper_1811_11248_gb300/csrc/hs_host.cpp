@@ -115,10 +115,67 @@ struct DBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Pinned host staging for host<->device copies (copies from pageable memory
+// are staged synchronously by the driver).  Data is appended; the area is
+// reused only after every stream with copies pending from it has drained.
+struct PinnedStage {
+    char* p = nullptr;
+    size_t cap = 0, used = 0;
+    std::vector<cudaStream_t> pending;
+    ~PinnedStage() {
+        if (p) cudaFreeHost(p);
+    }
+    void drain() {
+        for (cudaStream_t s : pending) cudaStreamSynchronize(s);
+        pending.clear();
+        used = 0;
+    }
+    // space for `bytes` that the caller fills, then copies on stream st
+    char* take(size_t bytes, cudaStream_t st) {
+        const size_t need = (bytes + 255) & ~(size_t)255;
+        if (used + need > cap) {
+            drain();
+            if (need > cap) {
+                if (p) cudaFreeHost(p);
+                p = nullptr;
+                cap = std::max(need, (size_t)16 << 20);
+                CK(cudaHostAlloc(reinterpret_cast<void**>(&p), cap, cudaHostAllocDefault));
+            }
+        }
+        char* d = p + used;
+        used += need;
+        if (std::find(pending.begin(), pending.end(), st) == pending.end()) pending.push_back(st);
+        return d;
+    }
+    // the caller has synchronised st: the area is free if st was the only user
+    void synced(cudaStream_t st) {
+        if (pending.size() == 1 && pending[0] == st) {
+            pending.clear();
+            used = 0;
+        }
+    }
+};
+thread_local PinnedStage g_stage;
+
 template <class T>
 void upload(DBuf& d, const std::vector<T>& h, cudaStream_t st) {
     d.alloc(sizeof(T) * std::max<size_t>(h.size(), 1));
-    if (!h.empty()) CK(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+    if (h.empty()) return;
+    char* pin = g_stage.take(sizeof(T) * h.size(), st);
+    std::memcpy(pin, h.data(), sizeof(T) * h.size());
+    CK(cudaMemcpyAsync(d.p, pin, sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+}
+
+// device -> host through the staging area; synchronises st
+template <class T>
+void download(std::vector<T>& h, const void* d, size_t count, cudaStream_t st) {
+    h.resize(count);
+    if (count == 0) return;
+    char* pin = g_stage.take(sizeof(T) * count, st);
+    CK(cudaMemcpyAsync(pin, d, sizeof(T) * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::memcpy(h.data(), pin, sizeof(T) * count);
+    g_stage.synced(st);
 }
 
 void sorted_insert(std::vector<int>& v, int x) {
@@ -184,24 +241,33 @@ struct Partitioner {
             return;
         }
         const size_t k = set.size(), left = (k + 1) / 2;
+        std::vector<int> a, b;
         if (have_coords) {
+            // the left part is the ceil(k/2) smallest lines in (coordinate,
+            // index) order along the longer extent; `set` is ascending and
+            // both parts stay ascending
             double x0 = lx[set[0]], x1 = x0, y0 = ly[set[0]], y1 = y0;
             for (int x : set) {
                 x0 = std::min(x0, lx[x]); x1 = std::max(x1, lx[x]);
                 y0 = std::min(y0, ly[x]); y1 = std::max(y1, ly[x]);
             }
             const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? lx : ly;
-            std::sort(set.begin(), set.end(), [&](int a, int b) {
-                return key[a] < key[b] || (key[a] == key[b] && a < b);
-            });
+            auto less = [&](int u, int v) { return key[u] < key[v] || (key[u] == key[v] && u < v); };
+            std::vector<int> tmp(set);
+            std::nth_element(tmp.begin(), tmp.begin() + (left - 1), tmp.end(), less);
+            const int piv = tmp[left - 1];
+            a.reserve(left);
+            b.reserve(k - left);
+            for (int x : set) (less(x, piv) || x == piv ? a : b).push_back(x);
         } else {
             const int lo = *std::min_element(set.begin(), set.end());
             std::vector<int> first = bfs(set, lo);
             set = bfs(set, first.back());
+            a.assign(set.begin(), set.begin() + left);
+            b.assign(set.begin() + left, set.end());
+            std::sort(a.begin(), a.end());
+            std::sort(b.begin(), b.end());
         }
-        std::vector<int> a(set.begin(), set.begin() + left), b(set.begin() + left, set.end());
-        std::sort(a.begin(), a.end());
-        std::sort(b.begin(), b.end());
         split(std::move(a), depth + 1);
         split(std::move(b), depth + 1);
     }
@@ -210,6 +276,7 @@ struct Partitioner {
 int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const double* val, const double* coords,
                    int leaf_lines, double theta, std::vector<int32_t>& perm, std::vector<int32_t>& leaf_ptr) {
     const int n = (int)n64;
+    Trace tr;
     // strongly coupled lines: union-find over |a_ij| >= theta * max_{k != i} |a_ik|
     std::vector<int> root(n);
     for (int i = 0; i < n; i++) root[i] = i;
@@ -230,6 +297,7 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
             }
         }
     }
+    tr.mark("  partition: union-find");
     Partitioner P;
     std::vector<int> line_of(n), first;
     {
@@ -242,21 +310,37 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     }
     P.nl = (int)first.size();
     {
-        std::vector<std::vector<int>> nb(P.nl);
-        for (int i = 0; i < n; i++)
-            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-                const int lj = line_of[col[e]];
-                if (lj != line_of[i]) nb[line_of[i]].push_back(lj);
-            }
-        P.gptr.assign(P.nl + 1, 0);
-        for (int l = 0; l < P.nl; l++) {
-            std::sort(nb[l].begin(), nb[l].end());
-            nb[l].erase(std::unique(nb[l].begin(), nb[l].end()), nb[l].end());
-            P.gptr[l + 1] = P.gptr[l] + (int)nb[l].size();
+        // DOFs grouped by line (counting sort), then each line's neighbour
+        // lines collected with a visit stamp and sorted
+        const int nl = P.nl;
+        std::vector<int> lptr(nl + 1, 0), ldof(n);
+        for (int i = 0; i < n; i++) lptr[line_of[i] + 1]++;
+        for (int l = 0; l < nl; l++) lptr[l + 1] += lptr[l];
+        {
+            std::vector<int> pos(lptr.begin(), lptr.end() - 1);
+            for (int i = 0; i < n; i++) ldof[pos[line_of[i]]++] = i;
         }
-        P.gadj.reserve(P.gptr[P.nl]);
-        for (int l = 0; l < P.nl; l++) P.gadj.insert(P.gadj.end(), nb[l].begin(), nb[l].end());
+        std::vector<int> stamp(nl, -1);
+        P.gptr.assign(nl + 1, 0);
+        P.gadj.clear();
+        P.gadj.reserve((size_t)nl * 8);
+        for (int l = 0; l < nl; l++) {
+            const size_t b = P.gadj.size();
+            for (int k = lptr[l]; k < lptr[l + 1]; k++) {
+                const int i = ldof[k];
+                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                    const int lj = line_of[col[e]];
+                    if (lj != l && stamp[lj] != l) {
+                        stamp[lj] = l;
+                        P.gadj.push_back(lj);
+                    }
+                }
+            }
+            std::sort(P.gadj.begin() + b, P.gadj.end());
+            P.gptr[l + 1] = (int)P.gadj.size();
+        }
     }
+    tr.mark("  partition: line graph");
     if (coords) {
         P.have_coords = true;
         P.lx.resize(P.nl);
@@ -274,6 +358,7 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     std::vector<int> all(P.nl);
     for (int l = 0; l < P.nl; l++) all[l] = l;
     P.split(std::move(all), 0);
+    tr.mark("  partition: bisection");
     const int nleaf = P.next_leaf;
     leaf_ptr.assign(nleaf + 1, 0);
     for (int i = 0; i < n; i++) leaf_ptr[P.leaf_of[line_of[i]] + 1]++;
@@ -460,9 +545,8 @@ struct hs_factor_s {
 namespace {
 
 void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
-    int32_t st[3];
-    CK(cudaMemcpyAsync(st, d_status.p, sizeof(st), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    std::vector<int32_t> st;
+    download(st, d_status.p, 3, h->st);
     if (st[0] == ST_NOT_SPD) {
         if (info) { info->fail_level = st[1] < 0 ? h->depth : st[1]; info->fail_cluster = st[2]; }
         throw HsError{HS_ERR_NOT_SPD};
@@ -562,25 +646,34 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             L.tasks.push_back(t);
         }
         ws_phase_max = std::max(ws_phase_max, ws);
-        // Schur targets of the phase: (p, q), p <= q, contributions ascending
-        std::map<std::pair<int, int>, std::vector<ContribDev>> tg;
+        // Schur targets of the phase: (p, q), p <= q, contributions in
+        // ascending task order (sort by target, stable in task order)
+        struct TC {
+            int p, q;
+            ContribDev c;
+        };
+        std::vector<TC> tcs;
         for (int c : P.phases[ph]) {
             const int ti = task_of[c];
             const auto& nlc = P.nl[c];
             for (int a = 0; a < (int)nlc.size(); a++)
                 for (int b = 0; b < (int)nlc.size(); b++)
-                    if (nlc[a] <= nlc[b]) tg[{nlc[a], nlc[b]}].push_back(ContribDev{ti, a, b});
+                    if (nlc[a] <= nlc[b]) tcs.push_back(TC{nlc[a], nlc[b], ContribDev{ti, a, b}});
         }
-        for (auto& kv : tg) {
+        std::stable_sort(tcs.begin(), tcs.end(),
+                         [](const TC& x, const TC& y) { return x.p < y.p || (x.p == y.p && x.q < y.q); });
+        for (size_t i = 0; i < tcs.size();) {
+            size_t j = i;
             TargetDev g{};
-            g.p = kv.first.first;
-            g.q = kv.first.second;
+            g.p = tcs[i].p;
+            g.q = tcs[i].q;
             g.blk_pq = T.find(g.p, g.q);
             g.blk_qp = T.find(g.q, g.p);
             g.c_begin = (int)contribs.size();
-            contribs.insert(contribs.end(), kv.second.begin(), kv.second.end());
+            while (j < tcs.size() && tcs[j].p == g.p && tcs[j].q == g.q) contribs.push_back(tcs[j++].c);
             g.c_end = (int)contribs.size();
             targets.push_back(g);
+            i = j;
         }
         L.ph_task.push_back((int)L.tasks.size());
         L.ph_target.push_back((int)targets.size());
@@ -639,11 +732,13 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     tr.mark("  launches");
     check_status(h, d_status, info);
     tr.mark("  kernels (sync)");
-    L.fin.assign(P.nc, 0);
-    CK(cudaMemcpyAsync(L.fin.data(), d_cur.p, sizeof(int32_t) * P.nc, cudaMemcpyDeviceToHost, st));
-    std::vector<int32_t> hmeta(meta);
-    if (meta) CK(cudaMemcpyAsync(hmeta.data(), L.d_meta.p, sizeof(int32_t) * meta, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    {
+        std::vector<int32_t> fin;
+        download(fin, d_cur.p, P.nc, st);
+        L.fin.assign(fin.begin(), fin.end());
+    }
+    std::vector<int32_t> hmeta;
+    download(hmeta, L.d_meta.p, meta, st);
     // solve-phase records with resolved offsets
     {
         std::vector<ApTask> at(L.tasks.size());
@@ -813,17 +908,27 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     const int32_t* cl = col;
     const double* vl = val;
     if (h->opt.mem == HS_MEM_DEVICE) {
-        hrp.resize(n + 1);
-        CK(cudaMemcpyAsync(hrp.data(), rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+        // the pattern (and values, for the partitioner) are read on the host
+        int64_t nnz0 = 0;
+        CK(cudaMemcpyAsync(&nnz0, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const int64_t nnz = hrp[n];
-        hcol.resize(nnz);
-        CK(cudaMemcpyAsync(hcol.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st));
-        if (!tree_in) {
-            hval.resize(nnz);
-            CK(cudaMemcpyAsync(hval.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-        }
+        if (nnz0 < 0) throw HsError{HS_ERR_ARG};
+        g_stage.drain();
+        const size_t b_rp = sizeof(int64_t) * (n + 1), b_col = sizeof(int32_t) * nnz0;
+        const size_t b_val = tree_in ? 0 : sizeof(double) * nnz0;
+        char* pin = g_stage.take(b_rp + b_col + b_val + 512, st);
+        int64_t* prp = reinterpret_cast<int64_t*>(pin);
+        int32_t* pcol = reinterpret_cast<int32_t*>(pin + ((b_rp + 255) & ~(size_t)255));
+        double* pval = reinterpret_cast<double*>(pin + ((b_rp + 255) & ~(size_t)255) + ((b_col + 255) & ~(size_t)255));
+        CK(cudaMemcpyAsync(prp, rowptr, b_rp, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(pcol, col, b_col, cudaMemcpyDeviceToHost, st));
+        if (b_val) CK(cudaMemcpyAsync(pval, val, b_val, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        // keep them: copy out of the staging area, which later uploads reuse
+        hrp.assign(prp, prp + n + 1);
+        hcol.assign(pcol, pcol + nnz0);
+        if (b_val) hval.assign(pval, pval + nnz0);
+        g_stage.synced(st);
         rp = hrp.data();
         cl = hcol.data();
         vl = hval.empty() ? nullptr : hval.data();
@@ -889,19 +994,28 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     P.size0.resize(nleaf);
     for (int c = 0; c < nleaf; c++) P.size0[c] = leaf_ptr[c + 1] - leaf_ptr[c];
     P.adj0.assign(nleaf, {});
-    for (int64_t i = 0; i < n; i++) {
-        const int p = dof_cluster[i];
-        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-            const int q = dof_cluster[cl[e]];
-            if (q != p) {  // block pattern kept symmetric even if the CSR pattern is not
-                P.adj0[p].push_back(q);
-                P.adj0[q].push_back(p);
+    {
+        // block pattern of level 0, kept symmetric even if the CSR pattern is not
+        std::vector<int> stamp(nleaf, -1);
+        for (int c = 0; c < nleaf; c++) {
+            auto& v = P.adj0[c];
+            for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
+                const int i = h->perm[k];
+                for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+                    const int q = dof_cluster[cl[e]];
+                    if (q != c && stamp[q] != c) {
+                        stamp[q] = c;
+                        v.push_back(q);
+                    }
+                }
             }
         }
-    }
-    for (auto& v : P.adj0) {
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
+        for (int c = 0; c < nleaf; c++)
+            for (int q : P.adj0[c])
+                if (!std::binary_search(P.adj0[q].begin(), P.adj0[q].end(), c) &&
+                    std::find(P.adj0[q].begin(), P.adj0[q].end(), c) == P.adj0[q].end())
+                    P.adj0[q].push_back(c);
+        for (auto& v : P.adj0) std::sort(v.begin(), v.end());
     }
 
     DBuf d_status;
