@@ -179,13 +179,15 @@ def run_ours(args):
     coords = np.ascontiguousarray(prob.coords)
     stream.synchronize()
 
-    def opt(mem, profile=0):
+    def opt(mem, profile=0, prec=None):
+        prec = hsolve.HS_PREC_MIXED if prec is None else prec
         return hsolve.hs_default_options(tol=args.tol, depth=8, leaf_lines=4, rtol=1e-8, mem=mem,
-                                         profile=profile, stream=stream.cuda_stream, coords=coords)
+                                         profile=profile, stream=stream.cuda_stream, coords=coords,
+                                         precision=prec)
 
-    def step(profile=0):
+    def step(profile=0, prec=None):
         """partition + setup + PCG, device-resident A and b."""
-        h = hsolve.hs_setup(n, rp, ci, va, opt=opt(hsolve.HS_MEM_DEVICE, profile))
+        h = hsolve.hs_setup(n, rp, ci, va, opt=opt(hsolve.HS_MEM_DEVICE, profile, prec))
         info, rc = h.hs_krylov(b, x)
         return h, info
 
@@ -200,31 +202,36 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(max(3, args.warmup)):
-        h, info = step()
-        h.close()
+    def timed(prec):
+        times, iters, resid, launches = [], [], [], 0
+        for _ in range(args.steps):
+            flush_l2()
+            barrier()
+            l0 = hsolve.hs_launch_count()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h, info = step(prec=prec)
+            e1.record(stream)
+            e1.synchronize()
+            launches += hsolve.hs_launch_count() - l0
+            barrier()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            iters.append(info.iters)
+            resid.append(info.rel_resid)
+            h.close()
+        return float(np.mean(times)), int(np.max(iters)), float(np.max(resid)), launches // max(args.steps, 1)
+
+    for prec in (hsolve.HS_PREC_FP64, hsolve.HS_PREC_MIXED):
+        for _ in range(max(3, args.warmup)):
+            h, info = step(prec=prec)
+            h.close()
 
     clocks = ClockSampler(local)
     clocks.start()
-    times, iters, resid, launches = [], [], [], 0
-    for _ in range(args.steps):
-        flush_l2()
-        barrier()
-        l0 = hsolve.hs_launch_count()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h, info = step()
-        e1.record(stream)
-        e1.synchronize()
-        launches += hsolve.hs_launch_count() - l0
-        barrier()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        iters.append(info.iters)
-        resid.append(info.rel_resid)
-        h.close()
+    t64, it64, res64, _ = timed(hsolve.HS_PREC_FP64)
+    t_step, it_mx, res_mx, launches = timed(hsolve.HS_PREC_MIXED)
     clk = clocks.stop()
-    t_step = float(np.mean(times))
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([t_step], device=dev)
@@ -237,7 +244,7 @@ def run_ours(args):
         flush_l2()
         barrier()
         t0 = time.perf_counter()
-        info_e, rc = hsolve.hs_solve(n, h_rp, h_ci, h_va, h_b, h_x, opt=opt(hsolve.HS_MEM_HOST))
+        info_e, rc = hsolve.hs_solve(n, h_rp, h_ci, h_va, h_b, h_x, opt=opt(hsolve.HS_MEM_HOST))  # mixed form
         e2e_times.append(time.perf_counter() - t0)
         assert rc == 0 and info_e.rel_resid <= 1e-8
     xe = h_x.numpy()
@@ -246,14 +253,19 @@ def run_ours(args):
     h2d = prob.rowptr.nbytes + prob.col.nbytes + prob.val.nbytes + prob.b.nbytes
     d2h = 8 * n
 
-    # per-kernel-class device times (profiled replica of one step)
+    # per-kernel-class device times (profiled replicas of one step of each form)
+    flush_l2()
+    barrier()
+    hp, infop = step(profile=1, prec=hsolve.HS_PREC_FP64)
+    stats = hp.kernel_stats()
+    hp.close()
     flush_l2()
     barrier()
     hp, infop = step(profile=1)
-    stats = hp.kernel_stats()
+    stats_mx = hp.kernel_stats()
     hp.close()
     fp64_peak = hsolve.hs_measure_fp64_peak(stream.cuda_stream)
-    fac = stats["factor"]
+    fac = stats_mx["factor"]
     achieved = fac["flops"] / (fac["ms"] * 1e-3) / 1e12 if fac["ms"] > 0 else 0.0
     roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": achieved / fp64_peak if fp64_peak > 0 else None, "traffic": None,
@@ -264,15 +276,19 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "flushed (320 MB write) before each step",
-                       "replicas": world},
-            "iters": int(np.max(iters)), "rel_resid": float(np.max(resid)),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "precision": "mixed: FP64 Cholesky/scaling/CPQR/Krylov residual, FP32 Schur products and "
+                                    "stored factor",
+                       "l2": "flushed (320 MB write) before each step", "replicas": world},
+            "iters": it_mx, "rel_resid": res_mx,
+            "plain_fp64": {"value": t64, "unit": "s", "iters": it64, "rel_resid": res64,
+                           "kernel_ms": {k: round(v["ms"], 4) for k, v in stats.items()}},
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches // max(args.steps, 1)),
             "roofline": roof, "clocks": clk,
-            "kernel_ms": {k: round(v["ms"], 4) for k, v in stats.items()}}
+            "kernel_ms": {k: round(v["ms"], 4) for k, v in stats_mx.items()}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, it = cpu_oracle_step(prob, args.tol, 8, 4)
         line["cpu_baseline"] = {"value": dt, "unit": "s", "cores": 1, "kind": "oracle",

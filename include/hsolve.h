@@ -78,6 +78,8 @@ typedef struct {
                             most this many DOFs (and the top) are applied as
                             one explicit dense operator formed at setup;
                             0 = never; default 4096                           */
+    int32_t fused_levels; /* nonzero (default): levels whose clusters have at
+                            most 32 DOFs run all their phases in one launch   */
 } hs_options;
 
 typedef struct {

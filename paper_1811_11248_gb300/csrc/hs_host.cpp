@@ -529,6 +529,7 @@ struct hs_factor_s {
     int64_t factor_bytes = 0;
     cudaGraphExec_t apply_graph = nullptr;
     int64_t graph_kernels = 0;
+    int fp32 = 0;          // factor stored and applied in FP32 (mixed-precision form)
     int first_coarse = 0;  // first level of the single-CTA chain (or of the dense operator)
     bool coarse_dense = false;
     int ncoarse = 0;       // size of the dense coarse operator
@@ -551,6 +552,7 @@ void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
         if (info) { info->fail_level = st[1] < 0 ? h->depth : st[1]; info->fail_cluster = st[2]; }
         throw HsError{HS_ERR_NOT_SPD};
     }
+    if (st[0] == ST_TIMEOUT) throw HsError{HS_ERR_TIMEOUT};
     if (st[0] != ST_OK) throw HsError{HS_ERR_UNSUPPORTED};
 }
 
@@ -592,6 +594,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                   DBuf& d_status, hs_info* info) {
     Level& L = *h->lev[l];
     cudaStream_t st = h->st;
+    Trace tr0;
     L.nc = P.nc;
     L.size0 = P.size0;
     L.phase = P.phase;
@@ -678,6 +681,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         L.ph_task.push_back((int)L.tasks.size());
         L.ph_target.push_back((int)targets.size());
     }
+    tr0.mark("  tasks+targets");
     // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
     // before its own transform (q in a later phase) or at level end (earlier)
     L.early.assign(P.nc, {});
@@ -689,6 +693,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             (P.phase[q] > P.phase[t.c] ? L.early[q] : L.late[q]).push_back({ti, k});
         }
     }
+    L.wmax = std::max(L.wmax, 64);  // the fused kernel's Schur step stages 32 x 4 int64 in the column table
     if (factor_smem_bytes(L.smax, L.wmax, L.lmax) > (size_t)kFactorMaxSmem) throw HsError{HS_ERR_UNSUPPORTED};
     Trace tr;
     tr.mark("  records");
@@ -699,7 +704,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     upload(d_targets, targets, st);
     upload(d_contribs, contribs, st);
     L.d_meta.alloc(sizeof(int32_t) * std::max<int32_t>(meta, 1));
-    L.d_fac.alloc(sizeof(double) * std::max<int64_t>(fac, 1));
+    L.d_fac.alloc((h->fp32 ? sizeof(float) : sizeof(double)) * std::max<int64_t>(fac, 1));
     L.fac_doubles = fac;
     L.d_stage.alloc(sizeof(double) * std::max<int64_t>(stage, 1));
     d_ws.alloc(sizeof(double) * std::max<int64_t>(ws_phase_max, 1));
@@ -711,21 +716,42 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     upload(d_ld, ld, st);
     const double eps2 = h->opt.tol * h->opt.tol;
     tr.mark("  uploads");
-    for (int ph = 0; ph < L.nphases; ph++) {
+    int64_t mcap = 0;  // largest block row (with the identity columns)
+    for (const TaskDev& t : L.tasks) mcap = std::max<int64_t>(mcap, (int64_t)t.s * (t.wcap + t.s));
+    const bool fused = h->opt.fused_levels && L.smax <= kFusedSmax &&
+                       fused_smem_bytes(L.smax, L.wmax, L.lmax, mcap) <= (size_t)kFactorMaxSmem;
+    if (fused) {
+        DBuf d_pht, d_phg, d_bar;
+        upload(d_pht, L.ph_task, st);
+        upload(d_phg, L.ph_target, st);
+        d_bar.alloc(2 * sizeof(unsigned));
+        int max_items = 1;
+        for (int ph = 0; ph < L.nphases; ph++)
+            max_items = std::max({max_items, L.ph_task[ph + 1] - L.ph_task[ph], L.ph_target[ph + 1] - L.ph_target[ph]});
+        h->prof.begin(KC_FACTOR, st);
+        CK(launch_factor_level_fused(st, L.d_tasks.as<TaskDev>(), d_pht.as<int32_t>(), d_targets.as<TargetDev>(),
+                                     d_phg.as<int32_t>(), d_contribs.as<ContribDev>(), L.nphases,
+                                     L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
+                                     d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
+                                     L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l,
+                                     L.smax, L.wmax, L.lmax, mcap, max_items, d_bar.as<unsigned>()));
+        h->prof.end(KC_FACTOR, st);
+    }
+    for (int ph = 0; ph < (fused ? 0 : L.nphases); ph++) {
         const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
         h->prof.begin(KC_FACTOR, st);
         CK(launch_factor_phase(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.wmax, L.lmax,
                                L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
-                               d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.as<double>(),
+                               d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
                                L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l));
         h->prof.end(KC_FACTOR, st);
         const int g0 = L.ph_target[ph], ng = L.ph_target[ph + 1] - g0;
         if (ng > 0) {
             h->prof.begin(KC_SCHUR, st);
             CK(launch_schur_phase(st, d_targets.as<TargetDev>(), g0, ng, d_contribs.as<ContribDev>(),
-                                  L.d_tasks.as<TaskDev>(), L.d_fac.as<double>(), L.d_meta.as<int32_t>(),
+                                  L.d_tasks.as<TaskDev>(), L.d_fac.p, L.d_meta.as<int32_t>(),
                                   blocks.as<double>(), d_off.as<int64_t>(), d_ld.as<int32_t>(),
-                                  d_cur.as<int32_t>(), h->opt.precision));
+                                  d_cur.as<int32_t>(), h->fp32));
             h->prof.end(KC_SCHUR, st);
         }
     }
@@ -739,6 +765,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     }
     std::vector<int32_t> hmeta;
     download(hmeta, L.d_meta.p, meta, st);
+    tr.mark("  downloads");
     // solve-phase records with resolved offsets
     {
         std::vector<ApTask> at(L.tasks.size());
@@ -806,6 +833,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         L.hmeta = std::move(hmeta);
         L.early.clear();
     }
+    tr.mark("  solve records");
     // algorithmic work: POTRF s^3/3, TRSM s^2 (n + w), CPQR sum_k 4 (s-k)(w-k) + 4 s r n, Schur n^2 f
     L.task_rank.resize(L.tasks.size());
     for (size_t ti = 0; ti < L.tasks.size(); ti++) {
@@ -1078,7 +1106,9 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
                 std::sort(v.begin(), v.end());
                 v.erase(std::unique(v.begin(), v.end()), v.end());
             }
+            tr.mark("next-level adjacency");
             plan_level(Pn);
+            tr.mark("next-level plan_level");
             BlockTable Tn = make_table(Pn);
             DBuf nblocks;
             nblocks.alloc(sizeof(double) * std::max<int64_t>(Tn.total, 1));
@@ -1143,7 +1173,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     int64_t fb = (int64_t)h->ntop * h->ntop * 8;
     for (auto& Lp : h->lev) {
         Lp->d_y.alloc(sizeof(double) * std::max<int64_t>(Lp->slot[Lp->nc], 1));
-        fb += Lp->fac_doubles * 8;
+        fb += Lp->fac_doubles * (h->fp32 ? 4 : 8);
     }
     h->factor_bytes = fb;
     CK(cudaStreamSynchronize(st));
@@ -1180,8 +1210,8 @@ void enqueue_apply(hs_factor_s* h) {
         Level& L = *h->lev[l];
         for (int k = 0; k < L.nstages; k++) {
             const int t0 = L.ap_stage[k], nt = L.ap_stage[k + 1] - t0;
-            CK(launch_ap_fwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.d_ap_pulls.as<ApPull>(),
-                             L.d_fac.as<double>(), L.d_stage.as<double>(), L.d_y.as<double>()));
+            CK(launch_ap_fwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.d_ap_pulls.as<ApPull>(), L.d_fac.p,
+                             h->fp32, L.d_stage.as<double>(), L.d_y.as<double>()));
         }
         CK(launch_ap_fin(st, L.d_ap_fins.as<ApFin>(), L.nfin, L.d_ap_pulls.as<ApPull>(), L.d_stage.as<double>(),
                          L.d_y.as<double>(), next_of(l)));
@@ -1190,14 +1220,14 @@ void enqueue_apply(hs_factor_s* h) {
         CK(launch_dense_gemv(st, h->ncoarse, h->d_coarse.as<double>(), vec_of(lc), h->d_ycout.as<double>()));
     else
         CK(launch_ap_coarse(st, h->d_aplevels.as<ApLevel>(), D - lc, h->ntop, h->d_top.as<double>(),
-                            h->d_ytop.as<double>()));
+                            h->d_ytop.as<double>(), h->fp32));
     for (int l = lc - 1; l >= 0; l--) {
         Level& L = *h->lev[l];
         CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, back_of(l), L.d_y.as<double>(), 1));
         for (int k = L.nstages - 1; k >= 0; k--) {
             const int t0 = L.ap_stage[k], nt = L.ap_stage[k + 1] - t0;
-            CK(launch_ap_bwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.nmax, L.d_ap_nbs.as<ApNb>(),
-                             L.d_fac.as<double>(), L.d_y.as<double>()));
+            CK(launch_ap_bwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.nmax, L.d_ap_nbs.as<ApNb>(), L.d_fac.p,
+                             h->fp32, L.d_y.as<double>()));
         }
     }
 }
@@ -1250,7 +1280,7 @@ void build_apply_graph(hs_factor_s* h) {
             a.nbs = L.d_ap_nbs.as<ApNb>();
             a.fins = L.d_ap_fins.as<ApFin>();
             a.vcopy = L.d_vcopy.as<VCopyDev>();
-            a.fac = L.d_fac.as<double>();
+            a.fac = L.d_fac.p;
             if (ws_base) {
                 a.stage = ws_base + soff[k];
                 a.y = ws_base + yoff[k];
@@ -1284,7 +1314,7 @@ void build_apply_graph(hs_factor_s* h) {
         upload(d_al, al, h->st);
         h->prof.begin(KC_TOP, h->st);
         CK(launch_ap_coarse_batch(h->st, d_al.as<ApLevel>(), (int)al.size(), h->ntop, h->d_top.as<double>(), ytop0,
-                                  yin0, n, stride, h->d_coarse.as<double>()));
+                                  yin0, n, stride, h->d_coarse.as<double>(), h->fp32));
         h->prof.end(KC_TOP, h->st);
         CK(cudaStreamSynchronize(h->st));
     } else {
@@ -1611,6 +1641,7 @@ int hs_default_options(hs_options* opt) {
     opt->stream = nullptr;
     opt->coords = nullptr;
     opt->coarse_dense = 4096;
+    opt->fused_levels = 1;
     return HS_OK;
 }
 
@@ -1660,7 +1691,8 @@ int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
     *out = nullptr;
     if (info) { std::memset(info, 0, sizeof(*info)); info->fail_level = -1; info->fail_cluster = -1; }
     if (n <= 0 || n > INT32_MAX || !rowptr || !col || !val || !opt) return HS_ERR_ARG;
-    if (!(opt->tol >= 0.0) || opt->leaf_lines <= 0 || (opt->mem != HS_MEM_HOST && opt->mem != HS_MEM_DEVICE))
+    if (!(opt->tol >= 0.0) || opt->leaf_lines <= 0 || (opt->mem != HS_MEM_HOST && opt->mem != HS_MEM_DEVICE) ||
+        (opt->precision != HS_PREC_FP64 && opt->precision != HS_PREC_MIXED))
         return HS_ERR_ARG;
     hs_factor_s* h = new (std::nothrow) hs_factor_s();
     if (!h) return HS_ERR_OOM;
@@ -1668,6 +1700,7 @@ int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
     h->opt = *opt;
     h->st = static_cast<cudaStream_t>(opt->stream);
     h->prof.on = opt->profile != 0;
+    h->fp32 = opt->precision == HS_PREC_MIXED ? 1 : 0;
     const double t0 = now_s();
     g_alloc_stream = h->st;
     prepare_pool();

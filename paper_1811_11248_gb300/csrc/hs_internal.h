@@ -68,7 +68,7 @@ struct ApLevel {
     const ApNb* nbs;
     const ApFin* fins;
     const VCopyDev* vcopy;
-    const double* fac;
+    const void* fac;  // double, or float in the mixed-precision form
     double* stage;
     double* y;
     double* ynext;
@@ -100,7 +100,7 @@ struct CopyDev {
 
 
 // status word written by kernels (0 = ok)
-enum : int32_t { ST_OK = 0, ST_NOT_SPD = 1, ST_TOO_BIG = 2 };
+enum : int32_t { ST_OK = 0, ST_NOT_SPD = 1, ST_TOO_BIG = 2, ST_TIMEOUT = 3 };
 
 // ---- kernel launchers (hs_kernels.cu) -------------------------------------
 cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col,
@@ -109,30 +109,30 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
                                const int32_t* blk_ld, double* blocks);
 cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
                                 int wmax, int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
-                                const int32_t* blk_ld, int32_t* cur, double* fac, int32_t* meta,
+                                const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                 double* ws, double eps2, int32_t* status, int32_t level);
 cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
-                               const ContribDev* contribs, const TaskDev* tasks, const double* fac,
+                               const ContribDev* contribs, const TaskDev* tasks, const void* fac,
                                const int32_t* meta, double* blocks, const int64_t* blk_off,
-                               const int32_t* blk_ld, const int32_t* cur, int precision);
+                               const int32_t* blk_ld, const int32_t* cur, int fp32);
 cudaError_t launch_copy_blocks(cudaStream_t st, const CopyDev* cps, int ncps, const double* src,
                                double* dst);
 cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* status);
 cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax,
-                          const ApPull* pulls, const double* fac, double* stage, double* y);
+                          const ApPull* pulls, const void* fac, int fp32, double* stage, double* y);
 cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const ApPull* pulls, const double* stage,
                           double* y, double* ynext);
 cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
-                          const ApNb* nbs, const double* fac, double* y);
+                          const ApNb* nbs, const void* fac, int fp32, double* y);
 // levels lvl[0..nlev) forward, dense top, then backward, in one CTA
 constexpr int kCoarseThreads = 1024;
 constexpr int kCoarseSmax = 64;   // largest cluster the coarse kernel handles
 constexpr int kCoarseNmax = 320;  // largest neighbour width (ncols) it handles
 cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
-                             double* ytop);
+                             double* ytop, int fp32);
 // explicit coarse operator (one CTA per unit vector) and its application
 cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
-                                   double* ytop0, double* yin0, int n, int64_t stride, double* Mc);
+                                   double* ytop0, double* yin0, int n, int64_t stride, double* Mc, int fp32);
 cudaError_t launch_dense_gemv(cudaStream_t st, int n, const double* Mc, const double* x, double* y);
 cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
                          int reverse);
@@ -156,6 +156,15 @@ cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, in
                           const double* w, double* partial, double* out);
 
 size_t factor_smem_bytes(int smax, int wmax, int lmax);
+// coarse levels: all phases of a level in one single-CTA launch (warp per task)
+constexpr int kFusedWarps = 16, kFusedSmax = 32;
+size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap);
+cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, const int32_t* ph_task,
+                                      const TargetDev* targets, const int32_t* ph_target, const ContribDev* contribs,
+                                      int nph, const ListDev* lists, double* blocks, const int64_t* blk_off,
+                                      const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
+                                      double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
+                                      int lmax, int64_t mcap, int max_items, unsigned* bar);
 // process-wide count of this library's kernel launches
 int64_t launch_count();
 void launch_count_add(int64_t k);

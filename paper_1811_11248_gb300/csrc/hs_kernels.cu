@@ -107,36 +107,75 @@ __global__ void k_scatter_csr(int64_t n, const int64_t* __restrict__ rowptr, con
 // Factor one phase: one CTA per cluster.
 // Shared memory: G (s*s) | rdiag (s) | v (s) | cn (wmax) | red (64) | ioff (lmax+1 ints) | flags
 // ---------------------------------------------------------------------------
-constexpr int kFactorThreads = 256;
+constexpr int kFactorThreads = 512;
 
-__global__ void __launch_bounds__(kFactorThreads)
-k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
-               double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
-               const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, double* __restrict__ fac,
-               int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
-               int32_t level, int smax, int wmax) {
-    extern __shared__ double sm[];
-    const TaskDev T = tasks[t0 + blockIdx.x];
-    const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
+// Thread groups that run one cluster elimination: a whole CTA (fine levels)
+// or one warp (coarse levels).  Reductions return the same value to every
+// member and use a fixed tree (deterministic).
+struct CtaGroup {
+    int rank, size;
+    __device__ CtaGroup() : rank(threadIdx.x), size(blockDim.x) {}
+    __device__ void sync() const { __syncthreads(); }
+    __device__ double sum(double v, double* red) const { return block_sum(v, red); }
+    __device__ double max(double v, double* red) const { return block_max(v, red); }
+    __device__ int minint(int v, double* red) const { return block_min_int(v, reinterpret_cast<int*>(red)); }
+};
+struct WarpGroup {
+    int rank, size;
+    __device__ WarpGroup() : rank(threadIdx.x & 31), size(32) {}
+    __device__ void sync() const { __syncwarp(); }
+    __device__ double sum(double v, double*) const { return warp_sum(v); }
+    __device__ double max(double v, double*) const { return warp_max(v); }
+    __device__ int minint(int v, double*) const { return warp_min_int(v); }
+};
+
+// Per list entry of a cluster's row: block offsets / leading dimensions of
+// (c, q) and (q, c) and q's current width, staged in shared memory so that the
+// entries' chains of dependent loads run in parallel.
+struct EntryMeta {
+    int64_t cq, qc;
+    int32_t ldcq, ldqc, w, pad;
+};
+
+constexpr int kNB = 16;  // Cholesky panel width
+
+// One scaled low-rank elimination (Sec. 3.1) by the group g.  Shared memory
+// of the group: G (s*s), rdiag (s), v (s), cn (fill columns), red (>= 64
+// doubles), ioff (list length + 1 ints), flag, hh (3 doubles).
+// FT: element type of the stored factor (W, C): double, or float in the
+// mixed-precision form.  All arithmetic here is FP64.
+template <typename FT, typename Grp>
+__device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* rdiag, double* v, double* cn,
+                            double* red, int* ioff, int* s_flag, double* s_hh, double* Msh, EntryMeta* em,
+                            int64_t* colsrc, const ListDev* __restrict__ lists,
+                            double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+                            const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
+                            int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
+                            int32_t level) {
+    const int s = T.s, tid = g.rank, NT = g.size;
     const int L = T.nn + T.nw;
-    double* G = sm;
-    double* rdiag = G + (size_t)smax * smax;
-    double* v = rdiag + smax;
-    double* cn = v + smax;
-    double* red = cn + wmax;
-    int* ioff = reinterpret_cast<int*>(red + 64);
-    __shared__ int s_flag;
-    __shared__ double s_hh[3];
-
-    // column offsets of the row blocks (compact, current widths)
+    // entry metadata (one round of loads for all entries), then the column
+    // offsets of the row blocks (compact, current widths)
+    for (int e = tid; e < L; e += NT) {
+        const ListDev le = lists[T.list + e];
+        EntryMeta m;
+        m.cq = blk_off[le.blk_cq];
+        m.qc = blk_off[le.blk_qc];
+        m.ldcq = blk_ld[le.blk_cq];
+        m.ldqc = blk_ld[le.blk_qc];
+        m.w = cur[le.q];
+        m.pad = 0;
+        em[e] = m;
+    }
+    g.sync();
     if (tid == 0) {
         int o = 0;
         for (int e = 0; e < L; e++) {
             ioff[e] = o;
-            o += cur[lists[T.list + e].q];
+            o += em[e].w;
         }
         ioff[L] = o;
-        s_flag = 0;
+        *s_flag = 0;
     }
     // A_ss -> shared memory
     {
@@ -144,75 +183,106 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         const int ld = blk_ld[T.diag_blk];
         for (int idx = tid; idx < s * s; idx += NT) G[idx] = A[(int64_t)(idx / s) * ld + idx % s];
     }
-    __syncthreads();
+    g.sync();
     const int W = ioff[L], ncols = ioff[T.nn], Wn = W - ncols;
 
-    // Cholesky A_ss = G G^T (right-looking, in shared memory)
-    for (int j = 0; j < s; j++) {
-        if (tid == 0) {
-            const double d = G[j * s + j];
-            if (!(d > 0.0)) {
-                s_flag = 1;
-            } else {
-                const double g = sqrt(d);
-                G[j * s + j] = g;
-                rdiag[j] = 1.0 / g;
+    // Cholesky A_ss = G G^T in shared memory, right-looking in panels of kNB
+    // columns: the diagonal block by one warp (warp-synchronous), then the
+    // panel below it and the trailing update by the whole group.
+    for (int k0 = 0; k0 < s; k0 += kNB) {
+        const int kb = min(kNB, s - k0), k1 = k0 + kb;
+        if (tid < 32) {
+            const int lane = tid;
+            for (int j = k0; j < k1; j++) {
+                if (lane == 0) {
+                    const double d = G[j * s + j];
+                    if (!(d > 0.0)) {
+                        *s_flag = 1;
+                    } else {
+                        const double gj = sqrt(d);
+                        G[j * s + j] = gj;
+                        rdiag[j] = 1.0 / gj;
+                    }
+                }
+                __syncwarp();
+                if (*s_flag) break;
+                const int i = j + 1 + lane;
+                if (i < k1) G[i * s + j] *= rdiag[j];
+                __syncwarp();
+                if (i < k1)
+                    for (int k = j + 1; k <= i; k++) G[i * s + k] -= G[i * s + j] * G[k * s + j];
+                __syncwarp();
             }
         }
-        __syncthreads();
-        if (s_flag) {
+        g.sync();
+        if (*s_flag) {
             if (tid == 0 && atomicCAS(status, 0, ST_NOT_SPD) == 0) {
                 status[1] = level;
                 status[2] = T.c;
             }
             return;
         }
-        const double rj = rdiag[j];
-        for (int i = j + 1 + tid; i < s; i += NT) G[i * s + j] *= rj;
-        __syncthreads();
-        const int m = s - j - 1;
-        for (int idx = tid; idx < m * m; idx += NT) {
-            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
-            if (k <= i) G[i * s + k] -= G[i * s + j] * G[k * s + j];
+        // panel: rows below the block, G[i, k0:k1] <- A[i, k0:k1] L_kk^-T
+        for (int i = k1 + tid; i < s; i += NT) {
+            for (int j = k0; j < k1; j++) {
+                double a = G[i * s + j];
+                for (int k = k0; k < j; k++) a -= G[i * s + k] * G[j * s + k];
+                G[i * s + j] = a * rdiag[j];
+            }
         }
-        __syncthreads();
+        g.sync();
+        // trailing update of the lower triangle
+        const int m = s - k1;
+        for (int idx = tid; idx < m * m; idx += NT) {
+            const int i = k1 + idx / m, k = k1 + idx % m;
+            if (k <= i) {
+                double a = G[i * s + k];
+                for (int j = k0; j < k1; j++) a -= G[i * s + j] * G[k * s + j];
+                G[i * s + k] = a;
+            }
+        }
+        g.sync();
     }
     for (int idx = tid; idx < s * s; idx += NT)
         if (idx % s > idx / s) G[idx] = 0.0;
-    __syncthreads();
+    g.sync();
 
     // gather the block row [A_sn | A_sw | I] into the workspace (row-major, ld Wt);
     // the identity columns come out as W = U^T G^-1, the solve-phase operator
     const int Wt = W + s;
-    double* M = ws + T.m_off;
-    for (int e = 0; e < L; e++) {
-        const ListDev le = lists[T.list + e];
-        const int wq = ioff[e + 1] - ioff[e];
-        const double* src = blocks + blk_off[le.blk_cq];
-        const int ld = blk_ld[le.blk_cq];
-        const int o = ioff[e];
-        for (int idx = tid; idx < s * wq; idx += NT) {
-            const int i = idx / wq, j = idx % wq;
-            M[(int64_t)i * Wt + o + j] = src[(int64_t)i * ld + j];
+    double* M = Msh ? Msh : ws + T.m_off;  // block row in shared memory when the caller has room
+    // source of every column (block offset + column, leading dimension) so that
+    // the whole block row is gathered by one loop of independent loads
+    for (int e = tid; e < L; e += NT)
+        for (int j = 0; j < em[e].w; j++) {
+            colsrc[2 * (ioff[e] + j)] = em[e].cq + j;
+            colsrc[2 * (ioff[e] + j) + 1] = em[e].ldcq;
         }
+    g.sync();
+    for (int idx = tid; idx < s * W; idx += NT) {
+        const int i = idx / W, j = idx % W;
+        M[(int64_t)i * Wt + j] = blocks[colsrc[2 * j] + (int64_t)i * colsrc[2 * j + 1]];
     }
     for (int idx = tid; idx < s * s; idx += NT) {
         const int i = idx / s, j = idx % s;
         M[(int64_t)i * Wt + W + j] = (i == j) ? 1.0 : 0.0;
     }
-    __syncthreads();
+    g.sync();
 
-    // scaling: M <- G^-1 M (forward substitution, one thread per column;
-    // identity column j is zero above row j)
+    // scaling: M <- G^-1 M (forward substitution, one thread per column).
+    // A column that is zero above row i0 (identity column j: i0 = j; level-0
+    // face couplings: their first nonzero) keeps those zeros, so the
+    // substitution starts at i0; all-zero columns are skipped.
     for (int j = tid; j < Wt; j += NT) {
-        const int i0 = (j >= W) ? j - W : 0;
+        int i0 = (j >= W) ? j - W : 0;
+        while (i0 < s && M[(int64_t)i0 * Wt + j] == 0.0) i0++;
         for (int i = i0; i < s; i++) {
             double acc = M[(int64_t)i * Wt + j];
             for (int k = i0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * Wt + j];
             M[(int64_t)i * Wt + j] = acc * rdiag[i];
         }
     }
-    __syncthreads();
+    g.sync();
 
     // column-pivoted QR of the fill columns, reflectors applied to the whole row
     for (int j = tid; j < Wn; j += NT) {
@@ -223,7 +293,7 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         }
         cn[j] = c;
     }
-    __syncthreads();
+    g.sync();
     int k = 0;
     while (k < s) {
         double lt = 0.0, lm = 0.0;
@@ -234,8 +304,8 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
                 lm = fmax(lm, c);
             }
         }
-        const double total = block_sum(lt, red);
-        const double cmax = block_max(lm, red);
+        const double total = g.sum(lt, red);
+        const double cmax = g.max(lm, red);
         if (total <= eps2) break;
         const double thr = (1.0 - kPivotTie) * cmax;
         int lp = INT_MAX;
@@ -244,14 +314,14 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
                 lp = j;
                 break;  // lowest of this thread's columns
             }
-        const int p = block_min_int(lp, reinterpret_cast<int*>(red));
+        const int p = g.minint(lp, red);
         const int pc = ncols + p;
         double ls = 0.0;
         for (int i = k + 1 + tid; i < s; i += NT) {
             const double x = M[(int64_t)i * Wt + pc];
             ls += x * x;
         }
-        const double sig = block_sum(ls, red);
+        const double sig = g.sum(ls, red);
         if (tid == 0) {
             const double alpha = M[(int64_t)k * Wt + pc];
             const double nrm = sqrt(alpha * alpha + sig);
@@ -261,7 +331,7 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
             s_hh[2] = 1.0 / (alpha - beta);
             cn[p] = -1.0;
         }
-        __syncthreads();
+        g.sync();
         const double beta = s_hh[0], tau = s_hh[1], scal = s_hh[2];
         for (int i = tid; i < s; i += NT) {
             double vi = 0.0;
@@ -269,7 +339,7 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
             else if (i > k) vi = M[(int64_t)i * Wt + pc] * scal;
             v[i] = vi;
         }
-        __syncthreads();
+        g.sync();
         for (int i = k + tid; i < s; i += NT) M[(int64_t)i * Wt + pc] = (i == k) ? beta : 0.0;
         for (int j = tid; j < Wt; j += NT) {
             if (j == pc) continue;
@@ -287,7 +357,7 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
             }
             if (cand) cn[j - ncols] = c;
         }
-        __syncthreads();
+        g.sync();
         k++;
     }
     const int r = k;
@@ -300,24 +370,23 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
         mt[2 + 2 * e] = ioff[e + 1] - ioff[e];
     }
     {
-        double* Wf = fac + T.w_off;
-        for (int idx = tid; idx < s * s; idx += NT) Wf[idx] = M[(int64_t)(idx / s) * Wt + W + idx % s];
-        double* Cf = fac + T.c_off;
+        FT* Wf = fac + T.w_off;
+        for (int idx = tid; idx < s * s; idx += NT) Wf[idx] = (FT)M[(int64_t)(idx / s) * Wt + W + idx % s];
+        FT* Cf = fac + T.c_off;
         const int f = s - r;
         for (int idx = tid; idx < f * ncols; idx += NT) {
             const int i = idx / ncols, j = idx % ncols;
-            Cf[(int64_t)i * T.ncap + j] = M[(int64_t)(r + i) * Wt + j];
+            Cf[(int64_t)i * T.ncap + j] = (FT)M[(int64_t)(r + i) * Wt + j];
         }
     }
     // write back the coarse row (identity diagonal, U^T G^-1 A_sn, V1^T)
     if (T.nw > 0 && r > 0) {
         for (int e = 0; e < L; e++) {
-            const ListDev le = lists[T.list + e];
             const int wq = ioff[e + 1] - ioff[e], o = ioff[e];
-            double* dcq = blocks + blk_off[le.blk_cq];
-            const int ldcq = blk_ld[le.blk_cq];
-            double* dqc = blocks + blk_off[le.blk_qc];
-            const int ldqc = blk_ld[le.blk_qc];
+            double* dcq = blocks + em[e].cq;
+            const int ldcq = em[e].ldcq;
+            double* dqc = blocks + em[e].qc;
+            const int ldqc = em[e].ldqc;
             for (int idx = tid; idx < r * wq; idx += NT) {
                 const int i = idx / wq, j = idx % wq;
                 const double x = M[(int64_t)i * Wt + o + j];
@@ -335,37 +404,232 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
     if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
 }
 
+template <typename FT>
+__global__ void __launch_bounds__(kFactorThreads)
+k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
+               double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+               const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
+               int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
+               int32_t level, int smax, int wmax, int lmax) {
+    extern __shared__ double sm[];
+    __shared__ int s_flag;
+    __shared__ double s_hh[3];
+    const TaskDev T = tasks[t0 + blockIdx.x];
+    double* G = sm;
+    double* rdiag = G + (size_t)smax * smax;
+    double* v = rdiag + smax;
+    double* cn = v + smax;
+    double* red = cn + wmax;
+    EntryMeta* em = reinterpret_cast<EntryMeta*>(red + 64);
+    int64_t* colsrc = reinterpret_cast<int64_t*>(em + lmax);
+    int* ioff = reinterpret_cast<int*>(colsrc + 2 * (size_t)wmax);
+    CtaGroup g;
+    factor_task<FT>(T, g, G, rdiag, v, cn, red, ioff, &s_flag, s_hh, nullptr, em, colsrc, lists, blocks, blk_off,
+                    blk_ld, cur, fac, meta, ws, eps2, status, level);
+}
+
 // ---------------------------------------------------------------------------
 // Schur update of one phase: one CTA per target block (p, q), p <= q.
+// A(p,q) -= sum over contributions (ascending cluster order) of
+// C_t(:, p)^T C_t(:, q), products and their sum in FT (FP64, or FP32 in the
+// mixed form), subtracted from the FP64 block; the transpose goes to (q, p).
+// 64 x 64 output tiles, 16 x 16 threads with 4 x 4 outputs each, C staged in
+// shared memory KC rows at a time.
 // ---------------------------------------------------------------------------
+constexpr int kSchurTile = 64, kSchurKC = 16;
+
+template <typename FT>
 __global__ void __launch_bounds__(256)
 k_schur_phase(const TargetDev* __restrict__ targets, int g0, const ContribDev* __restrict__ contribs,
-              const TaskDev* __restrict__ tasks, const double* __restrict__ fac,
+              const TaskDev* __restrict__ tasks, const FT* __restrict__ fac,
               const int32_t* __restrict__ meta, double* __restrict__ blocks,
               const int64_t* __restrict__ blk_off, const int32_t* __restrict__ blk_ld,
               const int32_t* __restrict__ cur) {
+    __shared__ FT sp[kSchurKC][kSchurTile];
+    __shared__ FT sq[kSchurKC][kSchurTile];
     const TargetDev g = targets[g0 + blockIdx.x];
     const int mp = cur[g.p], mq = cur[g.q];
     double* A = blocks + blk_off[g.blk_pq];
     const int lda = blk_ld[g.blk_pq];
     double* At = blocks + blk_off[g.blk_qp];
     const int ldt = blk_ld[g.blk_qp];
-    for (int idx = threadIdx.x; idx < mp * mq; idx += blockDim.x) {
-        const int i = idx / mq, j = idx % mq;
-        double acc = A[(int64_t)i * lda + j];
-        for (int c = g.c_begin; c < g.c_end; c++) {
-            const ContribDev cb = contribs[c];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int ti = 0; ti < mp; ti += kSchurTile)
+        for (int tj = 0; tj < mq; tj += kSchurTile) {
+            FT acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = FT(0);
+            for (int c = g.c_begin; c < g.c_end; c++) {
+                const ContribDev cb = contribs[c];
+                const TaskDev T = tasks[cb.task];
+                const int32_t* mt = meta + T.meta;
+                const int f = T.s - mt[0];
+                const int op = mt[1 + 2 * cb.kp] + ti, oq = mt[1 + 2 * cb.kq] + tj;
+                const FT* C = fac + T.c_off;
+                for (int k0 = 0; k0 < f; k0 += kSchurKC) {
+                    __syncthreads();
+                    for (int idx = tid; idx < kSchurKC * kSchurTile; idx += 256) {
+                        const int kk = idx / kSchurTile, jj = idx % kSchurTile;
+                        const bool kin = k0 + kk < f;
+                        sp[kk][jj] = (kin && ti + jj < mp) ? C[(int64_t)(k0 + kk) * T.ncap + op + jj] : FT(0);
+                        sq[kk][jj] = (kin && tj + jj < mq) ? C[(int64_t)(k0 + kk) * T.ncap + oq + jj] : FT(0);
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int kk = 0; kk < kSchurKC; kk++) {
+                        FT a[4], b[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            a[u] = sp[kk][ty * 4 + u];
+                            b[u] = sq[kk][tx * 4 + u];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+#pragma unroll
+                            for (int v = 0; v < 4; v++) acc[u][v] += a[u] * b[v];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    const int i = ti + ty * 4 + u, j = tj + tx * 4 + v;
+                    if (i < mp && j < mq) {
+                        const double x = A[(int64_t)i * lda + j] - (double)acc[u][v];
+                        A[(int64_t)i * lda + j] = x;
+                        if (g.p != g.q) At[(int64_t)j * ldt + i] = x;
+                    }
+                }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse levels (clusters of at most 32 DOFs): every phase of the level in one
+// launch, one warp per cluster elimination and one warp per Schur target,
+// __syncthreads() between them.
+// ---------------------------------------------------------------------------
+// Per-warp shared memory of the fused kernel (doubles): G (smax^2), rdiag and v
+// (smax each), cn (wmax), red (64), hh (4), block row (mcap); then ints: ioff
+// (lmax + 1) and a flag.
+__host__ __device__ inline int64_t fused_warp_doubles(int smax, int wmax, int lmax, int64_t mcap) {
+    return (int64_t)smax * smax + 2 * smax + 3 * (int64_t)wmax + 68 + 4 * (int64_t)lmax + mcap;
+}
+template <typename FT>
+__device__ void schur_target_warp(const TargetDev& g, const ContribDev* __restrict__ contribs,
+                                  const TaskDev* __restrict__ tasks, const FT* __restrict__ fac,
+                                  const int32_t* __restrict__ meta, double* __restrict__ blocks,
+                                  const int64_t* __restrict__ blk_off, const int32_t* __restrict__ blk_ld,
+                                  const int32_t* __restrict__ cur, int64_t* cm) {
+    // cm (shared, 4 per contribution, at most 32 at a time): C of the
+    // contribution offset to p's and q's columns, its leading dimension and f
+    const int lane = threadIdx.x & 31;
+    const int mp = cur[g.p], mq = cur[g.q];
+    double* A = blocks + blk_off[g.blk_pq];
+    const int lda = blk_ld[g.blk_pq];
+    double* At = blocks + blk_off[g.blk_qp];
+    const int ldt = blk_ld[g.blk_qp];
+    for (int c0 = g.c_begin; c0 < g.c_end; c0 += 32) {
+        const int nc = min(32, g.c_end - c0);
+        if (lane < nc) {
+            const ContribDev cb = contribs[c0 + lane];
             const TaskDev T = tasks[cb.task];
             const int32_t* mt = meta + T.meta;
-            const int r = mt[0], f = T.s - r;
-            const int op = mt[1 + 2 * cb.kp], oq = mt[1 + 2 * cb.kq];
-            const double* C = fac + T.c_off;
-            double sub = 0.0;
-            for (int k = 0; k < f; k++) sub += C[(int64_t)k * T.ncap + op + i] * C[(int64_t)k * T.ncap + oq + j];
-            acc -= sub;
+            cm[4 * lane] = T.c_off + mt[1 + 2 * cb.kp];
+            cm[4 * lane + 1] = T.c_off + mt[1 + 2 * cb.kq];
+            cm[4 * lane + 2] = T.ncap;
+            cm[4 * lane + 3] = T.s - mt[0];
         }
-        A[(int64_t)i * lda + j] = acc;
-        if (g.p != g.q) At[(int64_t)j * ldt + i] = acc;
+        __syncwarp();
+        for (int idx = lane; idx < mp * mq; idx += 32) {
+            const int i = idx / mq, j = idx % mq;
+            FT acc = FT(0);
+            for (int c = 0; c < nc; c++) {
+                const FT* Cp = fac + cm[4 * c] + i;
+                const FT* Cq = fac + cm[4 * c + 1] + j;
+                const int64_t ld = cm[4 * c + 2];
+                const int f = (int)cm[4 * c + 3];
+                for (int k = 0; k < f; k++) acc += Cp[k * ld] * Cq[k * ld];
+            }
+            const double x = A[(int64_t)i * lda + j] - (double)acc;
+            A[(int64_t)i * lda + j] = x;
+            if (g.p != g.q) At[(int64_t)j * ldt + i] = x;
+        }
+        __syncwarp();
+    }
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
+// counts arrivals, bar[1] is the generation.  The wait is bounded: after
+// kBarrierSpins polls the CTA records ST_TIMEOUT and goes on (results are then
+// discarded by the host), so a broken launch cannot hang the GPU.
+constexpr long long kBarrierSpins = 1LL << 24;
+
+__device__ void grid_sync(unsigned* bar, int32_t* status) {
+    __threadfence();  // every thread's writes of this phase, device-visible
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                __nanosleep(40);
+                if (++spins > kBarrierSpins) {
+                    atomicCAS(status, 0, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    __threadfence();  // acquire side for every thread
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(kFusedWarps * 32)
+k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restrict__ ph_task,
+                     const TargetDev* __restrict__ targets, const int32_t* __restrict__ ph_target,
+                     const ContribDev* __restrict__ contribs, int nph, const ListDev* __restrict__ lists,
+                     double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+                     const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
+                     int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
+                     int32_t level, int smax, int wmax, int lmax, int64_t mcap, unsigned* bar) {
+    extern __shared__ double sm[];
+    const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int gw = blockIdx.x * nwarp + wid, GW = gridDim.x * nwarp;
+    const int64_t wd = fused_warp_doubles(smax, wmax, lmax, mcap);
+    double* d = sm + (size_t)wid * wd;
+    int* ii = reinterpret_cast<int*>(sm + (size_t)nwarp * wd) + (size_t)wid * (lmax + 2);
+    double* G = d;
+    double* rdiag = G + (size_t)smax * smax;
+    double* v = rdiag + smax;
+    double* cn = v + smax;
+    double* red = cn + wmax;
+    double* hh = red + 64;
+    EntryMeta* em = reinterpret_cast<EntryMeta*>(hh + 4);
+    int64_t* colsrc = reinterpret_cast<int64_t*>(hh + 4 + 4 * (size_t)lmax);
+    double* Msh = hh + 4 + 4 * (size_t)lmax + 2 * (size_t)wmax;
+    int* ioff = ii;
+    int* flag = ii + lmax + 1;
+    WarpGroup g;
+    for (int ph = 0; ph < nph; ph++) {
+        for (int t = ph_task[ph] + gw; t < ph_task[ph + 1]; t += GW)
+            factor_task<FT>(tasks[t], g, G, rdiag, v, cn, red, ioff, flag, hh, Msh, em, colsrc, lists, blocks,
+                            blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level);
+        grid_sync(bar, status);
+        for (int k = ph_target[ph] + gw; k < ph_target[ph + 1]; k += GW)
+            schur_target_warp<FT>(targets[k], contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur, colsrc);
+        grid_sync(bar, status);
     }
 }
 
@@ -431,9 +695,10 @@ constexpr int kApplyThreads = 128;
 //   y_c <- W_c y_c with W_c = U^T G^-1;
 //   stage d_c = C_c^T y_c(r:), the update of every neighbour of c (Eq. elim
 //          applied to the vector), consumed by later tasks or at level end.
+template <typename FT>
 __global__ void __launch_bounds__(kApplyThreads)
 k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pulls,
-         const double* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y, int smax) {
+         const FT* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y, int smax) {
     extern __shared__ double sh[];
     double* ys = sh;
     double* yn = sh + smax;
@@ -446,39 +711,39 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
         ys[j] = v;
     }
     __syncthreads();
-    const double* Wm = fac + T.w;
+    const FT* Wm = fac + T.w;
     const int lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
     for (int i0 = 4 * wid; i0 < s; i0 += 4 * nwarp) {
-        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        FT a[4] = {FT(0), FT(0), FT(0), FT(0)};
         for (int j = lane; j < s; j += 32) {
-            const double yj = ys[j];
+            const FT yj = (FT)ys[j];
 #pragma unroll
             for (int u = 0; u < 4; u++)
                 if (i0 + u < s) a[u] += Wm[(int64_t)(i0 + u) * s + j] * yj;
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const double t = warp_sum(a[u]);
+            const double t = warp_sum((double)a[u]);
             if (lane == 0 && i0 + u < s) yn[i0 + u] = t;
         }
     }
     __syncthreads();
     for (int j = tid; j < s; j += NT) yg[j] = yn[j];
     const int f = s - T.r;
-    const double* C = fac + T.cm;
+    const FT* C = fac + T.cm;
     const double* yf = yn + T.r;
     for (int j = tid; j < T.ncols; j += NT) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        const double* cj = C + j;
+        FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
+        const FT* cj = C + j;
         int i = 0;
         for (; i + 3 < f; i += 4) {
-            a0 += cj[(int64_t)i * T.ncap] * yf[i];
-            a1 += cj[(int64_t)(i + 1) * T.ncap] * yf[i + 1];
-            a2 += cj[(int64_t)(i + 2) * T.ncap] * yf[i + 2];
-            a3 += cj[(int64_t)(i + 3) * T.ncap] * yf[i + 3];
+            a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
+            a1 += cj[(int64_t)(i + 1) * T.ncap] * (FT)yf[i + 1];
+            a2 += cj[(int64_t)(i + 2) * T.ncap] * (FT)yf[i + 2];
+            a3 += cj[(int64_t)(i + 3) * T.ncap] * (FT)yf[i + 3];
         }
-        for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * yf[i];
-        stage[T.stg + j] = (a0 + a1) + (a2 + a3);
+        for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
+        stage[T.stg + j] = (double)((a0 + a1) + (a2 + a3));
     }
 }
 
@@ -496,8 +761,9 @@ k_ap_fin(const ApFin* __restrict__ fins, const ApPull* __restrict__ pulls, const
 }
 
 // Backward step of one phase: x_c(r:) -= C x_n, then x_c <- W_c^T x_c.
+template <typename FT>
 __global__ void __launch_bounds__(kApplyThreads)
-k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs, const double* __restrict__ fac,
+k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs, const FT* __restrict__ fac,
          double* __restrict__ y, int smax) {
     extern __shared__ double sh[];
     double* xs = sh;
@@ -512,49 +778,49 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
         for (int j = tid; j < nb.m; j += NT) xn[nb.col + j] = y[nb.y + j];
     }
     __syncthreads();
-    const double* C = fac + T.cm;
+    const FT* C = fac + T.cm;
     const int lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
     for (int i0 = 2 * wid; i0 < f; i0 += 2 * nwarp) {
-        double a0 = 0.0, a1 = 0.0;
+        FT a0 = FT(0), a1 = FT(0);
         const bool two = i0 + 1 < f;
         for (int j = lane; j < T.ncols; j += 32) {
-            const double xj = xn[j];
+            const FT xj = (FT)xn[j];
             a0 += C[(int64_t)i0 * T.ncap + j] * xj;
             if (two) a1 += C[(int64_t)(i0 + 1) * T.ncap + j] * xj;
         }
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
+        const double s0 = warp_sum((double)a0);
+        const double s1 = warp_sum((double)a1);
         if (lane == 0) {
-            xs[r + i0] -= a0;
-            if (two) xs[r + i0 + 1] -= a1;
+            xs[r + i0] -= s0;
+            if (two) xs[r + i0 + 1] -= s1;
         }
     }
     __syncthreads();
-    const double* Wm = fac + T.w;
+    const FT* Wm = fac + T.w;
     if (s >= NT) {
         for (int jj = tid; jj < s; jj += NT) {
-            double a0 = 0.0, a1 = 0.0;
+            FT a0 = FT(0), a1 = FT(0);
             int i = 0;
             for (; i + 1 < s; i += 2) {
-                a0 += Wm[(int64_t)i * s + jj] * xs[i];
-                a1 += Wm[(int64_t)(i + 1) * s + jj] * xs[i + 1];
+                a0 += Wm[(int64_t)i * s + jj] * (FT)xs[i];
+                a1 += Wm[(int64_t)(i + 1) * s + jj] * (FT)xs[i + 1];
             }
-            if (i < s) a0 += Wm[(int64_t)i * s + jj] * xs[i];
-            yg[jj] = a0 + a1;
+            if (i < s) a0 += Wm[(int64_t)i * s + jj] * (FT)xs[i];
+            yg[jj] = (double)(a0 + a1);
         }
         return;
     }
     const int G = NT / s, g = tid / s, j = tid % s;
-    double a0 = 0.0, a1 = 0.0;
+    FT a0 = FT(0), a1 = FT(0);
     if (g < G) {
         int i = g;
         for (; i + G < s; i += 2 * G) {
-            a0 += Wm[(int64_t)i * s + j] * xs[i];
-            a1 += Wm[(int64_t)(i + G) * s + j] * xs[i + G];
+            a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
+            a1 += Wm[(int64_t)(i + G) * s + j] * (FT)xs[i + G];
         }
-        if (i < s) a0 += Wm[(int64_t)i * s + j] * xs[i];
+        if (i < s) a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
     }
-    part[tid] = a0 + a1;
+    part[tid] = (double)(a0 + a1);
     __syncthreads();
     if (tid < s) {
         double t = 0.0;
@@ -567,8 +833,9 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
 // Per-warp shared memory: the cluster's vector (kCoarseSmax doubles) and the
 // transformed vector / gathered neighbour values (kCoarseNmax doubles).
 
+template <typename FT>
 __device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPull* __restrict__ pulls,
-                          const double* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y,
+                          const FT* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y,
                           double* ys, double* yn) {
     const int s = act ? T.s : 0;
     for (int j = gl; j < s; j += gs) {
@@ -578,46 +845,47 @@ __device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPul
     }
     __syncwarp();
     if (act) {
-        const double* Wm = fac + T.w;
+        const FT* Wm = fac + T.w;
         for (int i = gl; i < s; i += gs) {
-            const double* wi = Wm + (int64_t)i * s;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            const FT* wi = Wm + (int64_t)i * s;
+            FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int j = 0;
             for (; j + 3 < s; j += 4) {
-                a0 += wi[j] * ys[j];
-                a1 += wi[j + 1] * ys[j + 1];
-                a2 += wi[j + 2] * ys[j + 2];
-                a3 += wi[j + 3] * ys[j + 3];
+                a0 += wi[j] * (FT)ys[j];
+                a1 += wi[j + 1] * (FT)ys[j + 1];
+                a2 += wi[j + 2] * (FT)ys[j + 2];
+                a3 += wi[j + 3] * (FT)ys[j + 3];
             }
-            for (; j < s; j++) a0 += wi[j] * ys[j];
-            yn[i] = (a0 + a1) + (a2 + a3);
+            for (; j < s; j++) a0 += wi[j] * (FT)ys[j];
+            yn[i] = (double)((a0 + a1) + (a2 + a3));
         }
     }
     __syncwarp();
     if (act) {
         for (int j = gl; j < s; j += gs) y[T.y + j] = yn[j];
         const int f = s - T.r;
-        const double* C = fac + T.cm;
+        const FT* C = fac + T.cm;
         const double* yf = yn + T.r;
         for (int j = gl; j < T.ncols; j += gs) {
-            const double* cj = C + j;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            const FT* cj = C + j;
+            FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int i = 0;
             for (; i + 3 < f; i += 4) {
-                a0 += cj[(int64_t)i * T.ncap] * yf[i];
-                a1 += cj[(int64_t)(i + 1) * T.ncap] * yf[i + 1];
-                a2 += cj[(int64_t)(i + 2) * T.ncap] * yf[i + 2];
-                a3 += cj[(int64_t)(i + 3) * T.ncap] * yf[i + 3];
+                a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
+                a1 += cj[(int64_t)(i + 1) * T.ncap] * (FT)yf[i + 1];
+                a2 += cj[(int64_t)(i + 2) * T.ncap] * (FT)yf[i + 2];
+                a3 += cj[(int64_t)(i + 3) * T.ncap] * (FT)yf[i + 3];
             }
-            for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * yf[i];
-            stage[T.stg + j] = (a0 + a1) + (a2 + a3);
+            for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
+            stage[T.stg + j] = (double)((a0 + a1) + (a2 + a3));
         }
     }
     __syncwarp();
 }
 
+template <typename FT>
 __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb* __restrict__ nbs,
-                          const double* __restrict__ fac, double* __restrict__ y, double* xs, double* xn) {
+                          const FT* __restrict__ fac, double* __restrict__ y, double* xs, double* xn) {
     const int s = act ? T.s : 0, r = T.r, f = s - r;
     for (int i = gl; i < s; i += gs) xs[i] = y[T.y + i];
     const int ncols = act ? T.ncols : 0;
@@ -627,35 +895,35 @@ __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb*
     }
     __syncwarp();
     if (act) {
-        const double* C = fac + T.cm;
+        const FT* C = fac + T.cm;
         for (int i = gl; i < f; i += gs) {
-            const double* ci = C + (int64_t)i * T.ncap;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            const FT* ci = C + (int64_t)i * T.ncap;
+            FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int j = 0;
             for (; j + 3 < ncols; j += 4) {
-                a0 += ci[j] * xn[j];
-                a1 += ci[j + 1] * xn[j + 1];
-                a2 += ci[j + 2] * xn[j + 2];
-                a3 += ci[j + 3] * xn[j + 3];
+                a0 += ci[j] * (FT)xn[j];
+                a1 += ci[j + 1] * (FT)xn[j + 1];
+                a2 += ci[j + 2] * (FT)xn[j + 2];
+                a3 += ci[j + 3] * (FT)xn[j + 3];
             }
-            for (; j < ncols; j++) a0 += ci[j] * xn[j];
-            xs[r + i] -= (a0 + a1) + (a2 + a3);
+            for (; j < ncols; j++) a0 += ci[j] * (FT)xn[j];
+            xs[r + i] -= (double)((a0 + a1) + (a2 + a3));
         }
     }
     __syncwarp();
     if (act) {
-        const double* Wm = fac + T.w;
+        const FT* Wm = fac + T.w;
         for (int j = gl; j < s; j += gs) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int i = 0;
             for (; i + 3 < s; i += 4) {
-                a0 += Wm[(int64_t)i * s + j] * xs[i];
-                a1 += Wm[(int64_t)(i + 1) * s + j] * xs[i + 1];
-                a2 += Wm[(int64_t)(i + 2) * s + j] * xs[i + 2];
-                a3 += Wm[(int64_t)(i + 3) * s + j] * xs[i + 3];
+                a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
+                a1 += Wm[(int64_t)(i + 1) * s + j] * (FT)xs[i + 1];
+                a2 += Wm[(int64_t)(i + 2) * s + j] * (FT)xs[i + 2];
+                a3 += Wm[(int64_t)(i + 3) * s + j] * (FT)xs[i + 3];
             }
-            for (; i < s; i++) a0 += Wm[(int64_t)i * s + j] * xs[i];
-            y[T.y + j] = (a0 + a1) + (a2 + a3);
+            for (; i < s; i++) a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
+            y[T.y + j] = (double)((a0 + a1) + (a2 + a3));
         }
     }
     __syncwarp();
@@ -665,6 +933,7 @@ __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb*
 // with __syncthreads between stages instead of kernel boundaries.  `off` is
 // added to every level vector, stage and top-vector address (a private
 // workspace per CTA when the chain is run on many right-hand sides at once).
+template <typename FT>
 __device__ void coarse_chain(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
                              double* __restrict__ ytop, int64_t off) {
     extern __shared__ double sh[];
@@ -680,7 +949,7 @@ __device__ void coarse_chain(const ApLevel* __restrict__ lvl, int nlev, int ntop
         double* yn = ys + kCoarseSmax;
         for (int ph = 0; ph < V.nph; ph++) {
             const int b = V.ph[ph], e = V.ph[ph + 1];
-            for (int t = b + wid; t < e; t += nwarp) group_fwd(true, V.tasks[t], lane, 32, V.pulls, V.fac, stg, yv, ys, yn);
+            for (int t = b + wid; t < e; t += nwarp) group_fwd<FT>(true, V.tasks[t], lane, 32, V.pulls, static_cast<const FT*>(V.fac), stg, yv, ys, yn);
             __syncthreads();
         }
         for (int k = wid; k < V.nfin; k += nwarp) {
@@ -721,21 +990,23 @@ __device__ void coarse_chain(const ApLevel* __restrict__ lvl, int nlev, int ntop
         __syncthreads();
         for (int ph = V.nph - 1; ph >= 0; ph--) {
             const int b = V.ph[ph], e = V.ph[ph + 1];
-            for (int t = b + wid; t < e; t += nwarp) group_bwd(true, V.tasks[t], lane, 32, V.nbs, V.fac, yv, xs, xn);
+            for (int t = b + wid; t < e; t += nwarp) group_bwd<FT>(true, V.tasks[t], lane, 32, V.nbs, static_cast<const FT*>(V.fac), yv, xs, xn);
             __syncthreads();
         }
     }
 }
 
+template <typename FT>
 __global__ void __launch_bounds__(kCoarseThreads)
 k_ap_coarse(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
             double* __restrict__ ytop) {
-    coarse_chain(lvl, nlev, ntop, Ltop, ytop, 0);
+    coarse_chain<FT>(lvl, nlev, ntop, Ltop, ytop, 0);
 }
 
 // Explicit coarse operator: CTA j runs the coarse chain on the unit vector e_j
 // in its own workspace (stride doubles apart) and writes the result as row j
 // of Mc (n x n; symmetric up to rounding).  yin0 is CTA 0's input vector.
+template <typename FT>
 __global__ void __launch_bounds__(kCoarseThreads)
 k_ap_coarse_batch(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
                   double* __restrict__ ytop, double* __restrict__ yin0, int n, int64_t stride,
@@ -744,7 +1015,7 @@ k_ap_coarse_batch(const ApLevel* __restrict__ lvl, int nlev, int ntop, const dou
     double* yin = yin0 + off;
     for (int i = threadIdx.x; i < n; i += blockDim.x) yin[i] = (i == (int)blockIdx.x) ? 1.0 : 0.0;
     __syncthreads();
-    coarse_chain(lvl, nlev, ntop, Ltop, ytop, off);
+    coarse_chain<FT>(lvl, nlev, ntop, Ltop, ytop, off);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) Mc[(int64_t)blockIdx.x * n + i] = yin[i];
 }
@@ -963,31 +1234,82 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
 
 size_t factor_smem_bytes(int smax, int wmax, int lmax) {
     return sizeof(double) * ((size_t)smax * smax + 2 * (size_t)smax + (size_t)wmax + 64) +
-           sizeof(int) * ((size_t)lmax + 1);
+           sizeof(EntryMeta) * (size_t)lmax + 2 * sizeof(int64_t) * (size_t)wmax + sizeof(int) * ((size_t)lmax + 1);
+}
+
+template <typename FT>
+cudaError_t factor_phase_t(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax, int wmax, int lmax,
+                           const ListDev* lists, double* blocks, const int64_t* blk_off, const int32_t* blk_ld,
+                           int32_t* cur, FT* fac, int32_t* meta, double* ws, double eps2, int32_t* status,
+                           int32_t level) {
+    const size_t smem = factor_smem_bytes(smax, wmax, lmax);
+    cudaError_t e = cudaFuncSetAttribute(k_factor_phase<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    counted();
+    k_factor_phase<FT><<<ntasks, kFactorThreads, smem, st>>>(tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta,
+                                                             ws, eps2, status, level, smax, wmax, lmax);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax, int wmax,
                                 int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
-                                const int32_t* blk_ld, int32_t* cur, double* fac, int32_t* meta, double* ws,
+                                const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta, double* ws,
                                 double eps2, int32_t* status, int32_t level) {
     if (ntasks <= 0) return cudaSuccess;
-    const size_t smem = factor_smem_bytes(smax, wmax, lmax);
-    cudaError_t e = cudaFuncSetAttribute(k_factor_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (fp32)
+        return factor_phase_t(st, tasks, t0, ntasks, smax, wmax, lmax, lists, blocks, blk_off, blk_ld, cur,
+                              static_cast<float*>(fac), meta, ws, eps2, status, level);
+    return factor_phase_t(st, tasks, t0, ntasks, smax, wmax, lmax, lists, blocks, blk_off, blk_ld, cur,
+                          static_cast<double*>(fac), meta, ws, eps2, status, level);
+}
+
+size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap) {
+    return sizeof(double) * (size_t)kFusedWarps * fused_warp_doubles(smax, wmax, lmax, mcap) +
+           sizeof(int) * (size_t)kFusedWarps * (lmax + 2);
+}
+
+cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, const int32_t* ph_task,
+                                      const TargetDev* targets, const int32_t* ph_target, const ContribDev* contribs,
+                                      int nph, const ListDev* lists, double* blocks, const int64_t* blk_off,
+                                      const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
+                                      double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
+                                      int lmax, int64_t mcap, int max_items, unsigned* bar) {
+    if (nph <= 0) return cudaSuccess;
+    const size_t smem = fused_smem_bytes(smax, wmax, lmax, mcap);
+    const void* fn = fp32 ? reinterpret_cast<const void*>(&k_factor_level_fused<float>)
+                          : reinterpret_cast<const void*>(&k_factor_level_fused<double>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFusedWarps * 32, smem)) != cudaSuccess)
+        return e;
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    // every CTA must be resident (grid barrier): at most per_sm * sms CTAs, and
+    // no more than the largest phase needs
+    const int want = (max_items + kFusedWarps - 1) / kFusedWarps;
+    const int grid = std::max(1, std::min(per_sm * sms, want));
+    if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
     counted();
-    k_factor_phase<<<ntasks, kFactorThreads, smem, st>>>(tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta,
-                                                         ws, eps2, status, level, smax, wmax);
-    return cudaGetLastError();
+    void* args[] = {&tasks,  &ph_task, &targets, &ph_target, &contribs, &nph,  &lists, &blocks,
+                    &blk_off, &blk_ld, &cur,     &fac,       &meta,     &ws,   &eps2,  &status,
+                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFusedWarps * 32), args, smem, st);
 }
 
 cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
-                               const ContribDev* contribs, const TaskDev* tasks, const double* fac,
+                               const ContribDev* contribs, const TaskDev* tasks, const void* fac,
                                const int32_t* meta, double* blocks, const int64_t* blk_off, const int32_t* blk_ld,
-                               const int32_t* cur, int precision) {
-    (void)precision;
+                               const int32_t* cur, int fp32) {
     if (ntargets <= 0) return cudaSuccess;
     counted();
-    k_schur_phase<<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur);
+    if (fp32)
+        k_schur_phase<float><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
+                                                       meta, blocks, blk_off, blk_ld, cur);
+    else
+        k_schur_phase<double><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const double*>(fac),
+                                                        meta, blocks, blk_off, blk_ld, cur);
     return cudaGetLastError();
 }
 
@@ -1006,10 +1328,16 @@ cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* st
 }
 
 cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax,
-                          const ApPull* pulls, const double* fac, double* stage, double* y) {
+                          const ApPull* pulls, const void* fac, int fp32, double* stage, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
-    k_ap_fwd<<<ntasks, kApplyThreads, sizeof(double) * 2 * smax, st>>>(tasks, t0, pulls, fac, stage, y, smax);
+    const size_t smem = sizeof(double) * 2 * smax;
+    if (fp32)
+        k_ap_fwd<float><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, pulls, static_cast<const float*>(fac), stage, y,
+                                                             smax);
+    else
+        k_ap_fwd<double><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, pulls, static_cast<const double*>(fac), stage,
+                                                              y, smax);
     return cudaGetLastError();
 }
 
@@ -1022,21 +1350,32 @@ cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const Ap
 }
 
 cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
-                          const ApNb* nbs, const double* fac, double* y) {
+                          const ApNb* nbs, const void* fac, int fp32, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
-    k_ap_bwd<<<ntasks, kApplyThreads, sizeof(double) * (smax + kApplyThreads + nmax), st>>>(tasks, t0, nbs, fac, y,
-                                                                                            smax);
+    const size_t smem = sizeof(double) * (smax + kApplyThreads + nmax);
+    if (fp32)
+        k_ap_bwd<float><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const float*>(fac), y, smax);
+    else
+        k_ap_bwd<double><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const double*>(fac), y, smax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
-                                   double* ytop0, double* yin0, int n, int64_t stride, double* Mc) {
+                                   double* ytop0, double* yin0, int n, int64_t stride, double* Mc, int fp32) {
     if (n <= 0) return cudaSuccess;
     counted();
-    const int threads = 256;
+    const int threads = 256;  // 4 CTAs per SM fit in registers: one wave for ~600 columns
     const size_t smem = sizeof(double) * (kCoarseSmax + kCoarseNmax) * (threads / 32);
-    k_ap_coarse_batch<<<n, threads, smem, st>>>(lvl, nlev, ntop, L, ytop0, yin0, n, stride, Mc);
+    cudaError_t e = fp32 ? cudaFuncSetAttribute(k_ap_coarse_batch<float>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                         : cudaFuncSetAttribute(k_ap_coarse_batch<double>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (fp32)
+        k_ap_coarse_batch<float><<<n, threads, smem, st>>>(lvl, nlev, ntop, L, ytop0, yin0, n, stride, Mc);
+    else
+        k_ap_coarse_batch<double><<<n, threads, smem, st>>>(lvl, nlev, ntop, L, ytop0, yin0, n, stride, Mc);
     return cudaGetLastError();
 }
 
@@ -1047,13 +1386,18 @@ cudaError_t launch_dense_gemv(cudaStream_t st, int n, const double* Mc, const do
     return cudaGetLastError();
 }
 
-cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L, double* ytop) {
+cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L, double* ytop,
+                             int fp32) {
     if (nlev <= 0 && ntop <= 0) return cudaSuccess;
     counted();
     const size_t smem = sizeof(double) * (kCoarseSmax + kCoarseNmax) * (kCoarseThreads / 32);
-    cudaError_t e = cudaFuncSetAttribute(k_ap_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = fp32 ? cudaFuncSetAttribute(k_ap_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem)
+                         : cudaFuncSetAttribute(k_ap_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem);
     if (e != cudaSuccess) return e;
-    k_ap_coarse<<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
+    if (fp32) k_ap_coarse<float><<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
+    else k_ap_coarse<double><<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ class hs_options(ctypes.Structure):
     _fields_ = [("tol", F64), ("depth", I32), ("leaf_lines", I32), ("theta", F64),
                 ("precision", I32), ("krylov", I32), ("restart", I32), ("rtol", F64),
                 ("maxit", I32), ("mem", I32), ("profile", I32), ("stream", P), ("coords", P),
-                ("coarse_dense", I32)]
+                ("coarse_dense", I32), ("fused_levels", I32)]
 
 
 class hs_info(ctypes.Structure):

@@ -129,6 +129,18 @@ def test_solve_phase_modes(hs, oracle_lib, coarse_dense):
     krylov_check(h, ref, p)
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+def test_fused_and_per_phase_levels(hs, oracle_lib, fused):
+    """Levels with clusters of at most 32 DOFs run all phases in one launch
+    (warp per cluster); the per-phase kernels (CTA per cluster) must give the
+    same decisions and operator."""
+    p = inputs.grid_operator(16, 16, 6, ratio=1e6, sigma=1.0, seed=8, bc="ice", shelf=0.5)
+    h, ref, depth = setup_both(hs, oracle_lib, p, 4, 1e-3, fused_levels=fused)
+    check_structure(h, ref, depth)
+    assert operator_diff(h, ref, p.n) <= max(1e-10, 100 * U * kappa(p))
+    krylov_check(h, ref, p)
+
+
 def test_dirichlet_16x16x8_workload(hs, oracle_lib):
     p = inputs.anisotropic_16x16x8()
     h, ref, depth = setup_both(hs, oracle_lib, p, 4, 1e-2)
@@ -204,3 +216,33 @@ def test_full_size_64x64x16_parity(hs, oracle_lib):
     d = operator_diff(h, ref, p.n, nvec=4)
     assert d <= 1e-8, d
     krylov_check(h, ref, p)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4])
+def test_mixed_precision_against_fp64(hs, oracle_lib, tol):
+    """Mixed form: FP32 Schur products and FP32 stored/applied factor, FP64
+    Cholesky, scaling, CPQR and Krylov residual.  Ranks may differ from FP64;
+    the bars are the true FP64 residual, the iteration count and the operator
+    difference relative to the FP64 GPU path (printed)."""
+    p = inputs.grid_operator(32, 32, 16, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
+    h64, ref, depth = setup_both(hs, oracle_lib, p, 6, tol)
+    h32, _, _ = setup_both(hs, oracle_lib, p, 6, tol, precision=hs.HS_PREC_MIXED)
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for _ in range(4):
+        r = dev(rng.uniform(-1, 1, p.n))
+        z64 = torch.empty_like(r)
+        z32 = torch.empty_like(r)
+        h64.hs_apply(r, z64)
+        h32.hs_apply(r, z32)
+        torch.cuda.synchronize()
+        worst = max(worst, float(torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64)))
+    x64 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    x32 = torch.empty_like(x64)
+    i64, _ = h64.hs_krylov(dev(p.b), x64)
+    i32, _ = h32.hs_krylov(dev(p.b), x32)
+    res = np.linalg.norm(p.b - p.matvec(x32.cpu().numpy())) / np.linalg.norm(p.b)
+    print(f"mixed vs fp64: operator diff {worst:.2e}, iterations {i32.iters} vs {i64.iters}, residual {res:.2e}")
+    assert worst <= 1e-3
+    assert res <= 1e-8 and i32.rel_resid <= 1e-8
+    assert i32.iters <= i64.iters + 2
