@@ -23,6 +23,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -188,6 +189,31 @@ void sorted_erase(std::vector<int>& v, int x) {
 }
 bool sorted_has(const std::vector<int>& v, int x) { return std::binary_search(v.begin(), v.end(), x); }
 
+// Run f(lo, hi, t) over [0, n) split into contiguous ranges on up to
+// hs_threads() host threads (the results never depend on the split).
+int hs_threads() {
+    static const int t = [] {
+        const unsigned h = std::thread::hardware_concurrency();
+        const char* e = std::getenv("HS_THREADS");
+        int v = e ? std::atoi(e) : (int)std::min(16u, std::max(1u, h));
+        return std::max(1, v);
+    }();
+    return t;
+}
+
+template <class F>
+void parallel_ranges(int64_t n, int64_t grain, F&& f) {
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / std::max<int64_t>(grain, 1)));
+    if (T <= 1) {
+        f((int64_t)0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; t++)
+        th.emplace_back([&, t] { f(n * t / T, n * (t + 1) / T, t); });
+    for (auto& x : th) x.join();
+}
+
 // ---------------------------------------------------------------------------
 // Partition (Sec. 4.2)
 // ---------------------------------------------------------------------------
@@ -234,10 +260,11 @@ struct Partitioner {
         return out;
     }
 
-    void split(std::vector<int> set, int depth) {
+    // leaf ids follow the depth-first order: the leaf below `set` at depth
+    // `depth` starts at `base` and the left half owns the first 2^(L-depth-1)
+    void split(std::vector<int> set, int depth, int base = 0) {
         if (depth == L) {
-            const int leaf = next_leaf++;
-            for (int x : set) leaf_of[x] = leaf;
+            for (int x : set) leaf_of[x] = base;
             return;
         }
         const size_t k = set.size(), left = (k + 1) / 2;
@@ -268,8 +295,15 @@ struct Partitioner {
             std::sort(a.begin(), a.end());
             std::sort(b.begin(), b.end());
         }
-        split(std::move(a), depth + 1);
-        split(std::move(b), depth + 1);
+        const int half = 1 << (L - depth - 1);
+        if (have_coords && depth < 3 && k > 4096) {  // top of the tree on two threads
+            std::thread left_thread([&] { split(std::move(a), depth + 1, base); });
+            split(std::move(b), depth + 1, base + half);
+            left_thread.join();
+        } else {
+            split(std::move(a), depth + 1, base);
+            split(std::move(b), depth + 1, base + half);
+        }
     }
 };
 
@@ -284,18 +318,27 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
         while (root[x] != x) { root[x] = root[root[x]]; x = root[x]; }
         return x;
     };
-    for (int i = 0; i < n; i++) {
-        double m = 0.0;
-        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++)
-            if (col[e] != i) m = std::max(m, std::fabs(val[e]));
-        if (m <= 0.0) continue;
-        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-            const int j = col[e];
-            if (j != i && std::fabs(val[e]) >= theta * m) {
-                const int a = find(i), b = find(j);
+    {
+        // strong edges found in parallel (row by row), unions applied after
+        std::vector<std::vector<std::pair<int, int>>> edges(hs_threads());
+        parallel_ranges(n, 4096, [&](int64_t lo, int64_t hi, int t) {
+            auto& ev = edges[t];
+            for (int64_t i = lo; i < hi; i++) {
+                double m = 0.0;
+                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++)
+                    if (col[e] != i) m = std::max(m, std::fabs(val[e]));
+                if (m <= 0.0) continue;
+                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                    const int j = col[e];
+                    if (j != i && std::fabs(val[e]) >= theta * m) ev.push_back({(int)i, j});
+                }
+            }
+        });
+        for (auto& ev : edges)
+            for (auto& pr : ev) {
+                const int a = find(pr.first), b = find(pr.second);
                 if (a != b) root[std::max(a, b)] = std::min(a, b);
             }
-        }
     }
     tr.mark("  partition: union-find");
     Partitioner P;
@@ -320,24 +363,43 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
             std::vector<int> pos(lptr.begin(), lptr.end() - 1);
             for (int i = 0; i < n; i++) ldof[pos[line_of[i]]++] = i;
         }
-        std::vector<int> stamp(nl, -1);
-        P.gptr.assign(nl + 1, 0);
-        P.gadj.clear();
-        P.gadj.reserve((size_t)nl * 8);
-        for (int l = 0; l < nl; l++) {
-            const size_t b = P.gadj.size();
-            for (int k = lptr[l]; k < lptr[l + 1]; k++) {
-                const int i = ldof[k];
-                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-                    const int lj = line_of[col[e]];
-                    if (lj != l && stamp[lj] != l) {
-                        stamp[lj] = l;
-                        P.gadj.push_back(lj);
+        // neighbour lines of each line, ranges of lines on separate threads
+        const int T = hs_threads();
+        std::vector<std::vector<int>> adj(T), cnt(T);
+        std::vector<int64_t> lo_of(T + 1, 0);
+        parallel_ranges(nl, 256, [&](int64_t lo, int64_t hi, int t) {
+            std::vector<int> stamp(nl, -1);
+            auto& a = adj[t];
+            auto& k = cnt[t];
+            lo_of[t] = lo;
+            for (int64_t l = lo; l < hi; l++) {
+                const size_t b = a.size();
+                for (int q = lptr[l]; q < lptr[l + 1]; q++) {
+                    const int i = ldof[q];
+                    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                        const int lj = line_of[col[e]];
+                        if (lj != l && stamp[lj] != (int)l) {
+                            stamp[lj] = (int)l;
+                            a.push_back(lj);
+                        }
                     }
                 }
+                std::sort(a.begin() + b, a.end());
+                k.push_back((int)(a.size() - b));
             }
-            std::sort(P.gadj.begin() + b, P.gadj.end());
-            P.gptr[l + 1] = (int)P.gadj.size();
+        });
+        P.gptr.assign(nl + 1, 0);
+        P.gadj.clear();
+        int64_t total = 0;
+        for (int t = 0; t < T; t++) total += (int64_t)adj[t].size();
+        P.gadj.reserve(total);
+        int l = 0;
+        for (int t = 0; t < T; t++) {
+            for (int k : cnt[t]) {
+                P.gptr[l + 1] = P.gptr[l] + k;
+                l++;
+            }
+            P.gadj.insert(P.gadj.end(), adj[t].begin(), adj[t].end());
         }
     }
     tr.mark("  partition: line graph");
@@ -357,9 +419,9 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     P.state.assign(P.nl, 0);
     std::vector<int> all(P.nl);
     for (int l = 0; l < P.nl; l++) all[l] = l;
-    P.split(std::move(all), 0);
+    P.split(std::move(all), 0, 0);
     tr.mark("  partition: bisection");
-    const int nleaf = P.next_leaf;
+    const int nleaf = 1 << L;
     leaf_ptr.assign(nleaf + 1, 0);
     for (int i = 0; i < n; i++) leaf_ptr[P.leaf_of[line_of[i]] + 1]++;
     for (int c = 0; c < nleaf; c++) leaf_ptr[c + 1] += leaf_ptr[c];
