@@ -144,6 +144,41 @@ int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info);
  * Allocates nothing: no cudaMalloc / cudaFree and no allocating library call. */
 int hs_krylov_noalloc(hs_handle h, const double* b, double* x, hs_info* info);
 
+/* Batched setup: nprob independent problems in one handle (no counterpart in
+ * the paper, which factors one operator; each problem gets exactly the
+ * factorization hs_setup would give it alone).  The problems come as one
+ * block-diagonal CSR of order n: problem p owns rows and columns
+ * prob_ptr[p] .. prob_ptr[p+1] (host array, nprob + 1 entries, prob_ptr[0] = 0,
+ * prob_ptr[nprob] = n, every problem non-empty) and no entry may couple two
+ * problems (else HS_ERR_ARG).  Each problem is partitioned on its own
+ * (options->coords rows of that problem, leaf_lines, theta) with its own
+ * default depth (or options->depth for all); every problem needs at least two
+ * leaves.  Level l of the handle holds level l of every problem that still
+ * has one (problem after problem), so each level of all problems is factored
+ * by the same launches, and a problem whose levels are done gets its own
+ * dense top.  hs_apply works on the whole block-diagonal system;
+ * hs_krylov / hs_krylov_batched run one PCG per problem (only
+ * HS_KRYLOV_PCG); hs_top_size gives the sum of the tops.  nprob <= 65535. */
+int hs_setup_batched(int32_t nprob, const int64_t* prob_ptr, int64_t n, const int64_t* rowptr,
+                     const int32_t* col, const double* val, const hs_options* opt, hs_handle* out,
+                     hs_info* info);
+
+/* PCG on every problem of a batched handle (x0 = 0; problem p stops when its
+ * own ||b_p - A_p x_p|| / ||b_p|| <= rtol, checked on the true residual).  All
+ * problems share each preconditioner apply and SpMV; the rest is per problem.
+ * b, x: device, n doubles.  iters, rel_resid: host arrays of nprob entries
+ * (may be NULL).  info: the largest count and residual over the problems.
+ * HS_ERR_NOCONV if some problem is still above rtol after maxit iterations;
+ * HS_ERR_UNSUPPORTED for a handle from hs_setup. */
+int hs_krylov_batched(hs_handle h, const double* b, double* x, int32_t* iters, double* rel_resid,
+                      hs_info* info);
+
+/* Problems in the handle (1 for hs_setup handles) and, for problem prob, its
+ * leaf range in the level-0 cluster numbering, its depth and its top size. */
+int hs_num_problems(hs_handle h, int32_t* nprob);
+int hs_problem_info(hs_handle h, int32_t prob, int32_t* leaf_lo, int32_t* leaf_hi, int32_t* depth,
+                    int32_t* ntop);
+
 /* Partition + setup + Krylov in one call; pointers in opt->mem. */
 int hs_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
              const double* b, double* x, const hs_options* opt, hs_info* info);

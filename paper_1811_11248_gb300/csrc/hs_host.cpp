@@ -14,6 +14,7 @@
 // input; eliminating a cluster's fine part creates a block between every pair
 // of its neighbours; a cluster with no fill block has rank 0 and leaves.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -201,10 +202,13 @@ int hs_threads() {
     return t;
 }
 
+// set on the worker threads of a batched partition: nested work stays serial
+thread_local bool tl_serial = false;
+
 template <class F>
 void parallel_ranges(int64_t n, int64_t grain, F&& f) {
     const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / std::max<int64_t>(grain, 1)));
-    if (T <= 1) {
+    if (T <= 1 || tl_serial) {
         f((int64_t)0, n, 0);
         return;
     }
@@ -296,7 +300,7 @@ struct Partitioner {
             std::sort(b.begin(), b.end());
         }
         const int half = 1 << (L - depth - 1);
-        if (have_coords && depth < 3 && k > 4096) {  // top of the tree on two threads
+        if (have_coords && depth < 3 && k > 4096 && !tl_serial) {  // top of the tree on two threads
             std::thread left_thread([&] { split(std::move(a), depth + 1, base); });
             split(std::move(b), depth + 1, base + half);
             left_thread.join();
@@ -577,7 +581,19 @@ struct Prof {
 }  // namespace
 
 struct hs_factor_s {
+    struct Group {  // one independent problem of the handle
+        int64_t leaf_lo, leaf_hi, dof_lo, dof_hi;
+        int depth;
+    };
     int64_t n = 0;
+    std::vector<Group> groups;
+    std::vector<int64_t> prob_ptr;  // DOF offsets of the problems (original order)
+    int64_t prob_maxlen = 0;
+    DBuf d_pp;
+    std::vector<DBuf> top_bufs;  // dense tops, one buffer per level at which problems end
+    std::vector<TopDev> tops;    // per problem
+    DBuf d_tops;
+    double* top_L = nullptr;     // the single problem's top (chain and dense coarse operator)
     int device = 0;
     cudaStream_t st = nullptr;
     hs_options opt{};
@@ -611,7 +627,13 @@ void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
     std::vector<int32_t> st;
     download(st, d_status.p, 3, h->st);
     if (st[0] == ST_NOT_SPD) {
-        if (info) { info->fail_level = st[1] < 0 ? h->depth : st[1]; info->fail_cluster = st[2]; }
+        if (info) {
+            // a dense top fails as (depth of its problem, problem index)
+            const bool top = st[1] < 0;
+            const int g = top && st[2] >= 0 && st[2] < (int)h->tops.size() ? h->tops[st[2]].pad : 0;
+            info->fail_level = top ? h->groups[g].depth : st[1];
+            info->fail_cluster = top ? g : st[2];
+        }
         throw HsError{HS_ERR_NOT_SPD};
     }
     if (st[0] == ST_TIMEOUT) throw HsError{HS_ERR_TIMEOUT};
@@ -921,20 +943,22 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
 // Coarse-vector copies from level l to the next level / the top: the
 // backward scatter (vcopy) and the forward end-of-level records (late
 // updates + gather); uploads the level's update list.
-void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& next_slot) {
+void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& dst_of, const std::vector<char>& to_top) {
     std::vector<VCopyDev> v;
     std::vector<ApFin> fins;
     for (int c = 0; c < L.nc; c++) {
         if (L.fin[c] <= 0) continue;
         VCopyDev x{};
         x.src = L.slot[c];
-        x.dst = next_slot[c / 2] + ((c & 1) ? L.fin[c - 1] : 0);
+        x.dst = dst_of[c];
         x.len = L.fin[c];
+        x.to_top = to_top[c];
         v.push_back(x);
         ApFin f{};
         f.y = L.slot[c];
         f.dst = x.dst;
         f.len = L.fin[c];
+        f.to_top = to_top[c];
         f.pull0 = (int)L.ap_pulls.size();
         for (auto& pk : L.late[c])
             L.ap_pulls.push_back(ApPull{L.stg[pk.first] + L.hmeta[L.tasks[pk.first].meta + 1 + 2 * pk.second]});
@@ -953,27 +977,31 @@ void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& next_slo
 // Block copies from level-l blocks (table T, final sizes fin, end pattern endp)
 // into the next level (table Tn) or, if Tn == nullptr, into the dense top
 // (row offsets top_off, leading dimension ntop).
+// Block copies from level-l blocks (table T, final sizes fin, end pattern
+// endp) into the parents: cluster a goes to parent par[a] at row offset
+// poff[a] (next level, table Tn, sizes nsize), or, when par[a] < 0, into its
+// problem's dense top at row tpos[a] of the matrix at tmat[a] (order tn[a]).
 std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& fin, const BlockTable& T,
-                                   const BlockTable* Tn, const std::vector<int>& nsize,
-                                   const std::vector<int64_t>& top_off, int ntop) {
+                                   const BlockTable* Tn, const std::vector<int>& nsize, const std::vector<int>& par,
+                                   const std::vector<int>& poff, const std::vector<int64_t>& tmat,
+                                   const std::vector<int64_t>& tpos, const std::vector<int>& tn, bool to_tops) {
     std::vector<CopyDev> cps;
     for (int a = 0; a < P.nc; a++) {
         if (fin[a] <= 0) continue;
-        const int A2 = a / 2, oa = (a & 1) ? fin[a - 1] : 0;
+        if ((par[a] < 0) != to_tops) continue;
         for (int b : P.endp[a]) {
             if (fin[b] <= 0) continue;
-            const int B2 = b / 2, ob = (b & 1) ? fin[b - 1] : 0;
             CopyDev c{};
             const int sb = T.find(a, b);
             c.src = T.off[sb];
             c.src_ld = T.ld[sb];
-            if (Tn) {
-                const int db = Tn->find(A2, B2);
-                c.dst = Tn->off[db] + (int64_t)oa * nsize[B2] + ob;
-                c.dst_ld = nsize[B2];
+            if (!to_tops) {
+                const int db = Tn->find(par[a], par[b]);
+                c.dst = Tn->off[db] + (int64_t)poff[a] * nsize[par[b]] + poff[b];
+                c.dst_ld = nsize[par[b]];
             } else {
-                c.dst = (top_off[A2] + oa) * (int64_t)ntop + top_off[B2] + ob;
-                c.dst_ld = ntop;
+                c.dst = tmat[a] + tpos[a] * (int64_t)tn[a] + tpos[b];
+                c.dst_ld = tn[a];
             }
             c.rows = fin[a];
             c.cols = fin[b];
@@ -984,6 +1012,64 @@ std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& f
 }
 
 void build_apply_graph(hs_factor_s* h);
+
+// Partitions every problem of a block-diagonal batch on its own (Sec. 4.2)
+// and concatenates the trees: problem p's leaves follow problem p-1's.
+void partition_batched(hs_factor_s* h, const int64_t* rp, const int32_t* cl, const double* vl,
+                       std::vector<int32_t>& leaf_ptr) {
+    const int np = (int)h->prob_ptr.size() - 1;
+    const int64_t* pp = h->prob_ptr.data();
+    std::vector<std::vector<int32_t>> perm(np), lp(np);
+    std::atomic<int> next{0}, bad{0};
+    auto work = [&] {
+        tl_serial = true;
+        std::vector<int64_t> srp;
+        std::vector<int32_t> scol;
+        for (int p = next++; p < np; p = next++) {
+            const int64_t lo = pp[p], hi = pp[p + 1], m = hi - lo;
+            srp.assign(m + 1, 0);
+            scol.clear();
+            for (int64_t i = lo; i < hi; i++) {
+                for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+                    if (cl[e] < lo || cl[e] >= hi) { bad = 1; break; }
+                    scol.push_back((int32_t)(cl[e] - lo));
+                }
+                srp[i - lo + 1] = (int64_t)scol.size();
+            }
+            if (bad) return;
+            partition_impl(m, srp.data(), scol.data(), vl + rp[lo], h->opt.coords ? h->opt.coords + 2 * lo : nullptr,
+                           h->opt.leaf_lines, h->opt.theta, perm[p], lp[p]);
+        }
+    };
+    {
+        const int T = std::min(hs_threads(), np);
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; t++) th.emplace_back(work);
+        work();
+        tl_serial = false;
+        for (auto& x : th) x.join();
+    }
+    if (bad) throw HsError{HS_ERR_ARG};  // an entry couples two problems
+    h->perm.resize(h->n);
+    leaf_ptr.assign(1, 0);
+    h->groups.clear();
+    for (int p = 0; p < np; p++) {
+        const int nleaf = (int)lp[p].size() - 1;
+        int depth = h->opt.depth;
+        if (depth < 0) {
+            int Lg = 0;
+            while ((1 << (Lg + 1)) <= nleaf) Lg++;
+            depth = std::max(nleaf >= 2 ? 1 : 0, Lg - 2);
+        }
+        // every problem needs one level at least: a lone leaf has none
+        if (depth < 1 || depth > 30 || nleaf % (1 << depth) != 0) throw HsError{HS_ERR_ARG};
+        hs_factor_s::Group G{(int64_t)leaf_ptr.size() - 1, 0, pp[p], pp[p + 1], depth};
+        for (int64_t k = 0; k < pp[p + 1] - pp[p]; k++) h->perm[pp[p] + k] = (int32_t)(perm[p][k] + pp[p]);
+        for (int c = 0; c < nleaf; c++) leaf_ptr.push_back((int32_t)(pp[p] + lp[p][c + 1]));
+        G.leaf_hi = (int64_t)leaf_ptr.size() - 1;
+        h->groups.push_back(G);
+    }
+}
 
 void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const double* val,
                 const hs_tree* tree_in, hs_info* info) {
@@ -1032,7 +1118,12 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     // partition tree
     std::vector<int32_t> leaf_ptr;
     int depth;
-    if (tree_in) {
+    const bool batched = !h->prob_ptr.empty();
+    if (batched) {
+        partition_batched(h, rp, cl, vl, leaf_ptr);
+        depth = 0;
+        for (const auto& G : h->groups) depth = std::max(depth, G.depth);
+    } else if (tree_in) {
         if (!tree_in->perm || !tree_in->leaf_ptr || tree_in->n_leaf <= 0) throw HsError{HS_ERR_ARG};
         h->perm.assign(tree_in->perm, tree_in->perm + n);
         leaf_ptr.assign(tree_in->leaf_ptr, tree_in->leaf_ptr + tree_in->n_leaf + 1);
@@ -1048,7 +1139,8 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         depth = std::max(nleaf >= 2 ? 1 : 0, Lg - 2);
     }
     if (leaf_ptr[0] != 0 || leaf_ptr[nleaf] != n) throw HsError{HS_ERR_ARG};
-    if (depth > 0 && (depth > 30 || nleaf % (1 << depth) != 0)) throw HsError{HS_ERR_ARG};
+    if (!batched && depth > 0 && (depth > 30 || nleaf % (1 << depth) != 0)) throw HsError{HS_ERR_ARG};
+    if (!batched) h->groups.assign(1, hs_factor_s::Group{0, nleaf, 0, n, depth});
     {
         std::vector<char> seen(n, 0);
         for (int64_t i = 0; i < n; i++) {
@@ -1138,31 +1230,130 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     tr.mark("level-0 scatter");
 
     h->lev.clear();
-    std::vector<int> fin = P.size0;  // depth 0: every cluster goes to the top as is
-    for (int l = 0; l < depth; l++) {
+    h->tops.clear();
+    h->top_bufs.clear();
+    int64_t ntop_total = 0;
+    // clusters of the current level: one contiguous range per problem still active
+    struct Active {
+        int g, lo, hi;
+    };
+    std::vector<Active> act;
+    {
+        int64_t base = 0;
+        for (int g = 0; g < (int)h->groups.size(); g++) {
+            const auto& G = h->groups[g];
+            if (G.depth >= 1) act.push_back(Active{g, (int)G.leaf_lo, (int)G.leaf_hi});
+            base += G.leaf_hi - G.leaf_lo;
+        }
+    }
+    if (act.empty()) {
+        // a single problem without levels: its level-0 matrix is the dense top
+        std::vector<int64_t> toff(P.nc + 1, 0);
+        for (int a = 0; a < P.nc; a++) toff[a + 1] = toff[a] + P.size0[a];
+        const int nt = (int)toff[P.nc];
+        h->top_bufs.emplace_back();
+        h->top_bufs.back().alloc(sizeof(double) * std::max<int64_t>((int64_t)nt * nt, 1));
+        CK(cudaMemsetAsync(h->top_bufs.back().p, 0, sizeof(double) * std::max<int64_t>((int64_t)nt * nt, 1), st));
+        std::vector<CopyDev> cps;
+        for (int a = 0; a < P.nc; a++)
+            for (int b : P.all[a]) {
+                CopyDev cp{};
+                const int sb = T.find(a, b);
+                cp.src = T.off[sb];
+                cp.src_ld = T.ld[sb];
+                cp.dst = toff[a] * (int64_t)nt + toff[b];
+                cp.dst_ld = nt;
+                cp.rows = P.size0[a];
+                cp.cols = P.size0[b];
+                cps.push_back(cp);
+            }
+        DBuf d_cps;
+        upload(d_cps, cps, st);
+        CK(launch_copy_blocks(st, d_cps.as<CopyDev>(), (int)cps.size(), blocks.as<double>(),
+                              h->top_bufs.back().as<double>()));
+        h->tops.push_back(TopDev{h->top_bufs.back().as<double>(), 0, nt, 0});
+        ntop_total = nt;
+    }
+    for (int l = 0; !act.empty(); l++) {
         h->lev.emplace_back(new Level());
         DBuf d_cur;
         upload(d_cur, P.size0, st);
         factor_level(h, l, P, T, blocks, d_cur, d_status, info);
         tr.mark("level factor (records+kernels)");
         Level& L = *h->lev[l];
-        fin = L.fin;
-        // next level (or the top)
-        const int nn = P.nc / 2;
-        std::vector<int> nsize(nn);
-        for (int c = 0; c < nn; c++) nsize[c] = fin[2 * c] + fin[2 * c + 1];
+        const std::vector<int>& fin = L.fin;
+        // parents: problems that go on get their sibling pairs merged at the
+        // next level; problems whose last level this was get a dense top
+        const int nc = P.nc;
+        std::vector<int> par(nc, -1), poff(nc, 0), tn(nc, 0);
+        std::vector<int64_t> tmat(nc, 0), tpos(nc, 0), dst(nc, 0);
+        std::vector<char> to_top(nc, 0);
+        std::vector<Active> nact;
+        std::vector<int> nsize;
+        struct Fin {
+            int g, lo, hi;
+            std::vector<int64_t> toff;
+            int n;
+            int64_t mat, vec;
+        };
+        std::vector<Fin> ending;
+        int64_t mat_total = 0;
+        for (const Active& a : act) {
+            const int cnt = a.hi - a.lo;
+            for (int cc = a.lo; cc < a.hi; cc++) poff[cc] = ((cc - a.lo) & 1) ? fin[cc - 1] : 0;
+            if (h->groups[a.g].depth > l + 1) {
+                const int nlo = (int)nsize.size();
+                for (int k = 0; k < cnt / 2; k++) nsize.push_back(fin[a.lo + 2 * k] + fin[a.lo + 2 * k + 1]);
+                for (int cc = a.lo; cc < a.hi; cc++) par[cc] = nlo + (cc - a.lo) / 2;
+                nact.push_back(Active{a.g, nlo, nlo + cnt / 2});
+            } else {
+                Fin f{a.g, a.lo, a.hi, std::vector<int64_t>(cnt / 2 + 1, 0), 0, 0, 0};
+                for (int k = 0; k < cnt / 2; k++)
+                    f.toff[k + 1] = f.toff[k] + fin[a.lo + 2 * k] + fin[a.lo + 2 * k + 1];
+                f.n = (int)f.toff[cnt / 2];
+                f.mat = mat_total;
+                mat_total += (int64_t)f.n * f.n;
+                f.vec = ntop_total;
+                ntop_total += f.n;
+                for (int cc = a.lo; cc < a.hi; cc++) {
+                    to_top[cc] = 1;
+                    tn[cc] = f.n;
+                    tmat[cc] = f.mat;
+                    tpos[cc] = f.toff[(cc - a.lo) / 2] + poff[cc];
+                    dst[cc] = f.vec + tpos[cc];
+                }
+                ending.push_back(std::move(f));
+            }
+        }
+        const int nn = (int)nsize.size();
         std::vector<int64_t> nslot(nn + 1, 0);
-        for (int c = 0; c < nn; c++) nslot[c + 1] = nslot[c] + nsize[c];
-        make_vcopies(h, L, nslot);
-        if (l + 1 < depth) {
+        for (int k = 0; k < nn; k++) nslot[k + 1] = nslot[k] + nsize[k];
+        for (int cc = 0; cc < nc; cc++)
+            if (par[cc] >= 0) dst[cc] = nslot[par[cc]] + poff[cc];
+        make_vcopies(h, L, dst, to_top);
+        if (!ending.empty()) {
+            // dense tops of the problems that end here
+            h->top_bufs.emplace_back();
+            DBuf& tb = h->top_bufs.back();
+            tb.alloc(sizeof(double) * std::max<int64_t>(mat_total, 1));
+            CK(cudaMemsetAsync(tb.p, 0, sizeof(double) * std::max<int64_t>(mat_total, 1), st));
+            std::vector<CopyDev> cps = make_assembly(P, fin, T, nullptr, nsize, par, poff, tmat, tpos, tn, true);
+            DBuf d_cps;
+            upload(d_cps, cps, st);
+            h->prof.begin(KC_TOP, st);
+            CK(launch_copy_blocks(st, d_cps.as<CopyDev>(), (int)cps.size(), blocks.as<double>(), tb.as<double>()));
+            h->prof.end(KC_TOP, st);
+            for (const Fin& f : ending) h->tops.push_back(TopDev{tb.as<double>() + f.mat, f.vec, f.n, f.g});
+        }
+        if (nn > 0) {
             LevelPlan Pn;
             Pn.nc = nn;
             Pn.size0 = nsize;
             Pn.adj0.assign(nn, {});
-            for (int a = 0; a < P.nc; a++) {
-                if (fin[a] <= 0) continue;
+            for (int a = 0; a < nc; a++) {
+                if (fin[a] <= 0 || par[a] < 0) continue;
                 for (int b : P.endp[a])
-                    if (fin[b] > 0 && a / 2 != b / 2) Pn.adj0[a / 2].push_back(b / 2);
+                    if (fin[b] > 0 && par[a] != par[b]) Pn.adj0[par[a]].push_back(par[b]);
             }
             for (auto& v : Pn.adj0) {
                 std::sort(v.begin(), v.end());
@@ -1175,7 +1366,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             DBuf nblocks;
             nblocks.alloc(sizeof(double) * std::max<int64_t>(Tn.total, 1));
             CK(cudaMemsetAsync(nblocks.p, 0, sizeof(double) * std::max<int64_t>(Tn.total, 1), st));
-            std::vector<CopyDev> cps = make_assembly(P, fin, T, &Tn, nsize, {}, 0);
+            std::vector<CopyDev> cps = make_assembly(P, fin, T, &Tn, nsize, par, poff, tmat, tpos, tn, false);
             DBuf d_cps;
             upload(d_cps, cps, st);
             h->prof.begin(KC_ASSEMBLY, st);
@@ -1187,52 +1378,28 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             P = std::move(Pn);
             T = std::move(Tn);
         }
+        act = std::move(nact);
         tr.mark("next-level plan+assembly");
     }
-    // dense top
-    {
-        std::vector<int> tsize;
-        const bool merge = depth > 0;
-        const int ntc = merge ? P.nc / 2 : P.nc;
-        tsize.resize(ntc);
-        for (int c = 0; c < ntc; c++) tsize[c] = merge ? fin[2 * c] + fin[2 * c + 1] : fin[c];
-        std::vector<int64_t> toff(ntc + 1, 0);
-        for (int c = 0; c < ntc; c++) toff[c + 1] = toff[c] + tsize[c];
-        h->ntop = (int)toff[ntc];
-        h->d_top.alloc(sizeof(double) * std::max<int64_t>((int64_t)h->ntop * h->ntop, 1));
-        h->d_ytop.alloc(sizeof(double) * std::max(h->ntop, 1));
-        if (h->ntop > 0) {
-            CK(cudaMemsetAsync(h->d_top.p, 0, sizeof(double) * (int64_t)h->ntop * h->ntop, st));
-            std::vector<CopyDev> cps;
-            if (merge) {
-                cps = make_assembly(P, fin, T, nullptr, tsize, toff, h->ntop);
-            } else {
-                for (int a = 0; a < P.nc; a++)
-                    for (int b : P.all[a]) {
-                        CopyDev c{};
-                        const int sb = T.find(a, b);
-                        c.src = T.off[sb];
-                        c.src_ld = T.ld[sb];
-                        c.dst = toff[a] * (int64_t)h->ntop + toff[b];
-                        c.dst_ld = h->ntop;
-                        c.rows = fin[a];
-                        c.cols = fin[b];
-                        cps.push_back(c);
-                    }
-            }
-            DBuf d_cps;
-            upload(d_cps, cps, st);
-            h->prof.begin(KC_TOP, st);
-            CK(launch_copy_blocks(st, d_cps.as<CopyDev>(), (int)cps.size(), blocks.as<double>(),
-                                  h->d_top.as<double>()));
-            CK(launch_dense_cholesky(st, h->ntop, h->d_top.as<double>(), d_status.as<int32_t>()));
-            h->prof.end(KC_TOP, st);
-            check_status(h, d_status, info);
-        }
+    // factor every dense top (one CTA per problem)
+    h->ntop = (int)ntop_total;
+    h->d_ytop.alloc(sizeof(double) * std::max<int64_t>(ntop_total, 1));
+    upload(h->d_tops, h->tops, st);
+    h->top_L = h->tops.empty() ? nullptr : h->tops[0].L;
+    if (h->groups.size() == 1 && !h->tops.empty()) h->ntop = h->tops[0].n;
+    if (ntop_total > 0) {
+        h->prof.begin(KC_TOP, st);
+        if (h->tops.size() == 1)
+            CK(launch_dense_cholesky(st, h->tops[0].n, h->tops[0].L, d_status.as<int32_t>()));
+        else
+            CK(launch_tops_cholesky(st, h->d_tops.as<TopDev>(), (int)h->tops.size(), d_status.as<int32_t>()));
+        h->prof.end(KC_TOP, st);
+        check_status(h, d_status, info);
     }
     blocks.release();
     // level vectors for the solve phase
-    int64_t fb = (int64_t)h->ntop * h->ntop * 8;
+    int64_t fb = 0;
+    for (const TopDev& tp : h->tops) fb += (int64_t)tp.n * tp.n * 8;
     for (auto& Lp : h->lev) {
         Lp->d_y.alloc(sizeof(double) * std::max<int64_t>(Lp->slot[Lp->nc], 1));
         fb += Lp->fac_doubles * (h->fp32 ? 4 : 8);
@@ -1276,16 +1443,21 @@ void enqueue_apply(hs_factor_s* h) {
                              h->fp32, L.d_stage.as<double>(), L.d_y.as<double>()));
         }
         CK(launch_ap_fin(st, L.d_ap_fins.as<ApFin>(), L.nfin, L.d_ap_pulls.as<ApPull>(), L.d_stage.as<double>(),
-                         L.d_y.as<double>(), next_of(l)));
+                         L.d_y.as<double>(), next_of(l), h->d_ytop.as<double>()));
     }
-    if (h->coarse_dense)
+    if (h->groups.size() > 1)  // every problem's dense top, one CTA each
+        CK(launch_tops_solve(st, h->d_tops.as<TopDev>(), (int)h->tops.size(), h->d_ytop.as<double>()));
+    else if (h->coarse_dense)
         CK(launch_dense_gemv(st, h->ncoarse, h->d_coarse.as<double>(), vec_of(lc), h->d_ycout.as<double>()));
     else
-        CK(launch_ap_coarse(st, h->d_aplevels.as<ApLevel>(), D - lc, h->ntop, h->d_top.as<double>(),
+        CK(launch_ap_coarse(st, h->d_aplevels.as<ApLevel>(), D - lc, h->ntop, h->top_L,
                             h->d_ytop.as<double>(), h->fp32));
     for (int l = lc - 1; l >= 0; l--) {
         Level& L = *h->lev[l];
-        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, back_of(l), L.d_y.as<double>(), 1));
+        // one problem: its top's solution sits where back_of points (the
+        // dense coarse operator's output, or the top vector)
+        CK(launch_vcopy(st, L.d_vcopy.as<VCopyDev>(), L.nvcopy, back_of(l), L.d_y.as<double>(), 1,
+                        h->groups.size() > 1 ? h->d_ytop.as<double>() : back_of(l)));
         for (int k = L.nstages - 1; k >= 0; k--) {
             const int t0 = L.ap_stage[k], nt = L.ap_stage[k + 1] - t0;
             CK(launch_ap_bwd(st, L.d_ap_tasks.as<ApTask>(), t0, nt, L.smax, L.nmax, L.d_ap_nbs.as<ApNb>(), L.d_fac.p,
@@ -1313,6 +1485,10 @@ void build_apply_graph(hs_factor_s* h) {
     }
     h->coarse_dense = ld >= 0;
     h->first_coarse = h->coarse_dense ? ld : lc0;
+    if (h->groups.size() > 1) {  // several problems: fine-level kernels down to the tops
+        h->coarse_dense = false;
+        h->first_coarse = D;
+    }
     if (std::getenv("HS_TRACE")) {
         for (size_t l = 0; l < h->lev.size(); l++)
             std::fprintf(stderr, "hs_trace level %zu: %d clusters, %d phases, %d solve stages, smax %d, ncap %d%s\n", l,
@@ -1375,7 +1551,7 @@ void build_apply_graph(hs_factor_s* h) {
         DBuf d_al;
         upload(d_al, al, h->st);
         h->prof.begin(KC_TOP, h->st);
-        CK(launch_ap_coarse_batch(h->st, d_al.as<ApLevel>(), (int)al.size(), h->ntop, h->d_top.as<double>(), ytop0,
+        CK(launch_ap_coarse_batch(h->st, d_al.as<ApLevel>(), (int)al.size(), h->ntop, h->top_L, ytop0,
                                   yin0, n, stride, h->d_coarse.as<double>(), h->fp32));
         h->prof.end(KC_TOP, h->st);
         CK(cudaStreamSynchronize(h->st));
@@ -1500,6 +1676,91 @@ int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
     info->iters = it;
     info->rel_resid = rn / bn;
     return rc;
+}
+
+// PCG on every problem of a batched handle at once: one preconditioner apply
+// and one SpMV per iteration serve all problems; scalars, stopping test and
+// true-residual restarts are per problem (each follows the single-problem
+// PCG above step for step).  iters / rel: host arrays, one entry per problem.
+int pcg_batched_impl(hs_factor_s* h, const double* b, double* x, int32_t* iters, double* rel, hs_info* info) {
+    cudaStream_t st = h->st;
+    const int64_t n = h->n;
+    const int np = (int)h->prob_ptr.size() - 1;
+    const int64_t ml = h->prob_maxlen;
+    const int64_t* pp = h->d_pp.as<int64_t>();
+    h->d_kv.ensure(sizeof(double) * 4 * n);
+    double* r = h->d_kv.as<double>();
+    double* z = r + n;
+    double* p = z + n;
+    double* q = p + n;
+    h->d_scal.ensure(sizeof(double) * kBScal * np + sizeof(int32_t) * (kBFlag * np + 4));
+    double* sc = h->d_scal.as<double>();
+    int32_t* fl = reinterpret_cast<int32_t*>(sc + (int64_t)kBScal * np);
+    int32_t* cnt = fl + (int64_t)kBFlag * np;
+    const double rtol = h->opt.rtol;
+    auto kr = [&](cudaError_t e) {
+        CK(e);
+    };
+    auto counts = [&]() {
+        int32_t v[2];
+        CK(cudaMemcpyAsync(v, cnt, sizeof(v), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return std::make_pair(v[0], v[1]);
+    };
+    h->prof.begin(KC_KRYLOV, st);
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    kr(launch_seg_dot(st, np, pp, b, b, sc, BS_BB));
+    kr(launch_bpcg_book(st, np, 0, rtol, sc, fl, cnt));
+    h->prof.end(KC_KRYLOV, st);
+    int active = counts().second;
+    int it = 0;
+    while (active > 0) {
+        apply_impl(h, r, z);
+        h->prof.begin(KC_KRYLOV, st);
+        kr(launch_seg_dot(st, np, pp, r, z, sc, BS_RZN));
+        kr(launch_bpcg_vec(st, 1, np, ml, pp, sc, fl, z, nullptr, p, nullptr));
+        kr(launch_bpcg_book(st, np, 1, rtol, sc, fl, cnt));
+        h->prof.end(KC_KRYLOV, st);
+        if (it >= h->opt.maxit) break;
+        h->prof.begin(KC_KRYLOV, st);
+        kr(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), p, q));
+        kr(launch_seg_dot(st, np, pp, p, q, sc, BS_PQ));
+        kr(launch_bpcg_vec(st, 0, np, ml, pp, sc, fl, p, q, x, r));
+        kr(launch_seg_dot(st, np, pp, r, r, sc, BS_RR));
+        kr(launch_bpcg_book(st, np, 2, rtol, sc, fl, cnt));
+        h->prof.end(KC_KRYLOV, st);
+        it++;
+        if (counts().first > 0) {
+            // true residual b - A x of every problem; the candidates stop or restart
+            h->prof.begin(KC_KRYLOV, st);
+            kr(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), x, q));
+            kr(launch_axpby(st, n, 1.0, b, -1.0, q));
+            kr(launch_seg_dot(st, np, pp, q, q, sc, BS_RRT));
+            kr(launch_bpcg_book(st, np, 3, rtol, sc, fl, cnt));
+            kr(launch_bpcg_vec(st, 2, np, ml, pp, sc, fl, q, nullptr, r, nullptr));
+            h->prof.end(KC_KRYLOV, st);
+            active = counts().second;
+        }
+    }
+    std::vector<double> hs((size_t)kBScal * np);
+    std::vector<int32_t> hf((size_t)kBFlag * np);
+    CK(cudaMemcpyAsync(hs.data(), sc, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hf.data(), fl, sizeof(int32_t) * hf.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    info->iters = 0;
+    info->rel_resid = 0.0;
+    bool all = true;
+    for (int k = 0; k < np; k++) {
+        const int32_t itk = hf[(size_t)k * kBFlag + BF_ITERS];
+        const double rk = hs[(size_t)k * kBScal + BS_REL];
+        if (iters) iters[k] = itk;
+        if (rel) rel[k] = rk;
+        info->iters = std::max(info->iters, itk);
+        info->rel_resid = std::max(info->rel_resid, rk);
+        if (hf[(size_t)k * kBFlag + BF_ACTIVE]) all = false;
+    }
+    return all ? HS_OK : HS_ERR_NOCONV;
 }
 
 int gmres_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
@@ -1783,6 +2044,87 @@ int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
     return HS_OK;
 }
 
+int hs_setup_batched(int32_t nprob, const int64_t* prob_ptr, int64_t n, const int64_t* rowptr, const int32_t* col,
+                     const double* val, const hs_options* opt, hs_handle* out, hs_info* info) {
+    if (!out) return HS_ERR_ARG;
+    *out = nullptr;
+    if (info) { std::memset(info, 0, sizeof(*info)); info->fail_level = -1; info->fail_cluster = -1; }
+    if (nprob <= 0 || nprob > 65535 || !prob_ptr || n <= 0 || n > INT32_MAX || !rowptr || !col || !val || !opt)
+        return HS_ERR_ARG;
+    if (prob_ptr[0] != 0 || prob_ptr[nprob] != n) return HS_ERR_ARG;
+    for (int p = 0; p < nprob; p++)
+        if (prob_ptr[p + 1] <= prob_ptr[p]) return HS_ERR_ARG;
+    if (!(opt->tol >= 0.0) || opt->leaf_lines <= 0 || (opt->mem != HS_MEM_HOST && opt->mem != HS_MEM_DEVICE) ||
+        (opt->precision != HS_PREC_FP64 && opt->precision != HS_PREC_MIXED))
+        return HS_ERR_ARG;
+    hs_factor_s* h = new (std::nothrow) hs_factor_s();
+    if (!h) return HS_ERR_OOM;
+    h->n = n;
+    h->opt = *opt;
+    h->st = static_cast<cudaStream_t>(opt->stream);
+    h->prof.on = opt->profile != 0;
+    h->fp32 = opt->precision == HS_PREC_MIXED ? 1 : 0;
+    h->prob_ptr.assign(prob_ptr, prob_ptr + nprob + 1);
+    for (int p = 0; p < nprob; p++) h->prob_maxlen = std::max(h->prob_maxlen, prob_ptr[p + 1] - prob_ptr[p]);
+    const double t0 = now_s();
+    g_alloc_stream = h->st;
+    prepare_pool();
+    const int rc = run_guarded([&] {
+        CK(cudaGetDevice(&h->device));
+        upload(h->d_pp, h->prob_ptr, h->st);
+        setup_impl(h, rowptr, col, val, nullptr, info);
+        h->prof.collect();
+    });
+    if (rc != HS_OK) {
+        delete h;
+        return rc;
+    }
+    if (info) {
+        info->setup_s = now_s() - t0;
+        info->factor_bytes = h->factor_bytes;
+    }
+    *out = h;
+    return HS_OK;
+}
+
+int hs_krylov_batched(hs_handle h, const double* b, double* x, int32_t* iters, double* rel_resid, hs_info* info) {
+    if (!h || !b || !x) return HS_ERR_ARG;
+    if (h->prob_ptr.empty()) return HS_ERR_UNSUPPORTED;
+    if (h->opt.krylov != HS_KRYLOV_PCG) return HS_ERR_UNSUPPORTED;
+    hs_info tmp{};
+    hs_info* inf = info ? info : &tmp;
+    const double t0 = now_s();
+    int krc = HS_OK;
+    g_alloc_stream = h->st;
+    const int rc = run_guarded([&] {
+        krc = pcg_batched_impl(h, b, x, iters, rel_resid, inf);
+        CK(cudaStreamSynchronize(h->st));
+        h->prof.collect();
+    });
+    inf->solve_s = now_s() - t0;
+    return rc != HS_OK ? rc : krc;
+}
+
+int hs_num_problems(hs_handle h, int32_t* nprob) {
+    if (!h || !nprob) return HS_ERR_ARG;
+    *nprob = h->prob_ptr.empty() ? 1 : (int32_t)h->prob_ptr.size() - 1;
+    return HS_OK;
+}
+
+int hs_problem_info(hs_handle h, int32_t prob, int32_t* leaf_lo, int32_t* leaf_hi, int32_t* depth, int32_t* ntop) {
+    if (!h || prob < 0 || prob >= (int32_t)h->groups.size()) return HS_ERR_ARG;
+    const auto& G = h->groups[prob];
+    if (leaf_lo) *leaf_lo = (int32_t)G.leaf_lo;
+    if (leaf_hi) *leaf_hi = (int32_t)G.leaf_hi;
+    if (depth) *depth = G.depth;
+    if (ntop) {
+        *ntop = 0;
+        for (const TopDev& t : h->tops)
+            if (t.pad == prob) *ntop = t.n;
+    }
+    return HS_OK;
+}
+
 int hs_apply(hs_handle h, const double* r, double* z) {
     if (!h || !r || !z || r == z) return HS_ERR_ARG;
     return run_guarded([&] { apply_impl(h, r, z); });
@@ -1796,7 +2138,11 @@ int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info) {
     int krc = HS_OK;
     g_alloc_stream = h->st;
     const int rc = run_guarded([&] {
-        krc = h->opt.krylov == HS_KRYLOV_GMRES ? gmres_impl(h, b, x, inf) : pcg_impl(h, b, x, inf);
+        if (!h->prob_ptr.empty())
+            krc = h->opt.krylov == HS_KRYLOV_PCG ? pcg_batched_impl(h, b, x, nullptr, nullptr, inf)
+                                                 : (int)HS_ERR_UNSUPPORTED;
+        else
+            krc = h->opt.krylov == HS_KRYLOV_GMRES ? gmres_impl(h, b, x, inf) : pcg_impl(h, b, x, inf);
         CK(cudaStreamSynchronize(h->st));
         h->prof.collect();
     });

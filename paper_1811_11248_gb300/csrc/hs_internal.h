@@ -12,10 +12,20 @@ namespace hs {
 // One cluster elimination ("scaled low-rank elimination", Sec. 3.1) of a
 // phase.  Column blocks of the cluster's row are listed n-neighbours first,
 // then fill ("w") blocks, each with its current width read on the device.
-// Vector slice copy (coarse parts between levels).
+// Vector slice copy (coarse parts between levels).  to_top: the destination is
+// the top vector (the cluster's problem ends at this level) instead of the next
+// level's vector.
 struct VCopyDev {
     int64_t src, dst;
-    int32_t len, pad;
+    int32_t len, to_top;
+};
+
+// Dense top of one problem: L (n x n, row-major, lower after factorization)
+// and the offset of its vector in the top vector.
+struct TopDev {
+    double* L;
+    int64_t vec_off;
+    int32_t n, pad;
 };
 
 struct TaskDev {
@@ -58,7 +68,7 @@ struct ApNb {
 // updates of tasks processed after it, copy the coarse part to the parent slot.
 struct ApFin {
     int64_t y, dst;
-    int32_t len, pull0, pull1, pad;
+    int32_t len, pull0, pull1, to_top;
 };
 // One level of the single-CTA coarse-levels kernel.
 struct ApLevel {
@@ -121,7 +131,7 @@ cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* st
 cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax,
                           const ApPull* pulls, const void* fac, int fp32, double* stage, double* y);
 cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const ApPull* pulls, const double* stage,
-                          double* y, double* ynext);
+                          double* y, double* ynext, double* ytop);
 cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
                           const ApNb* nbs, const void* fac, int fp32, double* y);
 // levels lvl[0..nlev) forward, dense top, then backward, in one CTA
@@ -135,7 +145,10 @@ cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev
                                    double* ytop0, double* yin0, int n, int64_t stride, double* Mc, int fp32);
 cudaError_t launch_dense_gemv(cudaStream_t st, int n, const double* Mc, const double* x, double* y);
 cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
-                         int reverse);
+                         int reverse, const double* ytop);
+// dense tops of several problems: Cholesky / forward+backward solve, one CTA each
+cudaError_t launch_tops_cholesky(cudaStream_t st, const TopDev* tops, int ntops, int32_t* status);
+cudaError_t launch_tops_solve(cudaStream_t st, const TopDev* tops, int ntops, double* ytop);
 cudaError_t launch_top_solve(cudaStream_t st, int n, const double* L, double* y);
 cudaError_t launch_permute(cudaStream_t st, int64_t n, const int32_t* perm, const double* src, double* dst,
                            int inverse);
@@ -150,6 +163,20 @@ cudaError_t launch_pcg_update_xr(cudaStream_t st, int64_t n, const double* rz, c
 cudaError_t launch_pcg_update_p(cudaStream_t st, int64_t n, const double* rz_new, const double* rz_old,
                                 const double* z, double* p);
 cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y);
+// batched PCG over independent problems (segments pp[p] .. pp[p+1])
+constexpr int kBScal = 8;  // per-problem scalars
+enum { BS_RZ = 0, BS_PQ = 1, BS_RZN = 2, BS_RR = 3, BS_BB = 4, BS_RRT = 5, BS_REL = 6 };
+constexpr int kBFlag = 4;  // per-problem flags
+enum { BF_ACTIVE = 0, BF_RESTART = 1, BF_CAND = 2, BF_ITERS = 3 };
+cudaError_t launch_seg_dot(cudaStream_t st, int nprob, const int64_t* pp, const double* a, const double* b,
+                           double* sc, int slot);
+// op 0: x(c) += alpha p(a), r(d) -= alpha q(b); op 1: p(c) = z(a) + beta p(c);
+// op 2: r(c) = q(a) where restarted.  Grid: (maxlen / 256, nprob).
+cudaError_t launch_bpcg_vec(cudaStream_t st, int op, int nprob, int64_t maxlen, const int64_t* pp, const double* sc,
+                            const int32_t* fl, const double* a, const double* b, double* c, double* d);
+cudaError_t launch_bpcg_book(cudaStream_t st, int nprob, int mode, double rtol, double* sc, int32_t* fl,
+                             int32_t* cnt);
+
 cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double* coef, const double* V,
                                 int64_t ldv, double* y, double sign);
 cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv,

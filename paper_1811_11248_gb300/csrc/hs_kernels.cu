@@ -750,13 +750,14 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
 // End of a level's forward solve, one CTA per cluster with a coarse part.
 __global__ void __launch_bounds__(kApplyThreads)
 k_ap_fin(const ApFin* __restrict__ fins, const ApPull* __restrict__ pulls, const double* __restrict__ stage,
-         double* __restrict__ y, double* __restrict__ ynext) {
+         double* __restrict__ y, double* __restrict__ ynext, double* __restrict__ ytop) {
     const ApFin F = fins[blockIdx.x];
+    double* dst = (F.to_top ? ytop : ynext) + F.dst;
     for (int j = threadIdx.x; j < F.len; j += blockDim.x) {
         double v = y[F.y + j];
         for (int pi = F.pull0; pi < F.pull1; pi++) v -= stage[pulls[pi].off + j];
         y[F.y + j] = v;
-        ynext[F.dst + j] = v;
+        dst[j] = v;
     }
 }
 
@@ -1038,14 +1039,77 @@ __global__ void __launch_bounds__(256) k_dense_gemv(int n, const double* __restr
     if (lane == 0) y[row] = t;
 }
 
+// reverse: y_level[src] <- (to_top ? ytop : y_next)[dst]; forward the other way
 __global__ void k_vcopy(const VCopyDev* __restrict__ cps, int ncps, const double* __restrict__ src,
-                        double* __restrict__ dst, int reverse) {
+                        double* __restrict__ dst, int reverse, const double* __restrict__ ytop) {
     const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (c >= ncps) return;
     const VCopyDev v = cps[c];
+    const double* from = (reverse && v.to_top) ? ytop : src;
     for (int i = threadIdx.x & 31; i < v.len; i += 32) {
-        if (reverse) dst[v.src + i] = src[v.dst + i];
+        if (reverse) dst[v.src + i] = from[v.dst + i];
         else dst[v.dst + i] = src[v.src + i];
+    }
+}
+
+// Dense Cholesky of every top (one CTA per problem), status like the factor.
+__global__ void __launch_bounds__(256) k_tops_cholesky(const TopDev* __restrict__ tops, int32_t* status) {
+    __shared__ int flag;
+    __shared__ double rd;
+    const TopDev tp = tops[blockIdx.x];
+    const int n = tp.n, tid = threadIdx.x, NT = blockDim.x;
+    double* a = tp.L;
+    if (tid == 0) flag = 0;
+    for (int j = 0; j < n; j++) {
+        __syncthreads();
+        if (tid == 0) {
+            const double d = a[(int64_t)j * n + j];
+            if (!(d > 0.0)) flag = 1;
+            else {
+                a[(int64_t)j * n + j] = sqrt(d);
+                rd = 1.0 / sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (flag) {
+            if (tid == 0 && atomicCAS(status, 0, ST_NOT_SPD) == 0) {
+                status[1] = -1;
+                status[2] = blockIdx.x;
+            }
+            return;
+        }
+        for (int i = j + 1 + tid; i < n; i += NT) a[(int64_t)i * n + j] *= rd;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int idx = tid; idx < m * m; idx += NT) {
+            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
+            if (k <= i) a[(int64_t)i * n + k] -= a[(int64_t)i * n + j] * a[(int64_t)k * n + j];
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += NT)
+        if (idx % n > idx / n) a[idx] = 0.0;
+}
+
+// y <- L^-T L^-1 y for every top (one CTA per problem).
+__global__ void __launch_bounds__(256) k_tops_solve(const TopDev* __restrict__ tops, double* __restrict__ ytop) {
+    const TopDev tp = tops[blockIdx.x];
+    const int n = tp.n, tid = threadIdx.x, NT = blockDim.x;
+    const double* L = tp.L;
+    double* y = ytop + tp.vec_off;
+    for (int k = 0; k < n; k++) {
+        __syncthreads();
+        const double yk = y[k] / L[(int64_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) y[k] = yk;
+        for (int i = k + 1 + tid; i < n; i += NT) y[i] -= L[(int64_t)i * n + k] * yk;
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        __syncthreads();
+        const double yk = y[k] / L[(int64_t)k * n + k];
+        __syncthreads();
+        if (tid == 0) y[k] = yk;
+        for (int i = tid; i < k; i += NT) y[i] -= L[(int64_t)k * n + i] * yk;
     }
 }
 
@@ -1123,6 +1187,95 @@ __global__ void k_pcg_p(int64_t n, const double* __restrict__ rzn, const double*
     if (i >= n) return;
     const double beta = *rzn / *rzo;
     p[i] = z[i] + beta * p[i];
+}
+
+// ---- batched PCG: independent problems on one block-diagonal system ----
+// Problem p owns entries pp[p] .. pp[p+1] of every vector; its scalars are
+// sc[p * kBScal + slot] and its flags fl[p * kBFlag + slot] (BF_* slots).
+
+// sc[p][slot] = a_p . b_p, one CTA per problem (fixed summation order).
+__global__ void __launch_bounds__(256) k_seg_dot(const int64_t* __restrict__ pp, const double* __restrict__ a,
+                                                 const double* __restrict__ b, double* __restrict__ sc, int slot) {
+    __shared__ double red[32];
+    const int p = blockIdx.x;
+    const int64_t lo = pp[p], hi = pp[p + 1];
+    double t = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) t += a[i] * b[i];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) sc[(int64_t)p * kBScal + slot] = t;
+}
+
+// x += alpha p, r -= alpha q on the active problems (alpha = rz / pq).
+__global__ void k_bpcg_xr(const int64_t* __restrict__ pp, const double* __restrict__ sc,
+                          const int32_t* __restrict__ fl, const double* __restrict__ p,
+                          const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
+    const int pr = blockIdx.y;
+    if (!fl[pr * kBFlag + BF_ACTIVE]) return;
+    const int64_t i = pp[pr] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pp[pr + 1]) return;
+    const double alpha = sc[pr * kBScal + BS_RZ] / sc[pr * kBScal + BS_PQ];
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+}
+
+// p = z + beta p on the active problems (beta = rz_new / rz, 0 on a restart).
+__global__ void k_bpcg_p(const int64_t* __restrict__ pp, const double* __restrict__ sc,
+                         const int32_t* __restrict__ fl, const double* __restrict__ z, double* __restrict__ p) {
+    const int pr = blockIdx.y;
+    if (!fl[pr * kBFlag + BF_ACTIVE]) return;
+    const int64_t i = pp[pr] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pp[pr + 1]) return;
+    const double beta = fl[pr * kBFlag + BF_RESTART] ? 0.0 : sc[pr * kBScal + BS_RZN] / sc[pr * kBScal + BS_RZ];
+    p[i] = z[i] + beta * p[i];
+}
+
+// r_p = q_p for the problems restarted from their true residual.
+__global__ void k_bpcg_restart_copy(const int64_t* __restrict__ pp, const int32_t* __restrict__ fl,
+                                    const double* __restrict__ q, double* __restrict__ r) {
+    const int pr = blockIdx.y;
+    if (!fl[pr * kBFlag + BF_ACTIVE] || !fl[pr * kBFlag + BF_RESTART]) return;
+    const int64_t i = pp[pr] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pp[pr + 1]) return;
+    r[i] = q[i];
+}
+
+// Per-problem bookkeeping, one CTA.  mode 0: start (active = b != 0,
+// restart = 1); 1: after the p update (rz = rz_new, restart = 0); 2: after
+// the x, r update (iteration count, candidates whose recursive residual is
+// below rtol); 3: true-residual check of the candidates (done, or restart).
+// cnt[0] = candidates, cnt[1] = active problems afterwards.
+__global__ void __launch_bounds__(256) k_bpcg_book(int nprob, int mode, double rtol, double* __restrict__ sc,
+                                                   int32_t* __restrict__ fl, int32_t* __restrict__ cnt) {
+    __shared__ int s_cand, s_act;
+    if (threadIdx.x == 0) { s_cand = 0; s_act = 0; }
+    __syncthreads();
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+        double* s = sc + (int64_t)p * kBScal;
+        int32_t* f = fl + (int64_t)p * kBFlag;
+        if (mode == 0) {
+            f[BF_ACTIVE] = s[BS_BB] > 0.0;
+            f[BF_RESTART] = 1;
+            f[BF_CAND] = 0;
+            f[BF_ITERS] = 0;
+            s[BS_REL] = 0.0;
+        } else if (mode == 1) {
+            if (f[BF_ACTIVE]) { s[BS_RZ] = s[BS_RZN]; f[BF_RESTART] = 0; }
+        } else if (mode == 2) {
+            if (f[BF_ACTIVE]) {
+                f[BF_ITERS] += 1;
+                s[BS_REL] = sqrt(s[BS_RR] / s[BS_BB]);
+                if (s[BS_REL] <= rtol) { f[BF_CAND] = 1; atomicAdd(&s_cand, 1); }
+            }
+        } else if (f[BF_ACTIVE] && f[BF_CAND]) {
+            f[BF_CAND] = 0;
+            s[BS_REL] = sqrt(s[BS_RRT] / s[BS_BB]);
+            if (s[BS_REL] <= rtol) f[BF_ACTIVE] = 0;
+            else f[BF_RESTART] = 1;
+        }
+        if (f[BF_ACTIVE]) atomicAdd(&s_act, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { cnt[0] = s_cand; cnt[1] = s_act; }
 }
 
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
@@ -1342,10 +1495,10 @@ cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntas
 }
 
 cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const ApPull* pulls, const double* stage,
-                          double* y, double* ynext) {
+                          double* y, double* ynext, double* ytop) {
     if (nfin <= 0) return cudaSuccess;
     counted();
-    k_ap_fin<<<nfin, kApplyThreads, 0, st>>>(fins, pulls, stage, y, ynext);
+    k_ap_fin<<<nfin, kApplyThreads, 0, st>>>(fins, pulls, stage, y, ynext, ytop);
     return cudaGetLastError();
 }
 
@@ -1402,10 +1555,24 @@ cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int 
 }
 
 cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
-                         int reverse) {
+                         int reverse, const double* ytop) {
     if (ncps <= 0) return cudaSuccess;
     counted();
-    k_vcopy<<<blocks_for(ncps, 8), 256, 0, st>>>(cps, ncps, src, dst, reverse);
+    k_vcopy<<<blocks_for(ncps, 8), 256, 0, st>>>(cps, ncps, src, dst, reverse, ytop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tops_cholesky(cudaStream_t st, const TopDev* tops, int ntops, int32_t* status) {
+    if (ntops <= 0) return cudaSuccess;
+    counted();
+    k_tops_cholesky<<<ntops, 256, 0, st>>>(tops, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tops_solve(cudaStream_t st, const TopDev* tops, int ntops, double* ytop) {
+    if (ntops <= 0) return cudaSuccess;
+    counted();
+    k_tops_solve<<<ntops, 256, 0, st>>>(tops, ytop);
     return cudaGetLastError();
 }
 
@@ -1451,6 +1618,33 @@ cudaError_t launch_pcg_update_p(cudaStream_t st, int64_t n, const double* rz_new
                                 const double* z, double* p) {
     counted();
     k_pcg_p<<<blocks_for(n, 256), 256, 0, st>>>(n, rz_new, rz_old, z, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_dot(cudaStream_t st, int nprob, const int64_t* pp, const double* a, const double* b,
+                           double* sc, int slot) {
+    if (nprob <= 0) return cudaSuccess;
+    counted();
+    k_seg_dot<<<nprob, 256, 0, st>>>(pp, a, b, sc, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bpcg_vec(cudaStream_t st, int op, int nprob, int64_t maxlen, const int64_t* pp, const double* sc,
+                            const int32_t* fl, const double* a, const double* b, double* c, double* d) {
+    if (nprob <= 0 || maxlen <= 0) return cudaSuccess;
+    if (nprob > 65535) return cudaErrorInvalidValue;
+    counted();
+    const dim3 grid((unsigned)blocks_for(maxlen, 256), (unsigned)nprob);
+    if (op == 0) k_bpcg_xr<<<grid, 256, 0, st>>>(pp, sc, fl, a, b, c, d);
+    else if (op == 1) k_bpcg_p<<<grid, 256, 0, st>>>(pp, sc, fl, a, c);
+    else k_bpcg_restart_copy<<<grid, 256, 0, st>>>(pp, fl, a, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bpcg_book(cudaStream_t st, int nprob, int mode, double rtol, double* sc, int32_t* fl,
+                             int32_t* cnt) {
+    counted();
+    k_bpcg_book<<<1, 256, 0, st>>>(nprob, mode, rtol, sc, fl, cnt);
     return cudaGetLastError();
 }
 

@@ -84,6 +84,11 @@ def lib():
     L.hs_reset_kernel_stats.argtypes = [P]
     L.hs_measure_fp64_peak.argtypes = [P, ctypes.POINTER(F64)]
     L.hs_launch_count.argtypes = [ctypes.POINTER(I64)]
+    L.hs_setup_batched.argtypes = [I32, P, I64, P, P, P, ctypes.POINTER(hs_options), ctypes.POINTER(P),
+                                   ctypes.POINTER(hs_info)]
+    L.hs_krylov_batched.argtypes = [P, P, P, P, P, ctypes.POINTER(hs_info)]
+    L.hs_num_problems.argtypes = [P, ctypes.POINTER(I32)]
+    L.hs_problem_info.argtypes = [P, I32, P, P, P, P]
     L.hs_status_str.argtypes = [ctypes.c_int]
     L.hs_status_str.restype = ctypes.c_char_p
     _lib = L
@@ -94,7 +99,8 @@ def lib():
 EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_setup", "hs_apply",
             "hs_krylov", "hs_krylov_noalloc", "hs_solve", "hs_destroy", "hs_num_levels", "hs_level_clusters",
             "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
-            "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str")
+            "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str", "hs_setup_batched",
+            "hs_krylov_batched", "hs_num_problems", "hs_problem_info")
 
 
 def _ptr(x):
@@ -211,6 +217,28 @@ class Handle:
         return {name: dict(ms=float(t[i]), launches=int(n[i]), flops=float(f[i]), bytes=float(b[i]))
                 for i, name in enumerate(KERNEL_CLASSES)}
 
+    def hs_krylov_batched(self, b, x, check=True):
+        """-> (info, rc, iters int32[nprob], rel_resid float64[nprob])."""
+        npb = self.num_problems()
+        it = np.zeros(npb, np.int32)
+        rr = np.zeros(npb)
+        info = hs_info()
+        rc = lib().hs_krylov_batched(self._h, _ptr(b), _ptr(x), _ptr(it), _ptr(rr), ctypes.byref(info))
+        if check:
+            _check(rc, "hs_krylov_batched", info)
+        return info, rc, it, rr
+
+    def num_problems(self):
+        v = I32()
+        _check(lib().hs_num_problems(self._h, ctypes.byref(v)), "hs_num_problems")
+        return int(v.value)
+
+    def problem_info(self, prob):
+        """-> (leaf_lo, leaf_hi, depth, ntop) of problem prob."""
+        v = [I32() for _ in range(4)]
+        _check(lib().hs_problem_info(self._h, int(prob), *[ctypes.byref(x) for x in v]), "hs_problem_info")
+        return tuple(int(x.value) for x in v)
+
     def reset_kernel_stats(self):
         _check(lib().hs_reset_kernel_stats(self._h), "hs_reset_kernel_stats")
 
@@ -234,6 +262,18 @@ def hs_setup(n, rowptr, col, val, tree=None, opt=None, **kw):
                         ctypes.byref(h), ctypes.byref(info))
     del keep
     _check(rc, "hs_setup", info)
+    return Handle(h, int(n), info)
+
+
+def hs_setup_batched(prob_ptr, n, rowptr, col, val, opt=None, **kw):
+    """Batched setup of a block-diagonal CSR; prob_ptr: host int64[nprob + 1]."""
+    opt = opt if opt is not None else hs_default_options(**kw)
+    pp = np.ascontiguousarray(prob_ptr, dtype=np.int64)
+    info = hs_info()
+    h = P()
+    rc = lib().hs_setup_batched(len(pp) - 1, _ptr(pp), int(n), _ptr(rowptr), _ptr(col), _ptr(val),
+                                ctypes.byref(opt), ctypes.byref(h), ctypes.byref(info))
+    _check(rc, "hs_setup_batched", info)
     return Handle(h, int(n), info)
 
 

@@ -246,3 +246,32 @@ def closed_form_eigenvalues(nx, ny, nz, ratio, kh=1.0):
     e = (kh * lam(nx)[:, None, None] + kh * lam(ny)[None, :, None]
          + kh * ratio * lam(nz)[None, None, :])
     return np.sort(e.ravel())
+
+
+def block_diagonal(problems):
+    """Stack independent problems into one block-diagonal system.
+
+    Returns (prob_ptr int64[len + 1], Problem): problem p owns rows and
+    columns prob_ptr[p] .. prob_ptr[p + 1]; b and coords are concatenated.
+    """
+    pp = np.zeros(len(problems) + 1, np.int64)
+    for k, q in enumerate(problems):
+        pp[k + 1] = pp[k] + q.n
+    rp = [np.zeros(1, np.int64)]
+    nz = 0
+    for q in problems:
+        rp.append(q.rowptr[1:] + nz)
+        nz += q.nnz
+    col = np.concatenate([q.col.astype(np.int64) + pp[k]
+                          for k, q in enumerate(problems)]).astype(np.int32)
+    out = Problem(n=int(pp[-1]), rowptr=np.concatenate(rp),
+                  col=col, val=np.concatenate([q.val for q in problems]),
+                  b=np.concatenate([q.b for q in problems]),
+                  coords=np.concatenate([q.coords for q in problems]),
+                  meta=dict(name=f"batch-{len(problems)}"))
+    return pp, out
+
+
+def batched_workload(count=256):
+    """The first `count` problems of the batched workload, stacked."""
+    return block_diagonal([batched_problem(p) for p in range(count)])

@@ -78,3 +78,26 @@ def test_seeded_and_named_workloads():
     b0b = inputs.batched_problem(0)
     assert b0.n == b0b.n and np.array_equal(b0.b, b0b.b)
     assert 16 <= b0.meta["nx"] <= 48 and b0.meta["nx"] % 2 == 0 and 4 <= b0.meta["nz"] <= 12
+
+
+def test_block_diagonal_stacks_problems():
+    probs = [inputs.grid_operator(4, 6, 3, ratio=1e2, sigma=1.0, seed=s, bc="ice", shelf=0.5)
+             for s in range(3)]
+    pp, A = inputs.block_diagonal(probs)
+    assert list(pp) == [0, 72, 144, 216]
+    D = A.dense()
+    for k, q in enumerate(probs):
+        s = slice(pp[k], pp[k + 1])
+        assert np.array_equal(D[s, s], q.dense())
+        assert np.array_equal(A.b[s], q.b)
+        off = D[s].copy()
+        off[:, s] = 0.0
+        assert not off.any()  # nothing couples two problems
+
+
+def test_batched_workload_shapes():
+    for k in (0, 1, 255):
+        q = inputs.batched_problem(k)
+        nx, ny, nz = q.meta["nx"], q.meta["ny"], q.meta["nz"]
+        assert 16 <= nx <= 48 and 16 <= ny <= 48 and 4 <= nz <= 12
+        assert nx % 2 == 0 and ny % 2 == 0 and q.n == nx * ny * nz
