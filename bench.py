@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=256,
+                    help="problems of the batched workload timed beside the main step (0: skip)")
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
@@ -147,6 +149,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_leg(args, stream, dev, barrier, flush_l2):
+    """The batched workload: setup + per-problem PCG of `args.batched`
+    independent problems (grids 16x16x4 .. 48x48x12, ratio 1e3 .. 1e6) in one
+    handle; problems/s = problems / device seconds (A, b resident in HBM)."""
+    import torch
+    from paper_1811_11248_gb300 import hsolve, inputs
+    cnt = args.batched
+    pp, A = inputs.batched_workload(cnt)
+    with torch.cuda.stream(stream):
+        rp = torch.from_numpy(A.rowptr).to(dev)
+        ci = torch.from_numpy(A.col).to(dev)
+        va = torch.from_numpy(A.val).to(dev)
+        b = torch.from_numpy(A.b).to(dev)
+        x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    coords = np.ascontiguousarray(A.coords)
+    stream.synchronize()
+    out = {"problems": cnt, "dofs": int(A.n), "workload": "batched anisotropic ice-sheet problems, seeds 0-%d" % (cnt - 1)}
+    for name, prec in (("fp64", hsolve.HS_PREC_FP64), ("mixed", hsolve.HS_PREC_MIXED)):
+        opt = hsolve.hs_default_options(tol=1e-2, rtol=1e-8, mem=hsolve.HS_MEM_DEVICE, stream=stream.cuda_stream,
+                                        coords=coords, precision=prec)
+        ts, its, res = [], 0, 0.0
+        for k in range(1 + max(1, args.steps // 2)):
+            flush_l2()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = hsolve.hs_setup_batched(pp, A.n, rp, ci, va, opt=opt)
+            info, rc, it, rel = h.hs_krylov_batched(b, x)
+            e1.record(stream)
+            e1.synchronize()
+            h.close()
+            if k > 0:  # the first pass is a warm-up
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            its, res = max(its, int(it.max())), max(res, float(rel.max()))
+        t = float(np.mean(ts))
+        out[name] = {"s": t, "problems_per_s": cnt / t, "iters_max": its, "rel_resid_max": res}
+    out["problems_per_s"] = out["mixed"]["problems_per_s"]
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -202,8 +245,19 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def nvtx(name=None):
+        """NVTX range around a timed loop (a profiler can filter on it)."""
+        try:
+            if name:
+                torch.cuda.nvtx.range_push(name)
+            else:
+                torch.cuda.nvtx.range_pop()
+        except Exception:
+            pass
+
     def timed(prec):
         times, iters, resid, launches = [], [], [], 0
+        nvtx("timed_fp64" if prec == hsolve.HS_PREC_FP64 else "timed_mixed")
         for _ in range(args.steps):
             flush_l2()
             barrier()
@@ -220,6 +274,7 @@ def run_ours(args):
             iters.append(info.iters)
             resid.append(info.rel_resid)
             h.close()
+        nvtx()
         return float(np.mean(times)), int(np.max(iters)), float(np.max(resid)), launches // max(args.steps, 1)
 
     for prec in (hsolve.HS_PREC_FP64, hsolve.HS_PREC_MIXED):
@@ -286,9 +341,11 @@ def run_ours(args):
                            "kernel_ms": {k: round(v["ms"], 4) for k, v in stats.items()}},
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(launches // max(args.steps, 1)),
+            "gpu_launches": int(launches),
             "roofline": roof, "clocks": clk,
             "kernel_ms": {k: round(v["ms"], 4) for k, v in stats_mx.items()}}
+    if args.batched > 0:
+        line["batched"] = batched_leg(args, stream, dev, barrier, flush_l2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, it = cpu_oracle_step(prob, args.tol, 8, 4)
         line["cpu_baseline"] = {"value": dt, "unit": "s", "cores": 1, "kind": "oracle",
