@@ -139,11 +139,160 @@ struct EntryMeta {
 
 constexpr int kNB = 16;  // Cholesky panel width
 
+// In-place FP64 -> FP32 conversion of count elements by the group: float i
+// overwrites bytes of double i / 2, which an earlier chunk (or this chunk,
+// before the barrier) has already read.
+template <typename Grp>
+__device__ __forceinline__ void to_float_inplace(const Grp& g, double* M, int64_t count) {
+    float* F = reinterpret_cast<float*>(M);
+    for (int64_t base = 0; base < count; base += g.size) {
+        const int64_t i = base + g.rank;
+        const double x = i < count ? M[i] : 0.0;
+        g.sync();
+        if (i < count) F[i] = (float)x;
+    }
+    g.sync();
+}
+
+// Column-pivoted QR of the fill columns of the scaled block row M (s x Wt,
+// row-major: n columns, fill columns, identity columns), every reflector
+// applied to the whole row; then the rank, W = U^T G^-1, C and the coarse
+// write-back.  CT: arithmetic of this step, double, or float in the mixed
+// form (the pivot and Householder scalars are formed in FP64 either way).
+template <typename CT, typename FT, typename Grp>
+__device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT* M, int Wt, int W, int ncols, CT* v, CT* cn,
+                              double* red, double* s_hh, const EntryMeta* em, const int* ioff,
+                              double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+                              const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
+                              int32_t* __restrict__ meta, double eps2) {
+    const int s = T.s, tid = g.rank, NT = g.size;
+    const int L = T.nn + T.nw, Wn = W - ncols;
+    // column-pivoted QR of the fill columns, reflectors applied to the whole row
+    for (int j = tid; j < Wn; j += NT) {
+        CT c = 0;
+        for (int i = 0; i < s; i++) {
+            const CT x = M[(int64_t)i * Wt + ncols + j];
+            c += x * x;
+        }
+        cn[j] = c;
+    }
+    g.sync();
+    int k = 0;
+    while (k < s) {
+        double lt = 0.0, lm = 0.0;
+        for (int j = tid; j < Wn; j += NT) {
+            const double c = (double)cn[j];
+            if (c >= 0.0) {
+                lt += c;
+                lm = fmax(lm, c);
+            }
+        }
+        const double total = g.sum(lt, red);
+        const double cmax = g.max(lm, red);
+        if (total <= eps2) break;
+        const double thr = (1.0 - kPivotTie) * cmax;
+        int lp = INT_MAX;
+        for (int j = tid; j < Wn; j += NT)
+            if (cn[j] >= (CT)0 && (double)cn[j] >= thr) {
+                lp = j;
+                break;  // lowest of this thread's columns
+            }
+        const int p = g.minint(lp, red);
+        const int pc = ncols + p;
+        double ls = 0.0;
+        for (int i = k + 1 + tid; i < s; i += NT) {
+            const double x = (double)M[(int64_t)i * Wt + pc];
+            ls += x * x;
+        }
+        const double sig = g.sum(ls, red);
+        if (tid == 0) {
+            const double alpha = (double)M[(int64_t)k * Wt + pc];
+            const double nrm = sqrt(alpha * alpha + sig);
+            const double beta = alpha >= 0.0 ? -nrm : nrm;
+            s_hh[0] = beta;
+            s_hh[1] = (beta - alpha) / beta;
+            s_hh[2] = 1.0 / (alpha - beta);
+            cn[p] = -1.0;
+        }
+        g.sync();
+        const CT beta = (CT)s_hh[0], tau = (CT)s_hh[1], scal = (CT)s_hh[2];
+        for (int i = tid; i < s; i += NT) {
+            CT vi = 0;
+            if (i == k) vi = 1;
+            else if (i > k) vi = M[(int64_t)i * Wt + pc] * scal;
+            v[i] = vi;
+        }
+        g.sync();
+        for (int i = k + tid; i < s; i += NT) M[(int64_t)i * Wt + pc] = (i == k) ? beta : (CT)0;
+        for (int j = tid; j < Wt; j += NT) {
+            if (j == pc) continue;
+            const bool cand = (j >= ncols && j < W);
+            if (cand && cn[j - ncols] < (CT)0) continue;  // pivoted: zero below its row
+            CT t = M[(int64_t)k * Wt + j];
+            for (int i = k + 1; i < s; i++) t += v[i] * M[(int64_t)i * Wt + j];
+            t *= tau;
+            M[(int64_t)k * Wt + j] -= t;
+            CT c = 0;
+            for (int i = k + 1; i < s; i++) {
+                const CT x = M[(int64_t)i * Wt + j] - t * v[i];
+                M[(int64_t)i * Wt + j] = x;
+                if (cand) c += x * x;
+            }
+            if (cand) cn[j - ncols] = c;
+        }
+        g.sync();
+        k++;
+    }
+    const int r = k;
+
+    // factor: rank and n-column layout, W = U^T G^-1, C = rows r.. of the n columns
+    int32_t* mt = meta + T.meta;
+    if (tid == 0) mt[0] = r;
+    for (int e = tid; e < T.nn; e += NT) {
+        mt[1 + 2 * e] = ioff[e];
+        mt[2 + 2 * e] = ioff[e + 1] - ioff[e];
+    }
+    {
+        FT* Wf = fac + T.w_off;
+        for (int idx = tid; idx < s * s; idx += NT) Wf[idx] = (FT)M[(int64_t)(idx / s) * Wt + W + idx % s];
+        FT* Cf = fac + T.c_off;
+        const int f = s - r;
+        for (int idx = tid; idx < f * ncols; idx += NT) {
+            const int i = idx / ncols, j = idx % ncols;
+            Cf[(int64_t)i * T.ncap + j] = (FT)M[(int64_t)(r + i) * Wt + j];
+        }
+    }
+    // write back the coarse row (identity diagonal, U^T G^-1 A_sn, V1^T)
+    if (T.nw > 0 && r > 0) {
+        for (int e = 0; e < L; e++) {
+            const int wq = ioff[e + 1] - ioff[e], o = ioff[e];
+            double* dcq = blocks + em[e].cq;
+            const int ldcq = em[e].ldcq;
+            double* dqc = blocks + em[e].qc;
+            const int ldqc = em[e].ldqc;
+            for (int idx = tid; idx < r * wq; idx += NT) {
+                const int i = idx / wq, j = idx % wq;
+                const double x = (double)M[(int64_t)i * Wt + o + j];
+                dcq[(int64_t)i * ldcq + j] = x;
+                dqc[(int64_t)j * ldqc + i] = x;
+            }
+        }
+        double* dcc = blocks + blk_off[T.diag_blk];
+        const int ld = blk_ld[T.diag_blk];
+        for (int idx = tid; idx < r * r; idx += NT) {
+            const int i = idx / r, j = idx % r;
+            dcc[(int64_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
+        }
+    }
+    if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
+}
+
 // One scaled low-rank elimination (Sec. 3.1) by the group g.  Shared memory
 // of the group: G (s*s), rdiag (s), v (s), cn (fill columns), red (>= 64
 // doubles), ioff (list length + 1 ints), flag, hh (3 doubles).
 // FT: element type of the stored factor (W, C): double, or float in the
-// mixed-precision form.  All arithmetic here is FP64.
+// mixed-precision form.  Cholesky and scaling are FP64; the compression runs
+// in FP32 in the mixed form (compress_task).
 template <typename FT, typename Grp>
 __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* rdiag, double* v, double* cn,
                             double* red, int* ioff, int* s_flag, double* s_hh, double* Msh, EntryMeta* em,
@@ -284,128 +433,20 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     }
     g.sync();
 
-    // column-pivoted QR of the fill columns, reflectors applied to the whole row
-    for (int j = tid; j < Wn; j += NT) {
-        double c = 0.0;
-        for (int i = 0; i < s; i++) {
-            const double x = M[(int64_t)i * Wt + ncols + j];
-            c += x * x;
-        }
-        cn[j] = c;
+    if constexpr (sizeof(FT) == sizeof(float)) {
+        // mixed form: the compression runs on an FP32 copy of the scaled row
+        to_float_inplace(g, M, (int64_t)s * Wt);
+        compress_task<float, FT>(T, g, reinterpret_cast<float*>(M), Wt, W, ncols, reinterpret_cast<float*>(v),
+                                 reinterpret_cast<float*>(cn), red, s_hh, em, ioff, blocks, blk_off, blk_ld, cur,
+                                 fac, meta, eps2);
+    } else {
+        compress_task<double, FT>(T, g, M, Wt, W, ncols, v, cn, red, s_hh, em, ioff, blocks, blk_off, blk_ld, cur,
+                                  fac, meta, eps2);
     }
-    g.sync();
-    int k = 0;
-    while (k < s) {
-        double lt = 0.0, lm = 0.0;
-        for (int j = tid; j < Wn; j += NT) {
-            const double c = cn[j];
-            if (c >= 0.0) {
-                lt += c;
-                lm = fmax(lm, c);
-            }
-        }
-        const double total = g.sum(lt, red);
-        const double cmax = g.max(lm, red);
-        if (total <= eps2) break;
-        const double thr = (1.0 - kPivotTie) * cmax;
-        int lp = INT_MAX;
-        for (int j = tid; j < Wn; j += NT)
-            if (cn[j] >= 0.0 && cn[j] >= thr) {
-                lp = j;
-                break;  // lowest of this thread's columns
-            }
-        const int p = g.minint(lp, red);
-        const int pc = ncols + p;
-        double ls = 0.0;
-        for (int i = k + 1 + tid; i < s; i += NT) {
-            const double x = M[(int64_t)i * Wt + pc];
-            ls += x * x;
-        }
-        const double sig = g.sum(ls, red);
-        if (tid == 0) {
-            const double alpha = M[(int64_t)k * Wt + pc];
-            const double nrm = sqrt(alpha * alpha + sig);
-            const double beta = alpha >= 0.0 ? -nrm : nrm;
-            s_hh[0] = beta;
-            s_hh[1] = (beta - alpha) / beta;
-            s_hh[2] = 1.0 / (alpha - beta);
-            cn[p] = -1.0;
-        }
-        g.sync();
-        const double beta = s_hh[0], tau = s_hh[1], scal = s_hh[2];
-        for (int i = tid; i < s; i += NT) {
-            double vi = 0.0;
-            if (i == k) vi = 1.0;
-            else if (i > k) vi = M[(int64_t)i * Wt + pc] * scal;
-            v[i] = vi;
-        }
-        g.sync();
-        for (int i = k + tid; i < s; i += NT) M[(int64_t)i * Wt + pc] = (i == k) ? beta : 0.0;
-        for (int j = tid; j < Wt; j += NT) {
-            if (j == pc) continue;
-            const bool cand = (j >= ncols && j < W);
-            if (cand && cn[j - ncols] < 0.0) continue;  // pivoted: zero below its row
-            double t = M[(int64_t)k * Wt + j];
-            for (int i = k + 1; i < s; i++) t += v[i] * M[(int64_t)i * Wt + j];
-            t *= tau;
-            M[(int64_t)k * Wt + j] -= t;
-            double c = 0.0;
-            for (int i = k + 1; i < s; i++) {
-                const double x = M[(int64_t)i * Wt + j] - t * v[i];
-                M[(int64_t)i * Wt + j] = x;
-                if (cand) c += x * x;
-            }
-            if (cand) cn[j - ncols] = c;
-        }
-        g.sync();
-        k++;
-    }
-    const int r = k;
-
-    // factor: rank and n-column layout, W = U^T G^-1, C = rows r.. of the n columns
-    int32_t* mt = meta + T.meta;
-    if (tid == 0) mt[0] = r;
-    for (int e = tid; e < T.nn; e += NT) {
-        mt[1 + 2 * e] = ioff[e];
-        mt[2 + 2 * e] = ioff[e + 1] - ioff[e];
-    }
-    {
-        FT* Wf = fac + T.w_off;
-        for (int idx = tid; idx < s * s; idx += NT) Wf[idx] = (FT)M[(int64_t)(idx / s) * Wt + W + idx % s];
-        FT* Cf = fac + T.c_off;
-        const int f = s - r;
-        for (int idx = tid; idx < f * ncols; idx += NT) {
-            const int i = idx / ncols, j = idx % ncols;
-            Cf[(int64_t)i * T.ncap + j] = (FT)M[(int64_t)(r + i) * Wt + j];
-        }
-    }
-    // write back the coarse row (identity diagonal, U^T G^-1 A_sn, V1^T)
-    if (T.nw > 0 && r > 0) {
-        for (int e = 0; e < L; e++) {
-            const int wq = ioff[e + 1] - ioff[e], o = ioff[e];
-            double* dcq = blocks + em[e].cq;
-            const int ldcq = em[e].ldcq;
-            double* dqc = blocks + em[e].qc;
-            const int ldqc = em[e].ldqc;
-            for (int idx = tid; idx < r * wq; idx += NT) {
-                const int i = idx / wq, j = idx % wq;
-                const double x = M[(int64_t)i * Wt + o + j];
-                dcq[(int64_t)i * ldcq + j] = x;
-                dqc[(int64_t)j * ldqc + i] = x;
-            }
-        }
-        double* dcc = blocks + blk_off[T.diag_blk];
-        const int ld = blk_ld[T.diag_blk];
-        for (int idx = tid; idx < r * r; idx += NT) {
-            const int i = idx / r, j = idx % r;
-            dcc[(int64_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
-        }
-    }
-    if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
 }
 
 template <typename FT>
-__global__ void __launch_bounds__(kFactorThreads)
+__global__ void __launch_bounds__(kFactorThreads, 2)
 k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
                double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,

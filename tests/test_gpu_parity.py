@@ -220,10 +220,12 @@ def test_full_size_64x64x16_parity(hs, oracle_lib):
 
 @pytest.mark.parametrize("tol", [1e-2, 1e-4])
 def test_mixed_precision_against_fp64(hs, oracle_lib, tol):
-    """Mixed form: FP32 Schur products and FP32 stored/applied factor, FP64
-    Cholesky, scaling, CPQR and Krylov residual.  Ranks may differ from FP64;
-    the bars are the true FP64 residual, the iteration count and the operator
-    difference relative to the FP64 GPU path (printed)."""
+    """Mixed form: FP32 compression (CPQR and its reflectors), FP32 Schur
+    products and FP32 stored/applied factor; FP64 Cholesky, scaling and Krylov
+    residual.  Ranks may differ from FP64 where a column norm sits at the
+    tolerance; the bars are the share of differing ranks, the true FP64
+    residual, the iteration count and the operator difference relative to
+    the FP64 GPU path (printed)."""
     p = inputs.grid_operator(32, 32, 16, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
     h64, ref, depth = setup_both(hs, oracle_lib, p, 6, tol)
     h32, _, _ = setup_both(hs, oracle_lib, p, 6, tol, precision=hs.HS_PREC_MIXED)
@@ -242,7 +244,15 @@ def test_mixed_precision_against_fp64(hs, oracle_lib, tol):
     i64, _ = h64.hs_krylov(dev(p.b), x64)
     i32, _ = h32.hs_krylov(dev(p.b), x32)
     res = np.linalg.norm(p.b - p.matvec(x32.cpu().numpy())) / np.linalg.norm(p.b)
-    print(f"mixed vs fp64: operator diff {worst:.2e}, iterations {i32.iters} vs {i64.iters}, residual {res:.2e}")
+    ndiff = ntot = 0
+    for l in range(depth):
+        _, f64, _ = h64.level_info(l)
+        _, f32, _ = h32.level_info(l)
+        ndiff += int(np.sum(f64 != f32))
+        ntot += len(f64)
+    print(f"mixed vs fp64: operator diff {worst:.2e}, iterations {i32.iters} vs {i64.iters}, residual {res:.2e}, "
+          f"ranks differing {ndiff} of {ntot}")
+    assert ndiff <= 0.05 * ntot
     assert worst <= 1e-3
     assert res <= 1e-8 and i32.rel_resid <= 1e-8
     assert i32.iters <= i64.iters + 2
