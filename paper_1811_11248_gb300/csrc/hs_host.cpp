@@ -20,6 +20,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <mutex>
 #include <map>
 #include <memory>
 #include <new>
@@ -205,6 +207,27 @@ int hs_threads() {
 // set on the worker threads of a batched partition: nested work stays serial
 thread_local bool tl_serial = false;
 
+// Runs fn(t) for t < T (t = 0 on the calling thread) and rethrows the first
+// exception any of them raised.
+template <class F>
+void run_threads(int T, F&& fn) {
+    std::exception_ptr err;
+    std::mutex mu;
+    auto wrap = [&](int t) {
+        try {
+            fn(t);
+        } catch (...) {
+            std::lock_guard<std::mutex> g(mu);
+            if (!err) err = std::current_exception();
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < T; t++) th.emplace_back(wrap, t);
+    wrap(0);
+    for (auto& x : th) x.join();
+    if (err) std::rethrow_exception(err);
+}
+
 template <class F>
 void parallel_ranges(int64_t n, int64_t grain, F&& f) {
     const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / std::max<int64_t>(grain, 1)));
@@ -212,10 +235,24 @@ void parallel_ranges(int64_t n, int64_t grain, F&& f) {
         f((int64_t)0, n, 0);
         return;
     }
-    std::vector<std::thread> th;
-    for (int t = 0; t < T; t++)
-        th.emplace_back([&, t] { f(n * t / T, n * (t + 1) / T, t); });
-    for (auto& x : th) x.join();
+    run_threads(T, [&](int t) { f(n * t / T, n * (t + 1) / T, t); });
+}
+
+// out = f(0) ++ f(1) ++ ... ++ f(n-1), items appended by f(i, out) in
+// parallel chunks and concatenated in index order.
+template <class T, class F>
+std::vector<T> parallel_collect(int64_t n, int64_t grain, F&& f) {
+    const int NT = (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / std::max<int64_t>(grain, 1)));
+    std::vector<std::vector<T>> part(NT);
+    parallel_ranges(n, grain, [&](int64_t lo, int64_t hi, int t) {
+        for (int64_t i = lo; i < hi; i++) f(i, part[t]);
+    });
+    std::vector<T> out;
+    size_t tot = 0;
+    for (auto& v : part) tot += v.size();
+    out.reserve(tot);
+    for (auto& v : part) out.insert(out.end(), v.begin(), v.end());
+    return out;
 }
 
 // ---------------------------------------------------------------------------
@@ -301,9 +338,10 @@ struct Partitioner {
         }
         const int half = 1 << (L - depth - 1);
         if (have_coords && depth < 3 && k > 4096 && !tl_serial) {  // top of the tree on two threads
-            std::thread left_thread([&] { split(std::move(a), depth + 1, base); });
-            split(std::move(b), depth + 1, base + half);
-            left_thread.join();
+            run_threads(2, [&](int t) {
+                if (t == 1) split(std::move(a), depth + 1, base);
+                else split(std::move(b), depth + 1, base + half);
+            });
         } else {
             split(std::move(a), depth + 1, base);
             split(std::move(b), depth + 1, base + half);
@@ -450,32 +488,32 @@ struct LevelPlan {
     std::vector<char> vanished;
 };
 
-void plan_level(LevelPlan& P) {
-    const int nc = P.nc;
-    std::vector<std::vector<int>> cur = P.adj0;
-    P.all = P.adj0;
-    for (int c = 0; c < nc; c++)
-        if (P.size0[c] > 0) sorted_insert(P.all[c], c);
-    P.phase.assign(nc, -1);
-    P.nl.assign(nc, {});
-    P.wl.assign(nc, {});
-    P.vanished.assign(nc, 0);
-    std::vector<char> done(nc, 0), insel(nc, 0);
+// Phase rule and fill pattern (Sec. 3.2, Sec. 4.2) of the clusters lo .. hi,
+// which share no block with any other cluster: phases are rounds of a greedy
+// maximal independent set in ascending cluster order on the current block
+// graph; eliminating c couples every pair of its neighbours.
+void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi,
+                std::vector<std::vector<int>>& phases) {
+    std::vector<char> done(hi - lo, 0), insel(hi - lo, 0);
+    auto D = [&](int c) -> char& { return done[c - lo]; };
+    auto S = [&](int c) -> char& { return insel[c - lo]; };
     int remaining = 0;
-    for (int c = 0; c < nc; c++) {
+    for (int c = lo; c < hi; c++) {
         if (P.size0[c] > 0) remaining++;
-        else done[c] = 1;
+        else D(c) = 1;
     }
+    int first = lo;  // clusters below `first` are all done
     while (remaining > 0) {
         std::vector<int> sel;
-        for (int c = 0; c < nc; c++) {
-            if (done[c]) continue;
+        while (first < hi && D(first)) first++;
+        for (int c = first; c < hi; c++) {
+            if (D(c)) continue;
             bool ok = true;
             for (int q : cur[c])
-                if (insel[q]) { ok = false; break; }
-            if (ok) { insel[c] = 1; sel.push_back(c); }
+                if (S(q)) { ok = false; break; }
+            if (ok) { S(c) = 1; sel.push_back(c); }
         }
-        const int ph = (int)P.phases.size();
+        const int ph = (int)phases.size();
         for (int c : sel) {
             auto& nlc = P.nl[c];
             auto& wlc = P.wl[c];
@@ -491,16 +529,48 @@ void plan_level(LevelPlan& P) {
                 for (int q : cur[c]) sorted_erase(cur[q], c);
                 cur[c].clear();
             }
-            done[c] = 1;
-            insel[c] = 0;
+            D(c) = 1;
+            S(c) = 0;
             P.phase[c] = ph;
             remaining--;
         }
-        P.phases.push_back(std::move(sel));
+        phases.push_back(std::move(sel));
     }
-    P.endp = cur;
-    for (int c = 0; c < nc; c++)
+    for (int c = lo; c < hi; c++) {
+        P.endp[c] = std::move(cur[c]);
         if (P.size0[c] > 0 && !P.vanished[c]) sorted_insert(P.endp[c], c);
+    }
+}
+
+// ranges: cluster ranges that share no block (independent problems); each
+// is planned on its own thread and phase k of the level is the union of the
+// ranges' phase k (identical to planning all clusters at once).
+void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {}) {
+    const int nc = P.nc;
+    std::vector<std::vector<int>> cur = P.adj0;
+    P.all = P.adj0;
+    for (int c = 0; c < nc; c++)
+        if (P.size0[c] > 0) sorted_insert(P.all[c], c);
+    P.phase.assign(nc, -1);
+    P.nl.assign(nc, {});
+    P.wl.assign(nc, {});
+    P.vanished.assign(nc, 0);
+    P.endp.assign(nc, {});
+    P.phases.clear();
+    std::vector<std::pair<int, int>> rg = ranges;
+    if (rg.empty()) rg.push_back({0, nc});
+    std::vector<std::vector<std::vector<int>>> ph(rg.size());
+    std::atomic<int> next{0};
+    auto work = [&] {
+        for (int k = next++; k < (int)rg.size(); k = next++) plan_range(P, cur, rg[k].first, rg[k].second, ph[k]);
+    };
+    run_threads(std::min<int>(hs_threads(), (int)rg.size()), [&](int) { work(); });
+    size_t nph = 0;
+    for (auto& v : ph) nph = std::max(nph, v.size());
+    P.phases.assign(nph, {});
+    for (size_t k = 0; k < nph; k++)
+        for (auto& v : ph)
+            if (k < v.size()) P.phases[k].insert(P.phases[k].end(), v[k].begin(), v[k].end());
 }
 
 // ---------------------------------------------------------------------------
@@ -519,7 +589,9 @@ struct Level {
     std::vector<ListDev> lists;
     // solve phase: (task, k) lists of the updates each cluster receives from
     // tasks of earlier phases (early) / later phases (late)
-    std::vector<std::vector<std::pair<int, int>>> early, late;
+    // (CSR over clusters: entries ptr[c] .. ptr[c+1], ascending task order)
+    std::vector<int32_t> early_ptr, late_ptr;
+    std::vector<std::pair<int, int>> early, late;
     std::vector<int64_t> stg;          // stage offset of every task
     std::vector<int32_t> hmeta;        // rank and n-column layout of every task
     std::vector<int> task_rank;        // filled after the level
@@ -675,7 +747,7 @@ BlockTable make_table(const LevelPlan& P) {
 // Factor one level: plan, device records, phases.  `blocks` holds the level's
 // assembled matrix (layout T).  Returns the final sizes.
 void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf& blocks, DBuf& d_cur,
-                  DBuf& d_status, hs_info* info) {
+                  DBuf& d_status, hs_info* info, const std::vector<std::pair<int, int>>& ranges) {
     Level& L = *h->lev[l];
     cudaStream_t st = h->st;
     Trace tr0;
@@ -695,86 +767,162 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     std::vector<TargetDev> targets;
     std::vector<ContribDev> contribs;
     L.smax = 1; L.wmax = 1; L.lmax = 1; L.nmax = 1;
+    // task ti = the ti-th cluster in phase order; sizes first (parallel),
+    // then prefix offsets, then the records (parallel)
+    std::vector<int> order;
+    for (int ph = 0; ph < L.nphases; ph++) {
+        order.insert(order.end(), P.phases[ph].begin(), P.phases[ph].end());
+        L.ph_task.push_back((int)order.size());
+    }
+    const int nt = (int)order.size();
+    std::vector<int32_t> t_ncap(nt), t_wcap(nt);
+    parallel_ranges(nt, 4096, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t ti = lo; ti < hi; ti++) {
+            const int c = (int)order[ti];
+            int ncap = 0, wcap = 0;
+            for (int q : P.nl[c]) ncap += P.size0[q];
+            wcap = ncap;
+            for (int q : P.wl[c]) wcap += P.size0[q];
+            t_ncap[ti] = ncap;
+            t_wcap[ti] = wcap;
+        }
+    });
+    L.tasks.resize(nt);
+    L.stg.resize(nt);
+    std::vector<int32_t> list_off(nt + 1, 0);
     for (int ph = 0; ph < L.nphases; ph++) {
         int64_t ws = 0;
-        for (int c : P.phases[ph]) {
-            TaskDev t{};
+        for (int ti = L.ph_task[ph]; ti < L.ph_task[ph + 1]; ti++) {
+            const int c = order[ti];
+            TaskDev& t = L.tasks[ti];
             t.c = c;
             t.s = P.size0[c];
             t.nn = (int)P.nl[c].size();
             t.nw = (int)P.wl[c].size();
-            t.list = (int)L.lists.size();
+            t.list = list_off[ti];
+            list_off[ti + 1] = list_off[ti] + t.nn + t.nw;
+            t.ncap = t_ncap[ti];
+            t.wcap = t_wcap[ti];
+            t.meta = meta;
+            meta += 1 + 2 * t.nn;
+            L.stg[ti] = stage;
+            stage += std::max(t.ncap, 1);
+            t.w_off = fac; fac += (int64_t)t.s * t.s;
+            t.c_off = fac; fac += (int64_t)t.s * std::max(t.ncap, 1);
+            t.m_off = ws; ws += (int64_t)t.s * (t.wcap + t.s);
+            L.smax = std::max(L.smax, t.s);
+            L.wmax = std::max(L.wmax, t.wcap);
+            L.lmax = std::max(L.lmax, t.nn + t.nw);
+            L.nmax = std::max(L.nmax, t.ncap);
+            task_of[c] = ti;
+        }
+        ws_phase_max = std::max(ws_phase_max, ws);
+    }
+    L.lists.resize(list_off[nt]);
+    parallel_ranges(nt, 2048, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t ti = lo; ti < hi; ti++) {
+            TaskDev& t = L.tasks[ti];
+            const int c = t.c;
             t.diag_blk = T.find(c, c);
-            int ncap = 0, wcap = 0;
             for (int k = 0; k < t.nn + t.nw; k++) {
                 const int q = k < t.nn ? P.nl[c][k] : P.wl[c][k - t.nn];
-                ListDev le{};
+                ListDev& le = L.lists[t.list + k];
+                le = ListDev{};
                 le.q = q;
                 le.blk_cq = T.find(c, q);
                 le.blk_qc = T.find(q, c);
-                L.lists.push_back(le);
-                wcap += P.size0[q];
-                if (k < t.nn) ncap += P.size0[q];
             }
-            t.ncap = ncap;
-            t.wcap = wcap;
-            t.meta = meta;
-            meta += 1 + 2 * t.nn;
-            L.stg.push_back(stage);
-            stage += std::max(ncap, 1);
-            t.w_off = fac; fac += (int64_t)t.s * t.s;
-            t.c_off = fac; fac += (int64_t)t.s * std::max(ncap, 1);
-            t.m_off = ws; ws += (int64_t)t.s * (wcap + t.s);
-            L.smax = std::max(L.smax, t.s);
-            L.wmax = std::max(L.wmax, wcap);
-            L.lmax = std::max(L.lmax, t.nn + t.nw);
-            L.nmax = std::max(L.nmax, ncap);
-            task_of[c] = (int)L.tasks.size();
-            L.tasks.push_back(t);
         }
-        ws_phase_max = std::max(ws_phase_max, ws);
-        // Schur targets of the phase: (p, q), p <= q, contributions in
-        // ascending task order (sort by target, stable in task order)
+    });
+    // Schur targets of every phase: (p, q), p <= q, contributions in
+    // ascending task order (sort by target, stable in task order).  The
+    // independent cluster ranges are handled on their own threads and
+    // concatenated (targets of a range lie in that range).
+    {
         struct TC {
             int p, q;
             ContribDev c;
         };
-        std::vector<TC> tcs;
-        for (int c : P.phases[ph]) {
-            const int ti = task_of[c];
-            const auto& nlc = P.nl[c];
-            for (int a = 0; a < (int)nlc.size(); a++)
-                for (int b = 0; b < (int)nlc.size(); b++)
-                    if (nlc[a] <= nlc[b]) tcs.push_back(TC{nlc[a], nlc[b], ContribDev{ti, a, b}});
+        const int nr = std::max<int>(1, (int)ranges.size());
+        std::vector<std::vector<std::vector<TargetDev>>> rt(nr, std::vector<std::vector<TargetDev>>(L.nphases));
+        std::vector<std::vector<std::vector<ContribDev>>> rc(nr, std::vector<std::vector<ContribDev>>(L.nphases));
+        std::atomic<int> next{0};
+        auto work = [&] {
+            std::vector<TC> tcs;
+            for (int k = next++; k < nr; k = next++) {
+                const int lo = ranges.empty() ? 0 : ranges[k].first, hi = ranges.empty() ? P.nc : ranges[k].second;
+                for (int ph = 0; ph < L.nphases; ph++) {
+                    const auto& cs = P.phases[ph];
+                    auto b0 = std::lower_bound(cs.begin(), cs.end(), lo), b1 = std::lower_bound(cs.begin(), cs.end(), hi);
+                    tcs.clear();
+                    for (auto it = b0; it != b1; ++it) {
+                        const int c = *it, ti = task_of[c];
+                        const auto& nlc = P.nl[c];
+                        for (int a = 0; a < (int)nlc.size(); a++)
+                            for (int b = 0; b < (int)nlc.size(); b++)
+                                if (nlc[a] <= nlc[b]) tcs.push_back(TC{nlc[a], nlc[b], ContribDev{ti, a, b}});
+                    }
+                    std::stable_sort(tcs.begin(), tcs.end(),
+                                     [](const TC& x, const TC& y) { return x.p < y.p || (x.p == y.p && x.q < y.q); });
+                    auto& tg = rt[k][ph];
+                    auto& ct = rc[k][ph];
+                    for (size_t i = 0; i < tcs.size();) {
+                        size_t j = i;
+                        TargetDev g{};
+                        g.p = tcs[i].p;
+                        g.q = tcs[i].q;
+                        g.blk_pq = T.find(g.p, g.q);
+                        g.blk_qp = T.find(g.q, g.p);
+                        g.c_begin = (int)ct.size();
+                        while (j < tcs.size() && tcs[j].p == g.p && tcs[j].q == g.q) ct.push_back(tcs[j++].c);
+                        g.c_end = (int)ct.size();
+                        tg.push_back(g);
+                        i = j;
+                    }
+                }
+            }
+        };
+        run_threads(std::min<int>(hs_threads(), nr), [&](int) { work(); });
+        for (int ph = 0; ph < L.nphases; ph++) {
+            for (int k = 0; k < nr; k++) {
+                const int base = (int)contribs.size();
+                for (TargetDev g : rt[k][ph]) {
+                    g.c_begin += base;
+                    g.c_end += base;
+                    targets.push_back(g);
+                }
+                contribs.insert(contribs.end(), rc[k][ph].begin(), rc[k][ph].end());
+            }
+            L.ph_target.push_back((int)targets.size());
         }
-        std::stable_sort(tcs.begin(), tcs.end(),
-                         [](const TC& x, const TC& y) { return x.p < y.p || (x.p == y.p && x.q < y.q); });
-        for (size_t i = 0; i < tcs.size();) {
-            size_t j = i;
-            TargetDev g{};
-            g.p = tcs[i].p;
-            g.q = tcs[i].q;
-            g.blk_pq = T.find(g.p, g.q);
-            g.blk_qp = T.find(g.q, g.p);
-            g.c_begin = (int)contribs.size();
-            while (j < tcs.size() && tcs[j].p == g.p && tcs[j].q == g.q) contribs.push_back(tcs[j++].c);
-            g.c_end = (int)contribs.size();
-            targets.push_back(g);
-            i = j;
-        }
-        L.ph_task.push_back((int)L.tasks.size());
-        L.ph_target.push_back((int)targets.size());
     }
     tr0.mark("  tasks+targets");
     // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
     // before its own transform (q in a later phase) or at level end (earlier)
-    L.early.assign(P.nc, {});
-    L.late.assign(P.nc, {});
-    for (int ti = 0; ti < (int)L.tasks.size(); ti++) {
-        const TaskDev& t = L.tasks[ti];
-        for (int k = 0; k < t.nn; k++) {
-            const int q = L.lists[t.list + k].q;
-            (P.phase[q] > P.phase[t.c] ? L.early[q] : L.late[q]).push_back({ti, k});
+    {
+        L.early_ptr.assign(P.nc + 1, 0);
+        L.late_ptr.assign(P.nc + 1, 0);
+        for (int ti = 0; ti < nt; ti++) {
+            const TaskDev& t = L.tasks[ti];
+            for (int k = 0; k < t.nn; k++) {
+                const int q = L.lists[t.list + k].q;
+                (P.phase[q] > P.phase[t.c] ? L.early_ptr : L.late_ptr)[q + 1]++;
+            }
+        }
+        for (int q = 0; q < P.nc; q++) {
+            L.early_ptr[q + 1] += L.early_ptr[q];
+            L.late_ptr[q + 1] += L.late_ptr[q];
+        }
+        L.early.resize(L.early_ptr[P.nc]);
+        L.late.resize(L.late_ptr[P.nc]);
+        std::vector<int32_t> fe(L.early_ptr.begin(), L.early_ptr.end() - 1), fl(L.late_ptr.begin(), L.late_ptr.end() - 1);
+        for (int ti = 0; ti < nt; ti++) {
+            const TaskDev& t = L.tasks[ti];
+            for (int k = 0; k < t.nn; k++) {
+                const int q = L.lists[t.list + k].q;
+                if (P.phase[q] > P.phase[t.c]) L.early[fe[q]++] = {ti, k};
+                else L.late[fl[q]++] = {ti, k};
+            }
         }
     }
     L.wmax = std::max(L.wmax, 64);  // the fused kernel's Schur step stages 32 x 4 int64 in the column table
@@ -852,47 +1000,61 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     tr.mark("  downloads");
     // solve-phase records with resolved offsets
     {
-        std::vector<ApTask> at(L.tasks.size());
-        std::vector<ApNb> nbs;
-        std::vector<int> ph_of(L.tasks.size());
-        for (int ph = 0; ph < L.nphases; ph++)
-            for (int ti = L.ph_task[ph]; ti < L.ph_task[ph + 1]; ti++) ph_of[ti] = ph;
-        std::vector<int64_t> work(L.nphases, 0);
-        for (size_t ti = 0; ti < L.tasks.size(); ti++) {
-            const TaskDev& t = L.tasks[ti];
-            const int32_t* mt = hmeta.data() + t.meta;
-            ApTask a{};
-            a.y = L.slot[t.c];
-            a.w = t.w_off;
-            a.cm = t.c_off;
-            a.stg = L.stg[ti];
-            a.s = t.s;
-            a.r = mt[0];
-            a.ncols = t.nn > 0 ? mt[1 + 2 * (t.nn - 1)] + mt[2 + 2 * (t.nn - 1)] : 0;
-            a.ncap = t.ncap;
-            a.pull0 = (int)L.ap_pulls.size();
-            for (auto& pk : L.early[t.c])
-                L.ap_pulls.push_back(ApPull{L.stg[pk.first] + hmeta[L.tasks[pk.first].meta + 1 + 2 * pk.second]});
-            a.pull1 = (int)L.ap_pulls.size();
-            a.nb0 = (int)nbs.size();
-            for (int e = 0; e < t.nn; e++) {
-                ApNb nb{};
-                nb.y = L.slot[L.lists[t.list + e].q];
-                nb.col = mt[1 + 2 * e];
-                nb.m = mt[2 + 2 * e];
-                nbs.push_back(nb);
-            }
-            a.nb1 = (int)nbs.size();
-            at[ti] = a;
-            work[ph_of[ti]] += (int64_t)a.s * a.s + (int64_t)(a.s - a.r) * a.ncols;
+        std::vector<ApTask> at(nt);
+        // pulls (early updates) and neighbour records: offsets first, then
+        // every task's records in parallel
+        const int pull_base = (int)L.ap_pulls.size();
+        std::vector<int32_t> nb_off(nt + 1, 0);
+        for (int ti = 0; ti < nt; ti++) nb_off[ti + 1] = nb_off[ti] + L.tasks[ti].nn;
+        std::vector<ApNb> nbs(nb_off[nt]);
+        L.ap_pulls.resize(pull_base + L.early.size());
+        std::vector<int32_t> pull_off(nt + 1, pull_base);
+        for (int ti = 0; ti < nt; ti++) {
+            const int c = L.tasks[ti].c;
+            pull_off[ti + 1] = pull_off[ti] + (L.early_ptr[c + 1] - L.early_ptr[c]);
         }
+        parallel_ranges(nt, 2048, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t ti = lo; ti < hi; ti++) {
+                const TaskDev& t = L.tasks[ti];
+                const int32_t* mt = hmeta.data() + t.meta;
+                ApTask a{};
+                a.y = L.slot[t.c];
+                a.w = t.w_off;
+                a.cm = t.c_off;
+                a.stg = L.stg[ti];
+                a.s = t.s;
+                a.r = mt[0];
+                a.ncols = t.nn > 0 ? mt[1 + 2 * (t.nn - 1)] + mt[2 + 2 * (t.nn - 1)] : 0;
+                a.ncap = t.ncap;
+                a.pull0 = pull_off[ti];
+                int o = pull_off[ti];
+                for (int e = L.early_ptr[t.c]; e < L.early_ptr[t.c + 1]; e++) {
+                    const auto& pk = L.early[e];
+                    L.ap_pulls[o++] = ApPull{L.stg[pk.first] + hmeta[L.tasks[pk.first].meta + 1 + 2 * pk.second]};
+                }
+                a.pull1 = o;
+                a.nb0 = nb_off[ti];
+                for (int e = 0; e < t.nn; e++) {
+                    ApNb nb{};
+                    nb.y = L.slot[L.lists[t.list + e].q];
+                    nb.col = mt[1 + 2 * e];
+                    nb.m = mt[2 + 2 * e];
+                    nbs[nb_off[ti] + e] = nb;
+                }
+                a.nb1 = nb_off[ti + 1];
+                at[ti] = a;
+            }
+        });
         // Solve stages: a task depends only on the tasks whose staged update
         // it subtracts (fill couplings were compressed away), so stage =
         // longest chain of such dependencies; the backward runs the stages in
         // reverse.  Tasks of a stage are independent.
-        std::vector<int> stage_of(L.tasks.size(), 0);
-        for (size_t ti = 0; ti < L.tasks.size(); ti++)
-            for (auto& pk : L.early[L.tasks[ti].c]) stage_of[ti] = std::max(stage_of[ti], stage_of[pk.first] + 1);
+        std::vector<int> stage_of(nt, 0);
+        for (int ti = 0; ti < nt; ti++) {
+            const int c = L.tasks[ti].c;
+            for (int e = L.early_ptr[c]; e < L.early_ptr[c + 1]; e++)
+                stage_of[ti] = std::max(stage_of[ti], stage_of[L.early[e].first] + 1);
+        }
         int nst = 0;
         for (int v : stage_of) nst = std::max(nst, v + 1);
         std::vector<int> order(L.tasks.size());
@@ -916,6 +1078,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         upload(L.d_ph, L.ap_stage, st);
         L.hmeta = std::move(hmeta);
         L.early.clear();
+        L.early_ptr.clear();
     }
     tr.mark("  solve records");
     // algorithmic work: POTRF s^3/3, TRSM s^2 (n + w), CPQR sum_k 4 (s-k)(w-k) + 4 s r n, Schur n^2 f
@@ -960,8 +1123,10 @@ void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& dst_of, 
         f.len = L.fin[c];
         f.to_top = to_top[c];
         f.pull0 = (int)L.ap_pulls.size();
-        for (auto& pk : L.late[c])
+        for (int e = L.late_ptr[c]; e < L.late_ptr[c + 1]; e++) {
+            const auto& pk = L.late[e];
             L.ap_pulls.push_back(ApPull{L.stg[pk.first] + L.hmeta[L.tasks[pk.first].meta + 1 + 2 * pk.second]});
+        }
         f.pull1 = (int)L.ap_pulls.size();
         fins.push_back(f);
     }
@@ -972,11 +1137,9 @@ void make_vcopies(hs_factor_s* h, Level& L, const std::vector<int64_t>& dst_of, 
     upload(L.d_ap_pulls, L.ap_pulls, h->st);
     L.late.clear();
     L.late.shrink_to_fit();
+    L.late_ptr.clear();
 }
 
-// Block copies from level-l blocks (table T, final sizes fin, end pattern endp)
-// into the next level (table Tn) or, if Tn == nullptr, into the dense top
-// (row offsets top_off, leading dimension ntop).
 // Block copies from level-l blocks (table T, final sizes fin, end pattern
 // endp) into the parents: cluster a goes to parent par[a] at row offset
 // poff[a] (next level, table Tn, sizes nsize), or, when par[a] < 0, into its
@@ -985,14 +1148,13 @@ std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& f
                                    const BlockTable* Tn, const std::vector<int>& nsize, const std::vector<int>& par,
                                    const std::vector<int>& poff, const std::vector<int64_t>& tmat,
                                    const std::vector<int64_t>& tpos, const std::vector<int>& tn, bool to_tops) {
-    std::vector<CopyDev> cps;
-    for (int a = 0; a < P.nc; a++) {
-        if (fin[a] <= 0) continue;
-        if ((par[a] < 0) != to_tops) continue;
+    return parallel_collect<CopyDev>(P.nc, 1024, [&](int64_t a, std::vector<CopyDev>& cps) {
+        if (fin[a] <= 0) return;
+        if ((par[a] < 0) != to_tops) return;
         for (int b : P.endp[a]) {
             if (fin[b] <= 0) continue;
             CopyDev c{};
-            const int sb = T.find(a, b);
+            const int sb = T.find((int)a, b);
             c.src = T.off[sb];
             c.src_ld = T.ld[sb];
             if (!to_tops) {
@@ -1007,8 +1169,7 @@ std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& f
             c.cols = fin[b];
             cps.push_back(c);
         }
-    }
-    return cps;
+    });
 }
 
 void build_apply_graph(hs_factor_s* h);
@@ -1022,7 +1183,10 @@ void partition_batched(hs_factor_s* h, const int64_t* rp, const int32_t* cl, con
     std::vector<std::vector<int32_t>> perm(np), lp(np);
     std::atomic<int> next{0}, bad{0};
     auto work = [&] {
-        tl_serial = true;
+        struct Serial {  // nested parallel loops of this thread stay serial
+            Serial() { tl_serial = true; }
+            ~Serial() { tl_serial = false; }
+        } serial;
         std::vector<int64_t> srp;
         std::vector<int32_t> scol;
         for (int p = next++; p < np; p = next++) {
@@ -1041,14 +1205,7 @@ void partition_batched(hs_factor_s* h, const int64_t* rp, const int32_t* cl, con
                            h->opt.leaf_lines, h->opt.theta, perm[p], lp[p]);
         }
     };
-    {
-        const int T = std::min(hs_threads(), np);
-        std::vector<std::thread> th;
-        for (int t = 1; t < T; t++) th.emplace_back(work);
-        work();
-        tl_serial = false;
-        for (auto& x : th) x.join();
-    }
+    run_threads(std::min(hs_threads(), np), [&](int) { work(); });
     if (bad) throw HsError{HS_ERR_ARG};  // an entry couples two problems
     h->perm.resize(h->n);
     leaf_ptr.assign(1, 0);
@@ -1166,11 +1323,13 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
 
     // level 0 pattern
     std::vector<int32_t> dof_cluster(n), dof_local(n);
-    for (int c = 0; c < nleaf; c++)
-        for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
-            dof_cluster[h->perm[k]] = c;
-            dof_local[h->perm[k]] = k - leaf_ptr[c];
-        }
+    parallel_ranges(nleaf, 256, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t c = lo; c < hi; c++)
+            for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
+                dof_cluster[h->perm[k]] = (int32_t)c;
+                dof_local[h->perm[k]] = k - leaf_ptr[c];
+            }
+    });
     LevelPlan P;
     P.nc = nleaf;
     P.size0.resize(nleaf);
@@ -1178,26 +1337,33 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     P.adj0.assign(nleaf, {});
     {
         // block pattern of level 0, kept symmetric even if the CSR pattern is not
-        std::vector<int> stamp(nleaf, -1);
-        for (int c = 0; c < nleaf; c++) {
-            auto& v = P.adj0[c];
-            for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
-                const int i = h->perm[k];
-                for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-                    const int q = dof_cluster[cl[e]];
-                    if (q != c && stamp[q] != c) {
-                        stamp[q] = c;
-                        v.push_back(q);
+        parallel_ranges(nleaf, 256, [&](int64_t lo, int64_t hi, int) {
+            std::vector<int> stamp(nleaf, -1);
+            for (int64_t c = lo; c < hi; c++) {
+                auto& v = P.adj0[c];
+                for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
+                    const int i = h->perm[k];
+                    for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+                        const int q = dof_cluster[cl[e]];
+                        if (q != c && stamp[q] != c) {
+                            stamp[q] = (int)c;
+                            v.push_back(q);
+                        }
                     }
                 }
+                std::sort(v.begin(), v.end());
             }
-        }
+        });
+        std::vector<std::pair<int, int>> missing;  // (q, c) with c -> q but not q -> c
         for (int c = 0; c < nleaf; c++)
             for (int q : P.adj0[c])
-                if (!std::binary_search(P.adj0[q].begin(), P.adj0[q].end(), c) &&
-                    std::find(P.adj0[q].begin(), P.adj0[q].end(), c) == P.adj0[q].end())
-                    P.adj0[q].push_back(c);
-        for (auto& v : P.adj0) std::sort(v.begin(), v.end());
+                if (!std::binary_search(P.adj0[q].begin(), P.adj0[q].end(), c)) missing.push_back({q, c});
+        for (auto& m : missing) P.adj0[m.first].push_back(m.second);
+        for (auto& m : missing) {
+            auto& v = P.adj0[m.first];
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+        }
     }
 
     DBuf d_status;
@@ -1205,7 +1371,9 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     CK(cudaMemsetAsync(d_status.p, 0, sizeof(int32_t) * 4, st));
 
     tr.mark("upload A, level-0 pattern");
-    plan_level(P);
+    std::vector<std::pair<int, int>> ranges;
+    for (const auto& G : h->groups) ranges.push_back({(int)G.leaf_lo, (int)G.leaf_hi});
+    plan_level(P, ranges);
     BlockTable T = make_table(P);
     tr.mark("level-0 plan");
     DBuf blocks;
@@ -1278,7 +1446,9 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         h->lev.emplace_back(new Level());
         DBuf d_cur;
         upload(d_cur, P.size0, st);
-        factor_level(h, l, P, T, blocks, d_cur, d_status, info);
+        ranges.clear();
+        for (const Active& a : act) ranges.push_back({a.lo, a.hi});
+        factor_level(h, l, P, T, blocks, d_cur, d_status, info, ranges);
         tr.mark("level factor (records+kernels)");
         Level& L = *h->lev[l];
         const std::vector<int>& fin = L.fin;
@@ -1350,17 +1520,25 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             Pn.nc = nn;
             Pn.size0 = nsize;
             Pn.adj0.assign(nn, {});
-            for (int a = 0; a < nc; a++) {
-                if (fin[a] <= 0 || par[a] < 0) continue;
-                for (int b : P.endp[a])
-                    if (fin[b] > 0 && par[a] != par[b]) Pn.adj0[par[a]].push_back(par[b]);
-            }
-            for (auto& v : Pn.adj0) {
-                std::sort(v.begin(), v.end());
-                v.erase(std::unique(v.begin(), v.end()), v.end());
-            }
+            std::vector<int> kid0(nn, -1);  // first child of every parent (children are consecutive)
+            for (int a = nc - 1; a >= 0; a--)
+                if (par[a] >= 0) kid0[par[a]] = a;
+            parallel_ranges(nn, 512, [&](int64_t lo, int64_t hi, int) {
+                for (int64_t k = lo; k < hi; k++) {
+                    auto& v = Pn.adj0[k];
+                    for (int a = kid0[k]; a < nc && par[a] == k; a++) {
+                        if (fin[a] <= 0) continue;
+                        for (int b : P.endp[a])
+                            if (fin[b] > 0 && par[b] != k) v.push_back(par[b]);
+                    }
+                    std::sort(v.begin(), v.end());
+                    v.erase(std::unique(v.begin(), v.end()), v.end());
+                }
+            });
             tr.mark("next-level adjacency");
-            plan_level(Pn);
+            ranges.clear();
+            for (const Active& a : nact) ranges.push_back({a.lo, a.hi});
+            plan_level(Pn, ranges);
             tr.mark("next-level plan_level");
             BlockTable Tn = make_table(Pn);
             DBuf nblocks;
