@@ -80,6 +80,19 @@ typedef struct {
                             0 = never; default 4096                           */
     int32_t fused_levels; /* nonzero (default): levels whose clusters have at
                             most 32 DOFs run all their phases in one launch   */
+    int32_t record_ranks; /* nonzero: keep the rank predictor's features and
+                            the rank of every eliminated cluster for
+                            hs_rank_samples (default 0)                       */
+    const float* rank_model; /* NULL (default), or a trained rank predictor
+                            (host, HS_MLP_MODEL floats: feature means (8),
+                            deviations (8), network parameters).  Mixed form
+                            only: a cluster predicted to have rank 0 scales
+                            its fill columns in FP32 only; if their squared
+                            norm is at most eps^2 / 2 its rank is 0 and the
+                            FP64 scaling of those columns and the QR are
+                            skipped, otherwise they are scaled again in FP64
+                            and the column-pivoted QR decides as usual.
+                            Copied during hs_setup.                           */
 } hs_options;
 
 typedef struct {
@@ -213,6 +226,55 @@ int hs_launch_count(int64_t* count);
 /* Measures the FP64 FMA throughput of the current device with a chain of
  * independent fma() operations (8 per thread, 8 CTAs per SM); TFLOP/s out. */
 int hs_measure_fp64_peak(void* stream, double* tflops);
+
+/* ---- Rank predictor ----
+ * No counterpart in the paper.  A three-layer perceptron of width 64 maps 8
+ * features of a scaled block row (the block G^-1 [A_sn A_sw] whose
+ * column-pivoted QR decides the rank, Sec. 3.1) to the fraction r / s of its
+ * numerical rank; the factorization can record (features, rank) pairs of
+ * every cluster it eliminates (hs_rank_samples) to train it on.  FP32.
+ * Parameter vector (HS_MLP_NPARAM floats): W1 (64 x 8, row-major), b1 (64),
+ * W2 (64 x 64, row-major), b2 (64), w3 (64), b3 (1);
+ * h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = w3 . h2 + b3; loss over a
+ * batch (1/B) sum (y - t)^2; Adam with beta1 0.9, beta2 0.999, eps 1e-8. */
+#define HS_MLP_NIN 8
+#define HS_MLP_NPARAM 4801
+#define HS_MLP_MAX_BATCH 256
+#define HS_MLP_MODEL (2 * HS_MLP_NIN + HS_MLP_NPARAM)
+
+/* y[i] = network(x[i * 8 .. i * 8 + 8)) for i < n.  Device pointers; stream-ordered. */
+int hs_mlp_forward(const float* params, const float* x, int64_t n, float* y, void* stream);
+
+/* Loss and gradient of one minibatch: rows idx[0..batch) of x (n x 8) and t
+ * (idx may be NULL: rows 0..batch).  batch in 1..HS_MLP_MAX_BATCH.  grad:
+ * HS_MLP_NPARAM floats, loss: 1 float.  Device pointers; stream-ordered;
+ * deterministic (fixed summation order). */
+int hs_mlp_grad(const float* params, const float* x, const float* t, const int32_t* idx, int32_t batch,
+                float* grad, float* loss, void* stream);
+
+/* One Adam update of params with grad (step counts from 1); m, v: moment
+ * vectors (HS_MLP_NPARAM floats, zero before step 1).  Device pointers. */
+int hs_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr, void* stream);
+
+/* Minibatch training on the GPU: step k (k < nsteps) takes the samples
+ * order[k * batch .. (k + 1) * batch) of x (n x 8) / t (n) and applies
+ * hs_mlp_grad + hs_mlp_adam.  Host arrays: params (in: initial, out:
+ * trained), x, t, order (nsteps * batch indices < n), losses (nsteps floats,
+ * the loss before each update; may be NULL).  Returns after completion. */
+int hs_mlp_train(float* params, const float* x, const float* t, int64_t n, const int32_t* order, int64_t nsteps,
+                 int32_t batch, float lr, float* losses, void* stream);
+
+/* (features, rank, size) of every cluster the factorization eliminated, in
+ * level order and, within a level, in elimination order; the handle must
+ * have been set up with options.record_ranks.  Host arrays: feat count x 8
+ * floats, rank and size count int32 each; pass feat = NULL to query *count.
+ * Features (all known before the scaling step): 0 s (rows of the block
+ * row), 1 n columns (neighbour blocks of the level input), 2 fill columns,
+ * 3 level, 4 blocks in the row, 5 log10 of ||D^-1 A_sw||_F / eps with D the
+ * diagonal of the Cholesky factor G, 6 log10 of max |A_ss| off its diagonal
+ * over max |[A_sn A_sw]|, 7 log10 of the largest column norm of D^-1 A_sw
+ * over eps (5 and 7 are -30 when the cluster has no fill columns). */
+int hs_rank_samples(hs_handle h, float* feat, int32_t* rank, int32_t* size, int64_t* count);
 
 /* Static string for a status code. */
 const char* hs_status_str(int status);

@@ -547,10 +547,8 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
 // ranges' phase k (identical to planning all clusters at once).
 void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {}) {
     const int nc = P.nc;
-    std::vector<std::vector<int>> cur = P.adj0;
-    P.all = P.adj0;
-    for (int c = 0; c < nc; c++)
-        if (P.size0[c] > 0) sorted_insert(P.all[c], c);
+    std::vector<std::vector<int>> cur(nc);
+    P.all.assign(nc, {});
     P.phase.assign(nc, -1);
     P.nl.assign(nc, {});
     P.wl.assign(nc, {});
@@ -562,7 +560,14 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
     std::vector<std::vector<std::vector<int>>> ph(rg.size());
     std::atomic<int> next{0};
     auto work = [&] {
-        for (int k = next++; k < (int)rg.size(); k = next++) plan_range(P, cur, rg[k].first, rg[k].second, ph[k]);
+        for (int k = next++; k < (int)rg.size(); k = next++) {
+            for (int c = rg[k].first; c < rg[k].second; c++) {
+                cur[c] = P.adj0[c];
+                P.all[c] = P.adj0[c];
+                if (P.size0[c] > 0) sorted_insert(P.all[c], c);
+            }
+            plan_range(P, cur, rg[k].first, rg[k].second, ph[k]);
+        }
     };
     run_threads(std::min<int>(hs_threads(), (int)rg.size()), [&](int) { work(); });
     size_t nph = 0;
@@ -594,6 +599,7 @@ struct Level {
     std::vector<std::pair<int, int>> early, late;
     std::vector<int64_t> stg;          // stage offset of every task
     std::vector<int32_t> hmeta;        // rank and n-column layout of every task
+    DBuf d_feat;                       // rank-predictor features per task (record_ranks)
     std::vector<int> task_rank;        // filled after the level
     std::vector<ApPull> ap_pulls;      // early pulls of the tasks, then the late pulls
     int64_t work_max_phase = 0;        // largest sum over a stage of s^2 + f * ncols
@@ -660,6 +666,7 @@ struct hs_factor_s {
     int64_t n = 0;
     std::vector<Group> groups;
     std::vector<int64_t> prob_ptr;  // DOF offsets of the problems (original order)
+    DBuf d_model;                   // rank predictor (options.rank_model), device copy
     int64_t prob_maxlen = 0;
     DBuf d_pp;
     std::vector<DBuf> top_bufs;  // dense tops, one buffer per level at which problems end
@@ -926,7 +933,8 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
     }
     L.wmax = std::max(L.wmax, 64);  // the fused kernel's Schur step stages 32 x 4 int64 in the column table
-    if (factor_smem_bytes(L.smax, L.wmax, L.lmax) > (size_t)kFactorMaxSmem) throw HsError{HS_ERR_UNSUPPORTED};
+    if (factor_smem_bytes(L.smax, L.wmax, L.lmax, h->opt.rank_model != nullptr) > (size_t)kFactorMaxSmem)
+        throw HsError{HS_ERR_UNSUPPORTED};
     Trace tr;
     tr.mark("  records");
 
@@ -947,6 +955,11 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     upload(d_off, T.off, st);
     upload(d_ld, ld, st);
     const double eps2 = h->opt.tol * h->opt.tol;
+    float* feat = nullptr;
+    if (h->opt.record_ranks) {
+        L.d_feat.alloc(sizeof(float) * kFeat * std::max(nt, 1));
+        feat = L.d_feat.as<float>();
+    }
     tr.mark("  uploads");
     int64_t mcap = 0;  // largest block row (with the identity columns)
     for (const TaskDev& t : L.tasks) mcap = std::max<int64_t>(mcap, (int64_t)t.s * (t.wcap + t.s));
@@ -966,7 +979,8 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                                      L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
                                      d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
                                      L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l,
-                                     L.smax, L.wmax, L.lmax, mcap, max_items, d_bar.as<unsigned>()));
+                                     L.smax, L.wmax, L.lmax, mcap, max_items, d_bar.as<unsigned>(), feat,
+                                     h->d_model.as<float>()));
         h->prof.end(KC_FACTOR, st);
     }
     for (int ph = 0; ph < (fused ? 0 : L.nphases); ph++) {
@@ -975,7 +989,8 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         CK(launch_factor_phase(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.wmax, L.lmax,
                                L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
                                d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
-                               L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l));
+                               L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l, feat,
+                               h->d_model.as<float>()));
         h->prof.end(KC_FACTOR, st);
         const int g0 = L.ph_target[ph], ng = L.ph_target[ph + 1] - g0;
         if (ng > 0) {
@@ -1309,6 +1324,10 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     h->depth = depth;
     tr.mark("pattern+partition");
 
+    if (h->opt.rank_model) {
+        h->d_model.alloc(sizeof(float) * kModelFloats);
+        CK(cudaMemcpyAsync(h->d_model.p, h->opt.rank_model, sizeof(float) * kModelFloats, cudaMemcpyHostToDevice, st));
+    }
     // device copies of A (SpMV) and of the permutation
     h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));
     h->d_col.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
@@ -2143,6 +2162,8 @@ int hs_default_options(hs_options* opt) {
     opt->coords = nullptr;
     opt->coarse_dense = 4096;
     opt->fused_levels = 1;
+    opt->record_ranks = 0;
+    opt->rank_model = nullptr;
     return HS_OK;
 }
 
@@ -2431,6 +2452,89 @@ int hs_reset_kernel_stats(hs_handle h) {
     if (!h) return HS_ERR_ARG;
     h->prof.reset();
     return HS_OK;
+}
+
+int hs_rank_samples(hs_handle h, float* feat, int32_t* rank, int32_t* size, int64_t* count) {
+    if (!h || !count) return HS_ERR_ARG;
+    int64_t k = 0;
+    for (auto& Lp : h->lev) k += (int64_t)Lp->tasks.size();
+    if (!feat) {
+        *count = h->opt.record_ranks ? k : 0;
+        return HS_OK;
+    }
+    if (!h->opt.record_ranks || !rank || !size) return HS_ERR_ARG;
+    return run_guarded([&] {
+        g_alloc_stream = h->st;
+        int64_t o = 0;
+        for (auto& Lp : h->lev) {
+            const Level& L = *Lp;
+            const int nt = (int)L.tasks.size();
+            if (nt == 0) continue;
+            CK(cudaMemcpyAsync(feat + o * kFeat, L.d_feat.p, sizeof(float) * kFeat * nt, cudaMemcpyDeviceToHost, h->st));
+            for (int ti = 0; ti < nt; ti++) {
+                rank[o + ti] = L.task_rank[ti];
+                size[o + ti] = L.tasks[ti].s;
+            }
+            o += nt;
+        }
+        CK(cudaStreamSynchronize(h->st));
+        *count = o;
+    });
+}
+
+int hs_mlp_forward(const float* params, const float* x, int64_t n, float* y, void* stream) {
+    if (!params || n < 0 || (n > 0 && (!x || !y))) return HS_ERR_ARG;
+    return run_guarded([&] { CK(launch_mlp_forward(static_cast<cudaStream_t>(stream), params, x, n, y)); });
+}
+
+int hs_mlp_grad(const float* params, const float* x, const float* t, const int32_t* idx, int32_t batch,
+                float* grad, float* loss, void* stream) {
+    if (!params || !x || !t || !grad || !loss || batch < 1 || batch > kMlpMaxBatch) return HS_ERR_ARG;
+    return run_guarded(
+        [&] { CK(launch_mlp_grad(static_cast<cudaStream_t>(stream), params, x, t, idx, batch, grad, loss)); });
+}
+
+int hs_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr, void* stream) {
+    if (!params || !grad || !m || !v || step < 1) return HS_ERR_ARG;
+    return run_guarded([&] { CK(launch_mlp_adam(static_cast<cudaStream_t>(stream), params, grad, m, v, step, lr)); });
+}
+
+int hs_mlp_train(float* params, const float* x, const float* t, int64_t n, const int32_t* order, int64_t nsteps,
+                 int32_t batch, float lr, float* losses, void* stream) {
+    if (!params || !x || !t || n <= 0 || !order || nsteps < 0 || batch < 1 || batch > kMlpMaxBatch)
+        return HS_ERR_ARG;
+    for (int64_t i = 0; i < nsteps * batch; i++)
+        if (order[i] < 0 || order[i] >= n) return HS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return run_guarded([&] {
+        g_alloc_stream = st;
+        DBuf d_th, d_x, d_t, d_ord, d_g, d_m, d_v, d_loss;
+        d_th.alloc(sizeof(float) * kMlpParams);
+        d_x.alloc(sizeof(float) * n * kMlpIn);
+        d_t.alloc(sizeof(float) * n);
+        d_ord.alloc(sizeof(int32_t) * std::max<int64_t>(nsteps * batch, 1));
+        d_g.alloc(sizeof(float) * kMlpParams);
+        d_m.alloc(sizeof(float) * kMlpParams);
+        d_v.alloc(sizeof(float) * kMlpParams);
+        d_loss.alloc(sizeof(float) * std::max<int64_t>(nsteps, 1));
+        CK(cudaMemcpyAsync(d_th.p, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_x.p, x, sizeof(float) * n * kMlpIn, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_t.p, t, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+        if (nsteps > 0)
+            CK(cudaMemcpyAsync(d_ord.p, order, sizeof(int32_t) * nsteps * batch, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(d_m.p, 0, sizeof(float) * kMlpParams, st));
+        CK(cudaMemsetAsync(d_v.p, 0, sizeof(float) * kMlpParams, st));
+        for (int64_t k = 0; k < nsteps; k++) {
+            CK(launch_mlp_grad(st, d_th.as<float>(), d_x.as<float>(), d_t.as<float>(), d_ord.as<int32_t>() + k * batch,
+                               batch, d_g.as<float>(), d_loss.as<float>() + k));
+            CK(launch_mlp_adam(st, d_th.as<float>(), d_g.as<float>(), d_m.as<float>(), d_v.as<float>(), (int)(k + 1),
+                               lr));
+        }
+        CK(cudaMemcpyAsync(params, d_th.p, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st));
+        if (losses && nsteps > 0)
+            CK(cudaMemcpyAsync(losses, d_loss.p, sizeof(float) * nsteps, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    });
 }
 
 int hs_launch_count(int64_t* count) {

@@ -120,7 +120,8 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
 cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax,
                                 int wmax, int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
                                 const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
-                                double* ws, double eps2, int32_t* status, int32_t level);
+                                double* ws, double eps2, int32_t* status, int32_t level, float* feat,
+                                const float* model);
 cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
                                const ContribDev* contribs, const TaskDev* tasks, const void* fac,
                                const int32_t* meta, double* blocks, const int64_t* blk_off,
@@ -182,7 +183,7 @@ cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double*
 cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv,
                           const double* w, double* partial, double* out);
 
-size_t factor_smem_bytes(int smax, int wmax, int lmax);
+size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32 = false);
 // coarse levels: all phases of a level in one single-CTA launch (warp per task)
 constexpr int kFusedWarps = 16, kFusedSmax = 32;
 size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap);
@@ -191,8 +192,22 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
                                       int nph, const ListDev* lists, double* blocks, const int64_t* blk_off,
                                       const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                       double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
-                                      int lmax, int64_t mcap, int max_items, unsigned* bar);
+                                      int lmax, int64_t mcap, int max_items, unsigned* bar, float* feat,
+                                      const float* model);
 // process-wide count of this library's kernel launches
+// rank predictor (hs_mlp.cu): 8 -> 64 -> 64 -> 1 perceptron, FP32
+constexpr int kMlpIn = 8, kMlpHidden = 64;
+constexpr int kFeat = kMlpIn;  // features recorded per eliminated cluster
+constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + kMlpHidden + 1;
+constexpr int kMlpMaxBatch = 256, kMlpThreads = 512;
+constexpr int kModelFloats = 2 * kMlpIn + kMlpParams;  // mu, sd, network
+constexpr float kAdamBeta1 = 0.9f, kAdamBeta2 = 0.999f, kAdamEps = 1e-8f;
+size_t mlp_grad_smem_bytes();
+cudaError_t launch_mlp_forward(cudaStream_t st, const float* theta, const float* x, int64_t n, float* y);
+cudaError_t launch_mlp_grad(cudaStream_t st, const float* theta, const float* x, const float* t, const int32_t* idx,
+                            int B, float* grad, float* loss);
+cudaError_t launch_mlp_adam(cudaStream_t st, float* theta, const float* grad, float* m, float* v, int step,
+                            float lr);
 int64_t launch_count();
 void launch_count_add(int64_t k);
 cudaError_t launch_fp64_peak(cudaStream_t st, int nblocks, int iters, double* sink);

@@ -164,11 +164,12 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
                               double* red, double* s_hh, const EntryMeta* em, const int* ioff,
                               double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                               const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
-                              int32_t* __restrict__ meta, double eps2) {
+                              int32_t* __restrict__ meta, double eps2, bool rank0 = false) {
     const int s = T.s, tid = g.rank, NT = g.size;
     const int L = T.nn + T.nw, Wn = W - ncols;
     // column-pivoted QR of the fill columns, reflectors applied to the whole row
-    for (int j = tid; j < Wn; j += NT) {
+    // rank0: the rank is already known to be 0 (no reflector)
+    for (int j = tid; j < (rank0 ? 0 : Wn); j += NT) {
         CT c = 0;
         for (int i = 0; i < s; i++) {
             const CT x = M[(int64_t)i * Wt + ncols + j];
@@ -178,7 +179,7 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
     }
     g.sync();
     int k = 0;
-    while (k < s) {
+    while (k < s && !rank0) {
         double lt = 0.0, lm = 0.0;
         for (int j = tid; j < Wn; j += NT) {
             const double c = (double)cn[j];
@@ -287,6 +288,37 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
     if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
 }
 
+// Rank predictor inside a factor task: y = w3 . relu(W2 relu(W1 xn + b1) + b2)
+// + b3 on the standardised features xn = (f - mu) / sd.  model: mu (8), sd
+// (8), then the network's parameter vector (kMlpParams floats, the layout of
+// the training kernels).  h: 64 floats of scratch.  Every thread returns y.
+template <typename Grp>
+__device__ float predict_fraction(const Grp& g, const float* __restrict__ model, const float* f, float* h,
+                                  double* red) {
+    const float* mu = model;
+    const float* sd = model + kMlpIn;
+    const float* th = model + 2 * kMlpIn;
+    const float* W1 = th;
+    const float* b1 = W1 + kMlpHidden * kMlpIn;
+    const float* W2 = b1 + kMlpHidden;
+    const float* b2 = W2 + kMlpHidden * kMlpHidden;
+    const float* w3 = b2 + kMlpHidden;
+    const float b3 = w3[kMlpHidden];
+    for (int j = g.rank; j < kMlpHidden; j += g.size) {
+        float a = b1[j];
+        for (int i = 0; i < kMlpIn; i++) a += W1[j * kMlpIn + i] * ((f[i] - mu[i]) / sd[i]);
+        h[j] = a > 0.f ? a : 0.f;
+    }
+    g.sync();
+    double part = 0.0;
+    for (int j = g.rank; j < kMlpHidden; j += g.size) {
+        float a = b2[j];
+        for (int k = 0; k < kMlpHidden; k++) a += W2[j * kMlpHidden + k] * h[k];
+        part += (double)(w3[j] * (a > 0.f ? a : 0.f));
+    }
+    return (float)(g.sum(part, red) + (double)b3);
+}
+
 // One scaled low-rank elimination (Sec. 3.1) by the group g.  Shared memory
 // of the group: G (s*s), rdiag (s), v (s), cn (fill columns), red (>= 64
 // doubles), ioff (list length + 1 ints), flag, hh (3 doubles).
@@ -300,9 +332,10 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                             double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                             const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
                             int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
-                            int32_t level) {
+                            int32_t level, float* fe, const float* __restrict__ model, float* G32) {
     const int s = T.s, tid = g.rank, NT = g.size;
     const int L = T.nn + T.nw;
+    const bool want_feat = fe != nullptr || model != nullptr;
     // entry metadata (one round of loads for all entries), then the column
     // offsets of the row blocks (compact, current widths)
     for (int e = tid; e < L; e += NT) {
@@ -327,12 +360,18 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         *s_flag = 0;
     }
     // A_ss -> shared memory
+    double amax_ss = 0.0;  // largest |A_ss| off the diagonal (features only)
     {
         const double* A = blocks + blk_off[T.diag_blk];
         const int ld = blk_ld[T.diag_blk];
-        for (int idx = tid; idx < s * s; idx += NT) G[idx] = A[(int64_t)(idx / s) * ld + idx % s];
+        for (int idx = tid; idx < s * s; idx += NT) {
+            const double a = A[(int64_t)(idx / s) * ld + idx % s];
+            G[idx] = a;
+            if (idx / s != idx % s) amax_ss = fmax(amax_ss, fabs(a));
+        }
     }
     g.sync();
+    if (want_feat) amax_ss = g.max(amax_ss, red);
     const int W = ioff[L], ncols = ioff[T.nn], Wn = W - ncols;
 
     // Cholesky A_ss = G G^T in shared memory, right-looking in panels of kNB
@@ -408,23 +447,81 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             colsrc[2 * (ioff[e] + j) + 1] = em[e].ldcq;
         }
     g.sync();
+    double amax_row = 0.0;  // largest |[A_sn A_sw]| (features only)
     for (int idx = tid; idx < s * W; idx += NT) {
         const int i = idx / W, j = idx % W;
-        M[(int64_t)i * Wt + j] = blocks[colsrc[2 * j] + (int64_t)i * colsrc[2 * j + 1]];
+        const double a = blocks[colsrc[2 * j] + (int64_t)i * colsrc[2 * j + 1]];
+        M[(int64_t)i * Wt + j] = a;
+        amax_row = fmax(amax_row, fabs(a));
     }
     for (int idx = tid; idx < s * s; idx += NT) {
         const int i = idx / s, j = idx % s;
         M[(int64_t)i * Wt + W + j] = (i == j) ? 1.0 : 0.0;
     }
     g.sync();
+    // features of the block row (the column table is free from here on):
+    // structure, the coupling ratio, and the fill block scaled by the
+    // Cholesky diagonal, D^-1 A_sw (D = diag G), known before the scaling
+    float* fsh = reinterpret_cast<float*>(colsrc);  // 8 features, then 64 floats of scratch
+    if (want_feat) {
+        amax_row = g.max(amax_row, red);
+        double lt = 0.0, lm = 0.0;
+        for (int j = tid; j < Wn; j += NT) {
+            double cj = 0.0;
+            for (int i = 0; i < s; i++) {
+                const double x = M[(int64_t)i * Wt + ncols + j] * rdiag[i];
+                cj += x * x;
+            }
+            lt += cj;
+            lm = fmax(lm, cj);
+        }
+        const double total = g.sum(lt, red), cmax = g.max(lm, red);
+        if (tid == 0) {
+            const double e = eps2 > 0.0 ? sqrt(eps2) : 1e-300;
+            fsh[0] = (float)s;
+            fsh[1] = (float)ncols;
+            fsh[2] = (float)Wn;
+            fsh[3] = (float)level;
+            fsh[4] = (float)L;
+            fsh[5] = Wn > 0 ? (float)fmax(log10(fmax(sqrt(total), 1e-300) / e), -30.0) : -30.f;
+            // coupling inside the cluster against coupling to its neighbours
+            fsh[6] = (float)fmin(fmax(log10(fmax(amax_ss, 1e-300) / fmax(amax_row, 1e-300)), -30.0), 30.0);
+            fsh[7] = Wn > 0 ? (float)fmax(log10(fmax(sqrt(cmax), 1e-300) / e), -30.0) : -30.f;
+        }
+        g.sync();
+        if (fe && tid < kFeat) fe[tid] = fsh[tid];
+    }
+    // learned rank-0 speculation (mixed form): when the predictor says rank 0,
+    // the fill columns are scaled in FP32 only, and the rank is certified 0
+    // if their squared norm is at most eps^2 / 2; otherwise they are gathered
+    // again and scaled in FP64 and the column-pivoted QR decides as usual
+    bool spec0 = false;
+    if (model && G32 && sizeof(FT) == sizeof(float) && Wn > 0) {
+        const float y = predict_fraction(g, model, fsh, fsh + kFeat, red);
+        spec0 = y * (float)s < 0.5f;
+        if (spec0)
+            for (int idx = tid; idx < s * s; idx += NT) G32[idx] = (float)G[idx];
+        g.sync();
+    }
 
     // scaling: M <- G^-1 M (forward substitution, one thread per column).
     // A column that is zero above row i0 (identity column j: i0 = j; level-0
     // face couplings: their first nonzero) keeps those zeros, so the
-    // substitution starts at i0; all-zero columns are skipped.
+    // substitution starts at i0; all-zero columns are skipped.  Speculated
+    // fill columns run in FP32 (values kept in the first float of each slot).
     for (int j = tid; j < Wt; j += NT) {
         int i0 = (j >= W) ? j - W : 0;
         while (i0 < s && M[(int64_t)i0 * Wt + j] == 0.0) i0++;
+        if (spec0 && j >= ncols && j < W) {
+            float* Mf = reinterpret_cast<float*>(M);
+            for (int i = i0; i < s; i++) {
+                float acc = (float)M[(int64_t)i * Wt + j];
+                for (int k = i0; k < i; k++) acc -= G32[i * s + k] * Mf[2 * ((int64_t)k * Wt + j)];
+                Mf[2 * ((int64_t)i * Wt + j)] = acc * (float)rdiag[i];
+            }
+            for (int i = 0; i < i0; i++) Mf[2 * ((int64_t)i * Wt + j)] = 0.f;
+            continue;
+        }
         for (int i = i0; i < s; i++) {
             double acc = M[(int64_t)i * Wt + j];
             for (int k = i0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * Wt + j];
@@ -432,8 +529,46 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         }
     }
     g.sync();
+    bool rank0 = false;
+    if (spec0) {
+        const float* Mf = reinterpret_cast<const float*>(M);
+        double lt = 0.0;
+        for (int j = tid; j < Wn; j += NT)
+            for (int i = 0; i < s; i++) {
+                const double x = (double)Mf[2 * ((int64_t)i * Wt + ncols + j)];
+                lt += x * x;
+            }
+        rank0 = g.sum(lt, red) <= 0.5 * eps2;
+        if (!rank0) {
+            // fallback: the fill columns again from the blocks, scaled in FP64
+            for (int e = T.nn + tid; e < L; e += NT)
+                for (int j = 0; j < em[e].w; j++) {
+                    colsrc[2 * (ioff[e] + j)] = em[e].cq + j;
+                    colsrc[2 * (ioff[e] + j) + 1] = em[e].ldcq;
+                }
+            g.sync();
+            for (int idx = tid; idx < s * Wn; idx += NT) {
+                const int i = idx / Wn, j = ncols + idx % Wn;
+                M[(int64_t)i * Wt + j] = blocks[colsrc[2 * j] + (int64_t)i * colsrc[2 * j + 1]];
+            }
+            g.sync();
+            for (int j = ncols + tid; j < W; j += NT) {
+                int i0 = 0;
+                while (i0 < s && M[(int64_t)i0 * Wt + j] == 0.0) i0++;
+                for (int i = i0; i < s; i++) {
+                    double acc = M[(int64_t)i * Wt + j];
+                    for (int k = i0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * Wt + j];
+                    M[(int64_t)i * Wt + j] = acc * rdiag[i];
+                }
+            }
+            g.sync();
+        }
+    }
 
-    if constexpr (sizeof(FT) == sizeof(float)) {
+    if (rank0) {
+        compress_task<double, FT>(T, g, M, Wt, W, ncols, v, cn, red, s_hh, em, ioff, blocks, blk_off, blk_ld, cur,
+                                  fac, meta, eps2, true);
+    } else if constexpr (sizeof(FT) == sizeof(float)) {
         // mixed form: the compression runs on an FP32 copy of the scaled row
         to_float_inplace(g, M, (int64_t)s * Wt);
         compress_task<float, FT>(T, g, reinterpret_cast<float*>(M), Wt, W, ncols, reinterpret_cast<float*>(v),
@@ -451,7 +586,8 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
                double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
                int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
-               int32_t level, int smax, int wmax, int lmax) {
+               int32_t level, int smax, int wmax, int lmax, float* __restrict__ feat,
+               const float* __restrict__ model) {
     extern __shared__ double sm[];
     __shared__ int s_flag;
     __shared__ double s_hh[3];
@@ -464,9 +600,13 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
     EntryMeta* em = reinterpret_cast<EntryMeta*>(red + 64);
     int64_t* colsrc = reinterpret_cast<int64_t*>(em + lmax);
     int* ioff = reinterpret_cast<int*>(colsrc + 2 * (size_t)wmax);
+    // FP32 copy of G for the learned rank-0 speculation (only with a model)
+    float* G32 = model ? reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(ioff + lmax + 1) + 15) & ~uintptr_t(15))
+                       : nullptr;
     CtaGroup g;
     factor_task<FT>(T, g, G, rdiag, v, cn, red, ioff, &s_flag, s_hh, nullptr, em, colsrc, lists, blocks, blk_off,
-                    blk_ld, cur, fac, meta, ws, eps2, status, level);
+                    blk_ld, cur, fac, meta, ws, eps2, status, level,
+                    feat ? feat + (size_t)(t0 + blockIdx.x) * kFeat : nullptr, model, G32);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,7 +784,8 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
                      double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                      const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
                      int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
-                     int32_t level, int smax, int wmax, int lmax, int64_t mcap, unsigned* bar) {
+                     int32_t level, int smax, int wmax, int lmax, int64_t mcap, unsigned* bar,
+                     float* __restrict__ feat, const float* __restrict__ model) {
     extern __shared__ double sm[];
     const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int gw = blockIdx.x * nwarp + wid, GW = gridDim.x * nwarp;
@@ -666,7 +807,8 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
     for (int ph = 0; ph < nph; ph++) {
         for (int t = ph_task[ph] + gw; t < ph_task[ph + 1]; t += GW)
             factor_task<FT>(tasks[t], g, G, rdiag, v, cn, red, ioff, flag, hh, Msh, em, colsrc, lists, blocks,
-                            blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level);
+                            blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level,
+                            feat ? feat + (size_t)t * kFeat : nullptr, model, nullptr);
         grid_sync(bar, status);
         for (int k = ph_target[ph] + gw; k < ph_target[ph + 1]; k += GW)
             schur_target_warp<FT>(targets[k], contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur, colsrc);
@@ -1426,35 +1568,38 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
     return cudaGetLastError();
 }
 
-size_t factor_smem_bytes(int smax, int wmax, int lmax) {
-    return sizeof(double) * ((size_t)smax * smax + 2 * (size_t)smax + (size_t)wmax + 64) +
-           sizeof(EntryMeta) * (size_t)lmax + 2 * sizeof(int64_t) * (size_t)wmax + sizeof(int) * ((size_t)lmax + 1);
+size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32) {
+    const size_t base = sizeof(double) * ((size_t)smax * smax + 2 * (size_t)smax + (size_t)wmax + 64) +
+                        sizeof(EntryMeta) * (size_t)lmax + 2 * sizeof(int64_t) * (size_t)wmax +
+                        sizeof(int) * ((size_t)lmax + 1);
+    return g32 ? (base + 15) / 16 * 16 + sizeof(float) * (size_t)smax * smax : base;
 }
 
 template <typename FT>
 cudaError_t factor_phase_t(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax, int wmax, int lmax,
                            const ListDev* lists, double* blocks, const int64_t* blk_off, const int32_t* blk_ld,
                            int32_t* cur, FT* fac, int32_t* meta, double* ws, double eps2, int32_t* status,
-                           int32_t level) {
-    const size_t smem = factor_smem_bytes(smax, wmax, lmax);
+                           int32_t level, float* feat, const float* model) {
+    const size_t smem = factor_smem_bytes(smax, wmax, lmax, model != nullptr);
     cudaError_t e = cudaFuncSetAttribute(k_factor_phase<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     counted();
     k_factor_phase<FT><<<ntasks, kFactorThreads, smem, st>>>(tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta,
-                                                             ws, eps2, status, level, smax, wmax, lmax);
+                                                             ws, eps2, status, level, smax, wmax, lmax, feat,
+                                                             model);
     return cudaGetLastError();
 }
 
 cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax, int wmax,
                                 int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
                                 const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta, double* ws,
-                                double eps2, int32_t* status, int32_t level) {
+                                double eps2, int32_t* status, int32_t level, float* feat, const float* model) {
     if (ntasks <= 0) return cudaSuccess;
     if (fp32)
         return factor_phase_t(st, tasks, t0, ntasks, smax, wmax, lmax, lists, blocks, blk_off, blk_ld, cur,
-                              static_cast<float*>(fac), meta, ws, eps2, status, level);
+                              static_cast<float*>(fac), meta, ws, eps2, status, level, feat, model);
     return factor_phase_t(st, tasks, t0, ntasks, smax, wmax, lmax, lists, blocks, blk_off, blk_ld, cur,
-                          static_cast<double*>(fac), meta, ws, eps2, status, level);
+                          static_cast<double*>(fac), meta, ws, eps2, status, level, feat, model);
 }
 
 size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap) {
@@ -1467,7 +1612,8 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
                                       int nph, const ListDev* lists, double* blocks, const int64_t* blk_off,
                                       const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                       double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
-                                      int lmax, int64_t mcap, int max_items, unsigned* bar) {
+                                      int lmax, int64_t mcap, int max_items, unsigned* bar, float* feat,
+                                      const float* model) {
     if (nph <= 0) return cudaSuccess;
     const size_t smem = fused_smem_bytes(smax, wmax, lmax, mcap);
     const void* fn = fp32 ? reinterpret_cast<const void*>(&k_factor_level_fused<float>)
@@ -1488,7 +1634,7 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
     counted();
     void* args[] = {&tasks,  &ph_task, &targets, &ph_target, &contribs, &nph,  &lists, &blocks,
                     &blk_off, &blk_ld, &cur,     &fac,       &meta,     &ws,   &eps2,  &status,
-                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar};
+                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar,  &feat,  &model};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFusedWarps * 32), args, smem, st);
 }
 

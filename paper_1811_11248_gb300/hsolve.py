@@ -36,7 +36,8 @@ class hs_options(ctypes.Structure):
     _fields_ = [("tol", F64), ("depth", I32), ("leaf_lines", I32), ("theta", F64),
                 ("precision", I32), ("krylov", I32), ("restart", I32), ("rtol", F64),
                 ("maxit", I32), ("mem", I32), ("profile", I32), ("stream", P), ("coords", P),
-                ("coarse_dense", I32), ("fused_levels", I32)]
+                ("coarse_dense", I32), ("fused_levels", I32), ("record_ranks", I32),
+                ("rank_model", P)]
 
 
 class hs_info(ctypes.Structure):
@@ -89,6 +90,12 @@ def lib():
     L.hs_krylov_batched.argtypes = [P, P, P, P, P, ctypes.POINTER(hs_info)]
     L.hs_num_problems.argtypes = [P, ctypes.POINTER(I32)]
     L.hs_problem_info.argtypes = [P, I32, P, P, P, P]
+    F32 = ctypes.c_float
+    L.hs_mlp_forward.argtypes = [P, P, I64, P, P]
+    L.hs_mlp_grad.argtypes = [P, P, P, P, I32, P, P, P]
+    L.hs_mlp_adam.argtypes = [P, P, P, P, I32, F32, P]
+    L.hs_mlp_train.argtypes = [P, P, P, I64, P, I64, I32, F32, P, P]
+    L.hs_rank_samples.argtypes = [P, P, P, P, ctypes.POINTER(I64)]
     L.hs_status_str.argtypes = [ctypes.c_int]
     L.hs_status_str.restype = ctypes.c_char_p
     _lib = L
@@ -100,7 +107,9 @@ EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_s
             "hs_krylov", "hs_krylov_noalloc", "hs_solve", "hs_destroy", "hs_num_levels", "hs_level_clusters",
             "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
             "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str", "hs_setup_batched",
-            "hs_krylov_batched", "hs_num_problems", "hs_problem_info")
+            "hs_krylov_batched", "hs_num_problems", "hs_problem_info", "hs_mlp_forward", "hs_mlp_grad",
+            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples")
+MLP_NIN, MLP_NPARAM, MLP_MAX_BATCH = 8, 4801, 256
 
 
 def _ptr(x):
@@ -133,6 +142,10 @@ def hs_default_options(**kw):
             v = P(v) if v is not None else None
         elif k == "coords":
             o._coords_keep = v  # the caller's array must outlive the call
+            v = _ptr(v)
+        elif k == "rank_model":
+            v = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+            o._model_keep = v
             v = _ptr(v)
         setattr(o, k, v)
     return o
@@ -239,6 +252,17 @@ class Handle:
         _check(lib().hs_problem_info(self._h, int(prob), *[ctypes.byref(x) for x in v]), "hs_problem_info")
         return tuple(int(x.value) for x in v)
 
+    def rank_samples(self):
+        """-> (features float32[k, 8], rank int32[k], size int32[k])."""
+        cnt = I64()
+        _check(lib().hs_rank_samples(self._h, None, None, None, ctypes.byref(cnt)), "hs_rank_samples")
+        k = int(cnt.value)
+        f = np.zeros((k, 8), np.float32)
+        r = np.zeros(k, np.int32)
+        s = np.zeros(k, np.int32)
+        _check(lib().hs_rank_samples(self._h, _ptr(f), _ptr(r), _ptr(s), ctypes.byref(cnt)), "hs_rank_samples")
+        return f, r, s
+
     def reset_kernel_stats(self):
         _check(lib().hs_reset_kernel_stats(self._h), "hs_reset_kernel_stats")
 
@@ -298,3 +322,34 @@ def hs_measure_fp64_peak(stream=None):
     _check(lib().hs_measure_fp64_peak(P(stream) if stream else None, ctypes.byref(v)),
            "hs_measure_fp64_peak")
     return float(v.value)
+
+
+def hs_mlp_forward(params, x, n, y, stream=None):
+    """Device pointers (torch tensors): params float32[4801], x float32[n, 8] -> y float32[n]."""
+    _check(lib().hs_mlp_forward(_ptr(params), _ptr(x), int(n), _ptr(y), P(stream) if stream else None),
+           "hs_mlp_forward")
+
+
+def hs_mlp_grad(params, x, t, idx, batch, grad, loss, stream=None):
+    _check(lib().hs_mlp_grad(_ptr(params), _ptr(x), _ptr(t), _ptr(idx), int(batch), _ptr(grad), _ptr(loss),
+                             P(stream) if stream else None), "hs_mlp_grad")
+
+
+def hs_mlp_adam(params, grad, m, v, step, lr, stream=None):
+    _check(lib().hs_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
+                             P(stream) if stream else None), "hs_mlp_adam")
+
+
+def hs_mlp_train(params, x, t, order, batch, lr, stream=None):
+    """Host arrays: params float32[4801] (copied; the trained vector is
+    returned), x float32[n, 8], t float32[n], order int32[nsteps * batch].
+    -> (params, losses float32[nsteps])."""
+    th = np.ascontiguousarray(params, dtype=np.float32).copy()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    nsteps = len(order) // int(batch)
+    losses = np.zeros(max(nsteps, 1), np.float32)
+    _check(lib().hs_mlp_train(_ptr(th), _ptr(x), _ptr(t), len(t), _ptr(order), nsteps, int(batch), float(lr),
+                              _ptr(losses), P(stream) if stream else None), "hs_mlp_train")
+    return th, losses[:nsteps]

@@ -275,3 +275,21 @@ def block_diagonal(problems):
 def batched_workload(count=256):
     """The first `count` problems of the batched workload, stacked."""
     return block_diagonal([batched_problem(p) for p in range(count)])
+
+
+def mlp_init_params(seed, nin=8, nh=64):
+    """Seeded initial weights of the rank predictor (He-style normal weights,
+    zero biases) in its flat layout W1 (nh x nin), b1, W2 (nh x nh), b2, w3, b3."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.standard_normal(nh * nin) * np.sqrt(2.0 / nin), np.zeros(nh),
+             rng.standard_normal(nh * nh) * np.sqrt(2.0 / nh), np.zeros(nh),
+             rng.standard_normal(nh) * np.sqrt(1.0 / nh), np.zeros(1)]
+    return np.concatenate(parts)
+
+
+def mlp_batch_order(n, batch, epochs, seed):
+    """Sample order of minibatch training: one seeded permutation of the n
+    samples per epoch, cut into full batches (a ragged tail is dropped)."""
+    rng = np.random.default_rng(seed)
+    steps = n // batch
+    return np.concatenate([rng.permutation(n)[:steps * batch] for _ in range(epochs)]).astype(np.int32)

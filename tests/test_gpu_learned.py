@@ -1,0 +1,71 @@
+"""Learned rank predictor end to end on the GPU: ranks recorded by the
+factorization on the small and batched workloads train the network with the
+library's own kernels; on held-out problems it must beat the best constant
+predictor clearly, and the learned mixed form (the prediction gates the
+precision of each cluster's compression) must keep the mixed form's bars
+against FP64: iterations within 1, true residual <= 1e-8, at most 5% of
+ranks differing."""
+import numpy as np
+import pytest
+
+from paper_1811_11248_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_1811_11248_gb300 import build, hsolve, rank_model
+    build.build()
+    hsolve.lib()
+    f1, r1, s1 = rank_model.collect(inputs.anisotropic_16x16x8(), depth=4)
+    f3, r3, s3 = rank_model.collect_batched([inputs.batched_problem(k) for k in range(24)])
+    X = np.concatenate([f1, f3])
+    R = np.concatenate([r1, r3])
+    S = np.concatenate([s1, s3])
+    model, losses = rank_model.fit(X, R, S, epochs=30)
+    return hsolve, rank_model, model, losses
+
+
+def test_training_converges(trained):
+    _, _, _, losses = trained
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.2 * losses[:10].mean()
+
+
+def test_prediction_beats_constant_on_held_out(trained):
+    _, rank_model, model, _ = trained
+    f, r, s = rank_model.collect_batched([inputs.batched_problem(k) for k in range(240, 256)])
+    acc = rank_model.accuracy(model, f, r, s)
+    print("held-out batched problems:", acc)
+    assert acc["mae"] <= 0.6 * acc["mae_constant"]
+    assert acc["exact"] >= 0.6
+
+
+def test_learned_mixed_form(trained):
+    hs, rank_model, model, _ = trained
+    p = inputs.grid_operator(32, 32, 16, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def run(precision, model_vec):
+        opt = hs.hs_default_options(tol=1e-2, mem=hs.HS_MEM_HOST, coords=p.coords, stream=st, precision=precision,
+                                    rank_model=model_vec, profile=1)
+        h = hs.hs_setup(p.n, p.rowptr, p.col, p.val, opt=opt)
+        x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        info, rc = h.hs_krylov(torch.from_numpy(p.b).cuda(), x)
+        ranks = np.concatenate([h.level_info(l)[1] for l in range(h.num_levels())])
+        stats = h.kernel_stats()
+        h.close()
+        return info, x.cpu().numpy(), ranks, stats
+
+    i64, _, r64, _ = run(hs.HS_PREC_FP64, None)
+    imx, _, rmx, smx = run(hs.HS_PREC_MIXED, None)
+    ilr, xlr, rlr, slr = run(hs.HS_PREC_MIXED, model.packed())
+    res = np.linalg.norm(p.b - p.matvec(xlr)) / np.linalg.norm(p.b)
+    print(f"iterations fp64 {i64.iters} mixed {imx.iters} learned {ilr.iters}; factor ms mixed "
+          f"{smx['factor']['ms']:.3f} learned {slr['factor']['ms']:.3f}; ranks differing from fp64: "
+          f"mixed {int(np.sum(rmx != r64))} learned {int(np.sum(rlr != r64))} of {len(r64)}")
+    assert res <= 1e-8 and ilr.rel_resid <= 1e-8
+    assert abs(ilr.iters - i64.iters) <= 1
+    assert np.sum(rlr != r64) <= 0.05 * len(r64)
