@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=256,
                     help="problems of the batched workload timed beside the main step (0: skip)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-rank leg (512x512x20 workload)")
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
@@ -187,6 +189,60 @@ def batched_leg(args, stream, dev, barrier, flush_l2):
         t = float(np.mean(ts))
         out[name] = {"s": t, "problems_per_s": cnt / t, "iters_max": its, "rel_resid_max": res}
     out["problems_per_s"] = out["mixed"]["problems_per_s"]
+    return out
+
+
+def learned_leg(args, stream, dev, barrier, flush_l2):
+    """Rank predictor trained on the GPU with the library's kernels on ranks
+    recorded from the 16x16x8, 64x64x16 and batched workloads (problems
+    0-63), then the 512x512x20 workload (N = 5,242,880, ratio 1e6, sigma 1.5)
+    set up and solved by full RRQR in FP64, by the mixed form, and by the
+    mixed form with the predictor (rank-0 speculation)."""
+    import torch
+    from paper_1811_11248_gb300 import hsolve, inputs, rank_model
+    t0 = time.perf_counter()
+    f1, r1, s1 = rank_model.collect(inputs.anisotropic_16x16x8(), depth=4, stream=stream.cuda_stream)
+    f2, r2, s2 = rank_model.collect(inputs.anisotropic_64x64x16(), depth=8, stream=stream.cuda_stream)
+    f3, r3, s3 = rank_model.collect_batched([inputs.batched_problem(k) for k in range(64)], stream=stream.cuda_stream)
+    X, R, S = np.concatenate([f1, f2, f3]), np.concatenate([r1, r2, r3]), np.concatenate([s1, s2, s3])
+    model, losses = rank_model.fit(X, R, S, epochs=40)
+    t_train = time.perf_counter() - t0
+    prob = inputs.anisotropic_512x512x20()
+    with torch.cuda.stream(stream):
+        rp = torch.from_numpy(prob.rowptr).to(dev)
+        ci = torch.from_numpy(prob.col).to(dev)
+        va = torch.from_numpy(prob.val).to(dev)
+        b = torch.from_numpy(prob.b).to(dev)
+        x = torch.empty(prob.n, dtype=torch.float64, device=dev)
+    coords = np.ascontiguousarray(prob.coords)
+    stream.synchronize()
+    out = {"workload": "aniso-ice-512x512x20 (N=5242880), ratio 1e6, sigma 1.5, eps 1e-2, PCG rtol 1e-8",
+           "training": {"samples": int(len(R)), "steps": int(len(losses)), "loss_first": float(losses[:10].mean()),
+                        "loss_last": float(losses[-50:].mean()), "collect_and_train_s": t_train}}
+    packed = model.packed()
+    for name, prec, mv in (("fp64_rrqr", hsolve.HS_PREC_FP64, None), ("mixed", hsolve.HS_PREC_MIXED, None),
+                           ("learned", hsolve.HS_PREC_MIXED, packed)):
+        ts = []
+        for k in range(3 if name == "fp64_rrqr" else 2):
+            # pass 0 warms up, pass 1 is timed, pass 2 records the ranks
+            opt = hsolve.hs_default_options(tol=1e-2, rtol=1e-8, mem=hsolve.HS_MEM_DEVICE, stream=stream.cuda_stream,
+                                            coords=coords, precision=prec, rank_model=mv, record_ranks=int(k == 2))
+            flush_l2()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = hsolve.hs_setup(prob.n, rp, ci, va, opt=opt)
+            info, rc = h.hs_krylov(b, x)
+            e1.record(stream)
+            e1.synchronize()
+            if k == 1:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            if k == 2:
+                f5, r5, s5 = h.rank_samples()
+            h.close()
+        out[name] = {"s": float(np.mean(ts)), "iters": int(info.iters), "rel_resid": float(info.rel_resid)}
+    out["predictor_on_512x512x20"] = rank_model.accuracy(model, f5, r5, s5)
     return out
 
 
@@ -346,6 +402,8 @@ def run_ours(args):
             "kernel_ms": {k: round(v["ms"], 4) for k, v in stats_mx.items()}}
     if args.batched > 0:
         line["batched"] = batched_leg(args, stream, dev, barrier, flush_l2)
+    if not args.no_learned:
+        line["learned"] = learned_leg(args, stream, dev, barrier, flush_l2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, it = cpu_oracle_step(prob, args.tol, 8, 4)
         line["cpu_baseline"] = {"value": dt, "unit": "s", "cores": 1, "kind": "oracle",

@@ -19,7 +19,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <exception>
 #include <mutex>
 #include <map>
@@ -207,13 +209,81 @@ int hs_threads() {
 // set on the worker threads of a batched partition: nested work stays serial
 thread_local bool tl_serial = false;
 
-// Runs fn(t) for t < T (t = 0 on the calling thread) and rethrows the first
-// exception any of them raised.
+// Persistent worker threads for the host planner (created on first use):
+// run(T, fn) hands fn(1) .. fn(T-1) to the workers, runs fn(0) on the
+// caller and returns when all are done.  A call from a worker, or while
+// another call is running, runs serially on its thread.
+thread_local bool tl_in_pool = false;
+
+class Pool {
+  public:
+    static Pool& get() {
+        static Pool p(hs_threads() - 1);
+        return p;
+    }
+    int workers() const { return (int)th_.size(); }
+    bool try_run(int T, const std::function<void(int)>& fn) {
+        std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
+        if (!busy.owns_lock()) return false;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            job_ = &fn;
+            njob_ = T;
+            next_ = 1;
+            pending_ = T - 1;
+        }
+        cv_.notify_all();
+        fn(0);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+        return true;
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+
+  private:
+    explicit Pool(int n) {
+        for (int i = 0; i < n; i++) th_.emplace_back([this] { loop(); });
+    }
+    void loop() {
+        tl_in_pool = true;
+        for (;;) {
+            const std::function<void(int)>* f;
+            int t;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || (job_ && next_ < njob_); });
+                if (stop_) return;
+                f = job_;
+                t = next_++;
+            }
+            (*f)(t);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--pending_ == 0) done_.notify_all();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_, run_mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)>* job_ = nullptr;
+    int njob_ = 0, next_ = 0, pending_ = 0;
+    bool stop_ = false;
+};
+
+// Runs fn(t) for t < T (t = 0 on the calling thread; the others on the
+// pool's workers) and rethrows the first exception any of them raised.
 template <class F>
 void run_threads(int T, F&& fn) {
     std::exception_ptr err;
     std::mutex mu;
-    auto wrap = [&](int t) {
+    std::function<void(int)> wrap = [&](int t) {
         try {
             fn(t);
         } catch (...) {
@@ -221,10 +291,9 @@ void run_threads(int T, F&& fn) {
             if (!err) err = std::current_exception();
         }
     };
-    std::vector<std::thread> th;
-    for (int t = 1; t < T; t++) th.emplace_back(wrap, t);
-    wrap(0);
-    for (auto& x : th) x.join();
+    T = std::max(1, std::min(T, Pool::get().workers() + 1));
+    if (T <= 1 || tl_in_pool || !Pool::get().try_run(T, wrap))
+        for (int t = 0; t < T; t++) wrap(t);
     if (err) std::rethrow_exception(err);
 }
 
@@ -376,6 +445,7 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
                 }
             }
         });
+        tr.mark("  partition: strong edges");
         for (auto& ev : edges)
             for (auto& pr : ev) {
                 const int a = find(pr.first), b = find(pr.second);
@@ -394,6 +464,7 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
         }
     }
     P.nl = (int)first.size();
+    tr.mark("  partition: line ids");
     {
         // DOFs grouped by line (counting sort), then each line's neighbour
         // lines collected with a visit stamp and sorted

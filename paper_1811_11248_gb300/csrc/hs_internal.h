@@ -183,7 +183,7 @@ cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double*
 cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv,
                           const double* w, double* partial, double* out);
 
-size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32 = false);
+size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32 = false, bool xsh = false);
 // coarse levels: all phases of a level in one single-CTA launch (warp per task)
 constexpr int kFusedWarps = 16, kFusedSmax = 32;
 size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap);
@@ -198,6 +198,7 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
 // rank predictor (hs_mlp.cu): 8 -> 64 -> 64 -> 1 perceptron, FP32
 constexpr int kMlpIn = 8, kMlpHidden = 64;
 constexpr int kFeat = kMlpIn;  // features recorded per eliminated cluster
+constexpr int kSparseNz = 4;   // scaling: columns with at most this many nonzeros use the columns of G^-1
 constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + kMlpHidden + 1;
 constexpr int kMlpMaxBatch = 256, kMlpThreads = 512;
 constexpr int kModelFloats = 2 * kMlpIn + kMlpParams;  // mu, sd, network

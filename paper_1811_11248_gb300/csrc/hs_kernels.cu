@@ -288,6 +288,19 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
     if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
 }
 
+// 1 / sqrt(d) for the Cholesky pivots: the FP32 estimate refined by two
+// Newton-Raphson steps y <- y + y (1 - d y^2) / 2 (each squares the relative
+// error: 2^-22 -> 2^-44 -> below FP64 rounding); outside the FP32 range the
+// FP64 square root and division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    double h = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, h, y);
+    h = fma(-d * y, y, 1.0);
+    return fma(0.5 * y, h, y);
+}
+
 // Rank predictor inside a factor task: y = w3 . relu(W2 relu(W1 xn + b1) + b2)
 // + b3 on the standardised features xn = (f - mu) / sd.  model: mu (8), sd
 // (8), then the network's parameter vector (kMlpParams floats, the layout of
@@ -332,7 +345,7 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                             double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                             const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
                             int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
-                            int32_t level, float* fe, const float* __restrict__ model, float* G32) {
+                            int32_t level, float* fe, const float* __restrict__ model, float* G32, double* Xsh) {
     const int s = T.s, tid = g.rank, NT = g.size;
     const int L = T.nn + T.nw;
     const bool want_feat = fe != nullptr || model != nullptr;
@@ -374,35 +387,32 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     if (want_feat) amax_ss = g.max(amax_ss, red);
     const int W = ioff[L], ncols = ioff[T.nn], Wn = W - ncols;
 
-    // Cholesky A_ss = G G^T in shared memory, right-looking in panels of kNB
-    // columns: the diagonal block by one warp (warp-synchronous), then the
-    // panel below it and the trailing update by the whole group.
-    for (int k0 = 0; k0 < s; k0 += kNB) {
-        const int kb = min(kNB, s - k0), k1 = k0 + kb;
-        if (tid < 32) {
-            const int lane = tid;
-            for (int j = k0; j < k1; j++) {
-                if (lane == 0) {
-                    const double d = G[j * s + j];
-                    if (!(d > 0.0)) {
-                        *s_flag = 1;
-                    } else {
-                        const double gj = sqrt(d);
-                        G[j * s + j] = gj;
-                        rdiag[j] = 1.0 / gj;
-                    }
-                }
-                __syncwarp();
-                if (*s_flag) break;
-                const int i = j + 1 + lane;
-                if (i < k1) G[i * s + j] *= rdiag[j];
-                __syncwarp();
-                if (i < k1)
-                    for (int k = j + 1; k <= i; k++) G[i * s + k] -= G[i * s + j] * G[k * s + j];
-                __syncwarp();
-            }
+    // Cholesky A_ss = G G^T and X = G^-1 together, right-looking, one column
+    // per step: with r = 1 / g_jj (pivot), column j of G scaled by r gives
+    // l (kept contiguous in v); every row i > j then loses l_i l^T over its
+    // columns j < c <= i of G and l_i times row j of X (scaled by r) over its
+    // columns c <= j of X.  Rows go to warps, columns to lanes; one FMA per
+    // element.  The warp that finishes row j + 1 takes the next pivot.  X
+    // lives in Xsh (s x s) when the caller has room, else in the identity
+    // columns of the block row.
+    const int Wt0 = W + s;
+    double* M0 = Msh ? Msh : ws + T.m_off;
+    double* X = Xsh ? Xsh : M0 + W;
+    const int ldx = Xsh ? s : Wt0;
+    double* lcol = v;  // s doubles
+    for (int idx = tid; idx < s * s; idx += NT) X[(idx / s) * ldx + idx % s] = (idx / s == idx % s) ? 1.0 : 0.0;
+    if (tid == 0) {
+        const double d = G[0];
+        if (!(d > 0.0)) {
+            *s_flag = 1;
+        } else {
+            const double r = rsqrt_newton(d);
+            rdiag[0] = r;
+            G[0] = d * r;
         }
-        g.sync();
+    }
+    g.sync();
+    for (int j = 0; j < s; j++) {
         if (*s_flag) {
             if (tid == 0 && atomicCAS(status, 0, ST_NOT_SPD) == 0) {
                 status[1] = level;
@@ -410,23 +420,44 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             }
             return;
         }
-        // panel: rows below the block, G[i, k0:k1] <- A[i, k0:k1] L_kk^-T
-        for (int i = k1 + tid; i < s; i += NT) {
-            for (int j = k0; j < k1; j++) {
-                double a = G[i * s + j];
-                for (int k = k0; k < j; k++) a -= G[i * s + k] * G[j * s + k];
-                G[i * s + j] = a * rdiag[j];
+        const double r = rdiag[j];
+        const int m = s - j - 1;
+        for (int idx = tid; idx < m + j + 1; idx += NT) {
+            if (idx < m) {
+                const int i = j + 1 + idx;
+                const double l = G[i * s + j] * r;
+                G[i * s + j] = l;
+                lcol[i] = l;
+            } else {
+                X[j * ldx + (idx - m)] *= r;
             }
         }
         g.sync();
-        // trailing update of the lower triangle
-        const int m = s - k1;
-        for (int idx = tid; idx < m * m; idx += NT) {
-            const int i = k1 + idx / m, k = k1 + idx % m;
-            if (k <= i) {
-                double a = G[i * s + k];
-                for (int j = k0; j < k1; j++) a -= G[i * s + j] * G[k * s + j];
-                G[i * s + k] = a;
+        // rows below j: X part (columns c <= j) and G part (j < c <= i), each
+        // as one flat index space so that every FP64 instruction is full
+        const int nx = m * (j + 1), ngt = m * (m + 1) / 2;
+        for (int idx = tid; idx < nx; idx += NT) {
+            const int t = idx / (j + 1), i = j + 1 + t, c0 = idx - t * (j + 1);
+            X[i * ldx + c0] = fma(-lcol[i], X[j * ldx + c0], X[i * ldx + c0]);
+        }
+        for (int idx = tid; idx < ngt; idx += NT) {
+            // entry idx of the packed trailing triangle: row t has t + 1 entries
+            int t = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+            while (t * (t + 1) / 2 > idx) t--;
+            while ((t + 1) * (t + 2) / 2 <= idx) t++;
+            const int i = j + 1 + t, c0 = j + 1 + idx - t * (t + 1) / 2;
+            G[i * s + c0] = fma(-lcol[i], lcol[c0], G[i * s + c0]);
+        }
+        // the next pivot: entry 0 of the triangle, updated by this thread only
+        if (tid == 0 && j + 1 < s) {
+            const int i = j + 1;
+            const double d = G[i * s + i];
+            if (!(d > 0.0)) {
+                *s_flag = 1;
+            } else {
+                const double rr = rsqrt_newton(d);
+                rdiag[i] = rr;
+                G[i * s + i] = d * rr;
             }
         }
         g.sync();
@@ -447,17 +478,64 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             colsrc[2 * (ioff[e] + j) + 1] = em[e].ldcq;
         }
     g.sync();
-    double amax_row = 0.0;  // largest |[A_sn A_sw]| (features only)
-    for (int idx = tid; idx < s * W; idx += NT) {
-        const int i = idx / W, j = idx % W;
-        const double a = blocks[colsrc[2 * j] + (int64_t)i * colsrc[2 * j + 1]];
-        M[(int64_t)i * Wt + j] = a;
-        amax_row = fmax(amax_row, fabs(a));
+    // pass 1, one thread per column of [A_sn | A_sw]: stream the column from
+    // the blocks (loads in groups of kGatherBatch, all in flight before they
+    // are used), store it, note its nonzeros.  Scaling M <- G^-1 M: a column
+    // with at most kSparseNz nonzeros (level-0 stencil couplings) is the
+    // combination sum_k a_k G^-1 e_{i_k} of columns of X = G^-1 and is
+    // finished here; a denser one is forward-substituted in pass 2.
+    constexpr int kGatherBatch = 8;
+    unsigned char* dense = reinterpret_cast<unsigned char*>(cn);  // per column (W bytes)
+    double amax_row = 0.0, lt = 0.0, lm = 0.0;  // features: max |a|, norms of D^-1 A_sw
+    for (int j = tid; j < W; j += NT) {
+        const int64_t src = colsrc[2 * j], ldc = colsrc[2 * j + 1];
+        const bool fill = j >= ncols;
+        int nz = 0, i0 = s;
+        int ri[kSparseNz];
+        double rv[kSparseNz];
+#pragma unroll
+        for (int k = 0; k < kSparseNz; k++) { ri[k] = 0; rv[k] = 0.0; }
+        double cj = 0.0;
+        for (int b = 0; b < s; b += kGatherBatch) {
+            double a[kGatherBatch];
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; u++) a[u] = (b + u < s) ? blocks[src + (int64_t)(b + u) * ldc] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; u++) {
+                const int i = b + u;
+                if (i >= s) break;
+                M[(int64_t)i * Wt + j] = a[u];
+                amax_row = fmax(amax_row, fabs(a[u]));
+                if (want_feat && fill) {
+                    const double x = a[u] * rdiag[i];
+                    cj = fma(x, x, cj);
+                }
+                if ((__double_as_longlong(a[u]) << 1) != 0) {  // nonzero (either sign of zero is zero)
+                    if (nz == 0) i0 = i;
+#pragma unroll
+                    for (int k = 0; k < kSparseNz; k++)
+                        if (k == nz) { ri[k] = i; rv[k] = a[u]; }
+                    nz++;
+                }
+            }
+        }
+        if (want_feat && fill) {
+            lt += cj;
+            lm = fmax(lm, cj);
+        }
+        const bool sparse = nz <= kSparseNz && 2 * nz <= s - i0;
+        dense[j] = sparse ? 0 : 1;
+        if (sparse)
+            for (int r = i0; r < s; r++) {
+                double x = 0.0;
+#pragma unroll
+                for (int k = 0; k < kSparseNz; k++)
+                    if (k < nz && ri[k] <= r) x = fma(rv[k], X[r * ldx + ri[k]], x);
+                M[(int64_t)r * Wt + j] = x;
+            }
     }
-    for (int idx = tid; idx < s * s; idx += NT) {
-        const int i = idx / s, j = idx % s;
-        M[(int64_t)i * Wt + W + j] = (i == j) ? 1.0 : 0.0;
-    }
+    if (Xsh)  // the identity columns become G^-1
+        for (int idx = tid; idx < s * s; idx += NT) M[(int64_t)(idx / s) * Wt + W + idx % s] = Xsh[idx];
     g.sync();
     // features of the block row (the column table is free from here on):
     // structure, the coupling ratio, and the fill block scaled by the
@@ -465,16 +543,6 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     float* fsh = reinterpret_cast<float*>(colsrc);  // 8 features, then 64 floats of scratch
     if (want_feat) {
         amax_row = g.max(amax_row, red);
-        double lt = 0.0, lm = 0.0;
-        for (int j = tid; j < Wn; j += NT) {
-            double cj = 0.0;
-            for (int i = 0; i < s; i++) {
-                const double x = M[(int64_t)i * Wt + ncols + j] * rdiag[i];
-                cj += x * x;
-            }
-            lt += cj;
-            lm = fmax(lm, cj);
-        }
         const double total = g.sum(lt, red), cmax = g.max(lm, red);
         if (tid == 0) {
             const double e = eps2 > 0.0 ? sqrt(eps2) : 1e-300;
@@ -492,9 +560,10 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         if (fe && tid < kFeat) fe[tid] = fsh[tid];
     }
     // learned rank-0 speculation (mixed form): when the predictor says rank 0,
-    // the fill columns are scaled in FP32 only, and the rank is certified 0
-    // if their squared norm is at most eps^2 / 2; otherwise they are gathered
-    // again and scaled in FP64 and the column-pivoted QR decides as usual
+    // dense fill columns are scaled in FP32 only, and the rank is certified 0
+    // if the fill block's squared norm is at most eps^2 / 2; otherwise they
+    // are gathered again and scaled in FP64 and the column-pivoted QR decides
+    // as usual
     bool spec0 = false;
     if (model && G32 && sizeof(FT) == sizeof(float) && Wn > 0) {
         const float y = predict_fraction(g, model, fsh, fsh + kFeat, red);
@@ -503,16 +572,14 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             for (int idx = tid; idx < s * s; idx += NT) G32[idx] = (float)G[idx];
         g.sync();
     }
-
-    // scaling: M <- G^-1 M (forward substitution, one thread per column).
-    // A column that is zero above row i0 (identity column j: i0 = j; level-0
-    // face couplings: their first nonzero) keeps those zeros, so the
-    // substitution starts at i0; all-zero columns are skipped.  Speculated
-    // fill columns run in FP32 (values kept in the first float of each slot).
-    for (int j = tid; j < Wt; j += NT) {
-        int i0 = (j >= W) ? j - W : 0;
-        while (i0 < s && M[(int64_t)i0 * Wt + j] == 0.0) i0++;
-        if (spec0 && j >= ncols && j < W) {
+    // pass 2: dense columns by forward substitution from their first nonzero
+    // row (zeros above stay zero); speculated fill columns in FP32 (values in
+    // the first float of each slot)
+    for (int j = tid; j < W; j += NT) {
+        if (!dense[j]) continue;
+        int i0 = 0;
+        while (i0 < s && (__double_as_longlong(M[(int64_t)i0 * Wt + j]) << 1) == 0) i0++;
+        if (spec0 && j >= ncols) {
             float* Mf = reinterpret_cast<float*>(M);
             for (int i = i0; i < s; i++) {
                 float acc = (float)M[(int64_t)i * Wt + j];
@@ -520,12 +587,12 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                 Mf[2 * ((int64_t)i * Wt + j)] = acc * (float)rdiag[i];
             }
             for (int i = 0; i < i0; i++) Mf[2 * ((int64_t)i * Wt + j)] = 0.f;
-            continue;
-        }
-        for (int i = i0; i < s; i++) {
-            double acc = M[(int64_t)i * Wt + j];
-            for (int k = i0; k < i; k++) acc -= G[i * s + k] * M[(int64_t)k * Wt + j];
-            M[(int64_t)i * Wt + j] = acc * rdiag[i];
+        } else {
+            for (int i = i0; i < s; i++) {
+                double acc = M[(int64_t)i * Wt + j];
+                for (int k = i0; k < i; k++) acc = fma(-G[i * s + k], M[(int64_t)k * Wt + j], acc);
+                M[(int64_t)i * Wt + j] = acc * rdiag[i];
+            }
         }
     }
     g.sync();
@@ -535,7 +602,8 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         double lt = 0.0;
         for (int j = tid; j < Wn; j += NT)
             for (int i = 0; i < s; i++) {
-                const double x = (double)Mf[2 * ((int64_t)i * Wt + ncols + j)];
+                const int64_t o = (int64_t)i * Wt + ncols + j;
+                const double x = dense[ncols + j] ? (double)Mf[2 * o] : M[o];
                 lt += x * x;
             }
         rank0 = g.sum(lt, red) <= 0.5 * eps2;
@@ -587,7 +655,7 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
                const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
                int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
                int32_t level, int smax, int wmax, int lmax, float* __restrict__ feat,
-               const float* __restrict__ model) {
+               const float* __restrict__ model, int use_x) {
     extern __shared__ double sm[];
     __shared__ int s_flag;
     __shared__ double s_hh[3];
@@ -600,13 +668,15 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
     EntryMeta* em = reinterpret_cast<EntryMeta*>(red + 64);
     int64_t* colsrc = reinterpret_cast<int64_t*>(em + lmax);
     int* ioff = reinterpret_cast<int*>(colsrc + 2 * (size_t)wmax);
-    // FP32 copy of G for the learned rank-0 speculation (only with a model)
-    float* G32 = model ? reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(ioff + lmax + 1) + 15) & ~uintptr_t(15))
-                       : nullptr;
+    // G^-1 (smax x smax doubles), then the FP32 copy of G for the learned
+    // rank-0 speculation (only with a model)
+    double* x0 = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(ioff + lmax + 2) + 15) & ~uintptr_t(15));
+    double* Xsh = use_x ? x0 : nullptr;
+    float* G32 = model ? reinterpret_cast<float*>(x0 + (use_x ? (size_t)smax * smax : 0)) : nullptr;
     CtaGroup g;
     factor_task<FT>(T, g, G, rdiag, v, cn, red, ioff, &s_flag, s_hh, nullptr, em, colsrc, lists, blocks, blk_off,
                     blk_ld, cur, fac, meta, ws, eps2, status, level,
-                    feat ? feat + (size_t)(t0 + blockIdx.x) * kFeat : nullptr, model, G32);
+                    feat ? feat + (size_t)(t0 + blockIdx.x) * kFeat : nullptr, model, G32, Xsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -808,7 +878,7 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
         for (int t = ph_task[ph] + gw; t < ph_task[ph + 1]; t += GW)
             factor_task<FT>(tasks[t], g, G, rdiag, v, cn, red, ioff, flag, hh, Msh, em, colsrc, lists, blocks,
                             blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level,
-                            feat ? feat + (size_t)t * kFeat : nullptr, model, nullptr);
+                            feat ? feat + (size_t)t * kFeat : nullptr, model, nullptr, nullptr);
         grid_sync(bar, status);
         for (int k = ph_target[ph] + gw; k < ph_target[ph + 1]; k += GW)
             schur_target_warp<FT>(targets[k], contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur, colsrc);
@@ -1568,11 +1638,13 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
     return cudaGetLastError();
 }
 
-size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32) {
+size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32, bool xsh) {
     const size_t base = sizeof(double) * ((size_t)smax * smax + 2 * (size_t)smax + (size_t)wmax + 64) +
                         sizeof(EntryMeta) * (size_t)lmax + 2 * sizeof(int64_t) * (size_t)wmax +
-                        sizeof(int) * ((size_t)lmax + 1);
-    return g32 ? (base + 15) / 16 * 16 + sizeof(float) * (size_t)smax * smax : base;
+                        sizeof(int) * ((size_t)lmax + 2);
+    // then G^-1 (doubles) and, with a rank model, an FP32 copy of G
+    return (base + 15) / 16 * 16 + (xsh ? sizeof(double) * (size_t)smax * smax : 0) +
+           (g32 ? sizeof(float) * (size_t)smax * smax : 0);
 }
 
 template <typename FT>
@@ -1580,13 +1652,15 @@ cudaError_t factor_phase_t(cudaStream_t st, const TaskDev* tasks, int t0, int nt
                            const ListDev* lists, double* blocks, const int64_t* blk_off, const int32_t* blk_ld,
                            int32_t* cur, FT* fac, int32_t* meta, double* ws, double eps2, int32_t* status,
                            int32_t level, float* feat, const float* model) {
-    const size_t smem = factor_smem_bytes(smax, wmax, lmax, model != nullptr);
+    // G^-1 in shared memory when it fits beside the rest
+    const int use_x = factor_smem_bytes(smax, wmax, lmax, model != nullptr, true) <= (size_t)kFactorMaxSmem;
+    const size_t smem = factor_smem_bytes(smax, wmax, lmax, model != nullptr, use_x);
     cudaError_t e = cudaFuncSetAttribute(k_factor_phase<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     counted();
     k_factor_phase<FT><<<ntasks, kFactorThreads, smem, st>>>(tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta,
                                                              ws, eps2, status, level, smax, wmax, lmax, feat,
-                                                             model);
+                                                             model, use_x);
     return cudaGetLastError();
 }
 
