@@ -422,43 +422,54 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
                    int leaf_lines, double theta, std::vector<int32_t>& perm, std::vector<int32_t>& leaf_ptr) {
     const int n = (int)n64;
     Trace tr;
-    // strongly coupled lines: union-find over |a_ij| >= theta * max_{k != i} |a_ik|
-    std::vector<int> root(n);
-    for (int i = 0; i < n; i++) root[i] = i;
+    // strongly coupled lines: union-find over |a_ij| >= theta * max_{k != i} |a_ik|.
+    // Strong edges are found and linked in parallel: a root is only ever
+    // linked (by compare-and-swap) under a smaller root, so every component
+    // ends with its smallest DOF as root whatever the order of the links.
+    std::vector<std::atomic<int>> root(n);
+    parallel_ranges(n, 1 << 16, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t i = lo; i < hi; i++) root[i].store((int)i, std::memory_order_relaxed);
+    });
     auto find = [&](int x) {
-        while (root[x] != x) { root[x] = root[root[x]]; x = root[x]; }
-        return x;
+        for (;;) {
+            int p = root[x].load(std::memory_order_relaxed);
+            if (p == x) return x;
+            const int gp = root[p].load(std::memory_order_relaxed);
+            // path halving (links only point to smaller indices, so a value
+            // read here is always an ancestor; a failed exchange is harmless)
+            if (gp != p) root[x].compare_exchange_weak(p, gp, std::memory_order_relaxed);
+            x = gp;
+        }
     };
-    {
-        // strong edges found in parallel (row by row), unions applied after
-        std::vector<std::vector<std::pair<int, int>>> edges(hs_threads());
-        parallel_ranges(n, 4096, [&](int64_t lo, int64_t hi, int t) {
-            auto& ev = edges[t];
-            for (int64_t i = lo; i < hi; i++) {
-                double m = 0.0;
-                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++)
-                    if (col[e] != i) m = std::max(m, std::fabs(val[e]));
-                if (m <= 0.0) continue;
-                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-                    const int j = col[e];
-                    if (j != i && std::fabs(val[e]) >= theta * m) ev.push_back({(int)i, j});
-                }
+    auto unite = [&](int a, int b) {
+        for (;;) {
+            a = find(a);
+            b = find(b);
+            if (a == b) return;
+            if (a < b) std::swap(a, b);  // link the larger root under the smaller
+            int expect = a;
+            if (root[a].compare_exchange_strong(expect, b, std::memory_order_relaxed)) return;
+        }
+    };
+    parallel_ranges(n, 4096, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t i = lo; i < hi; i++) {
+            double m = 0.0;
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++)
+                if (col[e] != i) m = std::max(m, std::fabs(val[e]));
+            if (m <= 0.0) continue;
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                const int j = col[e];
+                if (j != i && std::fabs(val[e]) >= theta * m) unite((int)i, j);
             }
-        });
-        tr.mark("  partition: strong edges");
-        for (auto& ev : edges)
-            for (auto& pr : ev) {
-                const int a = find(pr.first), b = find(pr.second);
-                if (a != b) root[std::max(a, b)] = std::min(a, b);
-            }
-    }
+        }
+    });
     tr.mark("  partition: union-find");
     Partitioner P;
     std::vector<int> line_of(n), first;
     {
         std::vector<int> id(n, -1);
         for (int i = 0; i < n; i++) {
-            const int r = find(i);
+            const int r = find(i);  // roots are final: no link is running
             if (id[r] < 0) { id[r] = (int)first.size(); first.push_back(i); }
             line_of[i] = id[r];
         }
@@ -879,13 +890,16 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             t.nw = (int)P.wl[c].size();
             t.list = list_off[ti];
             list_off[ti + 1] = list_off[ti] + t.nn + t.nw;
-            t.ncap = t_ncap[ti];
+            t.ncap = (t_ncap[ti] + 3) & ~3;  // ld of C: rows of whole float4 / double2 groups
             t.wcap = t_wcap[ti];
             t.meta = meta;
             meta += 1 + 2 * t.nn;
             L.stg[ti] = stage;
             stage += std::max(t.ncap, 1);
+            // W and C start on 4-element boundaries (vector loads in the solve phase)
+            fac = (fac + 3) & ~(int64_t)3;
             t.w_off = fac; fac += (int64_t)t.s * t.s;
+            fac = (fac + 3) & ~(int64_t)3;
             t.c_off = fac; fac += (int64_t)t.s * std::max(t.ncap, 1);
             t.m_off = ws; ws += (int64_t)t.s * (t.wcap + t.s);
             L.smax = std::max(L.smax, t.s);
@@ -1353,10 +1367,19 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         vl = hval.empty() ? nullptr : hval.data();
     }
     const int64_t nnz = rp[n];
-    for (int64_t i = 0; i < n; i++)
-        if (rp[i + 1] < rp[i]) throw HsError{HS_ERR_ARG};
-    for (int64_t e = 0; e < nnz; e++)
-        if (cl[e] < 0 || cl[e] >= n) throw HsError{HS_ERR_ARG};
+    {
+        std::atomic<int> bad{0};
+        parallel_ranges(n, 1 << 16, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t i = lo; i < hi; i++)
+                if (rp[i + 1] < rp[i]) bad = 1;
+        });
+        if (bad || rp[0] != 0) throw HsError{HS_ERR_ARG};
+        parallel_ranges(nnz, 1 << 18, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t e = lo; e < hi; e++)
+                if (cl[e] < 0 || cl[e] >= n) bad = 1;
+        });
+        if (bad) throw HsError{HS_ERR_ARG};
+    }
 
     // partition tree
     std::vector<int32_t> leaf_ptr;
@@ -1384,7 +1407,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     if (leaf_ptr[0] != 0 || leaf_ptr[nleaf] != n) throw HsError{HS_ERR_ARG};
     if (!batched && depth > 0 && (depth > 30 || nleaf % (1 << depth) != 0)) throw HsError{HS_ERR_ARG};
     if (!batched) h->groups.assign(1, hs_factor_s::Group{0, nleaf, 0, n, depth});
-    {
+    if (tree_in) {  // a caller's permutation (the partitioner's are valid by construction)
         std::vector<char> seen(n, 0);
         for (int64_t i = 0; i < n; i++) {
             const int32_t p = h->perm[i];

@@ -985,7 +985,39 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
     const int f = s - T.r;
     const FT* C = fac + T.cm;
     const double* yf = yn + T.r;
-    for (int j = tid; j < T.ncols; j += NT) {
+    int jv = 0;  // columns below jv done with vector loads
+    if constexpr (sizeof(FT) == sizeof(float)) {
+        // four columns per thread, one aligned float4 per row (C and its
+        // leading dimension are multiples of 4 floats), four rows in flight
+        jv = T.ncols & ~3;
+        for (int j4 = 4 * tid; j4 < jv; j4 += 4 * NT) {
+            float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+            const float* cj = reinterpret_cast<const float*>(C) + j4;
+            int i = 0;
+            for (; i + 3 < f; i += 4) {
+                const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
+                const float4 c1 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 1) * T.ncap);
+                const float4 c2 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 2) * T.ncap);
+                const float4 c3 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 3) * T.ncap);
+                const float y0 = (float)yf[i], y1 = (float)yf[i + 1], y2 = (float)yf[i + 2], y3 = (float)yf[i + 3];
+                p0.x += c0.x * y0 + c2.x * y2; p0.y += c0.y * y0 + c2.y * y2;
+                p0.z += c0.z * y0 + c2.z * y2; p0.w += c0.w * y0 + c2.w * y2;
+                p1.x += c1.x * y1 + c3.x * y3; p1.y += c1.y * y1 + c3.y * y3;
+                p1.z += c1.z * y1 + c3.z * y3; p1.w += c1.w * y1 + c3.w * y3;
+            }
+            for (; i < f; i++) {
+                const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
+                const float y0 = (float)yf[i];
+                p0.x += c0.x * y0; p0.y += c0.y * y0; p0.z += c0.z * y0; p0.w += c0.w * y0;
+            }
+            double* st = stage + T.stg + j4;
+            st[0] = (double)(p0.x + p1.x);
+            st[1] = (double)(p0.y + p1.y);
+            st[2] = (double)(p0.z + p1.z);
+            st[3] = (double)(p0.w + p1.w);
+        }
+    }
+    for (int j = jv + tid; j < T.ncols; j += NT) {
         FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
         const FT* cj = C + j;
         int i = 0;
@@ -1034,19 +1066,48 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
     __syncthreads();
     const FT* C = fac + T.cm;
     const int lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
-    for (int i0 = 2 * wid; i0 < f; i0 += 2 * nwarp) {
-        FT a0 = FT(0), a1 = FT(0);
-        const bool two = i0 + 1 < f;
-        for (int j = lane; j < T.ncols; j += 32) {
-            const FT xj = (FT)xn[j];
-            a0 += C[(int64_t)i0 * T.ncap + j] * xj;
-            if (two) a1 += C[(int64_t)(i0 + 1) * T.ncap + j] * xj;
+    if constexpr (sizeof(FT) == sizeof(float)) {
+        // four rows per warp, four columns per lane (aligned float4 loads)
+        const int jv = T.ncols & ~3;
+        for (int i0 = 4 * wid; i0 < f; i0 += 4 * nwarp) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int j4 = 4 * lane; j4 < jv; j4 += 128) {
+                const float x0 = (float)xn[j4], x1 = (float)xn[j4 + 1], x2 = (float)xn[j4 + 2], x3 = (float)xn[j4 + 3];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (i0 + u < f) {
+                        const float4 c4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(C) +
+                                                                          (int64_t)(i0 + u) * T.ncap + j4);
+                        a[u] += c4.x * x0 + c4.y * x1 + c4.z * x2 + c4.w * x3;
+                    }
+            }
+            for (int j = jv + lane; j < T.ncols; j += 32) {
+                const float xj = (float)xn[j];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (i0 + u < f) a[u] += (float)C[(int64_t)(i0 + u) * T.ncap + j] * xj;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const double su = warp_sum((double)a[u]);
+                if (lane == 0 && i0 + u < f) xs[r + i0 + u] -= su;
+            }
         }
-        const double s0 = warp_sum((double)a0);
-        const double s1 = warp_sum((double)a1);
-        if (lane == 0) {
-            xs[r + i0] -= s0;
-            if (two) xs[r + i0 + 1] -= s1;
+    } else {
+        for (int i0 = 2 * wid; i0 < f; i0 += 2 * nwarp) {
+            FT a0 = FT(0), a1 = FT(0);
+            const bool two = i0 + 1 < f;
+            for (int j = lane; j < T.ncols; j += 32) {
+                const FT xj = (FT)xn[j];
+                a0 += C[(int64_t)i0 * T.ncap + j] * xj;
+                if (two) a1 += C[(int64_t)(i0 + 1) * T.ncap + j] * xj;
+            }
+            const double s0 = warp_sum((double)a0);
+            const double s1 = warp_sum((double)a1);
+            if (lane == 0) {
+                xs[r + i0] -= s0;
+                if (two) xs[r + i0 + 1] -= s1;
+            }
         }
     }
     __syncthreads();
