@@ -74,10 +74,11 @@ typedef struct {
     void* stream;        /* cudaStream_t for all device work                   */
     const double* coords; /* host n x 2 horizontal DOF positions for the
                             partitioner when no tree is given (NULL: BFS)     */
-    int32_t coarse_dense; /* solve phase: the levels from the first one with at
-                            most this many DOFs (and the top) are applied as
-                            one explicit dense operator formed at setup;
-                            0 = never; default 4096                           */
+    int32_t coarse_dense; /* solve phase: the levels from one with at most
+                            this many DOFs (and the top) are applied as one
+                            explicit dense operator formed at setup; the
+                            level is picked by a cost model of forming it
+                            plus ten applies; 0 = never; default 4096         */
     int32_t fused_levels; /* nonzero (default): levels whose clusters have at
                             most 32 DOFs run all their phases in one launch   */
     int32_t record_ranks; /* nonzero: keep the rank predictor's features and

@@ -939,11 +939,15 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         std::vector<std::vector<std::vector<TargetDev>>> rt(nr, std::vector<std::vector<TargetDev>>(L.nphases));
         std::vector<std::vector<std::vector<ContribDev>>> rc(nr, std::vector<std::vector<ContribDev>>(L.nphases));
         std::atomic<int> next{0};
+        // work items: (range, phase) pairs, independent of each other
+        const int nitems = nr * L.nphases;
         auto work = [&] {
             std::vector<TC> tcs;
-            for (int k = next++; k < nr; k = next++) {
+            for (int item = next++; item < nitems; item = next++) {
+                const int k = item / L.nphases;
                 const int lo = ranges.empty() ? 0 : ranges[k].first, hi = ranges.empty() ? P.nc : ranges[k].second;
-                for (int ph = 0; ph < L.nphases; ph++) {
+                {
+                    const int ph = item % L.nphases;
                     const auto& cs = P.phases[ph];
                     auto b0 = std::lower_bound(cs.begin(), cs.end(), lo), b1 = std::lower_bound(cs.begin(), cs.end(), hi);
                     tcs.clear();
@@ -974,7 +978,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                 }
             }
         };
-        run_threads(std::min<int>(hs_threads(), nr), [&](int) { work(); });
+        run_threads(nt < 256 ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
         for (int ph = 0; ph < L.nphases; ph++) {
             for (int k = 0; k < nr; k++) {
                 const int base = (int)contribs.size();
@@ -1763,16 +1767,33 @@ void build_apply_graph(hs_factor_s* h) {
     const int D = (int)h->lev.size();
     const int lc0 = first_coarse_level(h);
     auto level_len = [&](int l) -> int64_t { return l < D ? h->lev[l]->slot[h->lev[l]->nc] : h->ntop; };
-    // dense coarse operator from the first level (>= lc0) small enough
+    // dense coarse operator: among the levels (>= lc0) with at most
+    // coarse_dense DOFs, the one with the smallest modelled cost of building
+    // it (one single-CTA pass over the remaining levels per unit vector, in
+    // waves over the SMs) plus kModelApplies applies (the levels above it as
+    // stage kernels, and the dense product)
     int ld = -1;
-    if (h->opt.coarse_dense > 0)
-        for (int l = lc0; l <= D; l++)
-            if (level_len(l) <= h->opt.coarse_dense) { ld = l; break; }
-    if (ld >= 0) {  // the batched build needs one workspace per unit vector
-        int64_t stride = 0;
-        for (int l = ld; l <= D; l++) stride += std::max<int64_t>(level_len(l), 1);
-        for (int l = ld; l < D; l++) stride += (int64_t)(h->lev[l]->d_stage.bytes / sizeof(double));
-        if ((double)stride * level_len(ld) * 8.0 > 2e9) ld = -1;
+    if (h->opt.coarse_dense > 0) {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        constexpr double kChainStageUs = 12.0, kLaunchUs = 1.0, kModelApplies = 10.0, kGemvBytesPerUs = 4e6;
+        auto stages = [&](int l) { return l < D ? 2.0 * h->lev[l]->nstages + 2.0 : 2.0; };
+        double best = 0.0;
+        for (int l = lc0; l <= D; l++) {
+            const int64_t n = level_len(l);
+            if (n > h->opt.coarse_dense) continue;
+            int64_t stride = 0;  // the batched build needs one workspace per unit vector
+            for (int k = l; k <= D; k++) stride += std::max<int64_t>(level_len(k), 1);
+            for (int k = l; k < D; k++) stride += (int64_t)(h->lev[k]->d_stage.bytes / sizeof(double));
+            if ((double)stride * n * 8.0 > 2e9) continue;
+            double chain = 0.0, above = 0.0;
+            for (int k = l; k <= D; k++) chain += stages(k);
+            for (int k = lc0; k < l; k++) above += stages(k);
+            const double waves = std::ceil((double)n / (8.0 * sms));
+            const double cost = waves * chain * kChainStageUs +
+                                kModelApplies * (above * kLaunchUs + 8.0 * (double)n * n / kGemvBytesPerUs);
+            if (ld < 0 || cost < best) { ld = l; best = cost; }
+        }
     }
     h->coarse_dense = ld >= 0;
     h->first_coarse = h->coarse_dense ? ld : lc0;
