@@ -1769,14 +1769,14 @@ void build_apply_graph(hs_factor_s* h) {
     auto level_len = [&](int l) -> int64_t { return l < D ? h->lev[l]->slot[h->lev[l]->nc] : h->ntop; };
     // dense coarse operator: among the levels (>= lc0) with at most
     // coarse_dense DOFs, the one with the smallest modelled cost of building
-    // it (one single-CTA pass over the remaining levels per unit vector, in
-    // waves over the SMs) plus kModelApplies applies (the levels above it as
-    // stage kernels, and the dense product)
+    // it (a single-CTA pass over the remaining stages per unit vector: the
+    // larger of a per-(vector x stage) cost and one chain's latency) plus
+    // kModelApplies applies (the levels above it as stage kernels, and the
+    // dense product).  Constants measured on GB300.
     int ld = -1;
     if (h->opt.coarse_dense > 0) {
-        int sms = 152;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-        constexpr double kChainStageUs = 12.0, kLaunchUs = 1.0, kModelApplies = 10.0, kGemvBytesPerUs = 4e6;
+        constexpr double kVecStageUs = 0.012, kChainStageUs = 2.4, kLaunchUs = 5.0, kModelApplies = 10.0,
+                         kGemvBytesPerUs = 4e6;
         auto stages = [&](int l) { return l < D ? 2.0 * h->lev[l]->nstages + 2.0 : 2.0; };
         double best = 0.0;
         for (int l = lc0; l <= D; l++) {
@@ -1789,9 +1789,11 @@ void build_apply_graph(hs_factor_s* h) {
             double chain = 0.0, above = 0.0;
             for (int k = l; k <= D; k++) chain += stages(k);
             for (int k = lc0; k < l; k++) above += stages(k);
-            const double waves = std::ceil((double)n / (8.0 * sms));
-            const double cost = waves * chain * kChainStageUs +
-                                kModelApplies * (above * kLaunchUs + 8.0 * (double)n * n / kGemvBytesPerUs);
+            const double build = std::max((double)n * chain * kVecStageUs, chain * kChainStageUs);
+            const double cost = build + kModelApplies * (above * kLaunchUs + 8.0 * (double)n * n / kGemvBytesPerUs);
+            if (std::getenv("HS_TRACE"))
+                std::fprintf(stderr, "hs_trace dense candidate level %d: n %lld, modelled cost %.1f us\n", l,
+                             (long long)n, cost);
             if (ld < 0 || cost < best) { ld = l; best = cost; }
         }
     }
