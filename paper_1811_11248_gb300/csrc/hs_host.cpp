@@ -585,6 +585,7 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
         else D(c) = 1;
     }
     int first = lo;  // clusters below `first` are all done
+    std::vector<int> merged;
     while (remaining > 0) {
         std::vector<int> sel;
         while (first < hi && D(first)) first++;
@@ -600,12 +601,21 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
             auto& nlc = P.nl[c];
             auto& wlc = P.wl[c];
             for (int q : cur[c]) (sorted_has(P.adj0[c], q) ? nlc : wlc).push_back(q);
-            for (int p : nlc)
-                for (int q : nlc)
-                    if (p != q) {
-                        sorted_insert(cur[p], q);
-                        sorted_insert(P.all[p], q);
+            // every neighbour p gains all the others (sorted merges)
+            for (int p : nlc) {
+                for (auto* v : {&cur[p], &P.all[p]}) {
+                    merged.clear();
+                    auto a = v->begin(), ae = v->end();
+                    auto b = nlc.begin(), be = nlc.end();
+                    while (a != ae || b != be) {
+                        if (b != be && *b == p) { ++b; continue; }  // p does not gain itself
+                        if (b == be || (a != ae && *a < *b)) merged.push_back(*a++);
+                        else if (a == ae || *b < *a) merged.push_back(*b++);
+                        else { merged.push_back(*a++); ++b; }
                     }
+                    v->swap(merged);
+                }
+            }
             if (wlc.empty()) {
                 P.vanished[c] = 1;
                 for (int q : cur[c]) sorted_erase(cur[q], c);
@@ -910,6 +920,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
         ws_phase_max = std::max(ws_phase_max, ws);
     }
+    tr0.mark("  tasks: sizes and offsets");
     L.lists.resize(list_off[nt]);
     parallel_ranges(nt, 2048, [&](int64_t lo, int64_t hi, int) {
         for (int64_t ti = lo; ti < hi; ti++) {
@@ -926,6 +937,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             }
         }
     });
+    tr0.mark("  tasks: lists");
     // Schur targets of every phase: (p, q), p <= q, contributions in
     // ascending task order (sort by target, stable in task order).  The
     // independent cluster ranges are handled on their own threads and
@@ -942,7 +954,8 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         // work items: (range, phase) pairs, independent of each other
         const int nitems = nr * L.nphases;
         auto work = [&] {
-            std::vector<TC> tcs;
+            std::vector<TC> tcs, tmp;
+            std::vector<int> cntv;
             for (int item = next++; item < nitems; item = next++) {
                 const int k = item / L.nphases;
                 const int lo = ranges.empty() ? 0 : ranges[k].first, hi = ranges.empty() ? P.nc : ranges[k].second;
@@ -958,8 +971,20 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                             for (int b = 0; b < (int)nlc.size(); b++)
                                 if (nlc[a] <= nlc[b]) tcs.push_back(TC{nlc[a], nlc[b], ContribDev{ti, a, b}});
                     }
-                    std::stable_sort(tcs.begin(), tcs.end(),
-                                     [](const TC& x, const TC& y) { return x.p < y.p || (x.p == y.p && x.q < y.q); });
+                    // stable order by (p, q): counting sort on q, then on p
+                    // (keys are cluster ids in [lo, hi))
+                    if (!tcs.empty()) {
+                        const int span = hi - lo;
+                        cntv.assign(span + 1, 0);
+                        tmp.resize(tcs.size());
+                        for (const TC& x : tcs) cntv[x.q - lo + 1]++;
+                        for (int u = 0; u < span; u++) cntv[u + 1] += cntv[u];
+                        for (const TC& x : tcs) tmp[cntv[x.q - lo]++] = x;
+                        cntv.assign(span + 1, 0);
+                        for (const TC& x : tmp) cntv[x.p - lo + 1]++;
+                        for (int u = 0; u < span; u++) cntv[u + 1] += cntv[u];
+                        for (const TC& x : tmp) tcs[cntv[x.p - lo]++] = x;
+                    }
                     auto& tg = rt[k][ph];
                     auto& ct = rc[k][ph];
                     for (size_t i = 0; i < tcs.size();) {
@@ -992,7 +1017,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             L.ph_target.push_back((int)targets.size());
         }
     }
-    tr0.mark("  tasks+targets");
+    tr0.mark("  targets");
     // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
     // before its own transform (q in a later phase) or at level end (earlier)
     {
