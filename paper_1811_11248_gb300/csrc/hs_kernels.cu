@@ -37,6 +37,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -648,8 +653,11 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     }
 }
 
-template <typename FT>
-__global__ void __launch_bounds__(kFactorThreads, 2)
+// NT threads per CTA: 512 (two CTAs per SM) when a phase fills the GPU,
+// 1024 (one per SM, twice the threads per cluster) when it has no more
+// clusters than SMs
+template <typename FT, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
 k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restrict__ lists,
                double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
                const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
@@ -952,16 +960,18 @@ template <typename FT>
 __global__ void __launch_bounds__(kApplyThreads)
 k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pulls,
          const FT* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y, int smax) {
+    // vectors in shared memory in the factor's type: each FP64 value is
+    // converted once (conversions run on the FP64 pipe)
     extern __shared__ double sh[];
-    double* ys = sh;
-    double* yn = sh + smax;
+    FT* ys = reinterpret_cast<FT*>(sh);
+    FT* yn = ys + smax;
     const ApTask T = tasks[t0 + blockIdx.x];
     const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
     double* yg = y + T.y;
     for (int j = tid; j < s; j += NT) {
         double v = yg[j];
         for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
-        ys[j] = v;
+        ys[j] = (FT)v;
     }
     __syncthreads();
     const FT* Wm = fac + T.w;
@@ -969,22 +979,22 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
     for (int i0 = 4 * wid; i0 < s; i0 += 4 * nwarp) {
         FT a[4] = {FT(0), FT(0), FT(0), FT(0)};
         for (int j = lane; j < s; j += 32) {
-            const FT yj = (FT)ys[j];
+            const FT yj = ys[j];
 #pragma unroll
             for (int u = 0; u < 4; u++)
                 if (i0 + u < s) a[u] += Wm[(int64_t)(i0 + u) * s + j] * yj;
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const double t = warp_sum((double)a[u]);
+            const FT t = warp_sum(a[u]);
             if (lane == 0 && i0 + u < s) yn[i0 + u] = t;
         }
     }
     __syncthreads();
-    for (int j = tid; j < s; j += NT) yg[j] = yn[j];
+    for (int j = tid; j < s; j += NT) yg[j] = (double)yn[j];
     const int f = s - T.r;
     const FT* C = fac + T.cm;
-    const double* yf = yn + T.r;
+    const FT* yf = yn + T.r;
     int jv = 0;  // columns below jv done with vector loads
     if constexpr (sizeof(FT) == sizeof(float)) {
         // four columns per thread, one aligned float4 per row (C and its
@@ -999,7 +1009,7 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
                 const float4 c1 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 1) * T.ncap);
                 const float4 c2 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 2) * T.ncap);
                 const float4 c3 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 3) * T.ncap);
-                const float y0 = (float)yf[i], y1 = (float)yf[i + 1], y2 = (float)yf[i + 2], y3 = (float)yf[i + 3];
+                const float y0 = yf[i], y1 = yf[i + 1], y2 = yf[i + 2], y3 = yf[i + 3];
                 p0.x += c0.x * y0 + c2.x * y2; p0.y += c0.y * y0 + c2.y * y2;
                 p0.z += c0.z * y0 + c2.z * y2; p0.w += c0.w * y0 + c2.w * y2;
                 p1.x += c1.x * y1 + c3.x * y3; p1.y += c1.y * y1 + c3.y * y3;
@@ -1007,7 +1017,7 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
             }
             for (; i < f; i++) {
                 const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
-                const float y0 = (float)yf[i];
+                const float y0 = yf[i];
                 p0.x += c0.x * y0; p0.y += c0.y * y0; p0.z += c0.z * y0; p0.w += c0.w * y0;
             }
             double* st = stage + T.stg + j4;
@@ -1022,12 +1032,12 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
         const FT* cj = C + j;
         int i = 0;
         for (; i + 3 < f; i += 4) {
-            a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
-            a1 += cj[(int64_t)(i + 1) * T.ncap] * (FT)yf[i + 1];
-            a2 += cj[(int64_t)(i + 2) * T.ncap] * (FT)yf[i + 2];
-            a3 += cj[(int64_t)(i + 3) * T.ncap] * (FT)yf[i + 3];
+            a0 += cj[(int64_t)i * T.ncap] * yf[i];
+            a1 += cj[(int64_t)(i + 1) * T.ncap] * yf[i + 1];
+            a2 += cj[(int64_t)(i + 2) * T.ncap] * yf[i + 2];
+            a3 += cj[(int64_t)(i + 3) * T.ncap] * yf[i + 3];
         }
-        for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
+        for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * yf[i];
         stage[T.stg + j] = (double)((a0 + a1) + (a2 + a3));
     }
 }
@@ -1050,18 +1060,21 @@ k_ap_fin(const ApFin* __restrict__ fins, const ApPull* __restrict__ pulls, const
 template <typename FT>
 __global__ void __launch_bounds__(kApplyThreads)
 k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs, const FT* __restrict__ fac,
-         double* __restrict__ y, int smax) {
+         double* __restrict__ y, int smax, int nmax) {
+    // xs in FP64 (it is updated in place), copies of xs and the neighbour
+    // values in the factor's type (each converted once)
     extern __shared__ double sh[];
     double* xs = sh;
     double* part = sh + smax;
-    double* xn = part + blockDim.x;
+    FT* xnf = reinterpret_cast<FT*>(part + blockDim.x);
+    FT* xsf = xnf + nmax;
     const ApTask T = tasks[t0 + blockIdx.x];
     const int s = T.s, r = T.r, f = s - r, tid = threadIdx.x, NT = blockDim.x;
     double* yg = y + T.y;
     for (int i = tid; i < s; i += NT) xs[i] = yg[i];
     for (int e = T.nb0; e < T.nb1; e++) {
         const ApNb nb = nbs[e];
-        for (int j = tid; j < nb.m; j += NT) xn[nb.col + j] = y[nb.y + j];
+        for (int j = tid; j < nb.m; j += NT) xnf[nb.col + j] = (FT)y[nb.y + j];
     }
     __syncthreads();
     const FT* C = fac + T.cm;
@@ -1072,7 +1085,7 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
         for (int i0 = 4 * wid; i0 < f; i0 += 4 * nwarp) {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
             for (int j4 = 4 * lane; j4 < jv; j4 += 128) {
-                const float x0 = (float)xn[j4], x1 = (float)xn[j4 + 1], x2 = (float)xn[j4 + 2], x3 = (float)xn[j4 + 3];
+                const float x0 = xnf[j4], x1 = xnf[j4 + 1], x2 = xnf[j4 + 2], x3 = xnf[j4 + 3];
 #pragma unroll
                 for (int u = 0; u < 4; u++)
                     if (i0 + u < f) {
@@ -1082,15 +1095,15 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
                     }
             }
             for (int j = jv + lane; j < T.ncols; j += 32) {
-                const float xj = (float)xn[j];
+                const float xj = xnf[j];
 #pragma unroll
                 for (int u = 0; u < 4; u++)
                     if (i0 + u < f) a[u] += (float)C[(int64_t)(i0 + u) * T.ncap + j] * xj;
             }
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const double su = warp_sum((double)a[u]);
-                if (lane == 0 && i0 + u < f) xs[r + i0 + u] -= su;
+                const float su = warp_sum(a[u]);
+                if (lane == 0 && i0 + u < f) xs[r + i0 + u] -= (double)su;
             }
         }
     } else {
@@ -1098,7 +1111,7 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
             FT a0 = FT(0), a1 = FT(0);
             const bool two = i0 + 1 < f;
             for (int j = lane; j < T.ncols; j += 32) {
-                const FT xj = (FT)xn[j];
+                const FT xj = xnf[j];
                 a0 += C[(int64_t)i0 * T.ncap + j] * xj;
                 if (two) a1 += C[(int64_t)(i0 + 1) * T.ncap + j] * xj;
             }
@@ -1111,16 +1124,18 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
         }
     }
     __syncthreads();
+    for (int i = tid; i < s; i += NT) xsf[i] = (FT)xs[i];
+    __syncthreads();
     const FT* Wm = fac + T.w;
     if (s >= NT) {
         for (int jj = tid; jj < s; jj += NT) {
             FT a0 = FT(0), a1 = FT(0);
             int i = 0;
             for (; i + 1 < s; i += 2) {
-                a0 += Wm[(int64_t)i * s + jj] * (FT)xs[i];
-                a1 += Wm[(int64_t)(i + 1) * s + jj] * (FT)xs[i + 1];
+                a0 += Wm[(int64_t)i * s + jj] * xsf[i];
+                a1 += Wm[(int64_t)(i + 1) * s + jj] * xsf[i + 1];
             }
-            if (i < s) a0 += Wm[(int64_t)i * s + jj] * (FT)xs[i];
+            if (i < s) a0 += Wm[(int64_t)i * s + jj] * xsf[i];
             yg[jj] = (double)(a0 + a1);
         }
         return;
@@ -1130,10 +1145,10 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
     if (g < G) {
         int i = g;
         for (; i + G < s; i += 2 * G) {
-            a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
-            a1 += Wm[(int64_t)(i + G) * s + j] * (FT)xs[i + G];
+            a0 += Wm[(int64_t)i * s + j] * xsf[i];
+            a1 += Wm[(int64_t)(i + G) * s + j] * xsf[i + G];
         }
-        if (i < s) a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
+        if (i < s) a0 += Wm[(int64_t)i * s + j] * xsf[i];
     }
     part[tid] = (double)(a0 + a1);
     __syncthreads();
@@ -1716,12 +1731,26 @@ cudaError_t factor_phase_t(cudaStream_t st, const TaskDev* tasks, int t0, int nt
     // G^-1 in shared memory when it fits beside the rest
     const int use_x = factor_smem_bytes(smax, wmax, lmax, model != nullptr, true) <= (size_t)kFactorMaxSmem;
     const size_t smem = factor_smem_bytes(smax, wmax, lmax, model != nullptr, use_x);
-    cudaError_t e = cudaFuncSetAttribute(k_factor_phase<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     counted();
-    k_factor_phase<FT><<<ntasks, kFactorThreads, smem, st>>>(tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta,
-                                                             ws, eps2, status, level, smax, wmax, lmax, feat,
-                                                             model, use_x);
+    if (ntasks <= sms) {
+        e = cudaFuncSetAttribute(k_factor_phase<FT, 2 * kFactorThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        k_factor_phase<FT, 2 * kFactorThreads><<<ntasks, 2 * kFactorThreads, smem, st>>>(
+            tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level, smax, wmax, lmax, feat,
+            model, use_x);
+    } else {
+        e = cudaFuncSetAttribute(k_factor_phase<FT, kFactorThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        k_factor_phase<FT, kFactorThreads><<<ntasks, kFactorThreads, smem, st>>>(
+            tasks, t0, lists, blocks, blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level, smax, wmax, lmax, feat,
+            model, use_x);
+    }
     return cudaGetLastError();
 }
 
@@ -1828,11 +1857,13 @@ cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntas
                           const ApNb* nbs, const void* fac, int fp32, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
-    const size_t smem = sizeof(double) * (smax + kApplyThreads + nmax);
+    const size_t smem = sizeof(double) * (2 * (size_t)smax + kApplyThreads + nmax);
     if (fp32)
-        k_ap_bwd<float><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const float*>(fac), y, smax);
+        k_ap_bwd<float><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const float*>(fac), y, smax,
+                                                             nmax);
     else
-        k_ap_bwd<double><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const double*>(fac), y, smax);
+        k_ap_bwd<double><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const double*>(fac), y,
+                                                              smax, nmax);
     return cudaGetLastError();
 }
 
