@@ -1167,11 +1167,15 @@ template <typename FT>
 __device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPull* __restrict__ pulls,
                           const FT* __restrict__ fac, double* __restrict__ stage, double* __restrict__ y,
                           double* ys, double* yn) {
+    // the vectors in the factor's type (each FP64 value converted once);
+    // with a float factor both fit in the space of ys
+    FT* ysf = reinterpret_cast<FT*>(ys);
+    FT* ynf = sizeof(FT) == sizeof(double) ? reinterpret_cast<FT*>(yn) : ysf + kCoarseSmax;
     const int s = act ? T.s : 0;
     for (int j = gl; j < s; j += gs) {
         double v = y[T.y + j];
         for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
-        ys[j] = v;
+        ysf[j] = (FT)v;
     }
     __syncwarp();
     if (act) {
@@ -1181,32 +1185,32 @@ __device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPul
             FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int j = 0;
             for (; j + 3 < s; j += 4) {
-                a0 += wi[j] * (FT)ys[j];
-                a1 += wi[j + 1] * (FT)ys[j + 1];
-                a2 += wi[j + 2] * (FT)ys[j + 2];
-                a3 += wi[j + 3] * (FT)ys[j + 3];
+                a0 += wi[j] * ysf[j];
+                a1 += wi[j + 1] * ysf[j + 1];
+                a2 += wi[j + 2] * ysf[j + 2];
+                a3 += wi[j + 3] * ysf[j + 3];
             }
-            for (; j < s; j++) a0 += wi[j] * (FT)ys[j];
-            yn[i] = (double)((a0 + a1) + (a2 + a3));
+            for (; j < s; j++) a0 += wi[j] * ysf[j];
+            ynf[i] = (a0 + a1) + (a2 + a3);
         }
     }
     __syncwarp();
     if (act) {
-        for (int j = gl; j < s; j += gs) y[T.y + j] = yn[j];
+        for (int j = gl; j < s; j += gs) y[T.y + j] = (double)ynf[j];
         const int f = s - T.r;
         const FT* C = fac + T.cm;
-        const double* yf = yn + T.r;
+        const FT* yf = ynf + T.r;
         for (int j = gl; j < T.ncols; j += gs) {
             const FT* cj = C + j;
             FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int i = 0;
             for (; i + 3 < f; i += 4) {
-                a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
-                a1 += cj[(int64_t)(i + 1) * T.ncap] * (FT)yf[i + 1];
-                a2 += cj[(int64_t)(i + 2) * T.ncap] * (FT)yf[i + 2];
-                a3 += cj[(int64_t)(i + 3) * T.ncap] * (FT)yf[i + 3];
+                a0 += cj[(int64_t)i * T.ncap] * yf[i];
+                a1 += cj[(int64_t)(i + 1) * T.ncap] * yf[i + 1];
+                a2 += cj[(int64_t)(i + 2) * T.ncap] * yf[i + 2];
+                a3 += cj[(int64_t)(i + 3) * T.ncap] * yf[i + 3];
             }
-            for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * (FT)yf[i];
+            for (; i < f; i++) a0 += cj[(int64_t)i * T.ncap] * yf[i];
             stage[T.stg + j] = (double)((a0 + a1) + (a2 + a3));
         }
     }
@@ -1216,12 +1220,17 @@ __device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPul
 template <typename FT>
 __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb* __restrict__ nbs,
                           const FT* __restrict__ fac, double* __restrict__ y, double* xs, double* xn) {
+    // xs (FP64, updated in place) and copies in the factor's type of the
+    // neighbour values and of xs: each FP64 value converted once.  With a
+    // float factor the copies fit in the space of xn (kCoarseNmax doubles).
+    FT* xnf = reinterpret_cast<FT*>(xn);
+    FT* xsf = sizeof(FT) == sizeof(double) ? reinterpret_cast<FT*>(xs) : xnf + kCoarseNmax;
     const int s = act ? T.s : 0, r = T.r, f = s - r;
     for (int i = gl; i < s; i += gs) xs[i] = y[T.y + i];
     const int ncols = act ? T.ncols : 0;
     for (int e = act ? T.nb0 : 0; e < (act ? T.nb1 : 0); e++) {
         const ApNb nb = nbs[e];
-        for (int j = gl; j < nb.m; j += gs) xn[nb.col + j] = y[nb.y + j];
+        for (int j = gl; j < nb.m; j += gs) xnf[nb.col + j] = (FT)y[nb.y + j];
     }
     __syncwarp();
     if (act) {
@@ -1231,15 +1240,18 @@ __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb*
             FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int j = 0;
             for (; j + 3 < ncols; j += 4) {
-                a0 += ci[j] * (FT)xn[j];
-                a1 += ci[j + 1] * (FT)xn[j + 1];
-                a2 += ci[j + 2] * (FT)xn[j + 2];
-                a3 += ci[j + 3] * (FT)xn[j + 3];
+                a0 += ci[j] * xnf[j];
+                a1 += ci[j + 1] * xnf[j + 1];
+                a2 += ci[j + 2] * xnf[j + 2];
+                a3 += ci[j + 3] * xnf[j + 3];
             }
-            for (; j < ncols; j++) a0 += ci[j] * (FT)xn[j];
+            for (; j < ncols; j++) a0 += ci[j] * xnf[j];
             xs[r + i] -= (double)((a0 + a1) + (a2 + a3));
         }
     }
+    __syncwarp();
+    if (sizeof(FT) != sizeof(double))
+        for (int i = gl; i < s; i += gs) xsf[i] = (FT)xs[i];
     __syncwarp();
     if (act) {
         const FT* Wm = fac + T.w;
@@ -1247,12 +1259,12 @@ __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb*
             FT a0 = FT(0), a1 = FT(0), a2 = FT(0), a3 = FT(0);
             int i = 0;
             for (; i + 3 < s; i += 4) {
-                a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
-                a1 += Wm[(int64_t)(i + 1) * s + j] * (FT)xs[i + 1];
-                a2 += Wm[(int64_t)(i + 2) * s + j] * (FT)xs[i + 2];
-                a3 += Wm[(int64_t)(i + 3) * s + j] * (FT)xs[i + 3];
+                a0 += Wm[(int64_t)i * s + j] * xsf[i];
+                a1 += Wm[(int64_t)(i + 1) * s + j] * xsf[i + 1];
+                a2 += Wm[(int64_t)(i + 2) * s + j] * xsf[i + 2];
+                a3 += Wm[(int64_t)(i + 3) * s + j] * xsf[i + 3];
             }
-            for (; i < s; i++) a0 += Wm[(int64_t)i * s + j] * (FT)xs[i];
+            for (; i < s; i++) a0 += Wm[(int64_t)i * s + j] * xsf[i];
             y[T.y + j] = (double)((a0 + a1) + (a2 + a3));
         }
     }
