@@ -385,7 +385,7 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         for (int idx = tid; idx < s * s; idx += NT) {
             const double a = A[(int64_t)(idx / s) * ld + idx % s];
             G[idx] = a;
-            if (idx / s != idx % s) amax_ss = fmax(amax_ss, fabs(a));
+            if (want_feat && idx / s != idx % s) amax_ss = fmax(amax_ss, fabs(a));
         }
     }
     g.sync();
@@ -510,7 +510,9 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                 const int i = b + u;
                 if (i >= s) break;
                 M[(int64_t)i * Wt + j] = a[u];
-                amax_row = fmax(amax_row, fabs(a[u]));
+                if (want_feat) {
+                    amax_row = fmax(amax_row, fabs(a[u]));  // FP64 max: only for the features
+                }
                 if (want_feat && fill) {
                     const double x = a[u] * rdiag[i];
                     cj = fma(x, x, cj);
