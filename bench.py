@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 METRIC = "setup+solve s to 1e-8 rel. residual, mixed/batched vs plain FP64, one GB300"
 WORKLOAD = "aniso-ice-64x64x16 (N=65536), 1024 leaves x 64 DOF, depth 8, eps 1e-2, PCG rtol 1e-8"
 NOMINAL_FP64_TFLOPS = 1.25
+# DRAM read + write bytes per k_factor_phase launch of this workload's mixed step: mean of the
+# first three level-0 phase launches in an ncu capture of the current kernel
+FACTOR_TRAFFIC_BYTES = 75.8e6
 
 
 def parse():
@@ -379,7 +382,8 @@ def run_ours(args):
     fac = stats_mx["factor"]
     achieved = fac["flops"] / (fac["ms"] * 1e-3) / 1e12 if fac["ms"] > 0 else 0.0
     roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak if fp64_peak > 0 else None, "traffic": None,
+            "frac": achieved / fp64_peak if fp64_peak > 0 else None, "traffic": FACTOR_TRAFFIC_BYTES,
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
             "kernel": "k_factor_phase (FP64 Cholesky + scaling, FP32 CPQR in the mixed form)",
             "peak_kind": f"measured FP64 FMA probe (nominal {NOMINAL_FP64_TFLOPS} TFLOP/s)",
             "avg_launch_ms": fac["ms"] / max(fac["launches"], 1),
