@@ -868,7 +868,10 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
                      float* __restrict__ feat, const float* __restrict__ model) {
     extern __shared__ double sm[];
     const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int gw = blockIdx.x * nwarp + wid, GW = gridDim.x * nwarp;
+    // items go to CTAs round-robin first (item k: CTA k mod grid, warp k /
+    // grid), so that a phase's few clusters land on different SMs and do not
+    // share an SM's FP64 pipe
+    const int gw = wid * gridDim.x + blockIdx.x, GW = gridDim.x * nwarp;
     const int64_t wd = fused_warp_doubles(smax, wmax, lmax, mcap);
     double* d = sm + (size_t)wid * wd;
     int* ii = reinterpret_cast<int*>(sm + (size_t)nwarp * wd) + (size_t)wid * (lmax + 2);
@@ -1806,7 +1809,9 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     // every CTA must be resident (grid barrier): at most per_sm * sms CTAs, and
     // no more than the largest phase needs
-    const int want = (max_items + kFusedWarps - 1) / kFusedWarps;
+    // at least one CTA per SM (up to the largest phase's items), at most all
+    // that can be resident together
+    const int want = std::max(std::min(max_items, sms), (max_items + kFusedWarps - 1) / kFusedWarps);
     const int grid = std::max(1, std::min(per_sm * sms, want));
     if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
     counted();
