@@ -144,6 +144,30 @@ struct EntryMeta {
 
 constexpr int kNB = 16;  // Cholesky panel width
 
+// 1 / sqrt(d) for the Cholesky pivots: the FP32 estimate refined by two
+// Newton-Raphson steps y <- y + y (1 - d y^2) / 2 (each squares the relative
+// error: 2^-22 -> 2^-44 -> below FP64 rounding); outside the FP32 range the
+// FP64 square root and division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    double h = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, h, y);
+    h = fma(-d * y, y, 1.0);
+    return fma(0.5 * y, h, y);
+}
+
+// 1 / x for x > 0: the FP32 reciprocal refined by two Newton-Raphson steps
+// y <- y + y (1 - x y); outside the FP32 range the FP64 division.
+__device__ __forceinline__ double rcp_newton(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+    double y = (double)(1.0f / (float)x);
+    double h = fma(-x, y, 1.0);
+    y = fma(y, h, y);
+    h = fma(-x, y, 1.0);
+    return fma(y, h, y);
+}
+
 // In-place FP64 -> FP32 conversion of count elements by the group: float i
 // overwrites bytes of double i / 2, which an earlier chunk (or this chunk,
 // before the barrier) has already read.
@@ -212,12 +236,18 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
         }
         const double sig = g.sum(ls, red);
         if (tid == 0) {
+            // beta = -sign(alpha) nrm, tau = (beta - alpha) / beta and
+            // 1 / (alpha - beta) from 1 / nrm and 1 / (|alpha| + nrm) by
+            // Newton-Raphson (no FP64 square root or division)
             const double alpha = (double)M[(int64_t)k * Wt + pc];
-            const double nrm = sqrt(alpha * alpha + sig);
-            const double beta = alpha >= 0.0 ? -nrm : nrm;
-            s_hh[0] = beta;
-            s_hh[1] = (beta - alpha) / beta;
-            s_hh[2] = 1.0 / (alpha - beta);
+            const double q = fma(alpha, alpha, sig);
+            const double rs = rsqrt_newton(q);
+            const double nrm = q * rs;
+            const double sg = alpha >= 0.0 ? 1.0 : -1.0;
+            const double ra = rcp_newton(fabs(alpha) + nrm);
+            s_hh[0] = -sg * nrm;                   // beta
+            s_hh[1] = (fabs(alpha) + nrm) * rs;    // tau = (beta - alpha) / beta
+            s_hh[2] = sg * ra;                     // 1 / (alpha - beta)
             cn[p] = -1.0;
         }
         g.sync();
@@ -291,19 +321,6 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
         }
     }
     if (tid == 0) cur[T.c] = (T.nw > 0) ? r : 0;
-}
-
-// 1 / sqrt(d) for the Cholesky pivots: the FP32 estimate refined by two
-// Newton-Raphson steps y <- y + y (1 - d y^2) / 2 (each squares the relative
-// error: 2^-22 -> 2^-44 -> below FP64 rounding); outside the FP32 range the
-// FP64 square root and division.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
-    double h = fma(-d * y, y, 1.0);
-    y = fma(0.5 * y, h, y);
-    h = fma(-d * y, y, 1.0);
-    return fma(0.5 * y, h, y);
 }
 
 // Rank predictor inside a factor task: y = w3 . relu(W2 relu(W1 xn + b1) + b2)
