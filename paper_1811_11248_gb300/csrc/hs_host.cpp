@@ -825,21 +825,35 @@ struct BlockTable {
 };
 
 BlockTable make_table(const LevelPlan& P) {
+    // row starts and byte offsets by prefix sums, then the rows in parallel
     BlockTable T;
-    T.ptr.assign(P.nc + 1, 0);
-    for (int c = 0; c < P.nc; c++) T.ptr[c + 1] = T.ptr[c] + (int)P.all[c].size();
-    T.col.reserve(T.ptr[P.nc]);
-    T.off.reserve(T.ptr[P.nc]);
-    T.ld.reserve(T.ptr[P.nc]);
-    int64_t o = 0;
-    for (int c = 0; c < P.nc; c++)
-        for (int q : P.all[c]) {
-            T.col.push_back(q);
-            T.off.push_back(o);
-            T.ld.push_back(P.size0[q]);
-            o += (int64_t)P.size0[c] * P.size0[q];
+    const int nc = P.nc;
+    T.ptr.assign(nc + 1, 0);
+    std::vector<int64_t> rowsz(nc + 1, 0);
+    for (int c = 0; c < nc; c++) {
+        T.ptr[c + 1] = T.ptr[c] + (int)P.all[c].size();
+        int64_t w = 0;
+        for (int q : P.all[c]) w += P.size0[q];
+        rowsz[c + 1] = rowsz[c] + (int64_t)P.size0[c] * w;
+    }
+    const int nb = T.ptr[nc];
+    T.col.resize(nb);
+    T.off.resize(nb);
+    T.ld.resize(nb);
+    parallel_ranges(nc, 2048, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t c = lo; c < hi; c++) {
+            int64_t o = rowsz[c];
+            int b = T.ptr[c];
+            for (int q : P.all[c]) {
+                T.col[b] = q;
+                T.off[b] = o;
+                T.ld[b] = P.size0[q];
+                o += (int64_t)P.size0[c] * P.size0[q];
+                b++;
+            }
         }
-    T.total = o;
+    });
+    T.total = rowsz[nc];
     return T;
 }
 
@@ -1004,18 +1018,31 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             }
         };
         run_threads(nt < 256 ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
-        for (int ph = 0; ph < L.nphases; ph++) {
-            for (int k = 0; k < nr; k++) {
-                const int base = (int)contribs.size();
+        // concatenation in (phase, range) order: offsets first, then the
+        // copies item by item in parallel
+        std::vector<int64_t> toff(nitems + 1, 0), coff(nitems + 1, 0);
+        for (int ph = 0, it = 0; ph < L.nphases; ph++) {
+            for (int k = 0; k < nr; k++, it++) {
+                toff[it + 1] = toff[it] + (int64_t)rt[k][ph].size();
+                coff[it + 1] = coff[it] + (int64_t)rc[k][ph].size();
+            }
+            L.ph_target.push_back((int)toff[it]);
+        }
+        targets.resize(toff[nitems]);
+        contribs.resize(coff[nitems]);
+        parallel_ranges(nitems, 8, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t it = lo; it < hi; it++) {
+                const int ph = (int)(it / nr), k = (int)(it % nr);
+                const int base = (int)coff[it];
+                int64_t o = toff[it];
                 for (TargetDev g : rt[k][ph]) {
                     g.c_begin += base;
                     g.c_end += base;
-                    targets.push_back(g);
+                    targets[o++] = g;
                 }
-                contribs.insert(contribs.end(), rc[k][ph].begin(), rc[k][ph].end());
+                std::copy(rc[k][ph].begin(), rc[k][ph].end(), contribs.begin() + coff[it]);
             }
-            L.ph_target.push_back((int)targets.size());
-        }
+        });
     }
     tr0.mark("  targets");
     // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
