@@ -60,6 +60,16 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(value, device):
+    """The largest `value` over all ranks of the process group (the step
+    time of the slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -347,10 +357,7 @@ def run_ours(args):
     t_step, it_mx, res_mx, launches = timed(hsolve.HS_PREC_MIXED)
     clk = clocks.stop()
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+        t_step = max_over_ranks(t_step, dev)
 
     # e2e: hs_solve on host buffers (H2D of A and b, D2H of x inside)
     e2e_times = []

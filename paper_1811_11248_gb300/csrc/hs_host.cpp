@@ -29,6 +29,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <unistd.h>
 #include <unordered_map>
 #include <vector>
 
@@ -223,6 +224,7 @@ class Pool {
     }
     int workers() const { return (int)th_.size(); }
     bool try_run(int T, const std::function<void(int)>& fn) {
+        if (getpid() != pid_) return false;  // a forked child has no workers
         std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
         if (!busy.owns_lock()) return false;
         {
@@ -240,6 +242,10 @@ class Pool {
         return true;
     }
     ~Pool() {
+        if (getpid() != pid_) {  // forked child: the threads are not ours
+            for (auto& t : th_) t.detach();
+            return;
+        }
         {
             std::lock_guard<std::mutex> lk(mu_);
             stop_ = true;
@@ -249,7 +255,7 @@ class Pool {
     }
 
   private:
-    explicit Pool(int n) {
+    explicit Pool(int n) : pid_(getpid()) {
         for (int i = 0; i < n; i++) th_.emplace_back([this] { loop(); });
     }
     void loop() {
@@ -275,6 +281,7 @@ class Pool {
     const std::function<void(int)>* job_ = nullptr;
     int njob_ = 0, next_ = 0, pending_ = 0;
     bool stop_ = false;
+    pid_t pid_;
 };
 
 // Runs fn(t) for t < T (t = 0 on the calling thread; the others on the

@@ -57,3 +57,30 @@ def test_partition_rejects_bad_arguments(hs):
     p = inputs.grid_operator(4, 4, 2, ratio=10.0)
     with pytest.raises(hs.HsError):
         hs.hs_partition_extruded(p.n, p.rowptr, p.col, p.val, None, 0, 0.5)
+
+
+def _partition_in_child(q):
+    from paper_1811_11248_gb300 import hsolve as hs2
+    p = inputs.anisotropic_64x64x16()
+    perm, lp, depth = hs2.hs_partition_extruded(p.n, p.rowptr, p.col, p.val,
+                                               np.ascontiguousarray(p.coords), 4, 0.5)
+    q.put(int(depth))
+
+
+def test_host_planner_survives_fork(hs):
+    """The planner's worker threads are created on first use; a process
+    forked afterwards has none, so its parallel loops must run serially
+    instead of waiting for workers that do not exist."""
+    import multiprocessing
+    p = inputs.anisotropic_64x64x16()
+    hs.hs_partition_extruded(p.n, p.rowptr, p.col, p.val, np.ascontiguousarray(p.coords), 4, 0.5)
+    ctx = multiprocessing.get_context("fork")
+    q = ctx.Queue()
+    child = ctx.Process(target=_partition_in_child, args=(q,))
+    child.start()
+    child.join(timeout=60)
+    alive = child.is_alive()
+    if alive:
+        child.kill()
+    assert not alive, "forked child hung in the host planner"
+    assert child.exitcode == 0 and q.get(timeout=5) == 8
