@@ -1,23 +1,37 @@
 // hs_kernels.cu -- sm_103a kernels of the hierarchical solver.
 //
 // Factorization (Algorithm 1), per phase of independent clusters:
-//   k_factor_phase : one CTA per cluster: Cholesky of A_ss (Sec. 2), scaling
-//                    G^-1 [A_sn A_sw] (Eq. scaling), column-pivoted QR of the
-//                    scaled fill block with every reflector applied to the
-//                    whole row (Eq. offdiag_new, Eq. sparse), write-back of the
-//                    coarse row (Eq. perm) and of the factor {G, U, C, r}.
-//   k_schur_phase  : one CTA per target block: X_nn = A_nn - C^T C (Eq. elim),
-//                    contributions summed in ascending cluster order.
-// Solve (Algorithm 2): k_apply_fwd / k_apply_bwd per phase with the explicit
-// per-cluster operator W = U^T G^-1, k_apply_fin / k_vcopy between levels,
-// k_top_solve for the dense top.
-// Krylov: CSR SpMV, deterministic two-stage dot products, vector updates.
+//   k_factor_phase       : one CTA per cluster (512 threads, or 1024 when a
+//                          phase has no more clusters than SMs): Cholesky of
+//                          A_ss together with G^-1 (Sec. 2), scaling
+//                          G^-1 [A_sn A_sw] (Eq. scaling; sparse level-0
+//                          columns as combinations of columns of G^-1),
+//                          column-pivoted QR of the scaled fill block with
+//                          every reflector applied to the whole row (Eq.
+//                          offdiag_new, Eq. sparse; FP32 in the mixed form),
+//                          write-back of the coarse row (Eq. perm) and of the
+//                          factor {W = U^T G^-1, C, r}.
+//   k_factor_level_fused : all phases of a coarse level in one cooperative
+//                          launch, one warp per cluster, bounded grid barrier.
+//   k_schur_phase        : one CTA per target block: X_nn = A_nn - C^T C (Eq.
+//                          elim), contributions summed in ascending cluster order.
+//   k_dense_cholesky / k_tops_cholesky : the dense top(s).
+// Solve (Algorithm 2): k_ap_fwd / k_ap_bwd per stage with the explicit
+// per-cluster operator W = U^T G^-1, k_ap_fin / k_vcopy between levels,
+// k_ap_coarse (single-CTA chain) or k_dense_gemv (explicit coarse operator
+// formed by k_ap_coarse_batch), k_tops_solve for batched tops.
+// Krylov: CSR SpMV, deterministic two-stage dot products, vector updates,
+// per-problem (segmented) PCG kernels for batched handles.
 //
 // Decisions that must agree with any other implementation of the method:
 // rank = smallest k with sum of squared trailing column norms <= eps^2;
 // pivot = lowest unpivoted column index with squared norm >= (1 - 1e-10) *
 // the largest; Householder beta = -sign(alpha) * norm, v_k = 1,
 // tau = (beta - alpha) / beta.
+//
+// On this GPU an SM completes about one warp-wide FP64 instruction every 16
+// cycles, and conversions between FP64 and FP32 run on the same pipe; the
+// kernels keep FP64 instructions full-warp and convert each value once.
 #include <atomic>
 #include <cfloat>
 #include <climits>
