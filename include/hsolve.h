@@ -126,7 +126,10 @@ int hs_tree_free(hs_tree* t);
  * cluster, level by level, then dense Cholesky of the top.  tree may be NULL
  * (then hs_partition_extruded runs on options->coords, options->leaf_lines,
  * options->theta, and options->depth applies).  CSR in options->mem.  On HS_ERR_NOT_SPD the
- * failing (level, cluster) is written to *info when info is not NULL. */
+ * failing (level, cluster) is written to *info when info is not NULL.
+ * With device inputs the pattern (and, for the partitioner, the values) is
+ * read back into a pinned host buffer that the calling thread keeps for
+ * later calls (freed when the thread exits). */
 int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
              const hs_tree* tree, const hs_options* opt, hs_handle* out, hs_info* info);
 

@@ -163,6 +163,7 @@ struct PinnedStage {
     }
 };
 thread_local PinnedStage g_stage;
+thread_local PinnedStage g_pattern_stage;  // the pattern read back by a setup with device inputs
 
 template <class T>
 void upload(DBuf& d, const std::vector<T>& h, cudaStream_t st) {
@@ -1397,9 +1398,6 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     const int64_t n = h->n;
     Trace tr;
     // host copy of the pattern (the symbolic analysis runs on the host)
-    std::vector<int64_t> hrp;
-    std::vector<int32_t> hcol;
-    std::vector<double> hval;
     const int64_t* rp = rowptr;
     const int32_t* cl = col;
     const double* vl = val;
@@ -1409,10 +1407,12 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         CK(cudaMemcpyAsync(&nnz0, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (nnz0 < 0) throw HsError{HS_ERR_ARG};
-        g_stage.drain();
+        // into a pinned area of their own, used in place for the whole setup
+        // (kept between calls: later setups of the same size reuse it)
+        g_pattern_stage.drain();
         const size_t b_rp = sizeof(int64_t) * (n + 1), b_col = sizeof(int32_t) * nnz0;
         const size_t b_val = tree_in ? 0 : sizeof(double) * nnz0;
-        char* pin = g_stage.take(b_rp + b_col + b_val + 512, st);
+        char* pin = g_pattern_stage.take(b_rp + b_col + b_val + 512, st);
         int64_t* prp = reinterpret_cast<int64_t*>(pin);
         int32_t* pcol = reinterpret_cast<int32_t*>(pin + ((b_rp + 255) & ~(size_t)255));
         double* pval = reinterpret_cast<double*>(pin + ((b_rp + 255) & ~(size_t)255) + ((b_col + 255) & ~(size_t)255));
@@ -1420,14 +1420,9 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         CK(cudaMemcpyAsync(pcol, col, b_col, cudaMemcpyDeviceToHost, st));
         if (b_val) CK(cudaMemcpyAsync(pval, val, b_val, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        // keep them: copy out of the staging area, which later uploads reuse
-        hrp.assign(prp, prp + n + 1);
-        hcol.assign(pcol, pcol + nnz0);
-        if (b_val) hval.assign(pval, pval + nnz0);
-        g_stage.synced(st);
-        rp = hrp.data();
-        cl = hcol.data();
-        vl = hval.empty() ? nullptr : hval.data();
+        rp = prp;
+        cl = pcol;
+        vl = b_val ? pval : nullptr;
     }
     const int64_t nnz = rp[n];
     {
