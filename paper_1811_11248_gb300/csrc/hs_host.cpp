@@ -1082,7 +1082,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
     }
     L.wmax = std::max(L.wmax, 64);  // the fused kernel's Schur step stages 32 x 4 int64 in the column table
-    if (factor_smem_bytes(L.smax, L.wmax, L.lmax, h->opt.rank_model != nullptr) > (size_t)kFactorMaxSmem)
+    if (factor_smem_bytes(L.smax, L.wmax, L.lmax) > (size_t)kFactorMaxSmem)
         throw HsError{HS_ERR_UNSUPPORTED};
     Trace tr;
     tr.mark("  records");
@@ -1477,8 +1477,12 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     tr.mark("pattern+partition");
 
     if (h->opt.rank_model) {
-        h->d_model.alloc(sizeof(float) * kModelFloats);
-        CK(cudaMemcpyAsync(h->d_model.p, h->opt.rank_model, sizeof(float) * kModelFloats, cudaMemcpyHostToDevice, st));
+        // the caller's layout, then W2 transposed for the factor kernel
+        std::vector<float> mdl(h->opt.rank_model, h->opt.rank_model + kModelFloats);
+        const float* W2 = h->opt.rank_model + 2 * kMlpIn + kMlpHidden * kMlpIn + kMlpHidden;
+        for (int k = 0; k < kMlpHidden; k++)
+            for (int j = 0; j < kMlpHidden; j++) mdl.push_back(W2[j * kMlpHidden + k]);
+        upload(h->d_model, mdl, st);
     }
     // device copies of A (SpMV) and of the permutation
     h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));

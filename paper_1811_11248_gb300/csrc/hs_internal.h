@@ -183,7 +183,7 @@ cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double*
 cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv,
                           const double* w, double* partial, double* out);
 
-size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32 = false, bool xsh = false);
+size_t factor_smem_bytes(int smax, int wmax, int lmax, bool xsh = false);
 // coarse levels: all phases of a level in one single-CTA launch (warp per task)
 constexpr int kFusedWarps = 16, kFusedSmax = 32;
 size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap);

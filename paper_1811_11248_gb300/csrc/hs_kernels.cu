@@ -138,6 +138,7 @@ struct CtaGroup {
     __device__ double sum(double v, double* red) const { return block_sum(v, red); }
     __device__ double max(double v, double* red) const { return block_max(v, red); }
     __device__ int minint(int v, double* red) const { return block_min_int(v, reinterpret_cast<int*>(red)); }
+    __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
 };
 struct WarpGroup {
     int rank, size;
@@ -146,6 +147,11 @@ struct WarpGroup {
     __device__ double sum(double v, double*) const { return warp_sum(v); }
     __device__ double max(double v, double*) const { return warp_max(v); }
     __device__ int minint(int v, double*) const { return warp_min_int(v); }
+    // a barrier (with memory ordering, as sync) that also votes
+    __device__ bool any(bool p) const {
+        __syncwarp();
+        return __any_sync(0xffffffffu, p) != 0;
+    }
 };
 
 // Per list entry of a cluster's row: block offsets / leading dimensions of
@@ -180,6 +186,25 @@ __device__ __forceinline__ double rcp_newton(double x) {
     y = fma(y, h, y);
     h = fma(-x, y, 1.0);
     return fma(y, h, y);
+}
+
+// |a| as a float from the bit pattern alone (integer operations only, so the
+// FP64 pipe is not used): the exponent rebiased and the top 20 mantissa bits
+// kept, a relative error below 2^-20; magnitudes below 2^-126 give 0 and
+// magnitudes above 2^63 (with infinities and NaN) give 2^63.  For the rank
+// features, where a squared norm to six digits is plenty.
+__device__ __forceinline__ float approx_abs_float(double a) {
+    const int hi = __double2hiint(a);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    if (e < -126) return 0.f;
+    if (e > 63) return 9.223372e18f;
+    return __int_as_float(((e + 127) << 23) | ((hi & 0xfffff) << 3));
+}
+
+// |a| as its bit pattern: for non-negative doubles the integer order is the
+// numeric order, so maxima of magnitudes need no FP64 instruction.
+__device__ __forceinline__ long long abs_bits(double a) {
+    return __double_as_longlong(a) & 0x7fffffffffffffffLL;
 }
 
 // In-place FP64 -> FP32 conversion of count elements by the group: float i
@@ -339,33 +364,51 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
 
 // Rank predictor inside a factor task: y = w3 . relu(W2 relu(W1 xn + b1) + b2)
 // + b3 on the standardised features xn = (f - mu) / sd.  model: mu (8), sd
-// (8), then the network's parameter vector (kMlpParams floats, the layout of
-// the training kernels).  h: 64 floats of scratch.  Every thread returns y.
+// (8), the network's parameter vector (kMlpParams floats, the layout of the
+// training kernels), then W2 transposed (so that neighbouring threads read
+// neighbouring floats).  f: the 8 features, standardised in place; h: 64
+// floats; part: kPredChunks * 64 floats.  The 64 x 64 layer is split over
+// the group in kPredChunks slices of the inner index (each thread's loads
+// independent of one another), then summed per output.  Every thread
+// returns y.
+constexpr int kPredChunks = 8;
 template <typename Grp>
-__device__ float predict_fraction(const Grp& g, const float* __restrict__ model, const float* f, float* h,
+__device__ float predict_fraction(const Grp& g, const float* __restrict__ model, float* f, float* h, float* part,
                                   double* red) {
     const float* mu = model;
     const float* sd = model + kMlpIn;
-    const float* th = model + 2 * kMlpIn;
-    const float* W1 = th;
+    const float* W1 = model + 2 * kMlpIn;
     const float* b1 = W1 + kMlpHidden * kMlpIn;
-    const float* W2 = b1 + kMlpHidden;
-    const float* b2 = W2 + kMlpHidden * kMlpHidden;
+    const float* b2 = b1 + kMlpHidden + kMlpHidden * kMlpHidden;
     const float* w3 = b2 + kMlpHidden;
     const float b3 = w3[kMlpHidden];
+    const float* W2t = model + kModelFloats;
+    if (g.rank < kMlpIn) f[g.rank] = (f[g.rank] - mu[g.rank]) / sd[g.rank];
+    g.sync();
     for (int j = g.rank; j < kMlpHidden; j += g.size) {
         float a = b1[j];
-        for (int i = 0; i < kMlpIn; i++) a += W1[j * kMlpIn + i] * ((f[i] - mu[i]) / sd[i]);
+#pragma unroll
+        for (int i = 0; i < kMlpIn; i++) a += W1[j * kMlpIn + i] * f[i];
         h[j] = a > 0.f ? a : 0.f;
     }
     g.sync();
-    double part = 0.0;
+    constexpr int kSlice = kMlpHidden / kPredChunks;
+    for (int t = g.rank; t < kMlpHidden * kPredChunks; t += g.size) {
+        const int j = t % kMlpHidden, k0 = (t / kMlpHidden) * kSlice;
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSlice; k++) a += W2t[(k0 + k) * kMlpHidden + j] * h[k0 + k];
+        part[t] = a;
+    }
+    g.sync();
+    double out = 0.0;
     for (int j = g.rank; j < kMlpHidden; j += g.size) {
         float a = b2[j];
-        for (int k = 0; k < kMlpHidden; k++) a += W2[j * kMlpHidden + k] * h[k];
-        part += (double)(w3[j] * (a > 0.f ? a : 0.f));
+#pragma unroll
+        for (int c = 0; c < kPredChunks; c++) a += part[c * kMlpHidden + j];
+        out += (double)(w3[j] * (a > 0.f ? a : 0.f));
     }
-    return (float)(g.sum(part, red) + (double)b3);
+    return (float)(g.sum(out, red) + (double)b3);
 }
 
 // One scaled low-rank elimination (Sec. 3.1) by the group g.  Shared memory
@@ -384,7 +427,10 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                             int32_t level, float* fe, const float* __restrict__ model, float* G32, double* Xsh) {
     const int s = T.s, tid = g.rank, NT = g.size;
     const int L = T.nn + T.nw;
-    const bool want_feat = fe != nullptr || model != nullptr;
+    // features for the caller's record, or for the predictor (mixed form,
+    // where the speculation has room for its FP32 copy of G)
+    const bool use_model = model != nullptr && G32 != nullptr && sizeof(FT) == sizeof(float);
+    const bool want_feat = fe != nullptr || use_model;
     // entry metadata (one round of loads for all entries), then the column
     // offsets of the row blocks (compact, current widths)
     for (int e = tid; e < L; e += NT) {
@@ -409,18 +455,18 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         *s_flag = 0;
     }
     // A_ss -> shared memory
-    double amax_ss = 0.0;  // largest |A_ss| off the diagonal (features only)
+    long long amax_ss_bits = 0;  // largest |A_ss| off the diagonal (features only)
     {
         const double* A = blocks + blk_off[T.diag_blk];
         const int ld = blk_ld[T.diag_blk];
         for (int idx = tid; idx < s * s; idx += NT) {
             const double a = A[(int64_t)(idx / s) * ld + idx % s];
             G[idx] = a;
-            if (want_feat && idx / s != idx % s) amax_ss = fmax(amax_ss, fabs(a));
+            if (want_feat && idx / s != idx % s) amax_ss_bits = max(amax_ss_bits, abs_bits(a));
         }
     }
     g.sync();
-    if (want_feat) amax_ss = g.max(amax_ss, red);
+    const double amax_ss = want_feat ? g.max(__longlong_as_double(amax_ss_bits), red) : 0.0;
     const int W = ioff[L], ncols = ioff[T.nn], Wn = W - ncols;
 
     // Cholesky A_ss = G G^T and X = G^-1 together, right-looking, one column
@@ -513,6 +559,9 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             colsrc[2 * (ioff[e] + j)] = em[e].cq + j;
             colsrc[2 * (ioff[e] + j) + 1] = em[e].ldcq;
         }
+    float* rdf = reinterpret_cast<float*>(v);  // D^-1 as floats, for the features
+    if (want_feat)
+        for (int i = tid; i < s; i += NT) rdf[i] = approx_abs_float(rdiag[i]);
     g.sync();
     // pass 1, one thread per column of [A_sn | A_sw]: stream the column from
     // the blocks (loads in groups of kGatherBatch, all in flight before they
@@ -522,7 +571,13 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     // finished here; a denser one is forward-substituted in pass 2.
     constexpr int kGatherBatch = 8;
     unsigned char* dense = reinterpret_cast<unsigned char*>(cn);  // per column (W bytes)
-    double amax_row = 0.0, lt = 0.0, lm = 0.0;  // features: max |a|, norms of D^-1 A_sw
+    // features (integer and FP32 operations only): max |a|, norms of D^-1 A_sw;
+    // a sparse column contributes its few nonzeros here, a dense one once the
+    // features are known to be wanted (its values stay in the block row
+    // until pass 2)
+    long long amax_bits = 0;
+    float lt = 0.f, lm = 0.f;
+    bool dense_fill = false;  // this thread met a dense fill column
     for (int j = tid; j < W; j += NT) {
         const int64_t src = colsrc[2 * j], ldc = colsrc[2 * j + 1];
         const bool fill = j >= ncols;
@@ -531,7 +586,6 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         double rv[kSparseNz];
 #pragma unroll
         for (int k = 0; k < kSparseNz; k++) { ri[k] = 0; rv[k] = 0.0; }
-        double cj = 0.0;
         for (int b = 0; b < s; b += kGatherBatch) {
             double a[kGatherBatch];
 #pragma unroll
@@ -541,13 +595,6 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                 const int i = b + u;
                 if (i >= s) break;
                 M[(int64_t)i * Wt + j] = a[u];
-                if (want_feat) {
-                    amax_row = fmax(amax_row, fabs(a[u]));  // FP64 max: only for the features
-                }
-                if (want_feat && fill) {
-                    const double x = a[u] * rdiag[i];
-                    cj = fma(x, x, cj);
-                }
                 if ((__double_as_longlong(a[u]) << 1) != 0) {  // nonzero (either sign of zero is zero)
                     if (nz == 0) i0 = i;
 #pragma unroll
@@ -557,12 +604,23 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                 }
             }
         }
-        if (want_feat && fill) {
-            lt += cj;
-            lm = fmax(lm, cj);
-        }
         const bool sparse = nz <= kSparseNz && 2 * nz <= s - i0;
         dense[j] = sparse ? 0 : 1;
+        dense_fill |= fill && !sparse;
+        if (want_feat && sparse) {
+            float cj = 0.f;
+#pragma unroll
+            for (int k = 0; k < kSparseNz; k++)
+                if (k < nz) {
+                    amax_bits = max(amax_bits, abs_bits(rv[k]));
+                    const float x = approx_abs_float(rv[k]) * rdf[ri[k]];
+                    cj = fmaf(x, x, cj);
+                }
+            if (fill) {
+                lt += cj;
+                lm = fmaxf(lm, cj);
+            }
+        }
         if (sparse)
             for (int r = i0; r < s; r++) {
                 double x = 0.0;
@@ -574,25 +632,43 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     }
     if (Xsh)  // the identity columns become G^-1
         for (int idx = tid; idx < s * s; idx += NT) M[(int64_t)(idx / s) * Wt + W + idx % s] = Xsh[idx];
-    g.sync();
+    // the predictor runs only where dense fill columns leave FP64 work to
+    // spare, and where the space of G^-1 holds its scratch (s >= 16)
+    const bool predict = use_model && Wn > 0 && s >= 16 ? g.any(dense_fill) : (g.sync(), false);
     // features of the block row (the column table is free from here on):
     // structure, the coupling ratio, and the fill block scaled by the
     // Cholesky diagonal, D^-1 A_sw (D = diag G), known before the scaling
     float* fsh = reinterpret_cast<float*>(colsrc);  // 8 features, then 64 floats of scratch
-    if (want_feat) {
-        amax_row = g.max(amax_row, red);
-        const double total = g.sum(lt, red), cmax = g.max(lm, red);
-        if (tid == 0) {
-            const double e = eps2 > 0.0 ? sqrt(eps2) : 1e-300;
+    if (fe || predict) {
+        for (int j = tid; j < W; j += NT) {
+            if (!dense[j]) continue;
+            float cj = 0.f;
+            for (int i = 0; i < s; i++) {
+                const double a = M[(int64_t)i * Wt + j];
+                amax_bits = max(amax_bits, abs_bits(a));
+                const float x = approx_abs_float(a) * rdf[i];
+                cj = fmaf(x, x, cj);
+            }
+            if (j >= ncols) {
+                lt += cj;
+                lm = fmaxf(lm, cj);
+            }
+        }
+        const double amax_row = g.max(__longlong_as_double(amax_bits), red);
+        const double total = g.sum((double)lt, red), cmax = g.max((double)lm, red);
+        if (tid == 0) {  // FP32 logarithms (the features are FP32)
+            const float le = 0.5f * log10f(eps2 > 0.0 ? (float)eps2 : 1e-38f);  // log10 eps
+            const float lr = log10f(fminf(fmaxf((float)amax_ss, 1e-37f), 1e37f)) -
+                             log10f(fminf(fmaxf((float)amax_row, 1e-37f), 1e37f));
             fsh[0] = (float)s;
             fsh[1] = (float)ncols;
             fsh[2] = (float)Wn;
             fsh[3] = (float)level;
             fsh[4] = (float)L;
-            fsh[5] = Wn > 0 ? (float)fmax(log10(fmax(sqrt(total), 1e-300) / e), -30.0) : -30.f;
+            fsh[5] = Wn > 0 && total > 0.0 ? fmaxf(0.5f * log10f((float)total) - le, -30.f) : -30.f;
             // coupling inside the cluster against coupling to its neighbours
-            fsh[6] = (float)fmin(fmax(log10(fmax(amax_ss, 1e-300) / fmax(amax_row, 1e-300)), -30.0), 30.0);
-            fsh[7] = Wn > 0 ? (float)fmax(log10(fmax(sqrt(cmax), 1e-300) / e), -30.0) : -30.f;
+            fsh[6] = fminf(fmaxf(lr, -30.f), 30.f);
+            fsh[7] = Wn > 0 && cmax > 0.0 ? fmaxf(0.5f * log10f((float)cmax) - le, -30.f) : -30.f;
         }
         g.sync();
         if (fe && tid < kFeat) fe[tid] = fsh[tid];
@@ -603,8 +679,8 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     // are gathered again and scaled in FP64 and the column-pivoted QR decides
     // as usual
     bool spec0 = false;
-    if (model && G32 && sizeof(FT) == sizeof(float) && Wn > 0) {
-        const float y = predict_fraction(g, model, fsh, fsh + kFeat, red);
+    if (predict) {
+        const float y = predict_fraction(g, model, fsh, fsh + kFeat, G32, red);
         spec0 = y * (float)s < 0.5f;
         if (spec0)
             for (int idx = tid; idx < s * s; idx += NT) G32[idx] = (float)G[idx];
@@ -637,14 +713,22 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     bool rank0 = false;
     if (spec0) {
         const float* Mf = reinterpret_cast<const float*>(M);
-        double lt = 0.0;
-        for (int j = tid; j < Wn; j += NT)
-            for (int i = 0; i < s; i++) {
-                const int64_t o = (int64_t)i * Wt + ncols + j;
-                const double x = dense[ncols + j] ? (double)Mf[2 * o] : M[o];
-                lt += x * x;
+        double ld = 0.0;  // sparse fill columns (FP64 values)
+        float lf = 0.f;   // dense fill columns (FP32 values, summed in FP32)
+        for (int j = tid; j < Wn; j += NT) {
+            if (dense[ncols + j]) {
+                for (int i = 0; i < s; i++) {
+                    const float x = Mf[2 * ((int64_t)i * Wt + ncols + j)];
+                    lf = fmaf(x, x, lf);
+                }
+            } else {
+                for (int i = 0; i < s; i++) {
+                    const double x = M[(int64_t)i * Wt + ncols + j];
+                    ld = fma(x, x, ld);
+                }
             }
-        rank0 = g.sum(lt, red) <= 0.5 * eps2;
+        }
+        rank0 = g.sum(ld + (double)lf, red) <= 0.5 * eps2;
         if (!rank0) {
             // fallback: the fill columns again from the blocks, scaled in FP64
             for (int e = T.nn + tid; e < L; e += NT)
@@ -709,11 +793,13 @@ k_factor_phase(const TaskDev* __restrict__ tasks, int t0, const ListDev* __restr
     EntryMeta* em = reinterpret_cast<EntryMeta*>(red + 64);
     int64_t* colsrc = reinterpret_cast<int64_t*>(em + lmax);
     int* ioff = reinterpret_cast<int*>(colsrc + 2 * (size_t)wmax);
-    // G^-1 (smax x smax doubles), then the FP32 copy of G for the learned
-    // rank-0 speculation (only with a model)
+    // G^-1 (smax x smax doubles) when it fits; the FP32 copy of G for the
+    // learned rank-0 speculation (only with a model) reuses that space, free
+    // once pass 1 has moved G^-1 into the block row; without it, no
+    // speculation (so a model never costs occupancy)
     double* x0 = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(ioff + lmax + 2) + 15) & ~uintptr_t(15));
     double* Xsh = use_x ? x0 : nullptr;
-    float* G32 = model ? reinterpret_cast<float*>(x0 + (use_x ? (size_t)smax * smax : 0)) : nullptr;
+    float* G32 = model && use_x ? reinterpret_cast<float*>(x0) : nullptr;
     CtaGroup g;
     factor_task<FT>(T, g, G, rdiag, v, cn, red, ioff, &s_flag, s_hh, nullptr, em, colsrc, lists, blocks, blk_off,
                     blk_ld, cur, fac, meta, ws, eps2, status, level,
@@ -1762,13 +1848,12 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
     return cudaGetLastError();
 }
 
-size_t factor_smem_bytes(int smax, int wmax, int lmax, bool g32, bool xsh) {
+size_t factor_smem_bytes(int smax, int wmax, int lmax, bool xsh) {
     const size_t base = sizeof(double) * ((size_t)smax * smax + 2 * (size_t)smax + (size_t)wmax + 64) +
                         sizeof(EntryMeta) * (size_t)lmax + 2 * sizeof(int64_t) * (size_t)wmax +
                         sizeof(int) * ((size_t)lmax + 2);
-    // then G^-1 (doubles) and, with a rank model, an FP32 copy of G
-    return (base + 15) / 16 * 16 + (xsh ? sizeof(double) * (size_t)smax * smax : 0) +
-           (g32 ? sizeof(float) * (size_t)smax * smax : 0);
+    // then G^-1 (doubles)
+    return (base + 15) / 16 * 16 + (xsh ? sizeof(double) * (size_t)smax * smax : 0);
 }
 
 template <typename FT>
@@ -1777,8 +1862,8 @@ cudaError_t factor_phase_t(cudaStream_t st, const TaskDev* tasks, int t0, int nt
                            int32_t* cur, FT* fac, int32_t* meta, double* ws, double eps2, int32_t* status,
                            int32_t level, float* feat, const float* model) {
     // G^-1 in shared memory when it fits beside the rest
-    const int use_x = factor_smem_bytes(smax, wmax, lmax, model != nullptr, true) <= (size_t)kFactorMaxSmem;
-    const size_t smem = factor_smem_bytes(smax, wmax, lmax, model != nullptr, use_x);
+    const int use_x = factor_smem_bytes(smax, wmax, lmax, true) <= (size_t)kFactorMaxSmem;
+    const size_t smem = factor_smem_bytes(smax, wmax, lmax, use_x);
     int dev = 0, sms = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
