@@ -581,10 +581,15 @@ struct LevelPlan {
 // Phase rule and fill pattern (Sec. 3.2, Sec. 4.2) of the clusters lo .. hi,
 // which share no block with any other cluster: phases are rounds of a greedy
 // maximal independent set in ascending cluster order on the current block
-// graph; eliminating c couples every pair of its neighbours.
+// graph; eliminating c couples every pair of its neighbours.  The selection
+// is sequential; the eliminations of one phase are applied in parallel: the
+// selected clusters are pairwise non-adjacent, so each one's neighbour lists
+// are final when the phase starts, and a neighbour p that several of them
+// share receives the union of their couplings (set unions, so the order in
+// which they land does not matter).
 void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi,
                 std::vector<std::vector<int>>& phases) {
-    std::vector<char> done(hi - lo, 0), insel(hi - lo, 0);
+    std::vector<char> done(hi - lo, 0), insel(hi - lo, 0), target(hi - lo, 0);
     auto D = [&](int c) -> char& { return done[c - lo]; };
     auto S = [&](int c) -> char& { return insel[c - lo]; };
     int remaining = 0;
@@ -593,7 +598,19 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
         else D(c) = 1;
     }
     int first = lo;  // clusters below `first` are all done
-    std::vector<int> merged;
+    // v <- v u (add \ {p}), both sorted
+    auto merge_into = [](std::vector<int>& v, const std::vector<int>& add, int p, std::vector<int>& tmp) {
+        tmp.clear();
+        auto a = v.begin(), ae = v.end();
+        auto b = add.begin(), be = add.end();
+        while (a != ae || b != be) {
+            if (b != be && *b == p) { ++b; continue; }  // p does not gain itself
+            if (b == be || (a != ae && *a < *b)) tmp.push_back(*a++);
+            else if (a == ae || *b < *a) tmp.push_back(*b++);
+            else { tmp.push_back(*a++); ++b; }
+        }
+        v.swap(tmp);
+    };
     while (remaining > 0) {
         std::vector<int> sel;
         while (first < hi && D(first)) first++;
@@ -605,35 +622,44 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
             if (ok) { S(c) = 1; sel.push_back(c); }
         }
         const int ph = (int)phases.size();
-        for (int c : sel) {
-            auto& nlc = P.nl[c];
-            auto& wlc = P.wl[c];
-            for (int q : cur[c]) (sorted_has(P.adj0[c], q) ? nlc : wlc).push_back(q);
-            // every neighbour p gains all the others (sorted merges)
-            for (int p : nlc) {
-                for (auto* v : {&cur[p], &P.all[p]}) {
-                    merged.clear();
-                    auto a = v->begin(), ae = v->end();
-                    auto b = nlc.begin(), be = nlc.end();
-                    while (a != ae || b != be) {
-                        if (b != be && *b == p) { ++b; continue; }  // p does not gain itself
-                        if (b == be || (a != ae && *a < *b)) merged.push_back(*a++);
-                        else if (a == ae || *b < *a) merged.push_back(*b++);
-                        else { merged.push_back(*a++); ++b; }
-                    }
-                    v->swap(merged);
+        const int64_t ns = (int64_t)sel.size();
+        // each selected cluster: neighbours in the level's input pattern (n)
+        // and fill neighbours (w); without fill it vanishes from the graph
+        parallel_ranges(ns, 512, [&](int64_t a, int64_t b, int) {
+            for (int64_t i = a; i < b; i++) {
+                const int c = sel[i];
+                for (int q : cur[c]) (sorted_has(P.adj0[c], q) ? P.nl[c] : P.wl[c]).push_back(q);
+                if (P.wl[c].empty()) P.vanished[c] = 1;
+            }
+        });
+        // the clusters that gain couplings, each listed once
+        const std::vector<int> tg = parallel_collect<int>(ns, 512, [&](int64_t i, std::vector<int>& out) {
+            for (int p : P.nl[sel[i]])
+                if (!__atomic_exchange_n(&target[p - lo], (char)1, __ATOMIC_RELAXED)) out.push_back(p);
+        });
+        parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
+            std::vector<int> src, tmp;
+            for (int64_t i = a; i < b; i++) {
+                const int p = tg[i];
+                src.clear();
+                for (int c : cur[p])  // selected neighbours that couple p to the others
+                    if (S(c) && sorted_has(P.nl[c], p)) src.push_back(c);
+                for (int c : src) {
+                    merge_into(cur[p], P.nl[c], p, tmp);
+                    merge_into(P.all[p], P.nl[c], p, tmp);
                 }
+                for (int c : src)
+                    if (P.vanished[c]) sorted_erase(cur[p], c);
+                target[p - lo] = 0;
             }
-            if (wlc.empty()) {
-                P.vanished[c] = 1;
-                for (int q : cur[c]) sorted_erase(cur[q], c);
-                cur[c].clear();
-            }
+        });
+        for (int c : sel) {
+            if (P.vanished[c]) cur[c].clear();
             D(c) = 1;
             S(c) = 0;
             P.phase[c] = ph;
-            remaining--;
         }
+        remaining -= (int)ns;
         phases.push_back(std::move(sel));
     }
     for (int c = lo; c < hi; c++) {
