@@ -378,19 +378,17 @@ struct Partitioner {
         return out;
     }
 
-    // leaf ids follow the depth-first order: the leaf below `set` at depth
-    // `depth` starts at `base` and the left half owns the first 2^(L-depth-1)
-    void split(std::vector<int> set, int depth, int base = 0) {
-        if (depth == L) {
-            for (int x : set) leaf_of[x] = base;
-            return;
-        }
+    // One bisection of `set` (ascending): with coordinates the left part is
+    // the ceil(k/2) smallest lines in (coordinate, index) order along the
+    // longer extent, else the first ceil(k/2) lines of a BFS order started
+    // from a pseudo-peripheral line; both parts come out ascending.  Only the
+    // coordinate rule runs on several sets at once (the BFS reads the marks
+    // of neighbouring lines, which may belong to another set).
+    void bisect(const std::vector<int>& set, std::vector<int>& a, std::vector<int>& b) {
         const size_t k = set.size(), left = (k + 1) / 2;
-        std::vector<int> a, b;
+        a.clear();
+        b.clear();
         if (have_coords) {
-            // the left part is the ceil(k/2) smallest lines in (coordinate,
-            // index) order along the longer extent; `set` is ascending and
-            // both parts stay ascending
             double x0 = lx[set[0]], x1 = x0, y0 = ly[set[0]], y1 = y0;
             for (int x : set) {
                 x0 = std::min(x0, lx[x]); x1 = std::max(x1, lx[x]);
@@ -407,14 +405,29 @@ struct Partitioner {
         } else {
             const int lo = *std::min_element(set.begin(), set.end());
             std::vector<int> first = bfs(set, lo);
-            set = bfs(set, first.back());
-            a.assign(set.begin(), set.begin() + left);
-            b.assign(set.begin() + left, set.end());
+            std::vector<int> order = bfs(set, first.back());
+            a.assign(order.begin(), order.begin() + left);
+            b.assign(order.begin() + left, order.end());
             std::sort(a.begin(), a.end());
             std::sort(b.begin(), b.end());
         }
+    }
+
+    // Leaf ids follow the depth-first order: the left half of the set below
+    // leaf offset `base` at depth d keeps `base`, the right half starts
+    // 2^(L-d-1) further.  Depth-first recursion, the top on two threads with
+    // coordinates.
+    void split(std::vector<int> set, int depth, int base) {
+        if (depth == L) {
+            for (int x : set) leaf_of[x] = base;
+            return;
+        }
+        std::vector<int> a, b;
+        bisect(set, a, b);
+        const size_t k = set.size();
+        std::vector<int>().swap(set);
         const int half = 1 << (L - depth - 1);
-        if (have_coords && depth < 3 && k > 4096 && !tl_serial) {  // top of the tree on two threads
+        if (have_coords && depth < 3 && k > 4096 && !tl_serial) {
             run_threads(2, [&](int t) {
                 if (t == 1) split(std::move(a), depth + 1, base);
                 else split(std::move(b), depth + 1, base + half);
@@ -423,6 +436,37 @@ struct Partitioner {
             split(std::move(a), depth + 1, base);
             split(std::move(b), depth + 1, base + half);
         }
+    }
+
+    // The same leaves; for many lines with coordinates, in L rounds with all
+    // sets of a round bisected in parallel.
+    void split_all(std::vector<int> all) {
+        if (!(have_coords && nl > (1 << 15) && !tl_serial)) {
+            split(std::move(all), 0, 0);
+            return;
+        }
+        std::vector<std::vector<int>> sets(1), next;
+        sets[0] = std::move(all);
+        std::vector<int> base(1, 0), nbase;
+        for (int depth = 0; depth < L; depth++) {
+            const int ns = (int)sets.size(), half = 1 << (L - depth - 1);
+            next.assign(2 * (size_t)ns, {});
+            nbase.assign(2 * (size_t)ns, 0);
+            parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
+                for (int64_t i = lo; i < hi; i++) {
+                    bisect(sets[i], next[2 * i], next[2 * i + 1]);
+                    nbase[2 * i] = base[i];
+                    nbase[2 * i + 1] = base[i] + half;
+                    std::vector<int>().swap(sets[i]);
+                }
+            });
+            sets.swap(next);
+            base.swap(nbase);
+        }
+        parallel_ranges((int64_t)sets.size(), 64, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t i = lo; i < hi; i++)
+                for (int x : sets[i]) leaf_of[x] = base[i];
+        });
     }
 };
 
@@ -474,13 +518,45 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     tr.mark("  partition: union-find");
     Partitioner P;
     std::vector<int> line_of(n), first;
-    {
+    if (n <= (1 << 18) || tl_serial) {
         std::vector<int> id(n, -1);
         for (int i = 0; i < n; i++) {
             const int r = find(i);  // roots are final: no link is running
             if (id[r] < 0) { id[r] = (int)first.size(); first.push_back(i); }
             line_of[i] = id[r];
         }
+    } else {
+        // every root is the smallest DOF of its line, so numbering the roots
+        // in ascending order numbers the lines by their first DOF: chunk
+        // counts of roots, a prefix sum, then the ids (roots are final)
+        constexpr int nchunk = 64;
+        std::vector<int> rc(nchunk + 1, 0);
+        auto is_root = [&](int64_t i) { return root[i].load(std::memory_order_relaxed) == (int)i; };
+        parallel_ranges(nchunk, 1, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t ch = lo; ch < hi; ch++) {
+                int k = 0;
+                for (int64_t i = n * ch / nchunk; i < n * (ch + 1) / nchunk; i++) k += is_root(i);
+                rc[ch + 1] = k;
+            }
+        });
+        for (int ch = 0; ch < nchunk; ch++) rc[ch + 1] += rc[ch];
+        first.resize(rc[nchunk]);
+        parallel_ranges(nchunk, 1, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t ch = lo; ch < hi; ch++) {
+                int id = rc[ch];
+                for (int64_t i = n * ch / nchunk; i < n * (ch + 1) / nchunk; i++)
+                    if (is_root(i)) {
+                        first[id] = (int)i;
+                        line_of[i] = id++;
+                    }
+            }
+        });
+        parallel_ranges(n, 1 << 16, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t i = lo; i < hi; i++) {
+                const int r = find((int)i);
+                if (r != i) line_of[i] = line_of[r];
+            }
+        });
     }
     P.nl = (int)first.size();
     tr.mark("  partition: line ids");
@@ -551,15 +627,46 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     P.state.assign(P.nl, 0);
     std::vector<int> all(P.nl);
     for (int l = 0; l < P.nl; l++) all[l] = l;
-    P.split(std::move(all), 0, 0);
+    P.split_all(std::move(all));
     tr.mark("  partition: bisection");
+    // DOFs grouped by leaf, ascending within a leaf (a counting sort; for
+    // many DOFs over contiguous chunks: counts per leaf and chunk, offsets
+    // leaf by leaf with the chunks in order, then every chunk places its DOFs)
     const int nleaf = 1 << L;
+    const int nch = tl_serial ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / 65536));
     leaf_ptr.assign(nleaf + 1, 0);
-    for (int i = 0; i < n; i++) leaf_ptr[P.leaf_of[line_of[i]] + 1]++;
-    for (int c = 0; c < nleaf; c++) leaf_ptr[c + 1] += leaf_ptr[c];
-    std::vector<int32_t> pos(leaf_ptr.begin(), leaf_ptr.end() - 1);
     perm.assign(n, 0);
-    for (int i = 0; i < n; i++) perm[pos[P.leaf_of[line_of[i]]]++] = i;
+    if (nch == 1) {
+        for (int i = 0; i < n; i++) leaf_ptr[P.leaf_of[line_of[i]] + 1]++;
+        for (int c = 0; c < nleaf; c++) leaf_ptr[c + 1] += leaf_ptr[c];
+        std::vector<int32_t> pos(leaf_ptr.begin(), leaf_ptr.end() - 1);
+        for (int i = 0; i < n; i++) perm[pos[P.leaf_of[line_of[i]]]++] = i;
+    } else {
+        std::vector<int> leaf_dof(n);
+        std::vector<int32_t> cnt((size_t)nleaf * nch, 0);  // [leaf][chunk]
+        parallel_ranges(nch, 1, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t ch = lo; ch < hi; ch++)
+                for (int64_t i = (int64_t)n * ch / nch; i < (int64_t)n * (ch + 1) / nch; i++) {
+                    leaf_dof[i] = P.leaf_of[line_of[i]];
+                    cnt[(size_t)leaf_dof[i] * nch + ch]++;
+                }
+        });
+        int32_t run = 0;
+        for (int c = 0; c < nleaf; c++) {
+            for (int ch = 0; ch < nch; ch++) {
+                const int32_t k = cnt[(size_t)c * nch + ch];
+                cnt[(size_t)c * nch + ch] = run;
+                run += k;
+            }
+            leaf_ptr[c + 1] = run;
+        }
+        parallel_ranges(nch, 1, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t ch = lo; ch < hi; ch++)
+                for (int64_t i = (int64_t)n * ch / nch; i < (int64_t)n * (ch + 1) / nch; i++)
+                    perm[cnt[(size_t)leaf_dof[i] * nch + ch]++] = (int32_t)i;
+        });
+    }
+    tr.mark("  partition: permutation");
     return HS_OK;
 }
 
@@ -589,9 +696,12 @@ struct LevelPlan {
 // which they land does not matter).
 void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi,
                 std::vector<std::vector<int>>& phases) {
-    std::vector<char> done(hi - lo, 0), insel(hi - lo, 0), target(hi - lo, 0);
+    std::vector<char> done(hi - lo, 0), insel(hi - lo, 0), target(hi - lo, 0), blocked(hi - lo, 0);
     auto D = [&](int c) -> char& { return done[c - lo]; };
     auto S = [&](int c) -> char& { return insel[c - lo]; };
+    auto B = [&](int c) -> char& { return blocked[c - lo]; };  // has a selected neighbour
+    auto T = [&](int c) -> char& { return target[c - lo]; };   // gains couplings in this phase
+    std::vector<int> tg, scratch;
     int remaining = 0;
     for (int c = lo; c < hi; c++) {
         if (P.size0[c] > 0) remaining++;
@@ -614,46 +724,63 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
     while (remaining > 0) {
         std::vector<int> sel;
         while (first < hi && D(first)) first++;
+        // each selected cluster: neighbours in the level's input pattern (n)
+        // and fill neighbours (w), and without fill it vanishes from the
+        // graph; tg: the clusters that gain couplings, each listed once
+        tg.clear();
+        int64_t work = 0;  // size of the list merges ahead, roughly
         for (int c = first; c < hi; c++) {
-            if (D(c)) continue;
-            bool ok = true;
-            for (int q : cur[c])
-                if (S(q)) { ok = false; break; }
-            if (ok) { S(c) = 1; sel.push_back(c); }
+            if (D(c) || B(c)) continue;
+            S(c) = 1;
+            sel.push_back(c);
+            const auto& a0 = P.adj0[c];
+            size_t k = 0;  // merge-walk of cur[c] against adj0[c] (both sorted)
+            for (int q : cur[c]) {
+                B(q) = 1;  // the block graph is symmetric
+                while (k < a0.size() && a0[k] < q) k++;
+                if (k < a0.size() && a0[k] == q) {
+                    P.nl[c].push_back(q);
+                    if (!T(q)) { T(q) = 1; tg.push_back(q); }
+                } else {
+                    P.wl[c].push_back(q);
+                }
+            }
+            if (P.wl[c].empty()) P.vanished[c] = 1;
+            work += (int64_t)P.nl[c].size() * (int64_t)cur[c].size();
         }
         const int ph = (int)phases.size();
         const int64_t ns = (int64_t)sel.size();
-        // each selected cluster: neighbours in the level's input pattern (n)
-        // and fill neighbours (w); without fill it vanishes from the graph
-        parallel_ranges(ns, 512, [&](int64_t a, int64_t b, int) {
-            for (int64_t i = a; i < b; i++) {
-                const int c = sel[i];
-                for (int q : cur[c]) (sorted_has(P.adj0[c], q) ? P.nl[c] : P.wl[c]).push_back(q);
-                if (P.wl[c].empty()) P.vanished[c] = 1;
+        if (work < (1 << 17) || tl_serial || tl_in_pool) {
+            // a small phase: the eliminations one after another
+            for (int c : sel) {
+                const auto& nlc = P.nl[c];
+                for (int p : nlc) {
+                    merge_into(cur[p], nlc, p, scratch);
+                    merge_into(P.all[p], nlc, p, scratch);
+                }
+                if (P.vanished[c])
+                    for (int q : nlc) sorted_erase(cur[q], c);
             }
-        });
-        // the clusters that gain couplings, each listed once
-        const std::vector<int> tg = parallel_collect<int>(ns, 512, [&](int64_t i, std::vector<int>& out) {
-            for (int p : P.nl[sel[i]])
-                if (!__atomic_exchange_n(&target[p - lo], (char)1, __ATOMIC_RELAXED)) out.push_back(p);
-        });
-        parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
-            std::vector<int> src, tmp;
+            for (int p : tg) T(p) = 0;
+        } else parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
+            std::vector<int> src, tmp, add, tmp2;
             for (int64_t i = a; i < b; i++) {
                 const int p = tg[i];
                 src.clear();
                 for (int c : cur[p])  // selected neighbours that couple p to the others
                     if (S(c) && sorted_has(P.nl[c], p)) src.push_back(c);
-                for (int c : src) {
-                    merge_into(cur[p], P.nl[c], p, tmp);
-                    merge_into(P.all[p], P.nl[c], p, tmp);
-                }
+                // the union of what they bring, then one merge into each list
+                add.clear();
+                for (int c : src) merge_into(add, P.nl[c], p, tmp2);
+                merge_into(cur[p], add, -1, tmp);
+                merge_into(P.all[p], add, -1, tmp);
                 for (int c : src)
                     if (P.vanished[c]) sorted_erase(cur[p], c);
                 target[p - lo] = 0;
             }
         });
         for (int c : sel) {
+            for (int q : cur[c]) B(q) = 0;
             if (P.vanished[c]) cur[c].clear();
             D(c) = 1;
             S(c) = 0;
@@ -684,14 +811,20 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
     std::vector<std::pair<int, int>> rg = ranges;
     if (rg.empty()) rg.push_back({0, nc});
     std::vector<std::vector<std::vector<int>>> ph(rg.size());
+    // the lists start as the input pattern, made by the thread that plans
+    // them (one range: by all threads)
+    auto init = [&](int64_t lo, int64_t hi) {
+        for (int64_t c = lo; c < hi; c++) {
+            cur[c] = P.adj0[c];
+            P.all[c] = P.adj0[c];
+            if (P.size0[c] > 0) sorted_insert(P.all[c], (int)c);
+        }
+    };
+    if (rg.size() == 1) parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) { init(lo, hi); });
     std::atomic<int> next{0};
     auto work = [&] {
         for (int k = next++; k < (int)rg.size(); k = next++) {
-            for (int c = rg[k].first; c < rg[k].second; c++) {
-                cur[c] = P.adj0[c];
-                P.all[c] = P.adj0[c];
-                if (P.size0[c] > 0) sorted_insert(P.all[c], c);
-            }
+            if (rg.size() > 1) init(rg[k].first, rg[k].second);
             plan_range(P, cur, rg[k].first, rg[k].second, ph[k]);
         }
     };
@@ -1449,6 +1582,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         rp = prp;
         cl = pcol;
         vl = b_val ? pval : nullptr;
+        tr.mark("  pattern download");
     }
     const int64_t nnz = rp[n];
     {
@@ -1464,6 +1598,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         });
         if (bad) throw HsError{HS_ERR_ARG};
     }
+    tr.mark("  pattern checks");
 
     // partition tree
     std::vector<int32_t> leaf_ptr;
