@@ -36,7 +36,7 @@ WORKLOAD = "aniso-ice-64x64x16 (N=65536), 1024 leaves x 64 DOF, depth 8, eps 1e-
 NOMINAL_FP64_TFLOPS = 1.25
 # DRAM read + write bytes per k_factor_phase launch of this workload's mixed step: mean of the
 # first three level-0 phase launches in an ncu capture of the current kernel
-FACTOR_TRAFFIC_BYTES = 75.8e6
+FACTOR_TRAFFIC_BYTES = 71.9e6
 
 
 def parse():
