@@ -795,6 +795,20 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
     }
 }
 
+// Frees a plan's per-cluster lists on all threads: they were allocated by
+// the planning threads, and freeing tens of thousands of them from one thread
+// costs milliseconds.
+void release_plan(LevelPlan& P) {
+    const int64_t nc = (int64_t)P.all.size();
+    parallel_ranges(nc, 2048, [&](int64_t lo, int64_t hi, int) {
+        for (int64_t c = lo; c < hi; c++) {
+            for (auto* v : {&P.adj0, &P.nl, &P.wl, &P.all, &P.endp})
+                if (c < (int64_t)v->size()) std::vector<int>().swap((*v)[c]);
+        }
+    });
+    P = LevelPlan{};
+}
+
 // ranges: cluster ranges that share no block (independent problems); each
 // is planned on its own thread and phase k of the level is the union of the
 // ranges' phase k (identical to planning all clusters at once).
@@ -1251,6 +1265,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     DBuf d_targets, d_contribs, d_ws;
     upload(d_targets, targets, st);
     upload(d_contribs, contribs, st);
+    tr.mark("  uploads: records");
     L.d_meta.alloc(sizeof(int32_t) * std::max<int32_t>(meta, 1));
     L.d_fac.alloc((h->fp32 ? sizeof(float) : sizeof(double)) * std::max<int64_t>(fac, 1));
     L.fac_doubles = fac;
@@ -1877,10 +1892,12 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             plan_level(Pn, ranges);
             tr.mark("next-level plan_level");
             BlockTable Tn = make_table(Pn);
+            tr.mark("  make_table");
             DBuf nblocks;
             nblocks.alloc(sizeof(double) * std::max<int64_t>(Tn.total, 1));
             CK(cudaMemsetAsync(nblocks.p, 0, sizeof(double) * std::max<int64_t>(Tn.total, 1), st));
             std::vector<CopyDev> cps = make_assembly(P, fin, T, &Tn, nsize, par, poff, tmat, tpos, tn, false);
+            tr.mark("  make_assembly");
             DBuf d_cps;
             upload(d_cps, cps, st);
             h->prof.begin(KC_ASSEMBLY, st);
@@ -1888,7 +1905,9 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
                                   nblocks.as<double>()));
             h->prof.end(KC_ASSEMBLY, st);
             CK(cudaStreamSynchronize(st));
+            tr.mark("  assembly kernels (sync)");
             blocks = std::move(nblocks);
+            release_plan(P);
             P = std::move(Pn);
             T = std::move(Tn);
         }

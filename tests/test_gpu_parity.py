@@ -218,6 +218,20 @@ def test_full_size_64x64x16_parity(hs, oracle_lib):
     krylov_check(h, ref, p)
 
 
+@pytest.mark.slow
+def test_large_level_planning_parity(hs, oracle_lib):
+    """32,768 leaves of 16 DOFs (320x320x4): the first phases are large enough
+    for the host planner to apply their eliminations to the block graph in
+    parallel.  Phases, sizes and ranks of every level must equal the oracle's,
+    and the operators must agree."""
+    p = inputs.grid_operator(320, 320, 4, ratio=1e4, sigma=1.0, seed=5, bc="ice", shelf=0.5)
+    h, ref, depth = setup_both(hs, oracle_lib, p, 6, 1e-2)
+    check_structure(h, ref, depth)
+    d = operator_diff(h, ref, p.n, nvec=2)
+    assert d <= 1e-8, d
+    h.close()
+
+
 @pytest.mark.parametrize("tol", [1e-2, 1e-4])
 def test_mixed_precision_against_fp64(hs, oracle_lib, tol):
     """Mixed form: FP32 compression (CPQR and its reflectors), FP32 Schur

@@ -53,6 +53,19 @@ def test_partition_matches_oracle(hs, oracle_lib, make, use_coords):
     assert depth == oracle_lib.default_depth(len(lp) - 1)
 
 
+@pytest.mark.parametrize("use_coords", [True, False])
+def test_partition_matches_oracle_large(hs, oracle_lib, use_coords):
+    """409,600 DOFs in 102,400 lines: large enough for the partitioner's
+    parallel line numbering, bisection rounds (with coordinates) and chunked
+    leaf permutation."""
+    p = inputs.grid_operator(320, 320, 4, ratio=1e4, sigma=1.0, seed=5, bc="ice", shelf=0.5)
+    co = np.ascontiguousarray(p.coords) if use_coords else None
+    perm, lp, depth = hs.hs_partition_extruded(p.n, p.rowptr, p.col, p.val, co, 4, 0.5)
+    operm, olp = oracle_lib.partition(p, 4, use_coords=use_coords)
+    assert len(lp) - 1 == 32768
+    assert np.array_equal(perm, operm) and np.array_equal(lp, olp)
+
+
 def test_partition_rejects_bad_arguments(hs):
     p = inputs.grid_operator(4, 4, 2, ratio=10.0)
     with pytest.raises(hs.HsError):
