@@ -1021,7 +1021,7 @@ BlockTable make_table(const LevelPlan& P) {
     T.col.resize(nb);
     T.off.resize(nb);
     T.ld.resize(nb);
-    parallel_ranges(nc, 2048, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) {
         for (int64_t c = lo; c < hi; c++) {
             int64_t o = rowsz[c];
             int b = T.ptr[c];
@@ -1058,8 +1058,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     int32_t meta = 0;
     L.ph_task.assign(1, 0);
     L.ph_target.assign(1, 0);
-    std::vector<TargetDev> targets;
-    std::vector<ContribDev> contribs;
+    DBuf d_targets, d_contribs;
     L.smax = 1; L.wmax = 1; L.lmax = 1; L.nmax = 1;
     // task ti = the ti-th cluster in phase order; sizes first (parallel),
     // then prefix offsets, then the records (parallel)
@@ -1070,7 +1069,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     }
     const int nt = (int)order.size();
     std::vector<int32_t> t_ncap(nt), t_wcap(nt);
-    parallel_ranges(nt, 4096, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nt, 1024, [&](int64_t lo, int64_t hi, int) {
         for (int64_t ti = lo; ti < hi; ti++) {
             const int c = (int)order[ti];
             int ncap = 0, wcap = 0;
@@ -1117,7 +1116,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     }
     tr0.mark("  tasks: sizes and offsets");
     L.lists.resize(list_off[nt]);
-    parallel_ranges(nt, 2048, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nt, 1024, [&](int64_t lo, int64_t hi, int) {
         for (int64_t ti = lo; ti < hi; ti++) {
             TaskDev& t = L.tasks[ti];
             const int c = t.c;
@@ -1199,6 +1198,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             }
         };
         run_threads(nt < 256 ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
+        tr0.mark("  targets: pairs");
         // concatenation in (phase, range) order: offsets first, then the
         // copies item by item in parallel
         std::vector<int64_t> toff(nitems + 1, 0), coff(nitems + 1, 0);
@@ -1209,8 +1209,13 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             }
             L.ph_target.push_back((int)toff[it]);
         }
-        targets.resize(toff[nitems]);
-        contribs.resize(coff[nitems]);
+        // written straight into pinned staging (one area for both) and
+        // copied to the device from there
+        const size_t tb = sizeof(TargetDev) * (size_t)toff[nitems], cb = sizeof(ContribDev) * (size_t)coff[nitems];
+        const size_t tb_al = (tb + 255) & ~(size_t)255;
+        char* pin = g_stage.take(tb_al + cb, st);
+        TargetDev* targets = reinterpret_cast<TargetDev*>(pin);
+        ContribDev* contribs = reinterpret_cast<ContribDev*>(pin + tb_al);
         parallel_ranges(nitems, 8, [&](int64_t lo, int64_t hi, int) {
             for (int64_t it = lo; it < hi; it++) {
                 const int ph = (int)(it / nr), k = (int)(it % nr);
@@ -1221,9 +1226,16 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                     g.c_end += base;
                     targets[o++] = g;
                 }
-                std::copy(rc[k][ph].begin(), rc[k][ph].end(), contribs.begin() + coff[it]);
+                std::copy(rc[k][ph].begin(), rc[k][ph].end(), contribs + coff[it]);
+                // freed here, in parallel (a worker allocated them)
+                std::vector<TargetDev>().swap(rt[k][ph]);
+                std::vector<ContribDev>().swap(rc[k][ph]);
             }
         });
+        d_targets.alloc(std::max<size_t>(tb, 16));
+        d_contribs.alloc(std::max<size_t>(cb, 16));
+        if (tb) CK(cudaMemcpyAsync(d_targets.p, targets, tb, cudaMemcpyHostToDevice, st));
+        if (cb) CK(cudaMemcpyAsync(d_contribs.p, contribs, cb, cudaMemcpyHostToDevice, st));
     }
     tr0.mark("  targets");
     // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
@@ -1262,9 +1274,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
 
     upload(L.d_tasks, L.tasks, st);
     upload(L.d_lists, L.lists, st);
-    DBuf d_targets, d_contribs, d_ws;
-    upload(d_targets, targets, st);
-    upload(d_contribs, contribs, st);
+    DBuf d_ws;
     tr.mark("  uploads: records");
     L.d_meta.alloc(sizeof(int32_t) * std::max<int32_t>(meta, 1));
     L.d_fac.alloc((h->fp32 ? sizeof(float) : sizeof(double)) * std::max<int64_t>(fac, 1));
@@ -1351,7 +1361,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             const int c = L.tasks[ti].c;
             pull_off[ti + 1] = pull_off[ti] + (L.early_ptr[c + 1] - L.early_ptr[c]);
         }
-        parallel_ranges(nt, 2048, [&](int64_t lo, int64_t hi, int) {
+        parallel_ranges(nt, 1024, [&](int64_t lo, int64_t hi, int) {
             for (int64_t ti = lo; ti < hi; ti++) {
                 const TaskDev& t = L.tasks[ti];
                 const int32_t* mt = hmeta.data() + t.meta;
