@@ -277,7 +277,10 @@ int hs_mlp_train(float* params, const float* x, const float* t, int64_t n, const
  * 3 level, 4 blocks in the row, 5 log10 of ||D^-1 A_sw||_F / eps with D the
  * diagonal of the Cholesky factor G, 6 log10 of max |A_ss| off its diagonal
  * over max |[A_sn A_sw]|, 7 log10 of the largest column norm of D^-1 A_sw
- * over eps (5 and 7 are -30 when the cluster has no fill columns). */
+ * over eps (5 and 7 are -30 when the cluster has no fill columns or a zero
+ * fill block, and at least -30 otherwise; 6 is clamped to [-30, 30]).  The
+ * norms are formed in FP32 from the entries' magnitudes truncated to 20
+ * mantissa bits, and the logarithms are FP32. */
 int hs_rank_samples(hs_handle h, float* feat, int32_t* rank, int32_t* size, int64_t* count);
 
 /* Static string for a status code. */
