@@ -122,6 +122,28 @@ int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col,
                           double theta, hs_tree* out);
 int hs_tree_free(hs_tree* t);
 
+/* Phase plan of one level (host only, no device work; the same code the
+ * setup runs).  Input: the level's block graph over nc clusters as CSR
+ * (adj_ptr[nc+1] int64, adj sorted per row, symmetric, no self loops) and
+ * each cluster's size (a cluster of size 0 has no blocks and no phase).
+ * Algorithm 1 eliminates the clusters one at a time in an order it leaves
+ * open; here phases are repeated greedy maximal independent sets (ascending
+ * cluster index) of the unprocessed clusters in the current block graph.
+ * Eliminating a cluster couples every pair of its neighbours in the level's
+ * input graph (Sec. 3.1, Eq. elim), and a cluster none of whose blocks is
+ * fill leaves the graph (rank 0).  ranges: nranges pairs [lo, hi) of
+ * consecutive clusters covering [0, nc) with no block between two ranges
+ * (independent problems, planned on separate threads), or nranges = 0.
+ * Output (caller-owned host arrays): phase[nc] (-1 for size 0), vanished[nc]
+ * (1 = left the graph), end_ptr[nc+1] and, when end_adj is not NULL,
+ * end_adj[end_cap] with each cluster's blocks at the level's end (sorted,
+ * including itself unless it left or has size 0).  HS_ERR_ARG on malformed
+ * input or end_cap < end_ptr[nc] (end_ptr is filled first, so a call with
+ * end_adj = NULL queries the size). */
+int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const int32_t* size0, int32_t nranges,
+                  const int32_t* ranges, int32_t* phase, int32_t* vanished, int64_t* end_ptr, int32_t* end_adj,
+                  int64_t end_cap);
+
 /* Hierarchical_Factor (Algorithm 1): scaled low-rank elimination of every
  * cluster, level by level, then dense Cholesky of the top.  tree may be NULL
  * (then hs_partition_extruded runs on options->coords, options->leaf_lines,

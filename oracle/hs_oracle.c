@@ -1243,3 +1243,128 @@ int32_t or_dense_step(int32_t s, int32_t nn, int32_t nw, const double *A, double
     free(Ass); free(M); free(V); free(tau); free(R);
     return r;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Symbolic plan of one level (the phase rule and the fill pattern alone)   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int *v;
+    int n, cap;
+} ilist;
+
+static int il_find(const ilist *l, int x) { /* index of x, or -1 */
+    int i;
+    for (i = 0; i < l->n; i++)
+        if (l->v[i] == x) return i;
+    return -1;
+}
+
+static void il_add(ilist *l, int x) { /* sorted insert if absent */
+    int i;
+    if (il_find(l, x) >= 0) return;
+    if (l->n == l->cap) {
+        int *nv;
+        l->cap = l->cap ? 2 * l->cap : 8;
+        nv = (int *)xcalloc((size_t)l->cap, sizeof(int));
+        if (l->n) memcpy(nv, l->v, (size_t)l->n * sizeof(int));
+        free(l->v);
+        l->v = nv;
+    }
+    i = l->n;
+    while (i > 0 && l->v[i - 1] > x) {
+        l->v[i] = l->v[i - 1];
+        i--;
+    }
+    l->v[i] = x;
+    l->n++;
+}
+
+static void il_remove(ilist *l, int x) {
+    int i = il_find(l, x);
+    if (i < 0) return;
+    for (; i + 1 < l->n; i++) l->v[i] = l->v[i + 1];
+    l->n--;
+}
+
+/*
+ * The level plan of or_factor_create without the arithmetic: the block graph
+ * over nc clusters (adj: symmetric CSR without self loops; a cluster of size
+ * 0 has no blocks), phases by the phase rule, clusters of a phase eliminated
+ * one at a time in ascending order.  Eliminating c couples every pair of its
+ * neighbours in the level's input graph (Eq. elim); when none of c's blocks
+ * is fill, c has rank 0 and leaves the graph.  Out: phase (-1 for size 0),
+ * vanished, and the blocks present at the end of the level (end_ptr[nc+1];
+ * end_adj, sorted per cluster, with the cluster itself unless it left or has
+ * size 0; end_adj may be NULL to query end_ptr[nc]).
+ */
+int or_plan_level(int32_t nc, const int64_t *adj_ptr, const int32_t *adj, const int32_t *size0,
+                  int32_t *phase, int32_t *vanished, int64_t *end_ptr, int32_t *end_adj,
+                  int64_t end_cap) {
+    ilist *cur = (ilist *)xcalloc((size_t)nc + 1, sizeof(ilist));
+    char *processed = (char *)xcalloc((size_t)nc + 1, 1);
+    char *sel = (char *)xcalloc((size_t)nc + 1, 1);
+    int *order = (int *)xcalloc((size_t)nc + 1, sizeof(int));
+    int *nb = NULL;
+    int c, done = 0, ph = 0, rc = OR_OK;
+    int64_t e, tot = 0;
+    for (c = 0; c < nc; c++) {
+        for (e = adj_ptr[c]; e < adj_ptr[c + 1]; e++) il_add(&cur[c], adj[e]);
+        phase[c] = -1;
+        vanished[c] = 0;
+        if (size0[c] == 0) {
+            processed[c] = 1;
+            done++;
+        }
+    }
+    nb = (int *)xcalloc((size_t)nc + 1, sizeof(int));
+    while (done < nc) {
+        int cnt = 0, i;
+        memset(sel, 0, (size_t)nc);
+        for (c = 0; c < nc; c++) {
+            int t, ok = 1;
+            if (processed[c]) continue;
+            for (t = 0; t < cur[c].n; t++)
+                if (sel[cur[c].v[t]]) { ok = 0; break; }
+            if (ok) { sel[c] = 1; order[cnt++] = c; }
+        }
+        for (i = 0; i < cnt; i++) {
+            int pi = order[i], nn = 0, nw = 0, t, a, b;
+            /* n: current neighbours that are blocks of the input graph; w: fill */
+            for (t = 0; t < cur[pi].n; t++) {
+                int q = cur[pi].v[t], in0 = 0;
+                for (e = adj_ptr[pi]; e < adj_ptr[pi + 1]; e++)
+                    if (adj[e] == q) in0 = 1;
+                if (in0) nb[nn++] = q;
+                else nw++;
+            }
+            for (a = 0; a < nn; a++)
+                for (b = 0; b < nn; b++)
+                    if (a != b) il_add(&cur[nb[a]], nb[b]);
+            if (nw == 0) {
+                vanished[pi] = 1;
+                for (t = 0; t < cur[pi].n; t++) il_remove(&cur[cur[pi].v[t]], pi);
+                cur[pi].n = 0;
+            }
+            processed[pi] = 1;
+            phase[pi] = ph;
+            done++;
+        }
+        ph++;
+    }
+    for (c = 0; c < nc; c++) {
+        if (size0[c] > 0 && !vanished[c]) il_add(&cur[c], c);
+        end_ptr[c] = tot;
+        tot += cur[c].n;
+    }
+    end_ptr[nc] = tot;
+    if (end_adj) {
+        if (end_cap < tot) rc = OR_ERR_ARG;
+        else
+            for (c = 0; c < nc; c++)
+                if (cur[c].n) memcpy(end_adj + end_ptr[c], cur[c].v, (size_t)cur[c].n * sizeof(int));
+    }
+    for (c = 0; c < nc; c++) free(cur[c].v);
+    free(cur); free(processed); free(sel); free(order); free(nb);
+    return rc;
+}

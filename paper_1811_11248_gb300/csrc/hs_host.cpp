@@ -2572,6 +2572,68 @@ int hs_tree_free(hs_tree* t) {
     return HS_OK;
 }
 
+int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const int32_t* size0, int32_t nranges,
+                  const int32_t* ranges, int32_t* phase, int32_t* vanished, int64_t* end_ptr, int32_t* end_adj,
+                  int64_t end_cap) {
+    if (nc < 0 || !adj_ptr || !size0 || !phase || !vanished || !end_ptr || nranges < 0) return HS_ERR_ARG;
+    if (nranges > 0 && !ranges) return HS_ERR_ARG;
+    return run_guarded([&] {
+        if (adj_ptr[0] != 0) throw HsError{HS_ERR_ARG};
+        for (int32_t c = 0; c < nc; c++)
+            if (adj_ptr[c + 1] < adj_ptr[c] || size0[c] < 0) throw HsError{HS_ERR_ARG};
+        if (adj_ptr[nc] > 0 && !adj) throw HsError{HS_ERR_ARG};
+        LevelPlan P;
+        P.nc = nc;
+        P.size0.assign(size0, size0 + nc);
+        P.adj0.assign(nc, {});
+        for (int32_t c = 0; c < nc; c++) {
+            // sorted, no self loop, in range
+            for (int64_t e = adj_ptr[c]; e < adj_ptr[c + 1]; e++) {
+                const int32_t q = adj[e];
+                if (q < 0 || q >= nc || q == c || (e > adj_ptr[c] && adj[e - 1] >= q)) throw HsError{HS_ERR_ARG};
+                // a cluster without DOFs has no blocks
+                if (size0[c] == 0 || size0[q] == 0) throw HsError{HS_ERR_ARG};
+                P.adj0[c].push_back(q);
+            }
+        }
+        for (int32_t c = 0; c < nc; c++)  // symmetric
+            for (int q : P.adj0[c])
+                if (!sorted_has(P.adj0[q], c)) throw HsError{HS_ERR_ARG};
+        std::vector<std::pair<int, int>> rg;
+        if (nranges > 0) {
+            // consecutive, covering [0, nc), no block between two ranges
+            std::vector<int> range_of(nc, -1);
+            int next = 0;
+            for (int32_t k = 0; k < nranges; k++) {
+                const int lo = ranges[2 * k], hi = ranges[2 * k + 1];
+                if (lo != next || hi < lo || hi > nc) throw HsError{HS_ERR_ARG};
+                for (int c2 = lo; c2 < hi; c2++) range_of[c2] = k;
+                rg.push_back({lo, hi});
+                next = hi;
+            }
+            if (next != nc) throw HsError{HS_ERR_ARG};
+            for (int32_t c = 0; c < nc; c++)
+                for (int q : P.adj0[c])
+                    if (range_of[q] != range_of[c]) throw HsError{HS_ERR_ARG};
+        }
+        plan_level(P, rg);
+        int64_t tot = 0;
+        end_ptr[0] = 0;
+        for (int32_t c = 0; c < nc; c++) {
+            phase[c] = P.phase[c];
+            vanished[c] = P.vanished[c] ? 1 : 0;
+            tot += (int64_t)P.endp[c].size();
+            end_ptr[c + 1] = tot;
+        }
+        if (end_adj) {
+            if (end_cap < tot) throw HsError{HS_ERR_ARG};
+            for (int32_t c = 0; c < nc; c++)
+                std::copy(P.endp[c].begin(), P.endp[c].end(), end_adj + end_ptr[c]);
+        }
+        release_plan(P);
+    });
+}
+
 int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const hs_tree* tree,
              const hs_options* opt, hs_handle* out, hs_info* info) {
     if (!out) return HS_ERR_ARG;

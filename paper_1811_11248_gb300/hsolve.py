@@ -70,6 +70,7 @@ def lib():
     L.hs_default_options.argtypes = [ctypes.POINTER(hs_options)]
     L.hs_partition_extruded.argtypes = [I64, P, P, P, P, I32, F64, ctypes.POINTER(hs_tree)]
     L.hs_tree_free.argtypes = [ctypes.POINTER(hs_tree)]
+    L.hs_plan_level.argtypes = [I32, P, P, P, I32, P, P, P, P, P, I64]
     L.hs_setup.argtypes = [I64, P, P, P, ctypes.POINTER(hs_tree), ctypes.POINTER(hs_options),
                            ctypes.POINTER(P), ctypes.POINTER(hs_info)]
     L.hs_apply.argtypes = [P, P, P]
@@ -108,7 +109,7 @@ EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_s
             "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
             "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str", "hs_setup_batched",
             "hs_krylov_batched", "hs_num_problems", "hs_problem_info", "hs_mlp_forward", "hs_mlp_grad",
-            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples")
+            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples", "hs_plan_level")
 MLP_NIN, MLP_NPARAM, MLP_MAX_BATCH = 8, 4801, 256
 
 
@@ -164,6 +165,25 @@ def hs_partition_extruded(n, rowptr, col, val, coords=None, leaf_lines=4, theta=
     finally:
         lib().hs_tree_free(ctypes.byref(t))
     return perm, lp, depth
+
+
+def hs_plan_level(adj_ptr, adj, size0, ranges=None):
+    """Phase plan of one level on the host -> (phase, vanished, end_ptr, end_adj)."""
+    size0 = np.ascontiguousarray(size0, dtype=np.int32)
+    nc = len(size0)
+    adj_ptr = np.ascontiguousarray(adj_ptr, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    rg = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int32).reshape(-1)
+    nr = 0 if rg is None else len(rg) // 2
+    phase = np.empty(nc, np.int32)
+    vanished = np.empty(nc, np.int32)
+    end_ptr = np.empty(nc + 1, np.int64)
+    _check(lib().hs_plan_level(nc, _ptr(adj_ptr), _ptr(adj), _ptr(size0), nr, _ptr(rg), _ptr(phase),
+                               _ptr(vanished), _ptr(end_ptr), None, 0), "hs_plan_level")
+    end_adj = np.empty(max(int(end_ptr[-1]), 1), np.int32)
+    _check(lib().hs_plan_level(nc, _ptr(adj_ptr), _ptr(adj), _ptr(size0), nr, _ptr(rg), _ptr(phase),
+                               _ptr(vanished), _ptr(end_ptr), _ptr(end_adj), len(end_adj)), "hs_plan_level")
+    return phase, vanished, end_ptr, end_adj[:int(end_ptr[-1])]
 
 
 class Handle:

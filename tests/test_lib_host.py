@@ -66,6 +66,114 @@ def test_partition_matches_oracle_large(hs, oracle_lib, use_coords):
     assert np.array_equal(perm, operm) and np.array_equal(lp, olp)
 
 
+def _graph_csr(nc, a, b):
+    """Symmetric CSR (sorted rows, no self loops) from edge arrays."""
+    a, b = np.asarray(a, np.int64), np.asarray(b, np.int64)
+    m = a != b
+    a, b = np.concatenate([a[m], b[m]]), np.concatenate([b[m], a[m]])
+    key = np.unique(a * nc + b)
+    rows, cols = key // nc, key % nc
+    ptr = np.zeros(nc + 1, np.int64)
+    np.add.at(ptr, rows + 1, 1)
+    return np.cumsum(ptr), cols.astype(np.int32)
+
+
+def _grid_graph(nx, ny, diag=False):
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    a = [idx[:, :-1].ravel(), idx[:-1, :].ravel()]
+    b = [idx[:, 1:].ravel(), idx[1:, :].ravel()]
+    if diag:
+        a.append(idx[:-1, :-1].ravel())
+        b.append(idx[1:, 1:].ravel())
+    return _graph_csr(nx * ny, np.concatenate(a), np.concatenate(b))
+
+
+def _random_graph(rng, nc, deg):
+    """Random geometric graph in the unit square (about deg neighbours)."""
+    pts = rng.random((nc, 2))
+    cell = np.sqrt(deg / (np.pi * nc))
+    order = np.lexsort(((pts[:, 1] // cell), (pts[:, 0] // cell)))
+    a, b = [], []
+    grid = {}
+    for i in order:
+        grid.setdefault((int(pts[i, 0] // cell), int(pts[i, 1] // cell)), []).append(i)
+    for (gx, gy), members in grid.items():
+        near = [j for dx in (-1, 0, 1) for dy in (-1, 0, 1) for j in grid.get((gx + dx, gy + dy), [])]
+        near = np.array(near)
+        for i in members:
+            d = np.hypot(*(pts[near] - pts[i]).T)
+            for j in near[(d < cell) & (near > i)]:
+                a.append(i)
+                b.append(j)
+    return _graph_csr(nc, a, b)
+
+
+def _compare_plans(hs, oracle_lib, ptr, adj, size0, ranges=None):
+    got = hs.hs_plan_level(ptr, adj, size0, ranges)
+    ref = oracle_lib.plan_level(ptr, adj, size0)
+    for g, r, name in zip(got, ref, ("phase", "vanished", "end_ptr", "end_adj")):
+        assert np.array_equal(g, r), name
+    return got
+
+
+def test_level_plan_matches_oracle_on_a_large_grid(hs, oracle_lib):
+    """40,000 clusters: the first phases are large enough for the planner to
+    apply their eliminations to the block graph on all threads."""
+    ptr, adj = _grid_graph(200, 200)
+    size0 = np.random.default_rng(0).integers(1, 6, 200 * 200)
+    ph, van, _, _ = _compare_plans(hs, oracle_lib, ptr, adj, size0)
+    assert ph.max() >= 2 and van.sum() > 0
+
+
+def test_level_plan_matches_oracle_on_random_graphs(hs, oracle_lib):
+    rng = np.random.default_rng(1)
+    for nc, deg in ((3000, 5.0), (20000, 7.0)):
+        ptr, adj = _random_graph(rng, nc, deg)
+        size0 = rng.integers(1, 9, nc)
+        # clusters without blocks may have no DOFs
+        isolated = np.flatnonzero(np.diff(ptr) == 0)
+        size0[isolated[::2]] = 0
+        _compare_plans(hs, oracle_lib, ptr, adj, size0)
+
+
+def test_level_plan_with_independent_ranges(hs, oracle_lib):
+    """Many independent problems, each planned on its own thread: the same
+    plan as the whole block-diagonal graph planned at once."""
+    rng = np.random.default_rng(2)
+    ptrs, adjs, sizes, ranges, base = [], [], [], [], 0
+    for k in range(40):
+        if k % 3 == 0:
+            nx, ny = rng.integers(3, 20, 2)
+            ptr, adj = _grid_graph(int(nx), int(ny), diag=bool(k % 2))
+        else:
+            ptr, adj = _random_graph(rng, int(rng.integers(20, 600)), 6.0)
+        nc = len(ptr) - 1
+        ptrs.append(ptr[1:] + (adjs and sum(len(x) for x in adjs) or 0))
+        adjs.append(adj + base)
+        sizes.append(rng.integers(1, 5, nc))
+        ranges.append((base, base + nc))
+        base += nc
+    ptr = np.concatenate([[0]] + ptrs)
+    adj = np.concatenate(adjs).astype(np.int32)
+    _compare_plans(hs, oracle_lib, ptr, adj, np.concatenate(sizes), np.array(ranges))
+
+
+def test_level_plan_rejects_bad_input(hs):
+    ptr, adj = _grid_graph(3, 3)
+    ok = np.ones(9, np.int32)
+    hs.hs_plan_level(ptr, adj, ok)
+    bad = adj.copy()
+    bad[0] = 0  # self loop
+    with pytest.raises(hs.HsError):
+        hs.hs_plan_level(ptr, bad, ok)
+    with pytest.raises(hs.HsError):  # not symmetric
+        hs.hs_plan_level(np.array([0, 1, 1]), np.array([1], np.int32), np.ones(2, np.int32))
+    with pytest.raises(hs.HsError):  # a block of a cluster without DOFs
+        hs.hs_plan_level(ptr, adj, np.where(np.arange(9) == 4, 0, 1))
+    with pytest.raises(hs.HsError):  # a block between two ranges
+        hs.hs_plan_level(ptr, adj, ok, np.array([[0, 4], [4, 9]]))
+
+
 def test_partition_rejects_bad_arguments(hs):
     p = inputs.grid_operator(4, 4, 2, ratio=10.0)
     with pytest.raises(hs.HsError):
