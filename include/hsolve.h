@@ -137,12 +137,15 @@ int hs_tree_free(hs_tree* t);
  * Output (caller-owned host arrays): phase[nc] (-1 for size 0), vanished[nc]
  * (1 = left the graph), end_ptr[nc+1] and, when end_adj is not NULL,
  * end_adj[end_cap] with each cluster's blocks at the level's end (sorted,
- * including itself unless it left or has size 0).  HS_ERR_ARG on malformed
- * input or end_cap < end_ptr[nc] (end_ptr is filled first, so a call with
- * end_adj = NULL queries the size). */
+ * including itself unless it left or has size 0); all_ptr[nc+1] and, when
+ * all_adj is not NULL, all_adj[all_cap] with every block that existed at
+ * some point of the level (sorted, with the cluster itself unless it has
+ * size 0: the level's block store).  HS_ERR_ARG on malformed input or a
+ * capacity below end_ptr[nc] / all_ptr[nc] (the pointer arrays are filled
+ * first, so a call with NULL lists queries the sizes). */
 int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const int32_t* size0, int32_t nranges,
                   const int32_t* ranges, int32_t* phase, int32_t* vanished, int64_t* end_ptr, int32_t* end_adj,
-                  int64_t end_cap);
+                  int64_t end_cap, int64_t* all_ptr, int32_t* all_adj, int64_t all_cap);
 
 /* Hierarchical_Factor (Algorithm 1): scaled low-rank elimination of every
  * cluster, level by level, then dense Cholesky of the top.  tree may be NULL

@@ -69,7 +69,7 @@ def lib():
         L.or_dense_cpqr.restype = I32
         L.or_dense_step.argtypes = [I32, I32, I32, P, F64, P]
         L.or_dense_step.restype = I32
-        L.or_plan_level.argtypes = [I32, P, P, P, P, P, P, P, I64]
+        L.or_plan_level.argtypes = [I32, P, P, P, P, P, P, P, I64, P, P, I64]
         _lib = L
     return _lib
 
@@ -101,22 +101,25 @@ def partition(prob, leaf_lines=4, theta=0.5, use_coords=True):
 
 
 def plan_level(adj_ptr, adj, size0):
-    """Symbolic level plan -> (phase, vanished, end_ptr, end_adj)."""
+    """Symbolic level plan -> (phase, vanished, end_ptr, end_adj, all_ptr, all_adj)."""
     size0 = np.ascontiguousarray(size0, dtype=np.int32)
     nc = len(size0)
     adj_ptr = np.ascontiguousarray(adj_ptr, dtype=np.int64)
     adj = np.ascontiguousarray(adj, dtype=np.int32)
+    aj = _p(adj) if len(adj) else None
     phase = np.empty(nc, np.int32)
     vanished = np.empty(nc, np.int32)
     end_ptr = np.empty(nc + 1, np.int64)
-    lib().or_plan_level(nc, _p(adj_ptr), _p(adj) if len(adj) else None, _p(size0), _p(phase),
-                        _p(vanished), _p(end_ptr), None, 0)
+    all_ptr = np.empty(nc + 1, np.int64)
+    lib().or_plan_level(nc, _p(adj_ptr), aj, _p(size0), _p(phase), _p(vanished), _p(end_ptr), None, 0,
+                        _p(all_ptr), None, 0)
     end_adj = np.empty(max(int(end_ptr[-1]), 1), np.int32)
-    rc = lib().or_plan_level(nc, _p(adj_ptr), _p(adj) if len(adj) else None, _p(size0), _p(phase),
-                             _p(vanished), _p(end_ptr), _p(end_adj), len(end_adj))
+    all_adj = np.empty(max(int(all_ptr[-1]), 1), np.int32)
+    rc = lib().or_plan_level(nc, _p(adj_ptr), aj, _p(size0), _p(phase), _p(vanished), _p(end_ptr),
+                             _p(end_adj), len(end_adj), _p(all_ptr), _p(all_adj), len(all_adj))
     if rc != OK:
         raise RuntimeError(f"oracle plan failed: {rc}")
-    return phase, vanished, end_ptr, end_adj[:int(end_ptr[-1])]
+    return phase, vanished, end_ptr, end_adj[:int(end_ptr[-1])], all_ptr, all_adj[:int(all_ptr[-1])]
 
 
 def default_depth(nleaf: int) -> int:

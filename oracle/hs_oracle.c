@@ -1294,14 +1294,17 @@ static void il_remove(ilist *l, int x) {
  * one at a time in ascending order.  Eliminating c couples every pair of its
  * neighbours in the level's input graph (Eq. elim); when none of c's blocks
  * is fill, c has rank 0 and leaves the graph.  Out: phase (-1 for size 0),
- * vanished, and the blocks present at the end of the level (end_ptr[nc+1];
+ * vanished, the blocks present at the end of the level (end_ptr[nc+1];
  * end_adj, sorted per cluster, with the cluster itself unless it left or has
- * size 0; end_adj may be NULL to query end_ptr[nc]).
+ * size 0) and every block that existed at some point of the level (all_ptr,
+ * all_adj: sorted, with the cluster itself unless it has size 0).  A NULL
+ * list queries the size (the pointer array is filled either way).
  */
 int or_plan_level(int32_t nc, const int64_t *adj_ptr, const int32_t *adj, const int32_t *size0,
                   int32_t *phase, int32_t *vanished, int64_t *end_ptr, int32_t *end_adj,
-                  int64_t end_cap) {
+                  int64_t end_cap, int64_t *all_ptr, int32_t *all_adj, int64_t all_cap) {
     ilist *cur = (ilist *)xcalloc((size_t)nc + 1, sizeof(ilist));
+    ilist *ever = (ilist *)xcalloc((size_t)nc + 1, sizeof(ilist));
     char *processed = (char *)xcalloc((size_t)nc + 1, 1);
     char *sel = (char *)xcalloc((size_t)nc + 1, 1);
     int *order = (int *)xcalloc((size_t)nc + 1, sizeof(int));
@@ -1309,7 +1312,11 @@ int or_plan_level(int32_t nc, const int64_t *adj_ptr, const int32_t *adj, const 
     int c, done = 0, ph = 0, rc = OR_OK;
     int64_t e, tot = 0;
     for (c = 0; c < nc; c++) {
-        for (e = adj_ptr[c]; e < adj_ptr[c + 1]; e++) il_add(&cur[c], adj[e]);
+        for (e = adj_ptr[c]; e < adj_ptr[c + 1]; e++) {
+            il_add(&cur[c], adj[e]);
+            il_add(&ever[c], adj[e]);
+        }
+        if (size0[c] > 0) il_add(&ever[c], c);
         phase[c] = -1;
         vanished[c] = 0;
         if (size0[c] == 0) {
@@ -1340,7 +1347,10 @@ int or_plan_level(int32_t nc, const int64_t *adj_ptr, const int32_t *adj, const 
             }
             for (a = 0; a < nn; a++)
                 for (b = 0; b < nn; b++)
-                    if (a != b) il_add(&cur[nb[a]], nb[b]);
+                    if (a != b) {
+                        il_add(&cur[nb[a]], nb[b]);
+                        il_add(&ever[nb[a]], nb[b]);
+                    }
             if (nw == 0) {
                 vanished[pi] = 1;
                 for (t = 0; t < cur[pi].n; t++) il_remove(&cur[cur[pi].v[t]], pi);
@@ -1364,7 +1374,22 @@ int or_plan_level(int32_t nc, const int64_t *adj_ptr, const int32_t *adj, const 
             for (c = 0; c < nc; c++)
                 if (cur[c].n) memcpy(end_adj + end_ptr[c], cur[c].v, (size_t)cur[c].n * sizeof(int));
     }
-    for (c = 0; c < nc; c++) free(cur[c].v);
-    free(cur); free(processed); free(sel); free(order); free(nb);
+    tot = 0;
+    for (c = 0; c < nc; c++) {
+        all_ptr[c] = tot;
+        tot += ever[c].n;
+    }
+    all_ptr[nc] = tot;
+    if (all_adj) {
+        if (all_cap < tot) rc = OR_ERR_ARG;
+        else
+            for (c = 0; c < nc; c++)
+                if (ever[c].n) memcpy(all_adj + all_ptr[c], ever[c].v, (size_t)ever[c].n * sizeof(int));
+    }
+    for (c = 0; c < nc; c++) {
+        free(cur[c].v);
+        free(ever[c].v);
+    }
+    free(cur); free(ever); free(processed); free(sel); free(order); free(nb);
     return rc;
 }

@@ -701,25 +701,38 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
     auto S = [&](int c) -> char& { return insel[c - lo]; };
     auto B = [&](int c) -> char& { return blocked[c - lo]; };  // has a selected neighbour
     auto T = [&](int c) -> char& { return target[c - lo]; };   // gains couplings in this phase
-    std::vector<int> tg, scratch;
+    std::vector<int> tg, scratch, tgi(hi - lo, 0);
+    std::vector<std::vector<int>> src;  // per target of the phase: its selected neighbours
     int remaining = 0;
     for (int c = lo; c < hi; c++) {
         if (P.size0[c] > 0) remaining++;
         else D(c) = 1;
     }
     int first = lo;  // clusters below `first` are all done
-    // v <- v u (add \ {p}), both sorted
-    auto merge_into = [](std::vector<int>& v, const std::vector<int>& add, int p, std::vector<int>& tmp) {
-        tmp.clear();
-        auto a = v.begin(), ae = v.end();
-        auto b = add.begin(), be = add.end();
-        while (a != ae || b != be) {
-            if (b != be && *b == p) { ++b; continue; }  // p does not gain itself
-            if (b == be || (a != ae && *a < *b)) tmp.push_back(*a++);
-            else if (a == ae || *b < *a) tmp.push_back(*b++);
-            else { tmp.push_back(*a++); ++b; }
+    // v <- v u (add \ {p}), both sorted, in place: count the new entries,
+    // grow v by that much and merge from the back (no temporary list)
+    auto merge_into = [](std::vector<int>& v, const std::vector<int>& add, int p) {
+        size_t i = 0, nnew = 0;
+        for (int x : add) {
+            if (x == p) continue;  // p does not gain itself
+            while (i < v.size() && v[i] < x) i++;
+            if (i == v.size() || v[i] != x) nnew++;
         }
-        v.swap(tmp);
+        if (nnew == 0) return;
+        const size_t a = v.size();
+        v.resize(a + nnew);
+        ptrdiff_t ia = (ptrdiff_t)a - 1, ib = (ptrdiff_t)add.size() - 1, o = (ptrdiff_t)(a + nnew) - 1;
+        while (ib >= 0) {
+            const int x = add[ib];
+            if (x == p) { ib--; continue; }
+            if (ia >= 0 && v[ia] >= x) {
+                if (v[ia] == x) ib--;  // present already: kept once
+                v[o--] = v[ia--];
+            } else {
+                v[o--] = x;
+                ib--;
+            }
+        }
     };
     while (remaining > 0) {
         std::vector<int> sel;
@@ -734,13 +747,22 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
             S(c) = 1;
             sel.push_back(c);
             const auto& a0 = P.adj0[c];
+            P.nl[c].reserve(std::min(cur[c].size(), a0.size()));
+            P.wl[c].reserve(cur[c].size());
             size_t k = 0;  // merge-walk of cur[c] against adj0[c] (both sorted)
             for (int q : cur[c]) {
                 B(q) = 1;  // the block graph is symmetric
                 while (k < a0.size() && a0[k] < q) k++;
                 if (k < a0.size() && a0[k] == q) {
                     P.nl[c].push_back(q);
-                    if (!T(q)) { T(q) = 1; tg.push_back(q); }
+                    if (!T(q)) {
+                        T(q) = 1;
+                        tgi[q - lo] = (int)tg.size();
+                        if (tg.size() == src.size()) src.emplace_back();
+                        src[tg.size()].clear();
+                        tg.push_back(q);
+                    }
+                    src[tgi[q - lo]].push_back(c);
                 } else {
                     P.wl[c].push_back(q);
                 }
@@ -750,38 +772,44 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
         }
         const int ph = (int)phases.size();
         const int64_t ns = (int64_t)sel.size();
-        if (work < (1 << 17) || tl_serial || tl_in_pool) {
-            // a small phase: the eliminations one after another
-            for (int c : sel) {
-                const auto& nlc = P.nl[c];
-                for (int p : nlc) {
-                    merge_into(cur[p], nlc, p, scratch);
-                    merge_into(P.all[p], nlc, p, scratch);
-                }
-                if (P.vanished[c])
-                    for (int q : nlc) sorted_erase(cur[q], c);
-            }
-            for (int p : tg) T(p) = 0;
-        } else parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
-            std::vector<int> src, tmp, add, tmp2;
+        // every target: the union of what its selected neighbours bring,
+        // merged once into each of its lists; then the neighbours that left
+        // the graph are dropped from it
+        auto update = [&](int64_t a, int64_t b, std::vector<int>& add) {
             for (int64_t i = a; i < b; i++) {
                 const int p = tg[i];
-                src.clear();
-                for (int c : cur[p])  // selected neighbours that couple p to the others
-                    if (S(c) && sorted_has(P.nl[c], p)) src.push_back(c);
-                // the union of what they bring, then one merge into each list
-                add.clear();
-                for (int c : src) merge_into(add, P.nl[c], p, tmp2);
-                merge_into(cur[p], add, -1, tmp);
-                merge_into(P.all[p], add, -1, tmp);
-                for (int c : src)
-                    if (P.vanished[c]) sorted_erase(cur[p], c);
+                const auto& sp = src[i];
+                const std::vector<int>* u = &P.nl[sp[0]];
+                int skip = p;
+                if (sp.size() > 1) {
+                    add.clear();
+                    for (int c : sp) merge_into(add, P.nl[c], p);
+                    u = &add;
+                    skip = -1;
+                }
+                merge_into(cur[p], *u, skip);
+                for (int c : sp)
+                    if (P.vanished[c]) {
+                        sorted_erase(cur[p], c);
+                        P.all[p].push_back(c);  // the block existed during the level
+                    }
                 target[p - lo] = 0;
             }
-        });
+        };
+        if (work < (1 << 17) || tl_serial || tl_in_pool) {
+            update(0, (int64_t)tg.size(), scratch);
+        } else {
+            parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
+                std::vector<int> add;
+                update(a, b, add);
+            });
+        }
         for (int c : sel) {
             for (int q : cur[c]) B(q) = 0;
-            if (P.vanished[c]) cur[c].clear();
+            if (P.vanished[c]) {
+                P.all[c].insert(P.all[c].end(), cur[c].begin(), cur[c].end());
+                cur[c].clear();
+            }
             D(c) = 1;
             S(c) = 0;
             P.phase[c] = ph;
@@ -789,10 +817,22 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
         remaining -= (int)ns;
         phases.push_back(std::move(sel));
     }
-    for (int c = lo; c < hi; c++) {
-        P.endp[c] = std::move(cur[c]);
-        if (P.size0[c] > 0 && !P.vanished[c]) sorted_insert(P.endp[c], c);
-    }
+    // every block that existed during the level: the lists' final state, the
+    // blocks to clusters that left (recorded as they left) and the diagonal
+    auto finish = [&](int64_t a, int64_t b) {
+        for (int64_t c = a; c < b; c++) {
+            auto& al = P.all[c];
+            al.reserve(al.size() + cur[c].size() + 1);
+            al.insert(al.end(), cur[c].begin(), cur[c].end());
+            if (P.size0[c] > 0) al.push_back((int)c);
+            std::sort(al.begin(), al.end());
+            al.erase(std::unique(al.begin(), al.end()), al.end());
+            P.endp[c] = std::move(cur[c]);
+            if (P.size0[c] > 0 && !P.vanished[c]) sorted_insert(P.endp[c], (int)c);
+        }
+    };
+    if (tl_serial || tl_in_pool) finish(lo, hi);
+    else parallel_ranges(hi - lo, 2048, [&](int64_t a, int64_t b, int) { finish(lo + a, lo + b); });
 }
 
 // Frees a plan's per-cluster lists on all threads: they were allocated by
@@ -827,11 +867,13 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
     std::vector<std::vector<std::vector<int>>> ph(rg.size());
     // the lists start as the input pattern, made by the thread that plans
     // them (one range: by all threads)
+    // (room for the fill to come, so that the phases seldom reallocate; the
+    // list of every block of the level is completed at the level's end)
     auto init = [&](int64_t lo, int64_t hi) {
         for (int64_t c = lo; c < hi; c++) {
-            cur[c] = P.adj0[c];
-            P.all[c] = P.adj0[c];
-            if (P.size0[c] > 0) sorted_insert(P.all[c], (int)c);
+            cur[c].reserve(4 * P.adj0[c].size() + 4);
+            cur[c].assign(P.adj0[c].begin(), P.adj0[c].end());
+            P.all[c].clear();
         }
     };
     if (rg.size() == 1) parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) { init(lo, hi); });
@@ -2574,8 +2616,9 @@ int hs_tree_free(hs_tree* t) {
 
 int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const int32_t* size0, int32_t nranges,
                   const int32_t* ranges, int32_t* phase, int32_t* vanished, int64_t* end_ptr, int32_t* end_adj,
-                  int64_t end_cap) {
-    if (nc < 0 || !adj_ptr || !size0 || !phase || !vanished || !end_ptr || nranges < 0) return HS_ERR_ARG;
+                  int64_t end_cap, int64_t* all_ptr, int32_t* all_adj, int64_t all_cap) {
+    if (nc < 0 || !adj_ptr || !size0 || !phase || !vanished || !end_ptr || !all_ptr || nranges < 0)
+        return HS_ERR_ARG;
     if (nranges > 0 && !ranges) return HS_ERR_ARG;
     return run_guarded([&] {
         if (adj_ptr[0] != 0) throw HsError{HS_ERR_ARG};
@@ -2617,18 +2660,26 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
                     if (range_of[q] != range_of[c]) throw HsError{HS_ERR_ARG};
         }
         plan_level(P, rg);
-        int64_t tot = 0;
+        int64_t tot = 0, tota = 0;
         end_ptr[0] = 0;
+        all_ptr[0] = 0;
         for (int32_t c = 0; c < nc; c++) {
             phase[c] = P.phase[c];
             vanished[c] = P.vanished[c] ? 1 : 0;
             tot += (int64_t)P.endp[c].size();
             end_ptr[c + 1] = tot;
+            tota += (int64_t)P.all[c].size();
+            all_ptr[c + 1] = tota;
         }
         if (end_adj) {
             if (end_cap < tot) throw HsError{HS_ERR_ARG};
             for (int32_t c = 0; c < nc; c++)
                 std::copy(P.endp[c].begin(), P.endp[c].end(), end_adj + end_ptr[c]);
+        }
+        if (all_adj) {
+            if (all_cap < tota) throw HsError{HS_ERR_ARG};
+            for (int32_t c = 0; c < nc; c++)
+                std::copy(P.all[c].begin(), P.all[c].end(), all_adj + all_ptr[c]);
         }
         release_plan(P);
     });

@@ -70,7 +70,7 @@ def lib():
     L.hs_default_options.argtypes = [ctypes.POINTER(hs_options)]
     L.hs_partition_extruded.argtypes = [I64, P, P, P, P, I32, F64, ctypes.POINTER(hs_tree)]
     L.hs_tree_free.argtypes = [ctypes.POINTER(hs_tree)]
-    L.hs_plan_level.argtypes = [I32, P, P, P, I32, P, P, P, P, P, I64]
+    L.hs_plan_level.argtypes = [I32, P, P, P, I32, P, P, P, P, P, I64, P, P, I64]
     L.hs_setup.argtypes = [I64, P, P, P, ctypes.POINTER(hs_tree), ctypes.POINTER(hs_options),
                            ctypes.POINTER(P), ctypes.POINTER(hs_info)]
     L.hs_apply.argtypes = [P, P, P]
@@ -168,7 +168,8 @@ def hs_partition_extruded(n, rowptr, col, val, coords=None, leaf_lines=4, theta=
 
 
 def hs_plan_level(adj_ptr, adj, size0, ranges=None):
-    """Phase plan of one level on the host -> (phase, vanished, end_ptr, end_adj)."""
+    """Phase plan of one level on the host ->
+    (phase, vanished, end_ptr, end_adj, all_ptr, all_adj)."""
     size0 = np.ascontiguousarray(size0, dtype=np.int32)
     nc = len(size0)
     adj_ptr = np.ascontiguousarray(adj_ptr, dtype=np.int64)
@@ -178,12 +179,15 @@ def hs_plan_level(adj_ptr, adj, size0, ranges=None):
     phase = np.empty(nc, np.int32)
     vanished = np.empty(nc, np.int32)
     end_ptr = np.empty(nc + 1, np.int64)
+    all_ptr = np.empty(nc + 1, np.int64)
     _check(lib().hs_plan_level(nc, _ptr(adj_ptr), _ptr(adj), _ptr(size0), nr, _ptr(rg), _ptr(phase),
-                               _ptr(vanished), _ptr(end_ptr), None, 0), "hs_plan_level")
+                               _ptr(vanished), _ptr(end_ptr), None, 0, _ptr(all_ptr), None, 0), "hs_plan_level")
     end_adj = np.empty(max(int(end_ptr[-1]), 1), np.int32)
+    all_adj = np.empty(max(int(all_ptr[-1]), 1), np.int32)
     _check(lib().hs_plan_level(nc, _ptr(adj_ptr), _ptr(adj), _ptr(size0), nr, _ptr(rg), _ptr(phase),
-                               _ptr(vanished), _ptr(end_ptr), _ptr(end_adj), len(end_adj)), "hs_plan_level")
-    return phase, vanished, end_ptr, end_adj[:int(end_ptr[-1])]
+                               _ptr(vanished), _ptr(end_ptr), _ptr(end_adj), len(end_adj), _ptr(all_ptr),
+                               _ptr(all_adj), len(all_adj)), "hs_plan_level")
+    return phase, vanished, end_ptr, end_adj[:int(end_ptr[-1])], all_ptr, all_adj[:int(all_ptr[-1])]
 
 
 class Handle:

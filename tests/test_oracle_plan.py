@@ -27,33 +27,37 @@ def test_path_of_four():
     couples 1 and 3; 1 then has only that fill block, so it stays (phase 1),
     and 3 follows in phase 2."""
     ptr, adj = csr(4, [(0, 1), (1, 2), (2, 3)])
-    ph, van, ep, ea = plan_level(ptr, adj, [2, 2, 2, 2])
+    ph, van, ep, ea, ap, aa = plan_level(ptr, adj, [2, 2, 2, 2])
     assert ph.tolist() == [0, 1, 0, 2]
     assert van.tolist() == [1, 0, 1, 0]
     assert ends(ep, ea) == [[], [1, 3], [], [1, 3]]
+    # every block of the level: the input's, the diagonal and the fill 1-3
+    assert ends(ap, aa) == [[0, 1], [0, 1, 2, 3], [1, 2, 3], [1, 2, 3]]
 
 
 def test_star():
     """Centre 0 with leaves 1-4: the centre goes first and leaves; the leaves
     become a clique of fill blocks and are taken one per phase."""
     ptr, adj = csr(5, [(0, k) for k in range(1, 5)])
-    ph, van, ep, ea = plan_level(ptr, adj, [3] * 5)
+    ph, van, ep, ea, ap, aa = plan_level(ptr, adj, [3] * 5)
     assert ph.tolist() == [0, 1, 2, 3, 4]
     assert van.tolist() == [1, 0, 0, 0, 0]
     e = ends(ep, ea)
     assert e[0] == []
     for k in range(1, 5):
         assert e[k] == [1, 2, 3, 4]
+    assert ends(ap, aa) == [[0, 1, 2, 3, 4]] * 5
 
 
 def test_empty_clusters_have_no_phase():
     """1 has no DOFs; 0 leaves first, after which 2 has no block at all (no
     fill), so it leaves too."""
     ptr, adj = csr(3, [(0, 2)])
-    ph, van, ep, ea = plan_level(ptr, adj, [1, 0, 1])
+    ph, van, ep, ea, ap, aa = plan_level(ptr, adj, [1, 0, 1])
     assert ph.tolist() == [0, -1, 1]
     assert van.tolist() == [1, 0, 1]
     assert ends(ep, ea) == [[], [], []]
+    assert ends(ap, aa) == [[0, 2], [], [0, 2]]
 
 
 def test_grid_first_phase_is_the_checkerboard():
@@ -66,7 +70,7 @@ def test_grid_first_phase_is_the_checkerboard():
     edges = [(idx(i, j), idx(i + 1, j)) for j in range(ny) for i in range(nx - 1)]
     edges += [(idx(i, j), idx(i, j + 1)) for j in range(ny - 1) for i in range(nx)]
     ptr, adj = csr(nx * ny, edges)
-    ph, van, ep, ea = plan_level(ptr, adj, [4] * (nx * ny))
+    ph, van, ep, ea, _, _ = plan_level(ptr, adj, [4] * (nx * ny))
     e = ends(ep, ea)
     nbr = [set(adj[ptr[c]:ptr[c + 1]].tolist()) for c in range(nx * ny)]
     for j in range(ny):
@@ -96,7 +100,7 @@ def test_matches_the_numeric_oracle_phases(oracle_lib):
     a, b = cl[rows], cl[p.col]
     m = a != b
     ptr, adj = csr(nleaf, set(zip(a[m].tolist(), b[m].tolist())))
-    ph, van, _, _ = plan_level(ptr, adj, np.diff(lp))
+    ph, van = plan_level(ptr, adj, np.diff(lp))[:2]
     f = oracle_lib.Factor(p, perm, lp, 4, 1e-2)
     s0, fin, oph = f.level_info(0)
     assert np.array_equal(ph, oph)
