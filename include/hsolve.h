@@ -87,13 +87,15 @@ typedef struct {
     const float* rank_model; /* NULL (default), or a trained rank predictor
                             (host, HS_MLP_MODEL floats: feature means (8),
                             deviations (8), network parameters).  Mixed form
-                            only: a cluster predicted to have rank 0 scales
-                            its fill columns in FP32 only; if their squared
-                            norm is at most eps^2 / 2 its rank is 0 and the
-                            FP64 scaling of those columns and the QR are
-                            skipped, otherwise they are scaled again in FP64
-                            and the column-pivoted QR decides as usual.
-                            Copied during hs_setup.                           */
+                            only, for clusters of at least 16 DOFs with
+                            dense fill columns on the per-cluster kernel: a
+                            cluster predicted to have rank 0 scales those
+                            columns in FP32 only; if the fill block's
+                            squared norm is then at most eps^2 / 2 its rank
+                            is 0 and the FP64 scaling of those columns and
+                            the QR are skipped, otherwise they are scaled
+                            again in FP64 and the column-pivoted QR decides
+                            as usual.  Copied during hs_setup.                */
 } hs_options;
 
 typedef struct {
