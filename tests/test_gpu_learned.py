@@ -69,3 +69,40 @@ def test_learned_mixed_form(trained):
     assert res <= 1e-8 and ilr.rel_resid <= 1e-8
     assert abs(ilr.iters - i64.iters) <= 1
     assert np.sum(rlr != r64) <= 0.05 * len(r64)
+
+
+@pytest.mark.slow
+def test_learned_form_saves_factor_time_at_512x512x20(trained):
+    """What the network gains over the method without it: trained as the
+    benchmark trains it (ranks of the 16x16x8, 64x64x16 and batched 0-63
+    workloads), it lets the factor kernels of the 512x512x20 workload skip
+    FP64 scaling for clusters it predicts to have rank 0.  The factor time
+    must drop by at least 2% (about 5% measured) while the solve keeps the
+    mixed form's iterations and residual."""
+    hs, rank_model, _, _ = trained
+    f1, r1, s1 = rank_model.collect(inputs.anisotropic_16x16x8(), depth=4)
+    f2, r2, s2 = rank_model.collect(inputs.anisotropic_64x64x16(), depth=8)
+    f3, r3, s3 = rank_model.collect_batched([inputs.batched_problem(k) for k in range(64)])
+    model, _ = rank_model.fit(np.concatenate([f1, f2, f3]), np.concatenate([r1, r2, r3]),
+                              np.concatenate([s1, s2, s3]), epochs=40)
+    p = inputs.anisotropic_512x512x20()
+    st = torch.cuda.current_stream().cuda_stream
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, va, b = dev(p.rowptr), dev(p.col), dev(p.val), dev(p.b)
+    coords = np.ascontiguousarray(p.coords)
+    best = {}
+    for _ in range(2):
+        for name, mv in (("mixed", None), ("learned", model.packed())):
+            opt = hs.hs_default_options(tol=1e-2, rtol=1e-8, mem=hs.HS_MEM_DEVICE, stream=st, coords=coords,
+                                        precision=hs.HS_PREC_MIXED, rank_model=mv, profile=1)
+            h = hs.hs_setup(p.n, rp, ci, va, opt=opt)
+            x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+            info, rc = h.hs_krylov(b, x)
+            ms = h.kernel_stats()["factor"]["ms"]
+            h.close()
+            prev = best.get(name)
+            best[name] = (min(ms, prev[0]) if prev else ms, info.iters, info.rel_resid)
+    print("factor ms and iterations:", best)
+    assert best["learned"][0] <= 0.98 * best["mixed"][0]
+    assert abs(best["learned"][1] - best["mixed"][1]) <= 1
+    assert best["learned"][2] <= 1e-8
