@@ -178,8 +178,11 @@ int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info);
  * dot-product partial sums live in a fixed array compiled into the library
  * (static __device__, 256-byte aligned, 4 * 262144 + 1040 doubles, about
  * 8.4 MB, held on every GPU that loads the library until the process exits).
- * Limits: n <= 262144 (else HS_ERR_ARG) and a handle set up with
- * HS_KRYLOV_PCG (else HS_ERR_UNSUPPORTED).  The first call on a device looks
+ * Limits: n <= 262144 (else HS_ERR_ARG); a handle from hs_setup with
+ * HS_KRYLOV_PCG (a GMRES handle or a batched handle from hs_setup_batched,
+ * whose problems each stop on their own residual, gives HS_ERR_UNSUPPORTED);
+ * the current CUDA device must be the one the handle was set up on (else
+ * HS_ERR_ARG, before any device work).  The first call on a device looks
  * up the array's device address and caches it; make that first call before
  * any stream capture.  All calls share the one array and it keeps the last
  * call's contents (this call zeroes or writes everything it reads): calls
@@ -238,14 +241,19 @@ int hs_level_info(hs_handle h, int32_t level, int32_t* size0, int32_t* final_siz
                   int32_t* phase);
 int hs_top_size(hs_handle h, int32_t* ntop);
 
-/* Kernel classes: 0 factor phase (Cholesky + scaling + CPQR + write-back),
- * 1 Schur update, 2 level assembly, 3 dense top, 4 preconditioner apply,
- * 5 Krylov SpMV / vector kernels.  For each class k < nclasses (host arrays,
- * any may be NULL): device milliseconds summed over its launches since setup
- * (CUDA events on the handle's stream; only when options.profile was set),
- * the number of launch sites used, and the algorithmic FP64 flops / bytes of
- * the factorization classes (POTRF s^3/3, scaling s^2 (n+w), CPQR
- * sum_k 4 (s-k)(w-k) + 4 s r n, Schur n^2 f; assembly 20 bytes per nonzero). */
+/* Kernel classes: 0 factor phase (Cholesky + scaling + CPQR + write-back,
+ * one launch per phase), 1 Schur update, 2 level assembly, 3 dense top (and
+ * forming the dense coarse operator), 4 preconditioner apply, 5 Krylov
+ * vector kernels (dots, updates), 6 fused coarse-level factor kernel (all
+ * phases of a level in one launch), 7 SpMV.  For each class k < nclasses
+ * (host arrays, any may be NULL): device milliseconds summed over its
+ * launches since setup (CUDA events on the handle's stream; only when
+ * options.profile was set), the number of launch sites used, and the
+ * algorithmic work: FP64-equivalent flops of the factorization classes
+ * (POTRF s^3/3, scaling s^2 (n+w), CPQR sum_k 4 (s-k)(w-k) + 4 s r n, Schur
+ * n^2 f) and bytes (assembly 20 per nonzero; apply: the stored factor twice,
+ * three vectors per level, the dense coarse operator or top, the two
+ * permutations; SpMV 12 nnz + 24 n per product). */
 int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops,
                     double* bytes);
 int hs_reset_kernel_stats(hs_handle h);
@@ -253,6 +261,14 @@ int hs_reset_kernel_stats(hs_handle h);
 /* Number of this library's kernels launched by the process so far (a kernel
  * inside the solve-phase CUDA graph counts once per graph launch). */
 int hs_launch_count(int64_t* count);
+
+/* Self-check of the reciprocals the factor kernels use for their Cholesky
+ * pivots (Sec. 2: G_s with A_ss = G_s G_s^T) and Householder scalars:
+ * rsqrt_out[i] = 1 / sqrt(x[i]) and rcp_out[i] = 1 / x[i], each an FP32
+ * estimate refined by two Newton-Raphson steps in FP64 (the FP64 square root
+ * and division outside 1e-30 < x < 1e30).  x, rsqrt_out, rcp_out: device
+ * arrays of n doubles, caller-owned; x > 0.  Returns after completion. */
+int hs_eval_pivot_reciprocals(int64_t n, const double* x, double* rsqrt_out, double* rcp_out, void* stream);
 
 /* Measures the FP64 FMA throughput of the current device with a chain of
  * independent fma() operations (8 per thread, 8 CTAs per SM); TFLOP/s out. */

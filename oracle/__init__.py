@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
                            "-fno-fast-math", "-ffp-contract=off",
                            _SRC, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
@@ -49,6 +49,7 @@ def lib():
         L = ctypes.CDLL(build())
         L.or_partition_extruded.argtypes = [I64, P, P, P, P, I32, F64, P, P, P]
         L.or_factor_create.argtypes = [I64, P, P, P, I32, P, P, I32, F64, P, P, P]
+        L.or_factor_create_ex.argtypes = [I64, P, P, P, I32, P, P, I32, F64, I32, I32, P, P, P]
         L.or_factor_free.argtypes = [P]
         L.or_apply.argtypes = [P, P, P]
         L.or_pcg.argtypes = [I64, P, P, P, P, P, P, F64, I32, P, P]
@@ -69,6 +70,8 @@ def lib():
         L.or_dense_cpqr.restype = I32
         L.or_dense_step.argtypes = [I32, I32, I32, P, F64, P]
         L.or_dense_step.restype = I32
+        L.or_dense_step_nodc.argtypes = [I32, I32, I32, P, F64, P]
+        L.or_dense_step_nodc.restype = I32
         L.or_plan_level.argtypes = [I32, P, P, P, P, P, P, P, I64, P, P, I64]
         _lib = L
     return _lib
@@ -137,7 +140,10 @@ class NotSPD(RuntimeError):
 class Factor:
     """Hierarchical_Factor (Algorithm 1) of a CSR matrix, plain FP64 on CPU."""
 
-    def __init__(self, prob, perm, leaf_ptr, depth, tol):
+    def __init__(self, prob, perm, leaf_ptr, depth, tol, nodc=False, threads=1):
+        """nodc: eliminate without deferred compression (plain LoRaSp: A_sw
+        compressed unscaled, Sec. 2 Eq. offdiag); threads: clusters of a phase
+        in parallel (the result does not depend on it)."""
         self.prob = prob
         self._rp, self._ci, self._va = _csr(prob)
         self.perm = np.ascontiguousarray(perm, dtype=np.int32)
@@ -146,11 +152,11 @@ class Factor:
         self.tol = float(tol)
         h = ctypes.c_void_p()
         fl, fc = np.zeros(1, np.int32), np.zeros(1, np.int32)
-        rc = lib().or_factor_create(prob.n, _p(self._rp), _p(self._ci),
-                                    _p(self._va), len(self.leaf_ptr) - 1,
-                                    _p(self.perm), _p(self.leaf_ptr),
-                                    self.depth, self.tol, ctypes.byref(h),
-                                    _p(fl), _p(fc))
+        rc = lib().or_factor_create_ex(prob.n, _p(self._rp), _p(self._ci),
+                                       _p(self._va), len(self.leaf_ptr) - 1,
+                                       _p(self.perm), _p(self.leaf_ptr),
+                                       self.depth, self.tol, int(bool(nodc)), int(threads),
+                                       ctypes.byref(h), _p(fl), _p(fc))
         if rc == ERR_NOT_SPD:
             raise NotSPD(int(fl[0]), int(fc[0]))
         if rc != OK:
@@ -244,15 +250,17 @@ def dense_cpqr(B, eps):
     return int(r), V, tau[:r].copy(), piv[:r].copy(), M
 
 
-def dense_step(A, s, nn, nw, eps):
-    """One scaled low-rank elimination on a dense (s, n, w) matrix.
+def dense_step(A, s, nn, nw, eps, nodc=False):
+    """One scaled low-rank elimination on a dense (s, n, w) matrix (nodc: the
+    step without deferred compression).
 
     Returns (rank, K) with K the matrix on (coarse DOFs, n, w) after the step.
     """
     N = s + nn + nw
     A = np.ascontiguousarray(A, dtype=np.float64)
     out = np.zeros(N * N)
-    r = lib().or_dense_step(s, nn, nw, _p(A), float(eps), _p(out))
+    fn = lib().or_dense_step_nodc if nodc else lib().or_dense_step
+    r = fn(s, nn, nw, _p(A), float(eps), _p(out))
     if r < 0:
         raise NotSPD(-1, -1)
     d = r + nn + nw

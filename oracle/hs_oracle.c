@@ -30,6 +30,17 @@
  *   top                    Algorithm 1: conventional Cholesky when small.
  *   or_apply               Algorithm 2: forward W_i y, recursion, backward W_i^T x.
  *   or_pcg / or_gmres      Sec. 5 (preconditioned Krylov solve).
+ *   step_nodc              the same elimination without deferred compression
+ *                          (the original LoRaSp step that Sec. 2 analyses:
+ *                          Eq. offdiag on the unscaled A_sw, then the
+ *                          rotation of Eq. sparse and the elimination of the
+ *                          fine DOFs, which here also updates the coarse ones).
+ *
+ * or_factor_create_ex runs the clusters of a phase on several threads
+ * (OpenMP) when asked: their own computations in parallel, the Schur updates
+ * in parallel over target rows with every block's contributions in ascending
+ * cluster order, the write-backs in cluster order, so the result is the same
+ * bit for bit as with one thread.
  *
  * Readings where the paper is silent (all shared with the CUDA path by
  * statement only, never by code):
@@ -44,7 +55,10 @@
  *   - a cluster with no fill block has rank 0 and leaves the matrix; every
  *     other cluster keeps a (possibly empty) coarse part and its blocks;
  *   - eliminating the fine part creates a block between every pair of the
- *     cluster's neighbours (structural, even when the update is zero).
+ *     cluster's neighbours (structural, even when the update is zero);
+ *   - without DC the same rank rule applies to the unscaled A_sw, at the
+ *     threshold eps * sqrt(max_i (A_ss)_ii): the threshold DC applies when
+ *     A_ss is a multiple of the identity, expressed in the units of A.
  */
 #include <math.h>
 #include <stdint.h>
@@ -528,13 +542,16 @@ static void bfree(bmat *m) {
 
 typedef struct {
     int c, s, r;   /* cluster, size when processed, rank */
-    double *G;     /* s x s */
+    int nodc;      /* 1: step without deferred compression (step_nodc) */
+    double *G;     /* s x s (with DC) */
     double *V;     /* s x s (first r columns used) */
     double *tau;   /* s */
     int nn;        /* number of n-neighbours */
     int *nq, *nm;  /* their ids and widths when processed */
     int ncols;     /* sum of nm */
     double *C;     /* (s - r) x ncols */
+    double *Gf;    /* without DC: (s - r) x (s - r), Cholesky factor of the fine block */
+    double *Kc;    /* without DC: (s - r) x r */
 } fstep;
 
 typedef struct {
@@ -565,6 +582,7 @@ typedef struct or_factor {
 
 static void step_free(fstep *st) {
     free(st->G); free(st->V); free(st->tau); free(st->nq); free(st->nm); free(st->C);
+    free(st->Gf); free(st->Kc);
 }
 
 void or_factor_free(or_factor *f) {
@@ -590,120 +608,259 @@ static int in_sorted(const int *a, int n, int x) {
     return 0;
 }
 
-/* Process one cluster pi of the current level (Algorithm 1, inner call). */
-static int process_cluster(bmat *m, int pi, const int *adj0, int nadj0, char *gone,
-                           double eps, fstep *st) {
+/*
+ * One cluster of a phase in three parts.  Clusters of a phase share no block
+ * (they are pairwise non-adjacent), so cluster_compute of one reads nothing
+ * that another's Schur update or write-back of the same phase writes; the
+ * Schur updates of a phase touch each target block in ascending cluster
+ * order, as they would one cluster after another.  The results equal those
+ * of processing the clusters of a phase strictly one after another.
+ */
+typedef struct {
+    int nn, nw, ncol, W;
+    int *nl, *wl; /* n-neighbours (blocks of the level input), fill blocks */
+    double *M;    /* transformed block row (s x W): coarse rows 0..r-1 */
+    double *Acc;  /* no DC: coarse diagonal block (r x r) after eliminating f */
+} cwork;
+
+static void cwork_free(cwork *w) {
+    free(w->nl); free(w->wl); free(w->M); free(w->Acc);
+    memset(w, 0, sizeof(*w));
+}
+
+/* Apply reflector k (column k of V, scalar tau) to rows k.. of the s x m
+ * matrix X from the left (X <- H_k X, H_k = I - tau v v^T). */
+static void reflect_rows(int s, const double *V, int k, double tau, int m, double *X) {
+    int i, j;
+    for (j = 0; j < m; j++) {
+        double t = 0.0;
+        for (i = k; i < s; i++) t += V[(size_t)i * s + k] * X[(size_t)i * m + j];
+        t *= tau;
+        for (i = k; i < s; i++) X[(size_t)i * m + j] -= t * V[(size_t)i * s + k];
+    }
+}
+
+/*
+ * Elimination step without deferred compression (plain LoRaSp, Sec. 2,
+ * Eq. offdiag and Eq. sc_old, with the sparsification of Eq. sparse and the
+ * elimination of the fine DOFs as in Sec. 3.1): A_sw itself is compressed,
+ * A_sw ~ U_1 V_1^T with ||V_2|| <= eps (same column-pivoted QR and rank rule
+ * as with DC, on the unscaled block); the block row and column are rotated by
+ * U^T, so that the fine DOFs f = r..s-1 have no fill coupling; then f is
+ * eliminated by Cholesky of (U^T A_ss U)_ff = G_f G_f^T, which updates the
+ * coarse DOFs c = 0..r-1 (diagonal and coupling to n) and the neighbours n:
+ *   K = G_f^-1 [ (U^T A_ss U)_fc | (U^T A_sn)_f ],
+ *   A_cc <- (U^T A_ss U)_cc - K_c^T K_c,  A_cn <- (U^T A_sn)_c - K_c^T K_n,
+ *   A_nn <- A_nn - K_n^T K_n,  A_cw <- V_1^T.
+ * In: Ass (s x s), M = [A_sn | A_sw] (s x W).  Out: M rows 0..r-1 = the
+ * coarse rows [A_cn | V_1^T], st->V / tau (r reflectors), st->Gf, st->Kc,
+ * st->C = K_n, *Acc_out (r x r).  Returns 0 or OR_ERR_NOT_SPD.
+ */
+static int step_nodc(int s, int nn, int nw, double *Ass, double *M, double eps, fstep *st,
+                     double **Acc_out) {
+    int W = nn + nw, r, f, i, j, k;
+    int *piv = (int *)xcalloc((size_t)s + 1, sizeof(int));
+    double *At, *Kc, *Acc, dmax = 0.0;
+    /* the threshold in the units of A: eps times the square root of the
+     * largest diagonal entry of A_ss (the threshold DC applies when A_ss is
+     * a multiple of the identity) */
+    for (i = 0; i < s; i++)
+        if (Ass[(size_t)i * s + i] > dmax) dmax = Ass[(size_t)i * s + i];
+    r = cpqr_apply(s, nn, nw, M, eps * sqrt(dmax), st->V, st->tau, piv); /* Eq. offdiag on A_sw */
+    free(piv);
+    f = s - r;
+    /* U^T A_ss U: the reflectors from the left, then (by symmetry) again on
+     * the transpose, which applies them from the right */
+    At = (double *)xcalloc((size_t)s * (size_t)s, sizeof(double));
+    memcpy(At, Ass, (size_t)s * (size_t)s * sizeof(double));
+    for (k = 0; k < r; k++) reflect_rows(s, st->V, k, st->tau[k], s, At);
+    for (i = 0; i < s; i++)
+        for (j = 0; j < i; j++) {
+            double t = At[(size_t)i * s + j];
+            At[(size_t)i * s + j] = At[(size_t)j * s + i];
+            At[(size_t)j * s + i] = t;
+        }
+    for (k = 0; k < r; k++) reflect_rows(s, st->V, k, st->tau[k], s, At);
+    /* G_f G_f^T = (U^T A_ss U)_ff */
+    st->Gf = (double *)xcalloc((size_t)f * (size_t)f + 1, sizeof(double));
+    for (i = 0; i < f; i++)
+        for (j = 0; j < f; j++) st->Gf[(size_t)i * f + j] = At[(size_t)(r + i) * s + r + j];
+    if (f > 0 && chol_lower(f, st->Gf)) {
+        free(At);
+        return OR_ERR_NOT_SPD;
+    }
+    /* K_c = G_f^-1 (U^T A_ss U)_fc, K_n = G_f^-1 (U^T A_sn)_f */
+    Kc = (double *)xcalloc((size_t)f * (size_t)r + 1, sizeof(double));
+    for (i = 0; i < f; i++)
+        for (j = 0; j < r; j++) Kc[(size_t)i * r + j] = At[(size_t)(r + i) * s + j];
+    lower_solve(f, st->Gf, r, Kc);
+    st->C = (double *)xcalloc((size_t)f * (size_t)nn + 1, sizeof(double));
+    for (i = 0; i < f; i++)
+        for (j = 0; j < nn; j++) st->C[(size_t)i * nn + j] = M[(size_t)(r + i) * W + j];
+    lower_solve(f, st->Gf, nn, st->C);
+    /* the coarse DOFs after eliminating f */
+    Acc = (double *)xcalloc((size_t)r * (size_t)r + 1, sizeof(double));
+    for (i = 0; i < r; i++)
+        for (j = 0; j < r; j++) {
+            double acc = 0.0;
+            for (k = 0; k < f; k++) acc += Kc[(size_t)k * r + i] * Kc[(size_t)k * r + j];
+            Acc[(size_t)i * r + j] = At[(size_t)i * s + j] - acc;
+        }
+    for (i = 0; i < r; i++)
+        for (j = 0; j < nn; j++) {
+            double acc = 0.0;
+            for (k = 0; k < f; k++) acc += Kc[(size_t)k * r + i] * st->C[(size_t)k * nn + j];
+            M[(size_t)i * W + j] -= acc;
+        }
+    st->Kc = Kc;
+    st->r = r;
+    *Acc_out = Acc;
+    free(At);
+    return OR_OK;
+}
+
+/* Part 1: the cluster's own computation (Algorithm 1, inner call): n / w
+ * lists, the block row, the elimination step (with or without DC) and the
+ * stored operators.  Reads only the cluster's own block row. */
+static int cluster_compute(bmat *m, int pi, const int *adj0, int nadj0, double eps, int nodc,
+                           fstep *st, cwork *w) {
     brow *row = &m->rows[pi];
-    int s = m->size[pi], nn = 0, nw = 0, W = 0, i, j, k, t, rc, r;
-    int *nl = (int *)xcalloc((size_t)row->n, sizeof(int));
-    int *wl = (int *)xcalloc((size_t)row->n, sizeof(int));
-    double *M, *Ass;
+    int s = m->size[pi], i, j, t, rc, r = 0, wcol = 0;
+    double *Ass;
+    memset(w, 0, sizeof(*w));
+    w->nl = (int *)xcalloc((size_t)row->n + 1, sizeof(int));
+    w->wl = (int *)xcalloc((size_t)row->n + 1, sizeof(int));
     /* n = present neighbours (blocks of the level input), w = other blocks */
     for (t = 0; t < row->n; t++) {
         int q = row->v[t].q;
         if (q == pi) continue;
-        if (in_sorted(adj0, nadj0, q)) nl[nn++] = q;
-        else wl[nw++] = q;
+        if (in_sorted(adj0, nadj0, q)) w->nl[w->nn++] = q;
+        else w->wl[w->nw++] = q;
     }
+    for (t = 0; t < w->nn; t++) w->ncol += m->size[w->nl[t]];
+    for (t = 0; t < w->nw; t++) wcol += m->size[w->wl[t]];
+    w->W = w->ncol + wcol;
+    st->ncols = w->ncol;
+    w->M = (double *)xcalloc((size_t)s * (size_t)w->W + 1, sizeof(double));
+    /* gather the block row [A_sn | A_sw] */
     {
-        int ncol = 0, wcol = 0;
-        for (t = 0; t < nn; t++) ncol += m->size[nl[t]];
-        for (t = 0; t < nw; t++) wcol += m->size[wl[t]];
-        W = ncol + wcol;
-        st->ncols = ncol;
-        M = (double *)xcalloc((size_t)s * (size_t)W, sizeof(double));
-        /* gather the block row [A_sn | A_sw] */
-        {
-            int c0 = 0;
-            for (t = 0; t < nn + nw; t++) {
-                int q = t < nn ? nl[t] : wl[t - nn];
-                int wq = m->size[q];
-                blk *b = bfind(m, pi, q);
-                for (i = 0; i < s; i++)
-                    for (j = 0; j < wq; j++) M[(size_t)i * W + c0 + j] = b->a[(size_t)i * wq + j];
-                c0 += wq;
-            }
+        int c0 = 0;
+        for (t = 0; t < w->nn + w->nw; t++) {
+            int q = t < w->nn ? w->nl[t] : w->wl[t - w->nn];
+            int wq = m->size[q];
+            blk *b = bfind(m, pi, q);
+            for (i = 0; i < s; i++)
+                for (j = 0; j < wq; j++) w->M[(size_t)i * w->W + c0 + j] = b->a[(size_t)i * wq + j];
+            c0 += wq;
         }
-        Ass = (double *)xcalloc((size_t)s * (size_t)s, sizeof(double));
-        memcpy(Ass, bfind(m, pi, pi)->a, (size_t)s * (size_t)s * sizeof(double));
-        st->V = (double *)xcalloc((size_t)s * (size_t)s, sizeof(double));
-        st->tau = (double *)xcalloc((size_t)s + 1, sizeof(double));
-        rc = step_core(s, ncol, wcol, Ass, M, eps, st->V, st->tau, &r);
+    }
+    Ass = (double *)xcalloc((size_t)s * (size_t)s, sizeof(double));
+    memcpy(Ass, bfind(m, pi, pi)->a, (size_t)s * (size_t)s * sizeof(double));
+    st->V = (double *)xcalloc((size_t)s * (size_t)s, sizeof(double));
+    st->tau = (double *)xcalloc((size_t)s + 1, sizeof(double));
+    st->c = pi;
+    st->s = s;
+    st->nodc = nodc;
+    if (nodc) {
+        rc = step_nodc(s, w->ncol, wcol, Ass, w->M, eps, st, &w->Acc);
+        free(Ass);
+        if (rc) return rc;
+        r = st->r;
+    } else {
+        rc = step_core(s, w->ncol, wcol, Ass, w->M, eps, st->V, st->tau, &r);
         if (rc) {
-            free(M); free(Ass); free(nl); free(wl);
+            free(Ass);
             return rc;
         }
-        st->c = pi; st->s = s; st->r = r; st->G = Ass;
-        st->nn = nn;
-        st->nq = (int *)xcalloc((size_t)nn, sizeof(int));
-        st->nm = (int *)xcalloc((size_t)nn, sizeof(int));
-        for (t = 0; t < nn; t++) {
-            st->nq[t] = nl[t];
-            st->nm[t] = m->size[nl[t]];
-        }
+        st->G = Ass;
+        st->r = r;
         /* C = fine rows of U^T G^-1 A_sn */
-        st->C = (double *)xcalloc((size_t)(s - r) * (size_t)ncol, sizeof(double));
+        st->C = (double *)xcalloc((size_t)(s - r) * (size_t)w->ncol + 1, sizeof(double));
         for (i = r; i < s; i++)
-            for (j = 0; j < ncol; j++) st->C[(size_t)(i - r) * ncol + j] = M[(size_t)i * W + j];
-        /* Schur update of the neighbours (Eq. elim), fill between every pair */
-        {
-            int op = 0;
-            for (t = 0; t < nn; t++) {
-                int p = nl[t], mp = m->size[p], oq = 0, u;
-                for (u = 0; u < nn; u++) {
-                    int q = nl[u], mq = m->size[q];
-                    blk *b = bensure(m, p, q);
-                    for (i = 0; i < mp; i++)
-                        for (j = 0; j < mq; j++) {
-                            double acc = 0.0;
-                            for (k = 0; k < s - r; k++)
-                                acc += st->C[(size_t)k * ncol + op + i] * st->C[(size_t)k * ncol + oq + j];
-                            b->a[(size_t)i * mq + j] -= acc;
-                        }
-                    oq += mq;
-                }
-                op += mp;
+            for (j = 0; j < w->ncol; j++) st->C[(size_t)(i - r) * w->ncol + j] = w->M[(size_t)i * w->W + j];
+    }
+    st->nn = w->nn;
+    st->nq = (int *)xcalloc((size_t)w->nn + 1, sizeof(int));
+    st->nm = (int *)xcalloc((size_t)w->nn + 1, sizeof(int));
+    for (t = 0; t < w->nn; t++) {
+        st->nq[t] = w->nl[t];
+        st->nm[t] = m->size[w->nl[t]];
+    }
+    return OR_OK;
+}
+
+/* The blocks (p, q), p and q n-neighbours of the step, that its Schur update
+ * touches (created empty if absent: fill between every pair of neighbours). */
+static void cluster_schur_blocks(bmat *m, const cwork *w) {
+    int t, u;
+    for (t = 0; t < w->nn; t++)
+        for (u = 0; u < w->nn; u++) bensure(m, w->nl[t], w->nl[u]);
+}
+
+/* Part 2 (Eq. elim): row p's share of the step's Schur update,
+ * A(p, q) -= C(:, p)^T C(:, q) for every n-neighbour q; t = p's position. */
+static void cluster_schur_row(bmat *m, const fstep *st, const cwork *w, int t) {
+    int p = w->nl[t], mp = m->size[p], op = 0, oq = 0, u, i, j, k, f = st->s - st->r;
+    for (u = 0; u < t; u++) op += m->size[w->nl[u]];
+    for (u = 0; u < w->nn; u++) {
+        int q = w->nl[u], mq = m->size[q];
+        blk *b = bfind(m, p, q);
+        for (i = 0; i < mp; i++)
+            for (j = 0; j < mq; j++) {
+                double acc = 0.0;
+                for (k = 0; k < f; k++)
+                    acc += st->C[(size_t)k * w->ncol + op + i] * st->C[(size_t)k * w->ncol + oq + j];
+                b->a[(size_t)i * mq + j] -= acc;
             }
+        oq += mq;
+    }
+}
+
+/* Part 3: write back the coarse part (Eq. perm).  With DC its diagonal is the
+ * identity (the scaled diagonal block); without DC it is the coarse block
+ * left by eliminating the fine DOFs. */
+static void cluster_writeback(bmat *m, int pi, const fstep *st, const cwork *w, char *gone) {
+    brow *row = &m->rows[pi];
+    int r = st->r, t, i, j;
+    if (w->nw == 0) {
+        /* no fill block: rank 0, the cluster leaves the matrix */
+        for (t = 0; t < row->n; t++) {
+            int q = row->v[t].q;
+            if (q != pi) bremove(m, q, pi);
         }
-        /* write back the coarse part (Eq. perm) */
-        if (nw == 0) {
-            /* no fill block: rank 0, the cluster leaves the matrix */
-            for (t = 0; t < row->n; t++) {
-                int q = row->v[t].q;
-                if (q != pi) bremove(m, q, pi);
-            }
-            for (t = 0; t < row->n; t++) free(row->v[t].a);
-            row->n = 0;
-            m->size[pi] = 0;
-            gone[pi] = 1;
-        } else {
-            int c0 = 0;
-            for (t = 0; t < nn + nw; t++) {
-                int q = t < nn ? nl[t] : wl[t - nn];
-                int wq = m->size[q];
-                blk *b = bfind(m, pi, q), *bt = bfind(m, q, pi);
-                double *a = (double *)xcalloc((size_t)r * (size_t)wq, sizeof(double));
-                double *at = (double *)xcalloc((size_t)wq * (size_t)r, sizeof(double));
-                for (i = 0; i < r; i++)
-                    for (j = 0; j < wq; j++) {
-                        a[(size_t)i * wq + j] = M[(size_t)i * W + c0 + j];
-                        at[(size_t)j * r + i] = M[(size_t)i * W + c0 + j];
-                    }
-                free(b->a); b->a = a;
-                free(bt->a); bt->a = at;
-                c0 += wq;
-            }
-            {
-                blk *d = bfind(m, pi, pi);
-                free(d->a);
-                d->a = (double *)xcalloc((size_t)r * (size_t)r, sizeof(double));
-                for (i = 0; i < r; i++) d->a[(size_t)i * r + i] = 1.0;
-            }
-            m->size[pi] = r;
+        for (t = 0; t < row->n; t++) free(row->v[t].a);
+        row->n = 0;
+        m->size[pi] = 0;
+        gone[pi] = 1;
+        return;
+    }
+    {
+        int c0 = 0;
+        for (t = 0; t < w->nn + w->nw; t++) {
+            int q = t < w->nn ? w->nl[t] : w->wl[t - w->nn];
+            int wq = m->size[q];
+            blk *b = bfind(m, pi, q), *bt = bfind(m, q, pi);
+            double *a = (double *)xcalloc((size_t)r * (size_t)wq + 1, sizeof(double));
+            double *at = (double *)xcalloc((size_t)wq * (size_t)r + 1, sizeof(double));
+            for (i = 0; i < r; i++)
+                for (j = 0; j < wq; j++) {
+                    a[(size_t)i * wq + j] = w->M[(size_t)i * w->W + c0 + j];
+                    at[(size_t)j * r + i] = w->M[(size_t)i * w->W + c0 + j];
+                }
+            free(b->a); b->a = a;
+            free(bt->a); bt->a = at;
+            c0 += wq;
         }
     }
-    free(M); free(nl); free(wl);
-    return OR_OK;
+    {
+        blk *d = bfind(m, pi, pi);
+        free(d->a);
+        d->a = (double *)xcalloc((size_t)r * (size_t)r + 1, sizeof(double));
+        for (i = 0; i < r; i++)
+            for (j = 0; j < r; j++)
+                d->a[(size_t)i * r + j] = w->Acc ? w->Acc[(size_t)i * r + j] : (i == j ? 1.0 : 0.0);
+    }
+    m->size[pi] = r;
 }
 
 /* Level-0 block matrix from CSR in partition order. */
@@ -766,11 +923,12 @@ static void build_parent(const bmat *m, bmat *pm) {
  * Hierarchical_Factor (Algorithm 1) with `depth` levels of scaled low-rank
  * elimination, then dense Cholesky of the remaining coarse system.
  */
-int or_factor_create(int64_t n64, const int64_t *rowptr, const int32_t *col,
-                     const double *val, int32_t nleaf, const int32_t *perm,
-                     const int32_t *leaf_ptr, int32_t depth, double eps,
-                     or_factor **out, int32_t *fail_level, int32_t *fail_cluster) {
-    int n = (int)n64, l, i, c;
+int or_factor_create_ex(int64_t n64, const int64_t *rowptr, const int32_t *col,
+                        const double *val, int32_t nleaf, const int32_t *perm,
+                        const int32_t *leaf_ptr, int32_t depth, double eps, int32_t nodc,
+                        int32_t nthreads, or_factor **out, int32_t *fail_level,
+                        int32_t *fail_cluster) {
+    int n = (int)n64, l, i, c, k, t;
     bmat m;
     or_factor *f;
     *out = NULL;
@@ -826,13 +984,28 @@ int or_factor_create(int64_t n64, const int64_t *rowptr, const int32_t *col,
                     if (sel[m.rows[c].v[t].q]) { ok = 0; break; }
                 if (ok) { sel[c] = 1; order[cnt++] = c; }
             }
-            for (i = 0; i < cnt; i++) {
-                int pi = order[i], rc;
-                rc = process_cluster(&m, pi, adj0[pi], nadj0[pi], gone, eps, &lv->steps[nproc]);
-                if (rc) {
+            {
+                /* the phase: every cluster's own computation (in parallel
+                 * when threads > 1), the first failure in cluster order
+                 * reported; then the Schur updates, target row by target row
+                 * (each row's blocks in ascending cluster order); then the
+                 * write-backs in cluster order */
+                cwork *wk = (cwork *)xcalloc((size_t)cnt + 1, sizeof(cwork));
+                int *rcs = (int *)xcalloc((size_t)cnt + 1, sizeof(int));
+                int fail = -1, nrow = 0, *rp, *rlist, *rpos, *tp;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+                for (i = 0; i < cnt; i++)
+                    rcs[i] = cluster_compute(&m, order[i], adj0[order[i]], nadj0[order[i]], eps, nodc,
+                                             &lv->steps[nproc + i], &wk[i]);
+                for (i = 0; i < cnt && fail < 0; i++)
+                    if (rcs[i]) fail = i;
+                if (fail >= 0) {
+                    int rc = rcs[fail];
                     if (fail_level) *fail_level = l;
-                    if (fail_cluster) *fail_cluster = pi;
-                    lv->nsteps = nproc;
+                    if (fail_cluster) *fail_cluster = order[fail];
+                    lv->nsteps = nproc + cnt; /* freed with the factor */
+                    for (i = 0; i < cnt; i++) cwork_free(&wk[i]);
+                    free(wk); free(rcs);
                     for (c = 0; c < nc; c++) free(adj0[c]);
                     free(adj0); free(nadj0); free(processed); free(gone); free(sel); free(order);
                     bfree(&m);
@@ -840,10 +1013,39 @@ int or_factor_create(int64_t n64, const int64_t *rowptr, const int32_t *col,
                     or_factor_free(f);
                     return rc;
                 }
-                nproc++;
-                processed[pi] = 1;
-                lv->phase[pi] = ph;
-                done++;
+                for (i = 0; i < cnt; i++) cluster_schur_blocks(&m, &wk[i]);
+                /* per target row p: the (step, position of p) pairs, ascending step */
+                rp = (int *)xcalloc((size_t)nc + 1, sizeof(int));
+                for (i = 0; i < cnt; i++)
+                    for (t = 0; t < wk[i].nn; t++) rp[wk[i].nl[t] + 1]++;
+                for (c = 0; c < nc; c++) rp[c + 1] += rp[c];
+                rlist = (int *)xcalloc((size_t)rp[nc] + 1, sizeof(int));
+                rpos = (int *)xcalloc((size_t)rp[nc] + 1, sizeof(int));
+                tp = (int *)xcalloc((size_t)nc + 1, sizeof(int));
+                memcpy(tp, rp, (size_t)nc * sizeof(int));
+                for (i = 0; i < cnt; i++)
+                    for (t = 0; t < wk[i].nn; t++) {
+                        int p = wk[i].nl[t];
+                        rlist[tp[p]] = i;
+                        rpos[tp[p]++] = t;
+                    }
+                for (c = 0; c < nc; c++)
+                    if (rp[c + 1] > rp[c]) tp[nrow++] = c;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+                for (k = 0; k < nrow; k++) {
+                    int e, p = tp[k];
+                    for (e = rp[p]; e < rp[p + 1]; e++)
+                        cluster_schur_row(&m, &lv->steps[nproc + rlist[e]], &wk[rlist[e]], rpos[e]);
+                }
+                for (i = 0; i < cnt; i++) {
+                    cluster_writeback(&m, order[i], &lv->steps[nproc + i], &wk[i], gone);
+                    processed[order[i]] = 1;
+                    lv->phase[order[i]] = ph;
+                    done++;
+                    cwork_free(&wk[i]);
+                }
+                nproc += cnt;
+                free(wk); free(rcs); free(rp); free(rlist); free(rpos); free(tp);
             }
             ph++;
         }
@@ -891,13 +1093,23 @@ int or_factor_create(int64_t n64, const int64_t *rowptr, const int32_t *col,
         for (l = 0; l < depth; l++)
             for (i = 0; i < f->lev[l].nsteps; i++) {
                 fstep *st = &f->lev[l].steps[i];
-                bytes += 8 * ((int64_t)st->s * st->s + (int64_t)st->s * st->r +
-                              (int64_t)(st->s - st->r) * st->ncols);
+                int64_t fs = st->s - st->r;
+                bytes += 8 * ((st->nodc ? fs * fs + fs * st->r : (int64_t)st->s * st->s) +
+                              (int64_t)st->s * st->r + fs * st->ncols);
             }
         f->factor_bytes = bytes;
     }
     *out = f;
     return OR_OK;
+}
+
+/* Hierarchical_Factor with deferred compression, one thread. */
+int or_factor_create(int64_t n64, const int64_t *rowptr, const int32_t *col,
+                     const double *val, int32_t nleaf, const int32_t *perm,
+                     const int32_t *leaf_ptr, int32_t depth, double eps,
+                     or_factor **out, int32_t *fail_level, int32_t *fail_cluster) {
+    return or_factor_create_ex(n64, rowptr, col, val, nleaf, perm, leaf_ptr, depth, eps, 0, 1, out,
+                               fail_level, fail_cluster);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -928,8 +1140,21 @@ void or_apply(const or_factor *f, const double *r, double *z) {
             const fstep *st = &lv->steps[t];
             double *ys = yl + lv->off[st->c];
             int oc = 0, u;
-            lower_solve_vec(st->s, st->G, ys);
-            for (k = 0; k < st->r; k++) apply_reflector(st->s, st->V, k, st->tau[k], ys);
+            if (st->nodc) {
+                /* rotate by U^T, then eliminate f: y_f <- G_f^-1 y_f,
+                 * y_c <- y_c - K_c^T y_f (y_n below, with C = K_n) */
+                int f = st->s - st->r, j;
+                for (k = 0; k < st->r; k++) apply_reflector(st->s, st->V, k, st->tau[k], ys);
+                lower_solve_vec(f, st->Gf, ys + st->r);
+                for (j = 0; j < st->r; j++) {
+                    double acc = 0.0;
+                    for (k = 0; k < f; k++) acc += st->Kc[(size_t)k * st->r + j] * ys[st->r + k];
+                    ys[j] -= acc;
+                }
+            } else {
+                lower_solve_vec(st->s, st->G, ys);
+                for (k = 0; k < st->r; k++) apply_reflector(st->s, st->V, k, st->tau[k], ys);
+            }
             for (u = 0; u < st->nn; u++) {
                 double *yq = yl + lv->off[st->nq[u]];
                 int j;
@@ -983,8 +1208,20 @@ void or_apply(const or_factor *f, const double *r, double *z) {
                 }
                 oc += st->nm[u];
             }
-            for (k = st->r - 1; k >= 0; k--) apply_reflector(st->s, st->V, k, st->tau[k], ys);
-            lower_t_solve_vec(st->s, st->G, ys);
+            if (st->nodc) {
+                /* x_f <- G_f^-T (x_f - K_c x_c), then rotate back by U */
+                int f = st->s - st->r, j;
+                for (k = 0; k < f; k++) {
+                    double acc = 0.0;
+                    for (j = 0; j < st->r; j++) acc += st->Kc[(size_t)k * st->r + j] * ys[j];
+                    ys[st->r + k] -= acc;
+                }
+                lower_t_solve_vec(f, st->Gf, ys + st->r);
+                for (k = st->r - 1; k >= 0; k--) apply_reflector(st->s, st->V, k, st->tau[k], ys);
+            } else {
+                for (k = st->r - 1; k >= 0; k--) apply_reflector(st->s, st->V, k, st->tau[k], ys);
+                lower_t_solve_vec(st->s, st->G, ys);
+            }
         }
         free(y[l + 1]);
     }
@@ -1241,6 +1478,53 @@ int32_t or_dense_step(int32_t s, int32_t nn, int32_t nw, const double *A, double
     for (i = 0; i < W; i++)
         for (j = 0; j < W; j++) out[(r + i) * d + r + j] = R[i * W + j];
     free(Ass); free(M); free(V); free(tau); free(R);
+    return r;
+}
+
+/*
+ * The same step without deferred compression (step_nodc, as the level loop
+ * runs it) on a dense (s, n, w) matrix; out (d x d, d = r + nn + nw) is the
+ * matrix on (coarse DOFs, n, w) afterwards: the coarse block left by
+ * eliminating the fine DOFs, its coupling to n and V_1^T to w, A_nn minus
+ * the fine elimination, A_nw, A_ww.  Returns the rank, or -1 if not SPD.
+ */
+int32_t or_dense_step_nodc(int32_t s, int32_t nn, int32_t nw, const double *A, double eps,
+                           double *out) {
+    int N = s + nn + nw, W = nn + nw, i, j, k, r, d, f;
+    double *Ass = (double *)xcalloc((size_t)s * s, sizeof(double));
+    double *M = (double *)xcalloc((size_t)s * W + 1, sizeof(double));
+    double *Acc = NULL;
+    fstep st;
+    memset(&st, 0, sizeof(st));
+    st.V = (double *)xcalloc((size_t)s * s, sizeof(double));
+    st.tau = (double *)xcalloc((size_t)s + 1, sizeof(double));
+    for (i = 0; i < s; i++)
+        for (j = 0; j < s; j++) Ass[i * s + j] = A[i * N + j];
+    for (i = 0; i < s; i++)
+        for (j = 0; j < W; j++) M[i * W + j] = A[i * N + s + j];
+    if (step_nodc(s, nn, nw, Ass, M, eps, &st, &Acc)) {
+        free(Ass); free(M); free(Acc); step_free(&st);
+        return -1;
+    }
+    r = st.r;
+    f = s - r;
+    d = r + W;
+    for (i = 0; i < d * d; i++) out[i] = 0.0;
+    for (i = 0; i < r; i++)
+        for (j = 0; j < r; j++) out[i * d + j] = Acc[i * r + j];
+    for (i = 0; i < r; i++)
+        for (j = 0; j < W; j++) {
+            out[i * d + r + j] = M[i * W + j];
+            out[(r + j) * d + i] = M[i * W + j];
+        }
+    for (i = 0; i < W; i++)
+        for (j = 0; j < W; j++) {
+            double acc = 0.0;
+            if (i < nn && j < nn)
+                for (k = 0; k < f; k++) acc += st.C[(size_t)k * nn + i] * st.C[(size_t)k * nn + j];
+            out[(r + i) * d + r + j] = A[(s + i) * N + s + j] - acc;
+        }
+    free(Ass); free(M); free(Acc); step_free(&st);
     return r;
 }
 

@@ -896,7 +896,13 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
 // ---------------------------------------------------------------------------
 // Handle
 // ---------------------------------------------------------------------------
-enum { KC_FACTOR = 0, KC_SCHUR = 1, KC_ASSEMBLY = 2, KC_TOP = 3, KC_APPLY = 4, KC_KRYLOV = 5, KC_N = 6 };
+// kernel classes of the profile: the per-phase factor kernel (level-wise
+// launches), Schur updates, assembly, dense tops, preconditioner applies,
+// Krylov vector kernels, the fused coarse-level factor kernel and the SpMV
+enum {
+    KC_FACTOR = 0, KC_SCHUR = 1, KC_ASSEMBLY = 2, KC_TOP = 3, KC_APPLY = 4, KC_KRYLOV = 5, KC_FACTOR_FUSED = 6,
+    KC_SPMV = 7, KC_N = 8
+};
 
 struct Level {
     int nc = 0;
@@ -978,7 +984,8 @@ struct hs_factor_s {
         int64_t leaf_lo, leaf_hi, dof_lo, dof_hi;
         int depth;
     };
-    int64_t n = 0;
+    int64_t n = 0, nnz = 0;
+    double apply_bytes = 0;  // algorithmic bytes of one preconditioner apply
     std::vector<Group> groups;
     std::vector<int64_t> prob_ptr;  // DOF offsets of the problems (original order)
     DBuf d_model;                   // rank predictor (options.rank_model), device copy
@@ -1348,7 +1355,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         int max_items = 1;
         for (int ph = 0; ph < L.nphases; ph++)
             max_items = std::max({max_items, L.ph_task[ph + 1] - L.ph_task[ph], L.ph_target[ph + 1] - L.ph_target[ph]});
-        h->prof.begin(KC_FACTOR, st);
+        h->prof.begin(KC_FACTOR_FUSED, st);
         CK(launch_factor_level_fused(st, L.d_tasks.as<TaskDev>(), d_pht.as<int32_t>(), d_targets.as<TargetDev>(),
                                      d_phg.as<int32_t>(), d_contribs.as<ContribDev>(), L.nphases,
                                      L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
@@ -1356,7 +1363,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                                      L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l,
                                      L.smax, L.wmax, L.lmax, mcap, max_items, d_bar.as<unsigned>(), feat,
                                      h->d_model.as<float>()));
-        h->prof.end(KC_FACTOR, st);
+        h->prof.end(KC_FACTOR_FUSED, st);
     }
     for (int ph = 0; ph < (fused ? 0 : L.nphases); ph++) {
         const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
@@ -1489,7 +1496,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         L.flops_factor += f;
         L.flops_schur += ncol * ncol * (s - r);  // symmetric half, FMA = 2
     }
-    h->work_flops[KC_FACTOR] += L.flops_factor;
+    h->work_flops[fused ? KC_FACTOR_FUSED : KC_FACTOR] += L.flops_factor;
     h->work_flops[KC_SCHUR] += L.flops_schur;
 }
 
@@ -1563,6 +1570,7 @@ std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& f
 }
 
 void build_apply_graph(hs_factor_s* h);
+double apply_work_bytes(const hs_factor_s* h);
 
 // Partitions every problem of a block-diagonal batch on its own (Sec. 4.2)
 // and concatenates the trees: problem p's leaves follow problem p-1's.
@@ -1652,6 +1660,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         tr.mark("  pattern download");
     }
     const int64_t nnz = rp[n];
+    h->nnz = nnz;
     {
         std::atomic<int> bad{0};
         parallel_ranges(n, 1 << 16, [&](int64_t lo, int64_t hi, int) {
@@ -1993,7 +2002,35 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     CK(cudaStreamSynchronize(st));
     tr.mark("top");
     build_apply_graph(h);
+    h->apply_bytes = apply_work_bytes(h);
     tr.mark("apply graph");
+}
+
+// Algorithmic bytes of one apply (Algorithm 2): every stored factor entry
+// (W = U^T G^-1 and the n-columns of C per cluster) is read once forward and
+// once backward; per level the vector is read and written in each direction
+// plus the staged neighbour updates (three vectors); the dense coarse
+// operator (or the top's lower triangle twice) once; the two permutations.
+double apply_work_bytes(const hs_factor_s* h) {
+    const double elt = h->fp32 ? 4.0 : 8.0;
+    const int D = (int)h->lev.size();
+    const int lc = (h->groups.size() > 1) ? D : h->first_coarse;
+    double bytes = 40.0 * (double)h->n;
+    for (int l = 0; l < D; l++) {
+        const Level& L = *h->lev[l];
+        if (l >= lc && h->coarse_dense) break;  // folded into the dense operator
+        double fac = 0.0;
+        for (size_t ti = 0; ti < L.tasks.size(); ti++) {
+            const TaskDev& t = L.tasks[ti];
+            const int32_t* mt = L.hmeta.data() + t.meta;
+            const int ncols = t.nn > 0 ? mt[1 + 2 * (t.nn - 1)] + mt[2 + 2 * (t.nn - 1)] : 0;
+            fac += (double)t.s * t.s + (double)(t.s - mt[0]) * ncols;
+        }
+        bytes += 2.0 * elt * fac + 3.0 * 8.0 * (double)L.slot[L.nc];
+    }
+    if (h->coarse_dense) bytes += 8.0 * (double)h->ncoarse * h->ncoarse + 16.0 * h->ncoarse;
+    else for (const TopDev& t : h->tops) bytes += 8.0 * (double)t.n * t.n;
+    return bytes;
 }
 
 // First level handled by the single-CTA coarse kernel: every level from there
@@ -2194,6 +2231,7 @@ void apply_impl(hs_factor_s* h, const double* r, double* z) {
     cudaStream_t st = h->st;
     double* y0 = h->lev.empty() ? h->d_ytop.as<double>() : h->lev[0]->d_y.as<double>();
     h->prof.begin(KC_APPLY, st);
+    h->work_bytes[KC_APPLY] += h->apply_bytes;
     CK(launch_permute(st, h->n, h->d_perm.as<int32_t>(), r, y0, 0));
     if (h->apply_graph) {
         CK(cudaGraphLaunch(h->apply_graph, st));
@@ -2210,6 +2248,16 @@ double read_scalar(hs_factor_s* h, const double* d) {
     return v;
 }
 
+// y = A x with the handle's CSR copy (profiled as its own class; algorithmic
+// bytes 12 nnz + 24 n: values and column indices once, row pointers, x and y)
+void spmv_prof(hs_factor_s* h, const double* x, double* y) {
+    const int64_t n = h->n;
+    h->prof.begin(KC_SPMV, h->st);
+    CK(launch_spmv(h->st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), x, y));
+    h->prof.end(KC_SPMV, h->st);
+    h->work_bytes[KC_SPMV] += 12.0 * (double)h->nnz + 24.0 * (double)n;
+}
+
 int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
     cudaStream_t st = h->st;
     const int64_t n = h->n;
@@ -2222,11 +2270,7 @@ int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
     h->d_scal.ensure(sizeof(double) * 8);
     double* part = h->d_part.as<double>();
     double* sc = h->d_scal.as<double>();  // 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb
-    auto spmv = [&](const double* xx, double* yy) {
-        h->prof.begin(KC_KRYLOV, st);
-        CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), xx, yy));
-        h->prof.end(KC_KRYLOV, st);
-    };
+    auto spmv = [&](const double* xx, double* yy) { spmv_prof(h, xx, yy); };
     auto dot = [&](const double* a, const double* bb, double* out) {
         h->prof.begin(KC_KRYLOV, st);
         CK(launch_dot(st, n, a, bb, part, out));
@@ -2327,8 +2371,8 @@ int pcg_batched_impl(hs_factor_s* h, const double* b, double* x, int32_t* iters,
         kr(launch_bpcg_book(st, np, 1, rtol, sc, fl, cnt));
         h->prof.end(KC_KRYLOV, st);
         if (it >= h->opt.maxit) break;
+        spmv_prof(h, p, q);
         h->prof.begin(KC_KRYLOV, st);
-        kr(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), p, q));
         kr(launch_seg_dot(st, np, pp, p, q, sc, BS_PQ));
         kr(launch_bpcg_vec(st, 0, np, ml, pp, sc, fl, p, q, x, r));
         kr(launch_seg_dot(st, np, pp, r, r, sc, BS_RR));
@@ -2337,8 +2381,8 @@ int pcg_batched_impl(hs_factor_s* h, const double* b, double* x, int32_t* iters,
         it++;
         if (counts().first > 0) {
             // true residual b - A x of every problem; the candidates stop or restart
+            spmv_prof(h, x, q);
             h->prof.begin(KC_KRYLOV, st);
-            kr(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), x, q));
             kr(launch_axpby(st, n, 1.0, b, -1.0, q));
             kr(launch_seg_dot(st, np, pp, q, q, sc, BS_RRT));
             kr(launch_bpcg_book(st, np, 3, rtol, sc, fl, cnt));
@@ -2402,7 +2446,7 @@ int gmres_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
     double rn = bn;
     for (;;) {
         // true residual (iterative refinement restart)
-        CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), x, w));
+        spmv_prof(h, x, w);
         CK(launch_axpby(st, n, 1.0, b, -1.0, w));
         const double beta = norm(w);
         rn = beta;
@@ -2414,9 +2458,8 @@ int gmres_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
         int kk = 0;
         for (int j = 0; j < m && it < h->opt.maxit; j++) {
             apply_impl(h, V + (size_t)j * n, Z + (size_t)j * n);
+            spmv_prof(h, Z + (size_t)j * n, w);
             h->prof.begin(KC_KRYLOV, st);
-            CK(launch_spmv(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(),
-                           Z + (size_t)j * n, w));
             // classical Gram-Schmidt, twice
             CK(launch_gemv_t(st, n, j + 1, V, n, w, part, dh));
             CK(launch_gmres_update(st, n, j + 1, dh, V, n, w, -1.0));
@@ -2830,7 +2873,15 @@ int hs_krylov(hs_handle h, const double* b, double* x, hs_info* info) {
 int hs_krylov_noalloc(hs_handle h, const double* b, double* x, hs_info* info) {
     if (!h || !b || !x) return HS_ERR_ARG;
     if (h->n > kNoAllocMaxN) return HS_ERR_ARG;               // beyond the fixed scratch
-    if (h->opt.krylov != HS_KRYLOV_PCG) return HS_ERR_UNSUPPORTED;
+    // one PCG over one operator: GMRES handles and batched handles (whose
+    // problems stop one by one) are not served
+    if (h->opt.krylov != HS_KRYLOV_PCG || !h->prob_ptr.empty()) return HS_ERR_UNSUPPORTED;
+    {
+        // the scratch address is looked up on the current device, which must
+        // be the one the handle's factor and stream live on
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) return HS_ERR_ARG;
+    }
     hs_info tmp{};
     hs_info* inf = info ? info : &tmp;
     const double t0 = now_s();
@@ -3019,6 +3070,15 @@ int hs_launch_count(int64_t* count) {
     if (!count) return HS_ERR_ARG;
     *count = launch_count();
     return HS_OK;
+}
+
+int hs_eval_pivot_reciprocals(int64_t n, const double* x, double* rsqrt_out, double* rcp_out, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !rsqrt_out || !rcp_out))) return HS_ERR_ARG;
+    return run_guarded([&] {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        CK(launch_eval_recip(st, n, x, rsqrt_out, rcp_out));
+        CK(cudaStreamSynchronize(st));
+    });
 }
 
 int hs_measure_fp64_peak(void* stream, double* tflops) {

@@ -1831,6 +1831,23 @@ cudaError_t noalloc_scratch(double** ptr) {
     return cudaSuccess;
 }
 
+// Evaluates the Cholesky pivot helpers element by element (a self-check of
+// the Newton-refined reciprocals against CUDA's own operations).
+__global__ void k_eval_recip(int64_t n, const double* x, double* rs, double* rc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    rs[i] = rsqrt_newton(v);
+    rc[i] = rcp_newton(v);
+}
+
+cudaError_t launch_eval_recip(cudaStream_t st, int64_t n, const double* x, double* rs, double* rc) {
+    if (n <= 0) return cudaSuccess;
+    k_eval_recip<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, rs, rc);
+    counted();
+    return cudaGetLastError();
+}
+
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void launch_count_add(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 

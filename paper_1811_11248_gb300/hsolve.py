@@ -21,7 +21,7 @@ HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_UNSUPPORTED, HS_ERR_TIMEOUT = 4, 5, 6, 7
 HS_MEM_HOST, HS_MEM_DEVICE = 0, 1
 HS_PREC_FP64, HS_PREC_MIXED = 0, 1
 HS_KRYLOV_PCG, HS_KRYLOV_GMRES = 0, 1
-KERNEL_CLASSES = ("factor", "schur", "assembly", "top", "apply", "krylov")
+KERNEL_CLASSES = ("factor", "schur", "assembly", "top", "apply", "krylov", "factor_fused", "spmv")
 
 P = ctypes.c_void_p
 I32, I64, F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -85,6 +85,7 @@ def lib():
     L.hs_kernel_stats.argtypes = [P, I32, P, P, P, P]
     L.hs_reset_kernel_stats.argtypes = [P]
     L.hs_measure_fp64_peak.argtypes = [P, ctypes.POINTER(F64)]
+    L.hs_eval_pivot_reciprocals.argtypes = [I64, P, P, P, P]
     L.hs_launch_count.argtypes = [ctypes.POINTER(I64)]
     L.hs_setup_batched.argtypes = [I32, P, I64, P, P, P, ctypes.POINTER(hs_options), ctypes.POINTER(P),
                                    ctypes.POINTER(hs_info)]
@@ -109,7 +110,7 @@ EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_s
             "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
             "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str", "hs_setup_batched",
             "hs_krylov_batched", "hs_num_problems", "hs_problem_info", "hs_mlp_forward", "hs_mlp_grad",
-            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples", "hs_plan_level")
+            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples", "hs_plan_level", "hs_eval_pivot_reciprocals")
 MLP_NIN, MLP_NPARAM, MLP_MAX_BATCH = 8, 4801, 256
 
 
@@ -128,6 +129,19 @@ def _ptr(x):
     if isinstance(x, int):
         return P(x)
     raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _dvec(t, n, name):
+    """Pointer of a device vector argument: a contiguous CUDA float64 tensor of
+    n elements (the kernels read and write exactly n doubles there, so a wrong
+    buffer is refused here instead of being accessed out of bounds)."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != "torch.float64":
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return _ptr(t)
 
 
 def _check(rc, where, info=None):
@@ -210,11 +224,13 @@ class Handle:
             pass
 
     def hs_apply(self, r, z):
-        _check(lib().hs_apply(self._h, _ptr(r), _ptr(z)), "hs_apply")
+        if r.data_ptr() == z.data_ptr():
+            raise ValueError("r and z may not alias")
+        _check(lib().hs_apply(self._h, _dvec(r, self.n, "r"), _dvec(z, self.n, "z")), "hs_apply")
 
     def hs_krylov(self, b, x, check=True):
         info = hs_info()
-        rc = lib().hs_krylov(self._h, _ptr(b), _ptr(x), ctypes.byref(info))
+        rc = lib().hs_krylov(self._h, _dvec(b, self.n, "b"), _dvec(x, self.n, "x"), ctypes.byref(info))
         if check:
             _check(rc, "hs_krylov", info)
         return info, rc
@@ -222,7 +238,7 @@ class Handle:
     def hs_krylov_noalloc(self, b, x, check=True):
         """PCG with the library's fixed device scratch (allocates nothing)."""
         info = hs_info()
-        rc = lib().hs_krylov_noalloc(self._h, _ptr(b), _ptr(x), ctypes.byref(info))
+        rc = lib().hs_krylov_noalloc(self._h, _dvec(b, self.n, "b"), _dvec(x, self.n, "x"), ctypes.byref(info))
         if check:
             _check(rc, "hs_krylov_noalloc", info)
         return info, rc
@@ -260,7 +276,8 @@ class Handle:
         it = np.zeros(npb, np.int32)
         rr = np.zeros(npb)
         info = hs_info()
-        rc = lib().hs_krylov_batched(self._h, _ptr(b), _ptr(x), _ptr(it), _ptr(rr), ctypes.byref(info))
+        rc = lib().hs_krylov_batched(self._h, _dvec(b, self.n, "b"), _dvec(x, self.n, "x"), _ptr(it), _ptr(rr),
+                                     ctypes.byref(info))
         if check:
             _check(rc, "hs_krylov_batched", info)
         return info, rc, it, rr
@@ -339,6 +356,14 @@ def hs_launch_count():
     v = I64()
     _check(lib().hs_launch_count(ctypes.byref(v)), "hs_launch_count")
     return int(v.value)
+
+
+def hs_eval_pivot_reciprocals(x, rsqrt_out, rcp_out, stream=None):
+    """Device tensors of n float64: the factor kernels' 1/sqrt(x) and 1/x."""
+    n = x.numel()
+    _check(lib().hs_eval_pivot_reciprocals(n, _dvec(x, n, "x"), _dvec(rsqrt_out, n, "rsqrt_out"),
+                                           _dvec(rcp_out, n, "rcp_out"), P(stream) if stream else None),
+           "hs_eval_pivot_reciprocals")
 
 
 def hs_measure_fp64_peak(stream=None):

@@ -38,6 +38,24 @@ def _setup(hs, p, **kw):
     return hs.hs_setup(p.n, p.rowptr, p.col, p.val, opt=opt)
 
 
+def _device_memory():
+    """(bytes in use in the device's default memory pool, free device bytes),
+    read through the CUDA driver API: the library allocates from that pool
+    (cudaMallocAsync), and any cudaMalloc would lower the free memory."""
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev = ctypes.c_int()
+    assert cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    used = ctypes.c_uint64()
+    CU_MEMPOOL_ATTR_USED_MEM_CURRENT = 7
+    assert cu.cuMemPoolGetAttribute(pool, CU_MEMPOOL_ATTR_USED_MEM_CURRENT, ctypes.byref(used)) == 0
+    free, total = ctypes.c_size_t(), ctypes.c_size_t()
+    assert cu.cuMemGetInfo_v2(ctypes.byref(free), ctypes.byref(total)) == 0
+    return int(used.value), int(free.value)
+
+
 def _close(x, xr, info, info_r):
     assert abs(info.iters - info_r.iters) <= 1
     assert info.rel_resid <= 1e-8
@@ -53,12 +71,37 @@ def test_noalloc_matches_krylov_on_consecutive_calls(hs):
     ref2 = torch.empty_like(b1)
     info_r1, _ = h.hs_krylov(b1, ref1)
     info_r2, _ = h.hs_krylov(b2, ref2)
-    for b, ref, info_r in ((b1, ref1, info_r1), (b1, ref1, info_r1), (b2, ref2, info_r2), (b1, ref1, info_r1)):
-        x = torch.full_like(b, float("nan"))  # output must be fully written
-        info, rc = h.hs_krylov_noalloc(b, x)
+    cases = ((b1, ref1, info_r1), (b1, ref1, info_r1), (b2, ref2, info_r2), (b1, ref1, info_r1))
+    xs = [torch.full_like(b1, float("nan")) for _ in cases]  # outputs must be fully written
+    out = []
+    for k, (b, _, _) in enumerate(cases):
+        out.append(h.hs_krylov_noalloc(b, xs[k]))
         torch.cuda.synchronize()
+        if k == 0:  # after the first call (which looks up the scratch address)
+            mem = _device_memory()
+    # calls 2-4 allocated nothing: the pool's usage and the free memory are unchanged
+    assert _device_memory() == mem
+    for (info, rc), x, (_, ref, info_r) in zip(out, xs, cases):
         assert rc == 0
         _close(x, ref, info, info_r)
+
+    # a second handle of another size reuses the array; then the first again
+    p2 = inputs.grid_operator(16, 16, 8, ratio=1e5, sigma=0.5, seed=3, bc="ice", shelf=0.5)
+    h2 = _setup(hs, p2)
+    c = _dev(p2.b)
+    ref_c = torch.empty_like(c)
+    info_rc, _ = h2.hs_krylov(c, ref_c)
+    xc = torch.full_like(c, float("nan"))
+    info, rc = h2.hs_krylov_noalloc(c, xc)
+    torch.cuda.synchronize()
+    assert rc == 0
+    _close(xc, ref_c, info, info_rc)
+    x = torch.full_like(b1, float("nan"))
+    info, rc = h.hs_krylov_noalloc(b1, x)
+    torch.cuda.synchronize()
+    assert rc == 0
+    _close(x, ref1, info, info_r1)
+    h2.close()
     h.close()
 
 
@@ -78,3 +121,27 @@ def test_noalloc_rejects_oversized_and_gmres(hs):
     info, rc = hg.hs_krylov_noalloc(bs, torch.zeros_like(bs), check=False)
     assert rc == hs.HS_ERR_UNSUPPORTED
     hg.close()
+    # a batched handle: its problems stop one by one, which this PCG does not do
+    pp, A = inputs.batched_workload(2)
+    opt = hs.hs_default_options(tol=1e-2, mem=hs.HS_MEM_HOST, coords=np.ascontiguousarray(A.coords),
+                                stream=torch.cuda.current_stream().cuda_stream)
+    hb = hs.hs_setup_batched(pp, A.n, A.rowptr, A.col, A.val, opt=opt)
+    bb = _dev(A.b)
+    xb = torch.zeros_like(bb)
+    info, rc = hb.hs_krylov_noalloc(bb, xb, check=False)
+    assert rc == hs.HS_ERR_UNSUPPORTED
+    assert torch.count_nonzero(xb) == 0
+    hb.close()
+
+
+def test_noalloc_rejects_bad_vectors(hs):
+    p = inputs.grid_operator(8, 8, 4, ratio=1e3)
+    h = _setup(hs, p)
+    b = _dev(p.b)
+    with pytest.raises(ValueError):
+        h.hs_krylov_noalloc(b[:-1], torch.zeros_like(b))  # too short
+    with pytest.raises(ValueError):
+        h.hs_krylov_noalloc(b, torch.zeros(p.n, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        h.hs_krylov_noalloc(b.cpu(), torch.zeros_like(b))
+    h.close()
