@@ -96,6 +96,18 @@ typedef struct {
                             the QR are skipped, otherwise they are scaled
                             again in FP64 and the column-pivoted QR decides
                             as usual.  Copied during hs_setup.                */
+    int32_t no_dc;       /* 0 (default): deferred compression (Sec. 2: A_sw
+                            scaled by G_s^-1 before it is compressed, Eq.
+                            offdiag_new).  1: without it, the original
+                            LoRaSp step that Sec. 2 compares against: the
+                            unscaled A_sw compressed (Eq. offdiag) at the
+                            threshold eps * sqrt(max_i (A_ss)_ii), the row
+                            rotated and the fine DOFs eliminated by Cholesky
+                            of the rotated fine block, which also updates the
+                            coarse DOFs.  For comparing the two schemes;
+                            every level runs the per-phase kernel (FP64
+                            compression in both precision forms); not with
+                            rank_model or record_ranks (HS_ERR_UNSUPPORTED). */
 } hs_options;
 
 typedef struct {

@@ -1316,7 +1316,9 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
     }
     L.wmax = std::max(L.wmax, 64);  // the fused kernel's Schur step stages 32 x 4 int64 in the column table
-    if (factor_smem_bytes(L.smax, L.wmax, L.lmax) > (size_t)kFactorMaxSmem)
+    const bool nodc = h->opt.no_dc != 0;
+    if ((nodc ? factor_nodc_smem_bytes(L.smax, L.wmax, L.lmax) : factor_smem_bytes(L.smax, L.wmax, L.lmax)) >
+        (size_t)kFactorMaxSmem)
         throw HsError{HS_ERR_UNSUPPORTED};
     Trace tr;
     tr.mark("  records");
@@ -1345,7 +1347,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     tr.mark("  uploads");
     int64_t mcap = 0;  // largest block row (with the identity columns)
     for (const TaskDev& t : L.tasks) mcap = std::max<int64_t>(mcap, (int64_t)t.s * (t.wcap + t.s));
-    const bool fused = h->opt.fused_levels && L.smax <= kFusedSmax &&
+    const bool fused = !nodc && h->opt.fused_levels && L.smax <= kFusedSmax &&
                        fused_smem_bytes(L.smax, L.wmax, L.lmax, mcap) <= (size_t)kFactorMaxSmem;
     if (fused) {
         DBuf d_pht, d_phg, d_bar;
@@ -1368,11 +1370,17 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     for (int ph = 0; ph < (fused ? 0 : L.nphases); ph++) {
         const int t0 = L.ph_task[ph], nt = L.ph_task[ph + 1] - t0;
         h->prof.begin(KC_FACTOR, st);
-        CK(launch_factor_phase(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.wmax, L.lmax,
-                               L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
-                               d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
-                               L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l, feat,
-                               h->d_model.as<float>()));
+        if (nodc)
+            CK(launch_factor_nodc(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.wmax, L.lmax,
+                                  L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
+                                  d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
+                                  L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l));
+        else
+            CK(launch_factor_phase(st, L.d_tasks.as<TaskDev>(), t0, nt, L.smax, L.wmax, L.lmax,
+                                   L.d_lists.as<ListDev>(), blocks.as<double>(), d_off.as<int64_t>(),
+                                   d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
+                                   L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l, feat,
+                                   h->d_model.as<float>()));
         h->prof.end(KC_FACTOR, st);
         const int g0 = L.ph_target[ph], ng = L.ph_target[ph + 1] - g0;
         if (ng > 0) {
@@ -2728,6 +2736,13 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
     });
 }
 
+// the no-DC elimination serves neither the rank predictor nor its records
+static int nodc_options_check(const hs_options* opt) {
+    if (opt->no_dc != 0 && opt->no_dc != 1) return HS_ERR_ARG;
+    if (opt->no_dc && (opt->rank_model || opt->record_ranks)) return HS_ERR_UNSUPPORTED;
+    return HS_OK;
+}
+
 int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const hs_tree* tree,
              const hs_options* opt, hs_handle* out, hs_info* info) {
     if (!out) return HS_ERR_ARG;
@@ -2737,6 +2752,7 @@ int hs_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
     if (!(opt->tol >= 0.0) || opt->leaf_lines <= 0 || (opt->mem != HS_MEM_HOST && opt->mem != HS_MEM_DEVICE) ||
         (opt->precision != HS_PREC_FP64 && opt->precision != HS_PREC_MIXED))
         return HS_ERR_ARG;
+    if (const int rc0 = nodc_options_check(opt)) return rc0;
     hs_factor_s* h = new (std::nothrow) hs_factor_s();
     if (!h) return HS_ERR_OOM;
     h->n = n;
@@ -2777,6 +2793,7 @@ int hs_setup_batched(int32_t nprob, const int64_t* prob_ptr, int64_t n, const in
     if (!(opt->tol >= 0.0) || opt->leaf_lines <= 0 || (opt->mem != HS_MEM_HOST && opt->mem != HS_MEM_DEVICE) ||
         (opt->precision != HS_PREC_FP64 && opt->precision != HS_PREC_MIXED))
         return HS_ERR_ARG;
+    if (const int rc0 = nodc_options_check(opt)) return rc0;
     hs_factor_s* h = new (std::nothrow) hs_factor_s();
     if (!h) return HS_ERR_OOM;
     h->n = n;

@@ -122,6 +122,13 @@ cudaError_t launch_factor_phase(cudaStream_t st, const TaskDev* tasks, int t0, i
                                 const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                 double* ws, double eps2, int32_t* status, int32_t level, float* feat,
                                 const float* model);
+// the elimination step without deferred compression (hs_nodc.cu): one CTA
+// per task, same records and outputs as launch_factor_phase
+size_t factor_nodc_smem_bytes(int smax, int wmax, int lmax);
+cudaError_t launch_factor_nodc(cudaStream_t st, const TaskDev* tasks, int t0, int ntasks, int smax, int wmax,
+                               int lmax, const ListDev* lists, double* blocks, const int64_t* blk_off,
+                               const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta, double* ws,
+                               double eps2, int32_t* status, int32_t level);
 cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
                                const ContribDev* contribs, const TaskDev* tasks, const void* fac,
                                const int32_t* meta, double* blocks, const int64_t* blk_off,
