@@ -261,13 +261,15 @@ int hs_top_size(hs_handle h, int32_t* ntop);
  * (host arrays, any may be NULL): device milliseconds summed over its
  * launches since setup (CUDA events on the handle's stream; only when
  * options.profile was set), the number of launch sites used, and the
- * algorithmic work: FP64-equivalent flops of the factorization classes
- * (POTRF s^3/3, scaling s^2 (n+w), CPQR sum_k 4 (s-k)(w-k) + 4 s r n, Schur
- * n^2 f) and bytes (assembly 20 per nonzero; apply: the stored factor twice,
- * three vectors per level, the dense coarse operator or top, the two
- * permutations; SpMV 12 nnz + 24 n per product). */
-int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops,
-                    double* bytes);
+ * algorithmic work of the paper's dense counts, split into the flops done in
+ * FP64 (flops64) and in FP32 (flops32: the mixed form's compression and
+ * Schur products): POTRF s^3/3 and scaling s^2 (n+w) in FP64; CPQR
+ * sum_k 4 (s-k)(w-k) + 4 s r n and Schur n^2 f in the form's compression /
+ * product precision; and bytes (assembly 20 per nonzero; apply: the stored
+ * factor twice, three vectors per level, the dense coarse operator or top,
+ * the two permutations; SpMV 12 nnz + 24 n per product). */
+int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops64,
+                    double* flops32, double* bytes);
 int hs_reset_kernel_stats(hs_handle h);
 
 /* Number of this library's kernels launched by the process so far (a kernel
@@ -285,6 +287,10 @@ int hs_eval_pivot_reciprocals(int64_t n, const double* x, double* rsqrt_out, dou
 /* Measures the FP64 FMA throughput of the current device with a chain of
  * independent fma() operations (8 per thread, 8 CTAs per SM); TFLOP/s out. */
 int hs_measure_fp64_peak(void* stream, double* tflops);
+
+/* The same probe on the FP32 pipe (fmaf chains), TFLOP/s out: the peak that
+ * the mixed form's FP32 compression and Schur products are measured against. */
+int hs_measure_fp32_peak(void* stream, double* tflops);
 
 /* ---- Rank predictor ----
  * No counterpart in the paper.  A three-layer perceptron of width 64 maps 8

@@ -931,7 +931,7 @@ struct Level {
     int nvcopy = 0, nfin = 0;
     int64_t fac_doubles = 0;
     // algorithmic work of the level (filled after it ran)
-    double flops_factor = 0, flops_schur = 0;
+    double flops_factor = 0, flops_compress = 0, flops_schur = 0;
 };
 
 struct Prof {
@@ -1015,7 +1015,8 @@ struct hs_factor_s {
     DBuf d_aplevels, d_coarse, d_ycout;
     double* apply_out = nullptr;  // level-0 vector holding the result of the graph
     Prof prof;
-    double work_flops[KC_N] = {0};
+    double work_flops[KC_N] = {0};    // FP64 flops
+    double work_flops32[KC_N] = {0};  // FP32 flops (the mixed form's compression and Schur products)
     double work_bytes[KC_N] = {0};
     ~hs_factor_s() {
         if (apply_graph) cudaGraphExecDestroy(apply_graph);
@@ -1499,13 +1500,18 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             (k < t.nn ? ncol : wcol) += w;
         }
         const double s = t.s;
-        double f = s * s * s / 3.0 + s * s * (ncol + wcol) + 4.0 * s * r * ncol;
-        for (int k = 0; k < r; k++) f += 4.0 * (s - k) * (wcol - k);
-        L.flops_factor += f;
+        // Cholesky + scaling (FP64 in both forms); compression and
+        // sparsification (FP32 in the mixed form)
+        L.flops_factor += s * s * s / 3.0 + s * s * (ncol + wcol);
+        double fq = 4.0 * s * r * ncol;
+        for (int k = 0; k < r; k++) fq += 4.0 * (s - k) * (wcol - k);
+        L.flops_compress += fq;
         L.flops_schur += ncol * ncol * (s - r);  // symmetric half, FMA = 2
     }
-    h->work_flops[fused ? KC_FACTOR_FUSED : KC_FACTOR] += L.flops_factor;
-    h->work_flops[KC_SCHUR] += L.flops_schur;
+    const int kc = fused ? KC_FACTOR_FUSED : KC_FACTOR;
+    h->work_flops[kc] += L.flops_factor;
+    (h->fp32 && !nodc ? h->work_flops32 : h->work_flops)[kc] += L.flops_compress;
+    (h->fp32 ? h->work_flops32 : h->work_flops)[KC_SCHUR] += L.flops_schur;
 }
 
 // Coarse-vector copies from level l to the next level / the top: the
@@ -2981,14 +2987,15 @@ int hs_top_size(hs_handle h, int32_t* ntop) {
     return HS_OK;
 }
 
-int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops,
-                    double* bytes) {
+int hs_kernel_stats(hs_handle h, int32_t nclasses, double* times_ms, int64_t* launches, double* flops64,
+                    double* flops32, double* bytes) {
     if (!h || nclasses < 0) return HS_ERR_ARG;
     for (int k = 0; k < nclasses; k++) {
         const bool ok = k < KC_N;
         if (times_ms) times_ms[k] = ok ? h->prof.ms[k] : 0.0;
         if (launches) launches[k] = ok ? h->prof.launches[k] : 0;
-        if (flops) flops[k] = ok ? h->work_flops[k] : 0.0;
+        if (flops64) flops64[k] = ok ? h->work_flops[k] : 0.0;
+        if (flops32) flops32[k] = ok ? h->work_flops32[k] : 0.0;
         if (bytes) bytes[k] = ok ? h->work_bytes[k] : 0.0;
     }
     return HS_OK;
@@ -3098,7 +3105,8 @@ int hs_eval_pivot_reciprocals(int64_t n, const double* x, double* rsqrt_out, dou
     });
 }
 
-int hs_measure_fp64_peak(void* stream, double* tflops) {
+// FMA throughput of the current device, FP64 (fp32 = 0) or FP32 pipe
+static int measure_fma_peak(void* stream, double* tflops, int fp32) {
     if (!tflops) return HS_ERR_ARG;
     return run_guarded([&] {
         cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -3107,13 +3115,17 @@ int hs_measure_fp64_peak(void* stream, double* tflops) {
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         DBuf sink;
         sink.alloc(64);
-        const int blocks = sms * 8, iters = 1 << 14;
+        const int blocks = sms * 8, iters = fp32 ? 1 << 16 : 1 << 14;
+        auto launch = [&](int it) {
+            return fp32 ? launch_fp32_peak(st, blocks, it, sink.as<double>())
+                        : launch_fp64_peak(st, blocks, it, sink.as<double>());
+        };
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a));
         CK(cudaEventCreate(&b));
-        CK(launch_fp64_peak(st, blocks, 256, sink.as<double>()));  // warm-up
+        CK(launch(256));  // warm-up
         CK(cudaEventRecord(a, st));
-        CK(launch_fp64_peak(st, blocks, iters, sink.as<double>()));
+        CK(launch(iters));
         CK(cudaEventRecord(b, st));
         CK(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -3123,6 +3135,10 @@ int hs_measure_fp64_peak(void* stream, double* tflops) {
         *tflops = 2.0 * 8.0 * (double)iters * blocks * 256 / (ms * 1e-3) / 1e12;
     });
 }
+
+int hs_measure_fp64_peak(void* stream, double* tflops) { return measure_fma_peak(stream, tflops, 0); }
+
+int hs_measure_fp32_peak(void* stream, double* tflops) { return measure_fma_peak(stream, tflops, 1); }
 
 const char* hs_status_str(int status) {
     switch (status) {

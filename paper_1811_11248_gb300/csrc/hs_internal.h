@@ -219,6 +219,7 @@ cudaError_t launch_mlp_adam(cudaStream_t st, float* theta, const float* grad, fl
 int64_t launch_count();
 void launch_count_add(int64_t k);
 cudaError_t launch_fp64_peak(cudaStream_t st, int nblocks, int iters, double* sink);
+cudaError_t launch_fp32_peak(cudaStream_t st, int nblocks, int iters, double* sink);
 // rs[i] = 1 / sqrt(x[i]) and rc[i] = 1 / x[i] by the Cholesky pivot helpers
 cudaError_t launch_eval_recip(cudaStream_t st, int64_t n, const double* x, double* rs, double* rc);
 

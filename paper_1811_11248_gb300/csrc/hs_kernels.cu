@@ -1783,19 +1783,22 @@ __global__ void __launch_bounds__(256) k_gemv_t_final(int k, int np, const doubl
 }
 
 // FP64 FMA throughput probe: 8 independent chains per thread.
-__global__ void __launch_bounds__(256) k_fp64_peak(int iters, double* sink) {
-    double a[8];
+// FMA throughput probe: 8 independent fma chains per thread (T = double for
+// the FP64 pipe, float for the FP32 pipe)
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, double* sink) {
+    T a[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) a[u] = 1.0 + 1e-9 * (threadIdx.x + u);
-    const double b = 0.999999999, c = 1e-12;
+    for (int u = 0; u < 8; u++) a[u] = (T)(1.0 + 1e-6 * (threadIdx.x + u));
+    const T b = (T)0.999999, c = (T)1e-7;
     for (int it = 0; it < iters; it++) {
 #pragma unroll
         for (int u = 0; u < 8; u++) a[u] = fma(a[u], b, c);
     }
-    double t = 0.0;
+    T t = 0;
 #pragma unroll
     for (int u = 0; u < 8; u++) t += a[u];
-    if (t == 12345.0) sink[0] = t;  // keeps the chains alive
+    if (t == (T)12345.0) sink[0] = (double)t;  // keeps the chains alive
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -2169,7 +2172,13 @@ cudaError_t launch_gmres_update(cudaStream_t st, int64_t n, int k, const double*
 
 cudaError_t launch_fp64_peak(cudaStream_t st, int nblocks, int iters, double* sink) {
     counted();
-    k_fp64_peak<<<nblocks, 256, 0, st>>>(iters, sink);
+    k_fma_peak<double><<<nblocks, 256, 0, st>>>(iters, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp32_peak(cudaStream_t st, int nblocks, int iters, double* sink) {
+    counted();
+    k_fma_peak<float><<<nblocks, 256, 0, st>>>(iters, sink);
     return cudaGetLastError();
 }
 

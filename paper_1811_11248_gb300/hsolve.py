@@ -82,9 +82,10 @@ def lib():
     L.hs_level_clusters.argtypes = [P, I32, ctypes.POINTER(I32)]
     L.hs_level_info.argtypes = [P, I32, P, P, P]
     L.hs_top_size.argtypes = [P, ctypes.POINTER(I32)]
-    L.hs_kernel_stats.argtypes = [P, I32, P, P, P, P]
+    L.hs_kernel_stats.argtypes = [P, I32, P, P, P, P, P]
     L.hs_reset_kernel_stats.argtypes = [P]
     L.hs_measure_fp64_peak.argtypes = [P, ctypes.POINTER(F64)]
+    L.hs_measure_fp32_peak.argtypes = [P, ctypes.POINTER(F64)]
     L.hs_eval_pivot_reciprocals.argtypes = [I64, P, P, P, P]
     L.hs_launch_count.argtypes = [ctypes.POINTER(I64)]
     L.hs_setup_batched.argtypes = [I32, P, I64, P, P, P, ctypes.POINTER(hs_options), ctypes.POINTER(P),
@@ -110,7 +111,8 @@ EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_s
             "hs_level_info", "hs_top_size", "hs_kernel_stats", "hs_reset_kernel_stats",
             "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str", "hs_setup_batched",
             "hs_krylov_batched", "hs_num_problems", "hs_problem_info", "hs_mlp_forward", "hs_mlp_grad",
-            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples", "hs_plan_level", "hs_eval_pivot_reciprocals")
+            "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples", "hs_plan_level", "hs_eval_pivot_reciprocals",
+            "hs_measure_fp32_peak")
 MLP_NIN, MLP_NPARAM, MLP_MAX_BATCH = 8, 4801, 256
 
 
@@ -265,9 +267,11 @@ class Handle:
         t = np.zeros(k)
         n = np.zeros(k, np.int64)
         f = np.zeros(k)
+        f32 = np.zeros(k)
         b = np.zeros(k)
-        _check(lib().hs_kernel_stats(self._h, k, _ptr(t), _ptr(n), _ptr(f), _ptr(b)), "hs_kernel_stats")
-        return {name: dict(ms=float(t[i]), launches=int(n[i]), flops=float(f[i]), bytes=float(b[i]))
+        _check(lib().hs_kernel_stats(self._h, k, _ptr(t), _ptr(n), _ptr(f), _ptr(f32), _ptr(b)), "hs_kernel_stats")
+        return {name: dict(ms=float(t[i]), launches=int(n[i]), flops=float(f[i]), flops32=float(f32[i]),
+                           bytes=float(b[i]))
                 for i, name in enumerate(KERNEL_CLASSES)}
 
     def hs_krylov_batched(self, b, x, check=True):
@@ -364,6 +368,13 @@ def hs_eval_pivot_reciprocals(x, rsqrt_out, rcp_out, stream=None):
     _check(lib().hs_eval_pivot_reciprocals(n, _dvec(x, n, "x"), _dvec(rsqrt_out, n, "rsqrt_out"),
                                            _dvec(rcp_out, n, "rcp_out"), P(stream) if stream else None),
            "hs_eval_pivot_reciprocals")
+
+
+def hs_measure_fp32_peak(stream=None):
+    v = F64()
+    _check(lib().hs_measure_fp32_peak(P(stream) if stream else None, ctypes.byref(v)),
+           "hs_measure_fp32_peak")
+    return float(v.value)
 
 
 def hs_measure_fp64_peak(stream=None):
