@@ -673,16 +673,71 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
 // ---------------------------------------------------------------------------
 // Symbolic plan of one level
 // ---------------------------------------------------------------------------
+// Per-cluster sorted index lists in one flat array (CSR): list c is
+// idx[ptr[c] .. ptr[c + 1]).  One allocation per kind of list, not one per
+// cluster (small allocations dominated the planning of small levels).
+struct ListSet {
+    std::vector<int64_t> ptr = std::vector<int64_t>(1, 0);
+    std::vector<int32_t> idx;
+    struct View {
+        const int32_t *b, *e;
+        const int32_t* begin() const { return b; }
+        const int32_t* end() const { return e; }
+        size_t size() const { return (size_t)(e - b); }
+        bool empty() const { return b == e; }
+        int32_t operator[](size_t i) const { return b[i]; }
+    };
+    View operator[](int64_t c) const { return View{idx.data() + ptr[c], idx.data() + ptr[c + 1]}; }
+};
+
+// ListSet of n lists, list i made by f(i, out, t) appending to out (t: the
+// chunk, for per-chunk scratch; at most hs_threads() chunks); contiguous
+// chunks of lists on separate threads, concatenated in order.
+template <class F>
+ListSet build_lists(int64_t n, int64_t grain, F&& f) {
+    ListSet L;
+    L.ptr.assign(n + 1, 0);
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / std::max<int64_t>(grain, 1)));
+    std::vector<std::vector<int32_t>> part(T);
+    auto chunk = [&](int t) {
+        const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+        for (int64_t i = lo; i < hi; i++) {
+            const size_t before = part[t].size();
+            f(i, part[t], t);
+            L.ptr[i + 1] = (int64_t)(part[t].size() - before);
+        }
+    };
+    if (T == 1 || tl_serial) for (int t = 0; t < T; t++) chunk(t);
+    else run_threads(T, chunk);
+    for (int64_t i = 0; i < n; i++) L.ptr[i + 1] += L.ptr[i];
+    L.idx.resize((size_t)L.ptr[n]);
+    size_t o = 0;
+    for (auto& v : part) {
+        std::copy(v.begin(), v.end(), L.idx.begin() + o);
+        o += v.size();
+    }
+    return L;
+}
+
 struct LevelPlan {
     int nc = 0;
     std::vector<int> size0;
-    std::vector<std::vector<int>> adj0;  // level input pattern (no diagonal)
+    ListSet adj0;                        // level input pattern (no diagonal)
     std::vector<int> phase;              // -1: empty cluster
     std::vector<std::vector<int>> phases;
-    std::vector<std::vector<int>> nl, wl;
-    std::vector<std::vector<int>> all;   // every block that exists during the level (with diagonal)
-    std::vector<std::vector<int>> endp;  // blocks at level end (with diagonal of kept clusters)
+    ListSet nl, wl;                      // n / w blocks of each cluster when it is eliminated
+    ListSet all;                         // every block that exists during the level (with diagonal)
+    ListSet endp;                        // blocks at level end (with diagonal of kept clusters)
     std::vector<char> vanished;
+};
+
+// The lists a planner makes for the clusters lo .. hi of one range, in
+// cluster order: for each kind (n, w, all, end) the concatenated entries and
+// every cluster's count.
+enum { LS_NL = 0, LS_WL = 1, LS_ALL = 2, LS_END = 3, LS_N = 4 };
+struct RangeLists {
+    std::vector<int32_t> data[LS_N];
+    std::vector<int32_t> cnt[LS_N];
 };
 
 // Phase rule and fill pattern (Sec. 3.2, Sec. 4.2) of the clusters lo .. hi,
@@ -694,7 +749,11 @@ struct LevelPlan {
 // are final when the phase starts, and a neighbour p that several of them
 // share receives the union of their couplings (set unions, so the order in
 // which they land does not matter).
-void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi,
+struct PlanLists {  // the list planner's per-cluster lists (indexed by cluster)
+    std::vector<std::vector<int>> nl, wl, all, endp;
+};
+
+void plan_range(LevelPlan& P, PlanLists& Q, std::vector<std::vector<int>>& cur, int lo, int hi,
                 std::vector<std::vector<int>>& phases) {
     std::vector<char> done(hi - lo, 0), insel(hi - lo, 0), target(hi - lo, 0), blocked(hi - lo, 0);
     auto D = [&](int c) -> char& { return done[c - lo]; };
@@ -747,14 +806,14 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
             S(c) = 1;
             sel.push_back(c);
             const auto& a0 = P.adj0[c];
-            P.nl[c].reserve(std::min(cur[c].size(), a0.size()));
-            P.wl[c].reserve(cur[c].size());
+            Q.nl[c].reserve(std::min(cur[c].size(), a0.size()));
+            Q.wl[c].reserve(cur[c].size());
             size_t k = 0;  // merge-walk of cur[c] against adj0[c] (both sorted)
             for (int q : cur[c]) {
                 B(q) = 1;  // the block graph is symmetric
                 while (k < a0.size() && a0[k] < q) k++;
                 if (k < a0.size() && a0[k] == q) {
-                    P.nl[c].push_back(q);
+                    Q.nl[c].push_back(q);
                     if (!T(q)) {
                         T(q) = 1;
                         tgi[q - lo] = (int)tg.size();
@@ -764,11 +823,11 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
                     }
                     src[tgi[q - lo]].push_back(c);
                 } else {
-                    P.wl[c].push_back(q);
+                    Q.wl[c].push_back(q);
                 }
             }
-            if (P.wl[c].empty()) P.vanished[c] = 1;
-            work += (int64_t)P.nl[c].size() * (int64_t)cur[c].size();
+            if (Q.wl[c].empty()) P.vanished[c] = 1;
+            work += (int64_t)Q.nl[c].size() * (int64_t)cur[c].size();
         }
         const int ph = (int)phases.size();
         const int64_t ns = (int64_t)sel.size();
@@ -779,11 +838,11 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
             for (int64_t i = a; i < b; i++) {
                 const int p = tg[i];
                 const auto& sp = src[i];
-                const std::vector<int>* u = &P.nl[sp[0]];
+                const std::vector<int>* u = &Q.nl[sp[0]];
                 int skip = p;
                 if (sp.size() > 1) {
                     add.clear();
-                    for (int c : sp) merge_into(add, P.nl[c], p);
+                    for (int c : sp) merge_into(add, Q.nl[c], p);
                     u = &add;
                     skip = -1;
                 }
@@ -791,12 +850,12 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
                 for (int c : sp)
                     if (P.vanished[c]) {
                         sorted_erase(cur[p], c);
-                        P.all[p].push_back(c);  // the block existed during the level
+                        Q.all[p].push_back(c);  // the block existed during the level
                     }
                 target[p - lo] = 0;
             }
         };
-        if (work < (1 << 17) || tl_serial || tl_in_pool) {
+        if (work < (1 << 21) || tl_serial || tl_in_pool) {
             update(0, (int64_t)tg.size(), scratch);
         } else {
             parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
@@ -807,7 +866,7 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
         for (int c : sel) {
             for (int q : cur[c]) B(q) = 0;
             if (P.vanished[c]) {
-                P.all[c].insert(P.all[c].end(), cur[c].begin(), cur[c].end());
+                Q.all[c].insert(Q.all[c].end(), cur[c].begin(), cur[c].end());
                 cur[c].clear();
             }
             D(c) = 1;
@@ -821,76 +880,234 @@ void plan_range(LevelPlan& P, std::vector<std::vector<int>>& cur, int lo, int hi
     // blocks to clusters that left (recorded as they left) and the diagonal
     auto finish = [&](int64_t a, int64_t b) {
         for (int64_t c = a; c < b; c++) {
-            auto& al = P.all[c];
+            auto& al = Q.all[c];
             al.reserve(al.size() + cur[c].size() + 1);
             al.insert(al.end(), cur[c].begin(), cur[c].end());
             if (P.size0[c] > 0) al.push_back((int)c);
             std::sort(al.begin(), al.end());
             al.erase(std::unique(al.begin(), al.end()), al.end());
-            P.endp[c] = std::move(cur[c]);
-            if (P.size0[c] > 0 && !P.vanished[c]) sorted_insert(P.endp[c], (int)c);
+            Q.endp[c] = std::move(cur[c]);
+            if (P.size0[c] > 0 && !P.vanished[c]) sorted_insert(Q.endp[c], (int)c);
         }
     };
     if (tl_serial || tl_in_pool) finish(lo, hi);
     else parallel_ranges(hi - lo, 2048, [&](int64_t a, int64_t b, int) { finish(lo + a, lo + b); });
 }
 
-// Frees a plan's per-cluster lists on all threads: they were allocated by
-// the planning threads, and freeing tens of thousands of them from one thread
-// costs milliseconds.
-void release_plan(LevelPlan& P) {
-    const int64_t nc = (int64_t)P.all.size();
-    parallel_ranges(nc, 2048, [&](int64_t lo, int64_t hi, int) {
-        for (int64_t c = lo; c < hi; c++) {
-            for (auto* v : {&P.adj0, &P.nl, &P.wl, &P.all, &P.endp})
-                if (c < (int64_t)v->size()) std::vector<int>().swap((*v)[c]);
+// The same phase rule and fill pattern as plan_range for a range of at most
+// kBitsMax clusters, with the block graph held as one bit row per cluster:
+// selecting a cluster marks its row as blocked, the n / w split is the row
+// with / without the level's input pattern, and the fill of a phase is an OR
+// of the selected clusters' n rows into their neighbours' rows (unions, so
+// the order does not matter), after which the clusters that vanished are
+// cleared from them.  Lists come out sorted, as plan_range writes them.
+constexpr int kBitsMax = 2048;
+
+void plan_range_bits(LevelPlan& P, int lo, int hi, std::vector<std::vector<int>>& phases, RangeLists& out) {
+    const int m = hi - lo, W = (m + 63) / 64;
+    std::vector<uint64_t> cur((size_t)m * W, 0), in((size_t)m * W, 0), gone((size_t)m * W, 0);
+    std::vector<uint64_t> blocked(W), nlb((size_t)W);
+    auto row = [&](std::vector<uint64_t>& b, int c) { return b.data() + (size_t)(c - lo) * W; };
+    auto set = [&](uint64_t* r, int q) { r[(q - lo) >> 6] |= 1ull << ((q - lo) & 63); };
+    auto has = [&](const uint64_t* r, int q) { return (r[(q - lo) >> 6] >> ((q - lo) & 63)) & 1ull; };
+    // appends the set bits of r, ascending; returns their number
+    auto to_list = [&](const uint64_t* r, std::vector<int32_t>& o) {
+        const size_t b0 = o.size();
+        for (int w = 0; w < W; w++)
+            for (uint64_t x = r[w]; x; x &= x - 1) o.push_back(lo + 64 * w + __builtin_ctzll(x));
+        return (int32_t)(o.size() - b0);
+    };
+    // n and w lists in elimination order (offsets per cluster), put in
+    // cluster order at the end
+    std::vector<int32_t> nw;
+    std::vector<int64_t> off_n(m, 0), off_w(m, 0);
+    std::vector<int32_t> cnt_n(m, 0), cnt_w(m, 0);
+    std::vector<char> done(m, 0);
+    int remaining = 0;
+    for (int c = lo; c < hi; c++) {
+        for (int q : P.adj0[c]) {
+            set(row(cur, c), q);
+            set(row(in, c), q);
         }
-    });
-    P = LevelPlan{};
+        if (P.size0[c] > 0) remaining++;
+        else done[c - lo] = 1;
+    }
+    int first = lo;
+    std::vector<int> sel;
+    while (remaining > 0) {
+        sel.clear();
+        std::fill(blocked.begin(), blocked.end(), 0);
+        while (first < hi && done[first - lo]) first++;
+        for (int c = first; c < hi; c++) {
+            if (done[c - lo] || has(blocked.data(), c)) continue;
+            sel.push_back(c);
+            const uint64_t* r = row(cur, c);
+            for (int w = 0; w < W; w++) blocked[w] |= r[w];
+        }
+        const int ph = (int)phases.size();
+        // n / w lists; the fill: every n-neighbour p gains the others
+        for (int c : sel) {
+            const uint64_t *r = row(cur, c), *a = row(in, c);
+            bool fill = false;
+            for (int w = 0; w < W; w++) {
+                nlb[w] = r[w] & ~a[w];
+                fill |= nlb[w] != 0;
+            }
+            off_w[c - lo] = (int64_t)nw.size();
+            cnt_w[c - lo] = to_list(nlb.data(), nw);
+            for (int w = 0; w < W; w++) nlb[w] = r[w] & a[w];
+            off_n[c - lo] = (int64_t)nw.size();
+            cnt_n[c - lo] = to_list(nlb.data(), nw);
+            if (!fill) P.vanished[c] = 1;
+            for (int32_t e = 0; e < cnt_n[c - lo]; e++) {
+                const int p2 = nw[off_n[c - lo] + e];
+                uint64_t* rp = row(cur, p2);
+                for (int w = 0; w < W; w++) rp[w] |= nlb[w];
+                rp[(p2 - lo) >> 6] &= ~(1ull << ((p2 - lo) & 63));
+            }
+        }
+        // clusters without fill leave the graph (their blocks existed during
+        // the level); every selected cluster is done
+        for (int c : sel) {
+            if (P.vanished[c]) {
+                const uint64_t bit = 1ull << ((c - lo) & 63);
+                for (int32_t e = 0; e < cnt_n[c - lo]; e++) {
+                    const int p2 = nw[off_n[c - lo] + e];
+                    row(cur, p2)[(c - lo) >> 6] &= ~bit;
+                    row(gone, p2)[(c - lo) >> 6] |= bit;
+                }
+                uint64_t *rc = row(cur, c), *gc = row(gone, c);
+                for (int w = 0; w < W; w++) {
+                    gc[w] |= rc[w];
+                    rc[w] = 0;
+                }
+            }
+            done[c - lo] = 1;
+            P.phase[c] = ph;
+        }
+        remaining -= (int)sel.size();
+        phases.push_back(sel);
+    }
+    for (int k = 0; k < LS_N; k++) out.cnt[k].assign(m, 0);
+    for (int c = lo; c < hi; c++) {
+        const int i = c - lo;
+        out.cnt[LS_NL][i] = cnt_n[i];
+        out.data[LS_NL].insert(out.data[LS_NL].end(), nw.begin() + off_n[i], nw.begin() + off_n[i] + cnt_n[i]);
+        out.cnt[LS_WL][i] = cnt_w[i];
+        out.data[LS_WL].insert(out.data[LS_WL].end(), nw.begin() + off_w[i], nw.begin() + off_w[i] + cnt_w[i]);
+        uint64_t *rc = row(cur, c), *gc = row(gone, c);
+        for (int w = 0; w < W; w++) gc[w] |= rc[w];
+        if (P.size0[c] > 0) set(gc, c);
+        out.cnt[LS_ALL][i] = to_list(gc, out.data[LS_ALL]);
+        if (P.size0[c] > 0 && !P.vanished[c]) set(rc, c);
+        out.cnt[LS_END][i] = to_list(rc, out.data[LS_END]);
+    }
 }
+
+// The list planner's lists of the clusters lo .. hi into out, and the lists
+// freed (by the calling thread; a single large range: on all threads).
+void take_lists(PlanLists& Q, int lo, int hi, RangeLists& out, bool parallel_free) {
+    std::vector<std::vector<int>>* src[LS_N] = {&Q.nl, &Q.wl, &Q.all, &Q.endp};
+    for (int k = 0; k < LS_N; k++) {
+        auto& v = *src[k];
+        out.cnt[k].assign(hi - lo, 0);
+        size_t tot = 0;
+        for (int c = lo; c < hi; c++) tot += v[c].size();
+        out.data[k].resize(tot);
+        size_t o = 0;
+        for (int c = lo; c < hi; c++) {
+            out.cnt[k][c - lo] = (int32_t)v[c].size();
+            std::copy(v[c].begin(), v[c].end(), out.data[k].begin() + o);
+            o += v[c].size();
+        }
+    }
+    auto release = [&](int64_t a, int64_t b) {
+        for (int64_t c = a; c < b; c++)
+            for (auto* v : src) std::vector<int>().swap((*v)[c]);
+    };
+    if (parallel_free) parallel_ranges(hi - lo, 2048, [&](int64_t a, int64_t b, int) { release(lo + a, lo + b); });
+    else release(lo, hi);
+}
+
+void release_plan(LevelPlan& P) { P = LevelPlan{}; }
 
 // ranges: cluster ranges that share no block (independent problems); each
 // is planned on its own thread and phase k of the level is the union of the
-// ranges' phase k (identical to planning all clusters at once).
+// ranges' phase k (identical to planning all clusters at once).  Ranges of
+// at most kBitsMax clusters run the bit-row planner, larger ones the list
+// planner.
 void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {}) {
     const int nc = P.nc;
-    std::vector<std::vector<int>> cur(nc);
-    P.all.assign(nc, {});
     P.phase.assign(nc, -1);
-    P.nl.assign(nc, {});
-    P.wl.assign(nc, {});
     P.vanished.assign(nc, 0);
-    P.endp.assign(nc, {});
     P.phases.clear();
     std::vector<std::pair<int, int>> rg = ranges;
     if (rg.empty()) rg.push_back({0, nc});
-    std::vector<std::vector<std::vector<int>>> ph(rg.size());
-    // the lists start as the input pattern, made by the thread that plans
-    // them (one range: by all threads)
-    // (room for the fill to come, so that the phases seldom reallocate; the
-    // list of every block of the level is completed at the level's end)
+    const int nr = (int)rg.size();
+    std::vector<std::vector<std::vector<int>>> ph(nr);
+    std::vector<RangeLists> out(nr);
+    auto small = [&](int k) { return rg[k].second - rg[k].first <= kBitsMax; };
+    bool any_large = false;
+    for (int k = 0; k < nr; k++) any_large |= !small(k);
+    // the list planner's working lists start as the input pattern, made by
+    // the thread that plans them (one range: by all threads), with room for
+    // the fill to come so that the phases seldom reallocate
+    PlanLists Q;
+    std::vector<std::vector<int>> cur;
+    if (any_large) {
+        cur.resize(nc);
+        Q.nl.resize(nc);
+        Q.wl.resize(nc);
+        Q.all.resize(nc);
+        Q.endp.resize(nc);
+    }
     auto init = [&](int64_t lo, int64_t hi) {
         for (int64_t c = lo; c < hi; c++) {
-            cur[c].reserve(4 * P.adj0[c].size() + 4);
-            cur[c].assign(P.adj0[c].begin(), P.adj0[c].end());
-            P.all[c].clear();
+            const auto a0 = P.adj0[c];
+            cur[c].reserve(4 * a0.size() + 4);
+            cur[c].assign(a0.begin(), a0.end());
         }
     };
-    if (rg.size() == 1) parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) { init(lo, hi); });
+    if (nr == 1 && !small(0)) parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) { init(lo, hi); });
     std::atomic<int> next{0};
     auto work = [&] {
-        for (int k = next++; k < (int)rg.size(); k = next++) {
-            if (rg.size() > 1) init(rg[k].first, rg[k].second);
-            plan_range(P, cur, rg[k].first, rg[k].second, ph[k]);
+        for (int k = next++; k < nr; k = next++) {
+            if (small(k)) {
+                plan_range_bits(P, rg[k].first, rg[k].second, ph[k], out[k]);
+                continue;
+            }
+            if (nr > 1) init(rg[k].first, rg[k].second);
+            plan_range(P, Q, cur, rg[k].first, rg[k].second, ph[k]);
+            take_lists(Q, rg[k].first, rg[k].second, out[k], nr == 1);
         }
     };
-    run_threads(std::min<int>(hs_threads(), (int)rg.size()), [&](int) { work(); });
+    run_threads(std::min<int>(hs_threads(), nr), [&](int) { work(); });
     size_t nph = 0;
     for (auto& v : ph) nph = std::max(nph, v.size());
     P.phases.assign(nph, {});
     for (size_t k = 0; k < nph; k++)
         for (auto& v : ph)
             if (k < v.size()) P.phases[k].insert(P.phases[k].end(), v[k].begin(), v[k].end());
+    // the ranges' lists, concatenated in range (= cluster) order
+    ListSet* dst[LS_N] = {&P.nl, &P.wl, &P.all, &P.endp};
+    for (int t = 0; t < LS_N; t++) {
+        ListSet& L = *dst[t];
+        L.ptr.assign(nc + 1, 0);
+        std::vector<int64_t> base(nr + 1, 0);
+        for (int k = 0; k < nr; k++) {
+            const int lo = rg[k].first;
+            for (int i = 0; i < rg[k].second - lo; i++) L.ptr[lo + i + 1] = out[k].cnt[t][i];
+            base[k + 1] = base[k] + (int64_t)out[k].data[t].size();
+        }
+        for (int c = 0; c < nc; c++) L.ptr[c + 1] += L.ptr[c];
+        L.idx.resize((size_t)base[nr]);
+        auto copy = [&](int64_t a, int64_t b) {
+            for (int64_t k = a; k < b; k++)
+                std::copy(out[k].data[t].begin(), out[k].data[t].end(), L.idx.begin() + base[k]);
+        };
+        if (nr > 64) parallel_ranges(nr, 16, [&](int64_t a, int64_t b, int) { copy(a, b); });
+        else copy(0, nr);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1247,7 +1464,10 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                 }
             }
         };
-        run_threads(nt < 256 ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
+        // threads only when there are enough pairs to pay for waking them
+        int64_t npairs = 0;
+        for (int ti = 0; ti < nt; ti++) npairs += (int64_t)L.tasks[ti].nn * L.tasks[ti].nn;
+        run_threads(npairs < (1 << 16) ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
         tr0.mark("  targets: pairs");
         // concatenation in (phase, range) order: offsets first, then the
         // copies item by item in parallel
@@ -1760,35 +1980,44 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     P.nc = nleaf;
     P.size0.resize(nleaf);
     for (int c = 0; c < nleaf; c++) P.size0[c] = leaf_ptr[c + 1] - leaf_ptr[c];
-    P.adj0.assign(nleaf, {});
     {
         // block pattern of level 0, kept symmetric even if the CSR pattern is not
-        parallel_ranges(nleaf, 256, [&](int64_t lo, int64_t hi, int) {
-            std::vector<int> stamp(nleaf, -1);
-            for (int64_t c = lo; c < hi; c++) {
-                auto& v = P.adj0[c];
-                for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
-                    const int i = h->perm[k];
-                    for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-                        const int q = dof_cluster[cl[e]];
-                        if (q != c && stamp[q] != c) {
-                            stamp[q] = (int)c;
-                            v.push_back(q);
-                        }
+        std::vector<std::vector<int>> stamp(hs_threads());
+        P.adj0 = build_lists(nleaf, 256, [&](int64_t c, std::vector<int32_t>& out, int t) {
+            auto& st = stamp[t];
+            if (st.empty()) st.assign(nleaf, -1);
+            const size_t b0 = out.size();
+            for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
+                const int i = h->perm[k];
+                for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+                    const int q = dof_cluster[cl[e]];
+                    if (q != c && st[q] != c) {
+                        st[q] = (int)c;
+                        out.push_back(q);
                     }
                 }
-                std::sort(v.begin(), v.end());
             }
+            std::sort(out.begin() + b0, out.end());
         });
-        std::vector<std::pair<int, int>> missing;  // (q, c) with c -> q but not q -> c
+        std::vector<std::vector<int>> missing(nleaf);  // q gains c where c -> q but not q -> c
+        bool any = false;
         for (int c = 0; c < nleaf; c++)
-            for (int q : P.adj0[c])
-                if (!std::binary_search(P.adj0[q].begin(), P.adj0[q].end(), c)) missing.push_back({q, c});
-        for (auto& m : missing) P.adj0[m.first].push_back(m.second);
-        for (auto& m : missing) {
-            auto& v = P.adj0[m.first];
-            std::sort(v.begin(), v.end());
-            v.erase(std::unique(v.begin(), v.end()), v.end());
+            for (int q : P.adj0[c]) {
+                const auto r = P.adj0[q];
+                if (!std::binary_search(r.begin(), r.end(), c)) {
+                    missing[q].push_back(c);
+                    any = true;
+                }
+            }
+        if (any) {
+            ListSet old = std::move(P.adj0);
+            P.adj0 = build_lists(nleaf, 1 << 30, [&](int64_t c, std::vector<int32_t>& out, int) {
+                const size_t b0 = out.size();
+                out.insert(out.end(), old[c].begin(), old[c].end());
+                out.insert(out.end(), missing[c].begin(), missing[c].end());
+                std::sort(out.begin() + b0, out.end());
+                out.erase(std::unique(out.begin() + b0, out.end()), out.end());
+            });
         }
     }
 
@@ -1945,21 +2174,18 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             LevelPlan Pn;
             Pn.nc = nn;
             Pn.size0 = nsize;
-            Pn.adj0.assign(nn, {});
             std::vector<int> kid0(nn, -1);  // first child of every parent (children are consecutive)
             for (int a = nc - 1; a >= 0; a--)
                 if (par[a] >= 0) kid0[par[a]] = a;
-            parallel_ranges(nn, 512, [&](int64_t lo, int64_t hi, int) {
-                for (int64_t k = lo; k < hi; k++) {
-                    auto& v = Pn.adj0[k];
-                    for (int a = kid0[k]; a < nc && par[a] == k; a++) {
-                        if (fin[a] <= 0) continue;
-                        for (int b : P.endp[a])
-                            if (fin[b] > 0 && par[b] != k) v.push_back(par[b]);
-                    }
-                    std::sort(v.begin(), v.end());
-                    v.erase(std::unique(v.begin(), v.end()), v.end());
+            Pn.adj0 = build_lists(nn, 512, [&](int64_t k, std::vector<int32_t>& v, int) {
+                const size_t b0 = v.size();
+                for (int a = kid0[k]; a < nc && par[a] == k; a++) {
+                    if (fin[a] <= 0) continue;
+                    for (int b : P.endp[a])
+                        if (fin[b] > 0 && par[b] != k) v.push_back(par[b]);
                 }
+                std::sort(v.begin() + b0, v.end());
+                v.erase(std::unique(v.begin() + b0, v.end()), v.end());
             });
             tr.mark("next-level adjacency");
             ranges.clear();
@@ -2685,7 +2911,6 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
         LevelPlan P;
         P.nc = nc;
         P.size0.assign(size0, size0 + nc);
-        P.adj0.assign(nc, {});
         for (int32_t c = 0; c < nc; c++) {
             // sorted, no self loop, in range
             for (int64_t e = adj_ptr[c]; e < adj_ptr[c + 1]; e++) {
@@ -2693,12 +2918,15 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
                 if (q < 0 || q >= nc || q == c || (e > adj_ptr[c] && adj[e - 1] >= q)) throw HsError{HS_ERR_ARG};
                 // a cluster without DOFs has no blocks
                 if (size0[c] == 0 || size0[q] == 0) throw HsError{HS_ERR_ARG};
-                P.adj0[c].push_back(q);
             }
         }
+        P.adj0.ptr.assign(adj_ptr, adj_ptr + nc + 1);
+        P.adj0.idx.assign(adj, adj + adj_ptr[nc]);
         for (int32_t c = 0; c < nc; c++)  // symmetric
-            for (int q : P.adj0[c])
-                if (!sorted_has(P.adj0[q], c)) throw HsError{HS_ERR_ARG};
+            for (int q : P.adj0[c]) {
+                const auto r = P.adj0[q];
+                if (!std::binary_search(r.begin(), r.end(), c)) throw HsError{HS_ERR_ARG};
+            }
         std::vector<std::pair<int, int>> rg;
         if (nranges > 0) {
             // consecutive, covering [0, nc), no block between two ranges
