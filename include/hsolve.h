@@ -108,6 +108,14 @@ typedef struct {
                             every level runs the per-phase kernel (FP64
                             compression in both precision forms); not with
                             rank_model or record_ranks (HS_ERR_UNSUPPORTED). */
+    int32_t wait_polls;  /* bounded device waits (the grid barrier between the
+                            phases of a level factored in one launch): polls
+                            before the launch gives up with HS_ERR_TIMEOUT.
+                            0 (default): about a second; > 0: that many;
+                            < 0: none, the first wait gives up at once (for
+                            testing the timeout path).  A launch that gives
+                            up returns at once, and the call returns
+                            HS_ERR_TIMEOUT without a handle.                 */
 } hs_options;
 
 typedef struct {

@@ -1585,7 +1585,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                                      d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
                                      L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l,
                                      L.smax, L.wmax, L.lmax, mcap, max_items, d_bar.as<unsigned>(), feat,
-                                     h->d_model.as<float>()));
+                                     h->d_model.as<float>(), h->opt.wait_polls));
         h->prof.end(KC_FACTOR_FUSED, st);
     }
     for (int ph = 0; ph < (fused ? 0 : L.nphases); ph++) {

@@ -200,7 +200,7 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
                                       const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                       double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
                                       int lmax, int64_t mcap, int max_items, unsigned* bar, float* feat,
-                                      const float* model);
+                                      const float* model, int wait_polls);
 // process-wide count of this library's kernel launches
 // rank predictor (hs_mlp.cu): 8 -> 64 -> 64 -> 1 perceptron, FP32
 constexpr int kMlpIn = 8, kMlpHidden = 64;

@@ -941,18 +941,25 @@ __device__ void schur_target_warp(const TargetDev& g, const ContribDev* __restri
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0]
 // counts arrivals, bar[1] is the generation.  The wait is bounded: after
-// kBarrierSpins polls the CTA records ST_TIMEOUT and goes on (results are then
-// discarded by the host), so a broken launch cannot hang the GPU.
+// `limit` polls (about a second by default) the CTA records ST_TIMEOUT; a
+// CTA that sees ST_TIMEOUT recorded by another one while it waits stops
+// waiting too.  Returns false (the same value on every thread of the CTA)
+// when the launch has timed out: the caller then returns at once instead of
+// computing on blocks that other CTAs may not have finished.  limit 0: no
+// poll at all (a CTA that has to wait times out at once; for tests).
 constexpr long long kBarrierSpins = 1LL << 24;
 
-__device__ void grid_sync(unsigned* bar, int32_t* status) {
+__device__ bool grid_sync(unsigned* bar, int32_t* status, long long limit) {
+    __shared__ int s_ok;
     __threadfence();  // every thread's writes of this phase, device-visible
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* vgen = bar + 1;
+        volatile int32_t* vst = status;
         const unsigned gen = *vgen;
         __threadfence();
         const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        int ok = 1;
         if (arrived == gridDim.x) {
             atomicExch(bar, 0u);
             __threadfence();
@@ -960,17 +967,25 @@ __device__ void grid_sync(unsigned* bar, int32_t* status) {
         } else {
             long long spins = 0;
             while (*vgen == gen) {
-                __nanosleep(40);
-                if (++spins > kBarrierSpins) {
+                if (spins++ >= limit) {
                     atomicCAS(status, 0, ST_TIMEOUT);
+                    ok = 0;
                     break;
                 }
+                if (*vst == ST_TIMEOUT) {  // another CTA gave up: this barrier never completes
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(40);
             }
         }
+        if (*vst == ST_TIMEOUT) ok = 0;
+        s_ok = ok;
         __threadfence();
     }
     __syncthreads();
     __threadfence();  // acquire side for every thread
+    return s_ok != 0;
 }
 
 template <typename FT>
@@ -982,7 +997,7 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
                      const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
                      int32_t* __restrict__ meta, double* __restrict__ ws, double eps2, int32_t* status,
                      int32_t level, int smax, int wmax, int lmax, int64_t mcap, unsigned* bar,
-                     float* __restrict__ feat, const float* __restrict__ model) {
+                     float* __restrict__ feat, const float* __restrict__ model, long long wait_limit) {
     extern __shared__ double sm[];
     const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     // items go to CTAs round-robin first (item k: CTA k mod grid, warp k /
@@ -1009,10 +1024,10 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
             factor_task<FT>(tasks[t], g, G, rdiag, v, cn, red, ioff, flag, hh, Msh, em, colsrc, lists, blocks,
                             blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level,
                             feat ? feat + (size_t)t * kFeat : nullptr, model, nullptr, nullptr);
-        grid_sync(bar, status);
+        if (!grid_sync(bar, status, wait_limit)) return;
         for (int k = ph_target[ph] + gw; k < ph_target[ph + 1]; k += GW)
             schur_target_warp<FT>(targets[k], contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur, colsrc);
-        grid_sync(bar, status);
+        if (!grid_sync(bar, status, wait_limit)) return;
     }
 }
 
@@ -1930,7 +1945,7 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
                                       const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                       double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
                                       int lmax, int64_t mcap, int max_items, unsigned* bar, float* feat,
-                                      const float* model) {
+                                      const float* model, int wait_polls) {
     if (nph <= 0) return cudaSuccess;
     const size_t smem = fused_smem_bytes(smax, wmax, lmax, mcap);
     const void* fn = fp32 ? reinterpret_cast<const void*>(&k_factor_level_fused<float>)
@@ -1950,10 +1965,11 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
     const int want = std::max(std::min(max_items, sms), (max_items + kFusedWarps - 1) / kFusedWarps);
     const int grid = std::max(1, std::min(per_sm * sms, want));
     if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
+    long long wait_limit = wait_polls == 0 ? kBarrierSpins : (wait_polls < 0 ? 0LL : (long long)wait_polls);
     counted();
     void* args[] = {&tasks,  &ph_task, &targets, &ph_target, &contribs, &nph,  &lists, &blocks,
                     &blk_off, &blk_ld, &cur,     &fac,       &meta,     &ws,   &eps2,  &status,
-                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar,  &feat,  &model};
+                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar,  &feat,  &model, &wait_limit};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFusedWarps * 32), args, smem, st);
 }
 

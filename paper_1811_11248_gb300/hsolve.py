@@ -37,7 +37,7 @@ class hs_options(ctypes.Structure):
                 ("precision", I32), ("krylov", I32), ("restart", I32), ("rtol", F64),
                 ("maxit", I32), ("mem", I32), ("profile", I32), ("stream", P), ("coords", P),
                 ("coarse_dense", I32), ("fused_levels", I32), ("record_ranks", I32),
-                ("rank_model", P), ("no_dc", I32)]
+                ("rank_model", P), ("no_dc", I32), ("wait_polls", I32)]
 
 
 class hs_info(ctypes.Structure):
