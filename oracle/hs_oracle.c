@@ -48,7 +48,9 @@
  *     ||R[k:,k:]||_F <= eps, checked as sum of squared trailing column
  *     norms <= eps^2 (Frobenius norm bounds the 2-norm of V2 in Eq. offdiag_new);
  *   - pivot = lowest-index unpivoted column whose squared trailing norm is at
- *     least (1 - 1e-10) times the largest (norms recomputed every step);
+ *     least (1 - 1e-6) times the largest (norms recomputed every step; the
+ *     band lies well above the rounding of small trailing norms, so that
+ *     implementations summing in different orders pivot alike);
  *   - Householder: beta = -sign(alpha) * norm, v_k = 1, tau = (beta-alpha)/beta;
  *   - neighbours of a cluster are the blocks present in the level's input
  *     matrix; every other present block is fill ("w");
@@ -71,7 +73,7 @@
 #define OR_ERR_NOCONV 3
 #define OR_ERR_OOM 4
 
-#define PIVOT_TIE 1e-10
+#define PIVOT_TIE 1e-6
 
 /* ------------------------------------------------------------------------ */
 /* Small helpers                                                            */

@@ -25,7 +25,7 @@
 //
 // Decisions that must agree with any other implementation of the method:
 // rank = smallest k with sum of squared trailing column norms <= eps^2;
-// pivot = lowest unpivoted column index with squared norm >= (1 - 1e-10) *
+// pivot = lowest unpivoted column index with squared norm >= (1 - 1e-6) *
 // the largest; Householder beta = -sign(alpha) * norm, v_k = 1,
 // tau = (beta - alpha) / beta.
 //
@@ -44,7 +44,7 @@ namespace hs {
 
 namespace {
 
-constexpr double kPivotTie = 1e-10;
+constexpr double kPivotTie = 1e-6;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

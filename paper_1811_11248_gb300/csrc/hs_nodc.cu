@@ -21,7 +21,7 @@
 //      the same roles as W = U^T G^-1 and C with deferred compression: the
 //      forward solve step is y_s <- W y_s, y_n -= C^T y_f.
 // The pivot and Householder conventions are those of the other kernels:
-// lowest-index column with squared norm >= (1 - 1e-10) times the largest;
+// lowest-index column with squared norm >= (1 - 1e-6) times the largest;
 // beta = -sign(alpha) * norm, v_k = 1, tau = (beta - alpha) / beta.
 #include <cfloat>
 #include <climits>
@@ -34,7 +34,7 @@ namespace hs {
 namespace {
 
 constexpr int kNodcThreads = 256;
-constexpr double kNodcPivotTie = 1e-10;
+constexpr double kNodcPivotTie = 1e-6;
 
 __device__ double nd_block_sum(double v, double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;

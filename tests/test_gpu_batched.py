@@ -140,6 +140,34 @@ def test_batched_workload_problems(hs, oracle_lib):
     hm.close()
 
 
+@pytest.mark.slow
+def test_batched_workload_32_problems(hs, oracle_lib):
+    """32 problems spread over the 256-problem workload (every eighth), in
+    one handle: per problem the phases and ranks of the oracle run on that
+    problem alone, PCG iterations within 1 of the oracle's, true residuals
+    <= 1e-8 and solutions within 1e-6 (FP64); the mixed form reaches 1e-8
+    within 3 iterations of the oracle."""
+    probs = [inputs.batched_problem(k) for k in range(0, 256, 8)]
+    pp, A = inputs.block_diagonal(probs)
+    refs = oracle_factors(oracle_lib, probs, 1e-2)
+    h = setup_batched(hs, pp, A, 1e-2)
+    check_batched_structure(h, refs)
+    hm = setup_batched(hs, pp, A, 1e-2, precision=hs.HS_PREC_MIXED)
+    for hh, slack in ((h, 1), (hm, 3)):
+        x = torch.empty(A.n, dtype=torch.float64, device="cuda")
+        info, rc, its, rel = hh.hs_krylov_batched(dev(A.b), x)
+        xg = x.cpu().numpy()
+        for k, (p, (ref, _, _)) in enumerate(zip(probs, refs)):
+            xo, ito, _, _ = ref.pcg(rtol=1e-8)
+            assert abs(int(its[k]) - ito) <= slack, (k, its[k], ito)
+            xk = xg[pp[k]:pp[k + 1]]
+            assert np.linalg.norm(p.b - p.matvec(xk)) <= 1e-8 * np.linalg.norm(p.b)
+            if slack == 1:
+                assert np.linalg.norm(xk - xo) <= 1e-6 * np.linalg.norm(xo)
+    h.close()
+    hm.close()
+
+
 def test_batched_krylov_entry_and_zero_rhs(hs, oracle_lib):
     """hs_krylov on a batched handle runs the per-problem PCG; a problem with
     b = 0 returns x = 0 after no iteration."""

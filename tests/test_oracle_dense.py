@@ -69,7 +69,7 @@ def test_cpqr_invariants(oracle_lib, s, w, rank, eps):
     for k in range(r):
         cand = np.setdiff1d(np.arange(w), piv[:k])
         nrm = (Bk[k:][:, cand] ** 2).sum(0)
-        best = cand[np.flatnonzero(nrm >= (1 - 1e-10) * nrm.max())[0]]
+        best = cand[np.flatnonzero(nrm >= (1 - 1e-6) * nrm.max())[0]]
         assert piv[k] == best
         v = V[:, k]
         Bk = Bk - tau[k] * np.outer(v, v @ Bk)
