@@ -618,8 +618,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD,
-                       "precision": "mixed: FP64 Cholesky/scaling/Krylov residual, FP32 compression (CPQR), Schur products and "
-                                    "stored factor",
+                       "precision": "mixed: FP64 Cholesky/scaling/Krylov residual, FP32 compression (CPQR) and stored "
+                                    "factor, Schur products on the tensor cores (TF32 x3 split, FP32 accumulate)",
                        "l2": "flushed (320 MB write) before each step", "replicas": world},
             "iters": it_mx, "rel_resid": res_mx,
             "plain_fp64": {"value": t64, "unit": "s", "iters": it64, "rel_resid": res64,

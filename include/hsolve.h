@@ -47,6 +47,7 @@ typedef enum {
 enum { HS_MEM_HOST = 0, HS_MEM_DEVICE = 1 };
 enum { HS_PREC_FP64 = 0, HS_PREC_MIXED = 1 };
 enum { HS_KRYLOV_PCG = 0, HS_KRYLOV_GMRES = 1 };
+enum { HS_PRODUCTS_FP32 = 0, HS_PRODUCTS_TF32X3 = 1, HS_PRODUCTS_TF32 = 2 };
 
 /* Partition tree: leaf c owns the DOFs perm[leaf_ptr[c] .. leaf_ptr[c+1]);
  * siblings 2c, 2c+1 merge at the next level (Sec. 4.2, Sec. 5).  n_leaf must
@@ -116,6 +117,17 @@ typedef struct {
                             testing the timeout path).  A launch that gives
                             up returns at once, and the call returns
                             HS_ERR_TIMEOUT without a handle.                 */
+    int32_t schur_products; /* mixed form, Schur update X_nn -= C^T C (Eq.
+                            elim) of the per-phase levels (default
+                            HS_PRODUCTS_TF32X3): HS_PRODUCTS_FP32
+                            (FP32 products on the CUDA cores),
+                            HS_PRODUCTS_TF32X3 (tensor cores: each FP32
+                            entry split into two TF32 parts, three products,
+                            about 2^-21 relative error per product) or
+                            HS_PRODUCTS_TF32 (tensor cores, one TF32
+                            product, about 2^-11); FP32
+                            accumulation and an FP64 block store in every
+                            case.  Ignored by the FP64 form.                 */
 } hs_options;
 
 typedef struct {

@@ -729,6 +729,9 @@ struct LevelPlan {
     ListSet all;                         // every block that exists during the level (with diagonal)
     ListSet endp;                        // blocks at level end (with diagonal of kept clusters)
     std::vector<char> vanished;
+    // the list planner's per-cluster working lists, kept until the plan is
+    // released (then freed on all threads)
+    std::vector<std::vector<std::vector<int>>> scratch;
 };
 
 // The lists a planner makes for the clusters lo .. hi of one range, in
@@ -855,7 +858,7 @@ void plan_range(LevelPlan& P, PlanLists& Q, std::vector<std::vector<int>>& cur, 
                 target[p - lo] = 0;
             }
         };
-        if (work < (1 << 21) || tl_serial || tl_in_pool) {
+        if (work < (1 << 17) || tl_serial || tl_in_pool) {
             update(0, (int64_t)tg.size(), scratch);
         } else {
             parallel_ranges((int64_t)tg.size(), 256, [&](int64_t a, int64_t b, int) {
@@ -1004,32 +1007,44 @@ void plan_range_bits(LevelPlan& P, int lo, int hi, std::vector<std::vector<int>>
     }
 }
 
-// The list planner's lists of the clusters lo .. hi into out, and the lists
-// freed (by the calling thread; a single large range: on all threads).
-void take_lists(PlanLists& Q, int lo, int hi, RangeLists& out, bool parallel_free) {
+// The list planner's lists of the clusters lo .. hi into out (copied on all
+// threads when `parallel`); with `release` the lists are freed by the
+// calling thread (otherwise they stay with the plan until it is released).
+void take_lists(PlanLists& Q, int lo, int hi, RangeLists& out, bool parallel, bool release_here) {
     std::vector<std::vector<int>>* src[LS_N] = {&Q.nl, &Q.wl, &Q.all, &Q.endp};
+    std::vector<int64_t> off(hi - lo + 1);
     for (int k = 0; k < LS_N; k++) {
         auto& v = *src[k];
         out.cnt[k].assign(hi - lo, 0);
-        size_t tot = 0;
-        for (int c = lo; c < hi; c++) tot += v[c].size();
-        out.data[k].resize(tot);
-        size_t o = 0;
+        off[0] = 0;
         for (int c = lo; c < hi; c++) {
             out.cnt[k][c - lo] = (int32_t)v[c].size();
-            std::copy(v[c].begin(), v[c].end(), out.data[k].begin() + o);
-            o += v[c].size();
+            off[c - lo + 1] = off[c - lo] + (int64_t)v[c].size();
         }
+        out.data[k].resize((size_t)off[hi - lo]);
+        auto copy = [&](int64_t a, int64_t b) {
+            for (int64_t c = a; c < b; c++) std::copy(v[c].begin(), v[c].end(), out.data[k].begin() + off[c - lo]);
+        };
+        if (parallel) parallel_ranges(hi - lo, 4096, [&](int64_t a, int64_t b, int) { copy(lo + a, lo + b); });
+        else copy(lo, hi);
     }
-    auto release = [&](int64_t a, int64_t b) {
-        for (int64_t c = a; c < b; c++)
+    if (release_here)
+        for (int c = lo; c < hi; c++)
             for (auto* v : src) std::vector<int>().swap((*v)[c]);
-    };
-    if (parallel_free) parallel_ranges(hi - lo, 2048, [&](int64_t a, int64_t b, int) { release(lo + a, lo + b); });
-    else release(lo, hi);
 }
 
-void release_plan(LevelPlan& P) { P = LevelPlan{}; }
+// Frees a plan; the list planner's working lists on all threads (they were
+// allocated by the planning threads, and freeing hundreds of thousands of
+// them from one thread costs milliseconds).
+void release_plan(LevelPlan& P) {
+    for (auto& v : P.scratch) {
+        const int64_t n = (int64_t)v.size();
+        parallel_ranges(n, 2048, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t c = lo; c < hi; c++) std::vector<int>().swap(v[c]);
+        });
+    }
+    P = LevelPlan{};
+}
 
 // ranges: cluster ranges that share no block (independent problems); each
 // is planned on its own thread and phase k of the level is the union of the
@@ -1038,6 +1053,7 @@ void release_plan(LevelPlan& P) { P = LevelPlan{}; }
 // planner.
 void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {}) {
     const int nc = P.nc;
+    Trace tr;
     P.phase.assign(nc, -1);
     P.vanished.assign(nc, 0);
     P.phases.clear();
@@ -1069,6 +1085,7 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
         }
     };
     if (nr == 1 && !small(0)) parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) { init(lo, hi); });
+    tr.mark("    plan: working lists");
     std::atomic<int> next{0};
     auto work = [&] {
         for (int k = next++; k < nr; k = next++) {
@@ -1078,10 +1095,14 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
             }
             if (nr > 1) init(rg[k].first, rg[k].second);
             plan_range(P, Q, cur, rg[k].first, rg[k].second, ph[k]);
-            take_lists(Q, rg[k].first, rg[k].second, out[k], nr == 1);
+            if (nr == 1) tr.mark("    plan: list planner");
+            take_lists(Q, rg[k].first, rg[k].second, out[k], nr == 1, nr > 1);
         }
     };
     run_threads(std::min<int>(hs_threads(), nr), [&](int) { work(); });
+    tr.mark("    plan: phases and lists");
+    if (any_large && nr == 1)  // freed with the plan
+        for (auto* v : {&Q.nl, &Q.wl, &Q.all, &Q.endp}) P.scratch.push_back(std::move(*v));
     size_t nph = 0;
     for (auto& v : ph) nph = std::max(nph, v.size());
     P.phases.assign(nph, {});
@@ -1100,6 +1121,10 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
             base[k + 1] = base[k] + (int64_t)out[k].data[t].size();
         }
         for (int c = 0; c < nc; c++) L.ptr[c + 1] += L.ptr[c];
+        if (nr == 1) {  // one range: its entries are the list set's
+            L.idx = std::move(out[0].data[t]);
+            continue;
+        }
         L.idx.resize((size_t)base[nr]);
         auto copy = [&](int64_t a, int64_t b) {
             for (int64_t k = a; k < b; k++)
@@ -1108,6 +1133,7 @@ void plan_level(LevelPlan& P, const std::vector<std::pair<int, int>>& ranges = {
         if (nr > 64) parallel_ranges(nr, 16, [&](int64_t a, int64_t b, int) { copy(a, b); });
         else copy(0, nr);
     }
+    tr.mark("    plan: list sets");
 }
 
 // ---------------------------------------------------------------------------
@@ -1609,7 +1635,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             CK(launch_schur_phase(st, d_targets.as<TargetDev>(), g0, ng, d_contribs.as<ContribDev>(),
                                   L.d_tasks.as<TaskDev>(), L.d_fac.p, L.d_meta.as<int32_t>(),
                                   blocks.as<double>(), d_off.as<int64_t>(), d_ld.as<int32_t>(),
-                                  d_cur.as<int32_t>(), h->fp32));
+                                  d_cur.as<int32_t>(), h->fp32, h->opt.schur_products));
             h->prof.end(KC_SCHUR, st);
         }
     }
@@ -2839,6 +2865,7 @@ int hs_default_options(hs_options* opt) {
     if (!opt) return HS_ERR_ARG;
     std::memset(opt, 0, sizeof(*opt));
     opt->tol = 1e-2;
+    opt->schur_products = HS_PRODUCTS_TF32X3;
     opt->depth = -1;
     opt->leaf_lines = 4;
     opt->theta = 0.5;
@@ -2973,6 +3000,7 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
 // the no-DC elimination serves neither the rank predictor nor its records
 static int nodc_options_check(const hs_options* opt) {
     if (opt->no_dc != 0 && opt->no_dc != 1) return HS_ERR_ARG;
+    if (opt->schur_products < 0 || opt->schur_products > 2) return HS_ERR_ARG;
     if (opt->no_dc && (opt->rank_model || opt->record_ranks)) return HS_ERR_UNSUPPORTED;
     return HS_OK;
 }

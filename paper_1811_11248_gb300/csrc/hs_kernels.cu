@@ -885,6 +885,126 @@ k_schur_phase(const TargetDev* __restrict__ targets, int g0, const ContribDev* _
 }
 
 // ---------------------------------------------------------------------------
+// The same Schur update on the tensor cores (mixed form, FP32 factor): the
+// products C_t(:, p)^T C_t(:, q) as warp-level TF32 matrix multiply-adds
+// (mma.sync m16n8k8) with FP32 accumulation.  passes = 1: each FP32 entry
+// rounded to TF32 (10-bit mantissa); passes = 3: each entry split as
+// hi + lo (both TF32) and the product formed as hi*hi + hi*lo + lo*hi
+// (about 22 significant bits per entry, lo*lo dropped: about 2^-21 relative
+// error per product, against 2^-24 for FP32 and 2^-11 for one TF32 pass).  One CTA (8 warps) per target block, 64 x 64
+// output tiles, warp w computing rows 16 (w & 3) .. + 16 and columns
+// 32 (w >> 2) .. + 32 as four 16 x 8 tiles; C staged k-major in shared memory
+// (ld 72: the fragment loads of a warp hit 32 distinct banks).
+// ---------------------------------------------------------------------------
+constexpr int kTcKC = 32, kTcLd = 72;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return u;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int PASSES>
+__global__ void __launch_bounds__(256)
+k_schur_phase_tc(const TargetDev* __restrict__ targets, int g0, const ContribDev* __restrict__ contribs,
+                 const TaskDev* __restrict__ tasks, const float* __restrict__ fac,
+                 const int32_t* __restrict__ meta, double* __restrict__ blocks,
+                 const int64_t* __restrict__ blk_off, const int32_t* __restrict__ blk_ld,
+                 const int32_t* __restrict__ cur) {
+    constexpr int NS = PASSES == 1 ? 1 : 2;  // hi (and lo) parts
+    __shared__ uint32_t sp[NS][kTcKC][kTcLd];
+    __shared__ uint32_t sq[NS][kTcKC][kTcLd];
+    const TargetDev g = targets[g0 + blockIdx.x];
+    const int mp = cur[g.p], mq = cur[g.q];
+    double* A = blocks + blk_off[g.blk_pq];
+    const int lda = blk_ld[g.blk_pq];
+    double* At = blocks + blk_off[g.blk_qp];
+    const int ldt = blk_ld[g.blk_qp];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gi = lane >> 2, tg = lane & 3;       // fragment row group / thread in group
+    const int wi = 16 * (warp & 3), wj = 32 * (warp >> 2);
+    for (int ti = 0; ti < mp; ti += kSchurTile)
+        for (int tj = 0; tj < mq; tj += kSchurTile) {
+            float acc[4][4];
+#pragma unroll
+            for (int n = 0; n < 4; n++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[n][r] = 0.f;
+            for (int c = g.c_begin; c < g.c_end; c++) {
+                const ContribDev cb = contribs[c];
+                const TaskDev T = tasks[cb.task];
+                const int32_t* mt = meta + T.meta;
+                const int f = T.s - mt[0];
+                const int op = mt[1 + 2 * cb.kp] + ti, oq = mt[1 + 2 * cb.kq] + tj;
+                const float* C = fac + T.c_off;
+                for (int k0 = 0; k0 < f; k0 += kTcKC) {
+                    __syncthreads();
+                    for (int idx = tid; idx < kTcKC * kSchurTile; idx += 256) {
+                        const int kk = idx / kSchurTile, jj = idx % kSchurTile;
+                        const bool kin = k0 + kk < f;
+                        const float xp = (kin && ti + jj < mp) ? C[(int64_t)(k0 + kk) * T.ncap + op + jj] : 0.f;
+                        const float xq = (kin && tj + jj < mq) ? C[(int64_t)(k0 + kk) * T.ncap + oq + jj] : 0.f;
+                        const uint32_t hp = to_tf32(xp), hq = to_tf32(xq);
+                        sp[0][kk][jj] = hp;
+                        sq[0][kk][jj] = hq;
+                        if (NS == 2) {
+                            sp[NS - 1][kk][jj] = to_tf32(xp - __uint_as_float(hp));
+                            sq[NS - 1][kk][jj] = to_tf32(xq - __uint_as_float(hq));
+                        }
+                    }
+                    __syncthreads();
+                    const int kmax = min(kTcKC, f - k0);
+                    for (int k8 = 0; k8 < kmax; k8 += 8) {
+                        // A (16 x 8, row-major) = C_p^T: A[i][k] = sp[k][i]
+                        uint32_t a[NS][4];
+#pragma unroll
+                        for (int h = 0; h < NS; h++) {
+                            a[h][0] = sp[h][k8 + tg][wi + gi];
+                            a[h][1] = sp[h][k8 + tg][wi + gi + 8];
+                            a[h][2] = sp[h][k8 + tg + 4][wi + gi];
+                            a[h][3] = sp[h][k8 + tg + 4][wi + gi + 8];
+                        }
+#pragma unroll
+                        for (int n = 0; n < 4; n++) {
+                            // B (8 x 8, column-major) = C_q: B[k][j] = sq[k][j]
+                            uint32_t b[NS][2];
+#pragma unroll
+                            for (int h = 0; h < NS; h++) {
+                                b[h][0] = sq[h][k8 + tg][wj + 8 * n + gi];
+                                b[h][1] = sq[h][k8 + tg + 4][wj + 8 * n + gi];
+                            }
+                            if (PASSES == 3) {
+                                mma_tf32(acc[n], a[NS - 1], b[0]);  // lo * hi
+                                mma_tf32(acc[n], a[0], b[NS - 1]);  // hi * lo
+                            }
+                            mma_tf32(acc[n], a[0], b[0]);  // hi * hi
+                        }
+                    }
+                }
+            }
+            // D fragment: (gi, 2 tg + {0,1}) and (gi + 8, 2 tg + {0,1}) of each 16 x 8 tile
+#pragma unroll
+            for (int n = 0; n < 4; n++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int i = ti + wi + gi + 8 * (r >> 1), j = tj + wj + 8 * n + 2 * tg + (r & 1);
+                    if (i < mp && j < mq) {
+                        const double x = A[(int64_t)i * lda + j] - (double)acc[n][r];
+                        A[(int64_t)i * lda + j] = x;
+                        if (g.p != g.q) At[(int64_t)j * ldt + i] = x;
+                    }
+                }
+        }
+}
+
+// ---------------------------------------------------------------------------
 // Coarse levels (clusters of at most 32 DOFs): every phase of the level in one
 // launch, one warp per cluster elimination and one warp per Schur target,
 // __syncthreads() between them.
@@ -1976,10 +2096,16 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
 cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
                                const ContribDev* contribs, const TaskDev* tasks, const void* fac,
                                const int32_t* meta, double* blocks, const int64_t* blk_off, const int32_t* blk_ld,
-                               const int32_t* cur, int fp32) {
+                               const int32_t* cur, int fp32, int products) {
     if (ntargets <= 0) return cudaSuccess;
     counted();
-    if (fp32)
+    if (fp32 && products == kProductsTf32x3)
+        k_schur_phase_tc<3><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
+                                                      meta, blocks, blk_off, blk_ld, cur);
+    else if (fp32 && products == kProductsTf32)
+        k_schur_phase_tc<1><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
+                                                      meta, blocks, blk_off, blk_ld, cur);
+    else if (fp32)
         k_schur_phase<float><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
                                                        meta, blocks, blk_off, blk_ld, cur);
     else

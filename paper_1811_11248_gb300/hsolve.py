@@ -21,6 +21,7 @@ HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_UNSUPPORTED, HS_ERR_TIMEOUT = 4, 5, 6, 7
 HS_MEM_HOST, HS_MEM_DEVICE = 0, 1
 HS_PREC_FP64, HS_PREC_MIXED = 0, 1
 HS_KRYLOV_PCG, HS_KRYLOV_GMRES = 0, 1
+HS_PRODUCTS_FP32, HS_PRODUCTS_TF32X3, HS_PRODUCTS_TF32 = 0, 1, 2
 KERNEL_CLASSES = ("factor", "schur", "assembly", "top", "apply", "krylov", "factor_fused", "spmv")
 
 P = ctypes.c_void_p
@@ -37,7 +38,7 @@ class hs_options(ctypes.Structure):
                 ("precision", I32), ("krylov", I32), ("restart", I32), ("rtol", F64),
                 ("maxit", I32), ("mem", I32), ("profile", I32), ("stream", P), ("coords", P),
                 ("coarse_dense", I32), ("fused_levels", I32), ("record_ranks", I32),
-                ("rank_model", P), ("no_dc", I32), ("wait_polls", I32)]
+                ("rank_model", P), ("no_dc", I32), ("wait_polls", I32), ("schur_products", I32)]
 
 
 class hs_info(ctypes.Structure):

@@ -374,3 +374,52 @@ def test_full_size_vector_256x256x10_parity(hs, oracle_lib):
     assert rco == 0 and abs(i64 - ito) <= 1
     assert r64 <= 1e-8 and rmx <= 1e-8
     assert np.sum(kmx != k64) <= 0.05 * len(k64)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4])
+def test_tensor_core_schur_products(hs, oracle_lib, tol):
+    """The mixed form's Schur update (Eq. elim) with its products on the
+    tensor cores (mma.sync TF32, FP32 accumulation) against the same update
+    with FP32 products on the CUDA cores, each against the FP64 form on the
+    same inputs.  Three TF32 products per FP32 product (hi/lo split: about
+    22 significant bits, the lo*lo term dropped) err by about 2^-21 per
+    product against FP32's 2^-24, so the operator difference to FP64 stays
+    within 10x that of the FP32 products plus 1e-7.  One TF32 product (11
+    significant bits, about 2^-11 per product): within 1e-3.  Every mode reaches the true residual 1e-8 within 2 PCG iterations
+    of FP64 with at most 5% of the ranks differing."""
+    p = inputs.grid_operator(32, 32, 16, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
+    h64, ref, depth = setup_both(hs, oracle_lib, p, 6, tol)
+    rng = np.random.default_rng(4)
+    rs = [dev(rng.uniform(-1, 1, p.n)) for _ in range(3)]
+    z64 = []
+    for r in rs:
+        z = torch.empty_like(r)
+        h64.hs_apply(r, z)
+        z64.append(z)
+    x64 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    i64, _ = h64.hs_krylov(dev(p.b), x64)
+    f64 = np.concatenate([h64.level_info(l)[1] for l in range(depth)])
+    diffs, zs = {}, {}
+    for mode in (hs.HS_PRODUCTS_FP32, hs.HS_PRODUCTS_TF32X3, hs.HS_PRODUCTS_TF32):
+        h, _, _ = setup_both(hs, oracle_lib, p, 6, tol, precision=hs.HS_PREC_MIXED, schur_products=mode)
+        worst, zl = 0.0, []
+        for r, zr in zip(rs, z64):
+            z = torch.empty_like(r)
+            h.hs_apply(r, z)
+            zl.append(z)
+            worst = max(worst, float(torch.linalg.norm(z - zr) / torch.linalg.norm(zr)))
+        x = torch.empty_like(x64)
+        info, _ = h.hs_krylov(dev(p.b), x)
+        res = np.linalg.norm(p.b - p.matvec(x.cpu().numpy())) / np.linalg.norm(p.b)
+        fm = np.concatenate([h.level_info(l)[1] for l in range(depth)])
+        print(f"schur products mode {mode}: operator diff to FP64 {worst:.2e}, PCG {info.iters} vs {i64.iters}, "
+              f"residual {res:.2e}, ranks differing {int(np.sum(fm != f64))} of {len(f64)}")
+        assert res <= 1e-8 and info.iters <= i64.iters + 2
+        assert np.sum(fm != f64) <= 0.05 * len(f64)
+        diffs[mode], zs[mode] = worst, zl
+        h.close()
+    assert diffs[hs.HS_PRODUCTS_TF32X3] <= 10 * diffs[hs.HS_PRODUCTS_FP32] + 1e-7
+    assert diffs[hs.HS_PRODUCTS_TF32] <= 1e-3
+    # the tensor-core path ran: its results are not the CUDA-core ones
+    assert not torch.equal(zs[hs.HS_PRODUCTS_TF32][0], zs[hs.HS_PRODUCTS_FP32][0])
+    h64.close()
