@@ -21,7 +21,8 @@ Besides the headline step the line carries, each on its own workload:
   plain_fp64     the same step in FP64 throughout;
   tol_1e-4       the 64x64x16 workload at eps = 1e-4, FP64 and mixed;
   vector         the 256x256x10 two-component thin-shell operator
-                 (N = 1,310,720), GMRES(50) with FP64 restarts, FP64 and mixed;
+                 (N = 1,310,720), GMRES(50) with FP64 restarts, FP64, mixed
+                 and mixed with BF16 Schur products;
   batched        256 independent problems in one handle, problems/s;
   learned        the 512x512x20 workload (N = 5,242,880): full RRQR in FP64,
                  the mixed form, the mixed form with the trained rank
@@ -288,8 +289,10 @@ def leg_vector(ctx):
     prob = inputs.thin_shell_vector()
     d = ctx.to_dev(prob)
     out = {"workload": "vector-256x256x10x2 (N=1310720), ratio 1e6, coupling 0.5, eps 1e-2, GMRES(50)+IR rtol 1e-8"}
-    for name, prec in (("fp64", hsolve.HS_PREC_FP64), ("mixed", hsolve.HS_PREC_MIXED)):
-        ts, info, true, _ = ctx.timed_solve(prob, d, 2, tol=1e-2, rtol=1e-8, precision=prec,
+    for name, prec, prod in (("fp64", hsolve.HS_PREC_FP64, hsolve.HS_PRODUCTS_TF32X3),
+                             ("mixed", hsolve.HS_PREC_MIXED, hsolve.HS_PRODUCTS_TF32X3),
+                             ("mixed_bf16", hsolve.HS_PREC_MIXED, hsolve.HS_PRODUCTS_BF16)):
+        ts, info, true, _ = ctx.timed_solve(prob, d, 2, tol=1e-2, rtol=1e-8, precision=prec, schur_products=prod,
                                             krylov=hsolve.HS_KRYLOV_GMRES, restart=50)
         out[name] = summary(ts, info, true)
     del d

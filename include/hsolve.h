@@ -47,7 +47,7 @@ typedef enum {
 enum { HS_MEM_HOST = 0, HS_MEM_DEVICE = 1 };
 enum { HS_PREC_FP64 = 0, HS_PREC_MIXED = 1 };
 enum { HS_KRYLOV_PCG = 0, HS_KRYLOV_GMRES = 1 };
-enum { HS_PRODUCTS_FP32 = 0, HS_PRODUCTS_TF32X3 = 1, HS_PRODUCTS_TF32 = 2 };
+enum { HS_PRODUCTS_FP32 = 0, HS_PRODUCTS_TF32X3 = 1, HS_PRODUCTS_TF32 = 2, HS_PRODUCTS_BF16 = 3 };
 
 /* Partition tree: leaf c owns the DOFs perm[leaf_ptr[c] .. leaf_ptr[c+1]);
  * siblings 2c, 2c+1 merge at the next level (Sec. 4.2, Sec. 5).  n_leaf must
@@ -125,7 +125,8 @@ typedef struct {
                             entry split into two TF32 parts, three products,
                             about 2^-21 relative error per product) or
                             HS_PRODUCTS_TF32 (tensor cores, one TF32
-                            product, about 2^-11); FP32
+                            product, about 2^-11) or HS_PRODUCTS_BF16
+                            (tensor cores, BF16 products, about 2^-8); FP32
                             accumulation and an FP64 block store in every
                             case.  Ignored by the FP64 form.                 */
 } hs_options;

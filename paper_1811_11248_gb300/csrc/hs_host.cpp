@@ -3000,7 +3000,7 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
 // the no-DC elimination serves neither the rank predictor nor its records
 static int nodc_options_check(const hs_options* opt) {
     if (opt->no_dc != 0 && opt->no_dc != 1) return HS_ERR_ARG;
-    if (opt->schur_products < 0 || opt->schur_products > 2) return HS_ERR_ARG;
+    if (opt->schur_products < 0 || opt->schur_products > 3) return HS_ERR_ARG;
     if (opt->no_dc && (opt->rank_model || opt->record_ranks)) return HS_ERR_UNSUPPORTED;
     return HS_OK;
 }

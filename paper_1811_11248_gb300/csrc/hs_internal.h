@@ -130,8 +130,8 @@ cudaError_t launch_factor_nodc(cudaStream_t st, const TaskDev* tasks, int t0, in
                                const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta, double* ws,
                                double eps2, int32_t* status, int32_t level);
 // products of the mixed form's Schur update: FP32 on the CUDA cores, or
-// TF32 tensor-core products (one pass, or three with the hi/lo split)
-enum { kProductsFp32 = 0, kProductsTf32x3 = 1, kProductsTf32 = 2 };
+// tensor-core products: TF32 (one pass, or three with the hi/lo split), BF16
+enum { kProductsFp32 = 0, kProductsTf32x3 = 1, kProductsTf32 = 2, kProductsBf16 = 3 };
 cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0, int ntargets,
                                const ContribDev* contribs, const TaskDev* tasks, const void* fac,
                                const int32_t* meta, double* blocks, const int64_t* blk_off,

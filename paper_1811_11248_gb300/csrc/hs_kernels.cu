@@ -1004,6 +1004,97 @@ k_schur_phase_tc(const TargetDev* __restrict__ targets, int g0, const ContribDev
         }
 }
 
+// The same update with BF16 products (mma.sync m16n8k16, 8-bit mantissas,
+// about 2^-8 relative error per product) and FP32 accumulation: C staged as
+// FP32 k-major, pairs of consecutive k packed into bf16x2 fragment registers.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    uint32_t u;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(hi), "f"(lo));
+    return u;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256)
+k_schur_phase_bf16(const TargetDev* __restrict__ targets, int g0, const ContribDev* __restrict__ contribs,
+                   const TaskDev* __restrict__ tasks, const float* __restrict__ fac,
+                   const int32_t* __restrict__ meta, double* __restrict__ blocks,
+                   const int64_t* __restrict__ blk_off, const int32_t* __restrict__ blk_ld,
+                   const int32_t* __restrict__ cur) {
+    __shared__ float sp[kTcKC][kTcLd];
+    __shared__ float sq[kTcKC][kTcLd];
+    const TargetDev g = targets[g0 + blockIdx.x];
+    const int mp = cur[g.p], mq = cur[g.q];
+    double* A = blocks + blk_off[g.blk_pq];
+    const int lda = blk_ld[g.blk_pq];
+    double* At = blocks + blk_off[g.blk_qp];
+    const int ldt = blk_ld[g.blk_qp];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gi = lane >> 2, tg = lane & 3;
+    const int wi = 16 * (warp & 3), wj = 32 * (warp >> 2);
+    for (int ti = 0; ti < mp; ti += kSchurTile)
+        for (int tj = 0; tj < mq; tj += kSchurTile) {
+            float acc[4][4];
+#pragma unroll
+            for (int n = 0; n < 4; n++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[n][r] = 0.f;
+            for (int c = g.c_begin; c < g.c_end; c++) {
+                const ContribDev cb = contribs[c];
+                const TaskDev T = tasks[cb.task];
+                const int32_t* mt = meta + T.meta;
+                const int f = T.s - mt[0];
+                const int op = mt[1 + 2 * cb.kp] + ti, oq = mt[1 + 2 * cb.kq] + tj;
+                const float* C = fac + T.c_off;
+                for (int k0 = 0; k0 < f; k0 += kTcKC) {
+                    __syncthreads();
+                    for (int idx = tid; idx < kTcKC * kSchurTile; idx += 256) {
+                        const int kk = idx / kSchurTile, jj = idx % kSchurTile;
+                        const bool kin = k0 + kk < f;
+                        sp[kk][jj] = (kin && ti + jj < mp) ? C[(int64_t)(k0 + kk) * T.ncap + op + jj] : 0.f;
+                        sq[kk][jj] = (kin && tj + jj < mq) ? C[(int64_t)(k0 + kk) * T.ncap + oq + jj] : 0.f;
+                    }
+                    __syncthreads();
+                    const int kmax = min(kTcKC, f - k0);
+                    for (int k16 = 0; k16 < kmax; k16 += 16) {
+                        // A (16 x 16, row-major) = C_p^T: register r holds
+                        // A[row][col], A[row][col + 1] (low half first)
+                        uint32_t a[4];
+                        a[0] = pack_bf16(sp[k16 + 2 * tg][wi + gi], sp[k16 + 2 * tg + 1][wi + gi]);
+                        a[1] = pack_bf16(sp[k16 + 2 * tg][wi + gi + 8], sp[k16 + 2 * tg + 1][wi + gi + 8]);
+                        a[2] = pack_bf16(sp[k16 + 2 * tg + 8][wi + gi], sp[k16 + 2 * tg + 9][wi + gi]);
+                        a[3] = pack_bf16(sp[k16 + 2 * tg + 8][wi + gi + 8], sp[k16 + 2 * tg + 9][wi + gi + 8]);
+#pragma unroll
+                        for (int n = 0; n < 4; n++) {
+                            // B (16 x 8, column-major) = C_q: B[k][j], k pairs per register
+                            const int j = wj + 8 * n + gi;
+                            uint32_t b[2];
+                            b[0] = pack_bf16(sq[k16 + 2 * tg][j], sq[k16 + 2 * tg + 1][j]);
+                            b[1] = pack_bf16(sq[k16 + 2 * tg + 8][j], sq[k16 + 2 * tg + 9][j]);
+                            mma_bf16(acc[n], a, b);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < 4; n++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int i = ti + wi + gi + 8 * (r >> 1), j = tj + wj + 8 * n + 2 * tg + (r & 1);
+                    if (i < mp && j < mq) {
+                        const double x = A[(int64_t)i * lda + j] - (double)acc[n][r];
+                        A[(int64_t)i * lda + j] = x;
+                        if (g.p != g.q) At[(int64_t)j * ldt + i] = x;
+                    }
+                }
+        }
+}
+
 // ---------------------------------------------------------------------------
 // Coarse levels (clusters of at most 32 DOFs): every phase of the level in one
 // launch, one warp per cluster elimination and one warp per Schur target,
@@ -2102,6 +2193,9 @@ cudaError_t launch_schur_phase(cudaStream_t st, const TargetDev* targets, int g0
     if (fp32 && products == kProductsTf32x3)
         k_schur_phase_tc<3><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
                                                       meta, blocks, blk_off, blk_ld, cur);
+    else if (fp32 && products == kProductsBf16)
+        k_schur_phase_bf16<<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
+                                                     meta, blocks, blk_off, blk_ld, cur);
     else if (fp32 && products == kProductsTf32)
         k_schur_phase_tc<1><<<ntargets, 256, 0, st>>>(targets, g0, contribs, tasks, static_cast<const float*>(fac),
                                                       meta, blocks, blk_off, blk_ld, cur);

@@ -21,7 +21,7 @@ HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_UNSUPPORTED, HS_ERR_TIMEOUT = 4, 5, 6, 7
 HS_MEM_HOST, HS_MEM_DEVICE = 0, 1
 HS_PREC_FP64, HS_PREC_MIXED = 0, 1
 HS_KRYLOV_PCG, HS_KRYLOV_GMRES = 0, 1
-HS_PRODUCTS_FP32, HS_PRODUCTS_TF32X3, HS_PRODUCTS_TF32 = 0, 1, 2
+HS_PRODUCTS_FP32, HS_PRODUCTS_TF32X3, HS_PRODUCTS_TF32, HS_PRODUCTS_BF16 = 0, 1, 2, 3
 KERNEL_CLASSES = ("factor", "schur", "assembly", "top", "apply", "krylov", "factor_fused", "spmv")
 
 P = ctypes.c_void_p

@@ -385,8 +385,10 @@ def test_tensor_core_schur_products(hs, oracle_lib, tol):
     22 significant bits, the lo*lo term dropped) err by about 2^-21 per
     product against FP32's 2^-24, so the operator difference to FP64 stays
     within 10x that of the FP32 products plus 1e-7.  One TF32 product (11
-    significant bits, about 2^-11 per product): within 1e-3.  Every mode reaches the true residual 1e-8 within 2 PCG iterations
-    of FP64 with at most 5% of the ranks differing."""
+    significant bits, about 2^-11 per product): within 1e-3.  BF16 products
+    (8 significant bits, about 2^-8): within 1e-2.  Every mode reaches the
+    true residual 1e-8 with at most 5% of the ranks differing, within 2 PCG
+    iterations of FP64 (4 with BF16)."""
     p = inputs.grid_operator(32, 32, 16, ratio=1e6, sigma=1.0, seed=1, bc="ice", shelf=0.5)
     h64, ref, depth = setup_both(hs, oracle_lib, p, 6, tol)
     rng = np.random.default_rng(4)
@@ -400,7 +402,7 @@ def test_tensor_core_schur_products(hs, oracle_lib, tol):
     i64, _ = h64.hs_krylov(dev(p.b), x64)
     f64 = np.concatenate([h64.level_info(l)[1] for l in range(depth)])
     diffs, zs = {}, {}
-    for mode in (hs.HS_PRODUCTS_FP32, hs.HS_PRODUCTS_TF32X3, hs.HS_PRODUCTS_TF32):
+    for mode in (hs.HS_PRODUCTS_FP32, hs.HS_PRODUCTS_TF32X3, hs.HS_PRODUCTS_TF32, hs.HS_PRODUCTS_BF16):
         h, _, _ = setup_both(hs, oracle_lib, p, 6, tol, precision=hs.HS_PREC_MIXED, schur_products=mode)
         worst, zl = 0.0, []
         for r, zr in zip(rs, z64):
@@ -414,12 +416,13 @@ def test_tensor_core_schur_products(hs, oracle_lib, tol):
         fm = np.concatenate([h.level_info(l)[1] for l in range(depth)])
         print(f"schur products mode {mode}: operator diff to FP64 {worst:.2e}, PCG {info.iters} vs {i64.iters}, "
               f"residual {res:.2e}, ranks differing {int(np.sum(fm != f64))} of {len(f64)}")
-        assert res <= 1e-8 and info.iters <= i64.iters + 2
+        assert res <= 1e-8 and info.iters <= i64.iters + (4 if mode == hs.HS_PRODUCTS_BF16 else 2)
         assert np.sum(fm != f64) <= 0.05 * len(f64)
         diffs[mode], zs[mode] = worst, zl
         h.close()
     assert diffs[hs.HS_PRODUCTS_TF32X3] <= 10 * diffs[hs.HS_PRODUCTS_FP32] + 1e-7
     assert diffs[hs.HS_PRODUCTS_TF32] <= 1e-3
+    assert diffs[hs.HS_PRODUCTS_BF16] <= 1e-2
     # the tensor-core path ran: its results are not the CUDA-core ones
     assert not torch.equal(zs[hs.HS_PRODUCTS_TF32][0], zs[hs.HS_PRODUCTS_FP32][0])
     h64.close()
