@@ -91,12 +91,14 @@ typedef struct {
                             only, for clusters of at least 16 DOFs with
                             dense fill columns on the per-cluster kernel: a
                             cluster predicted to have rank 0 scales those
-                            columns in FP32 only; if the fill block's
-                            squared norm is then at most eps^2 / 2 its rank
-                            is 0 and the FP64 scaling of those columns and
-                            the QR are skipped, otherwise they are scaled
-                            again in FP64 and the column-pivoted QR decides
-                            as usual.  Copied during hs_setup.                */
+                            columns in FP32 only; if the FP32 result plus a
+                            forward-error bound of the FP32 substitution
+                            (from ||G^-1||_F, the input norm and
+                            || |G| |result| ||_F) proves ||G^-1 A_sw||_F <=
+                            eps, its rank is 0 and the FP64 scaling of those
+                            columns and the QR are skipped; otherwise they
+                            are scaled again in FP64 and the column-pivoted
+                            QR decides as usual.  Copied during hs_setup.   */
     int32_t no_dc;       /* 0 (default): deferred compression (Sec. 2: A_sw
                             scaled by G_s^-1 before it is compressed, Eq.
                             offdiag_new).  1: without it, the original

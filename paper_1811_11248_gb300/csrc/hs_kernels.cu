@@ -674,10 +674,10 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         if (fe && tid < kFeat) fe[tid] = fsh[tid];
     }
     // learned rank-0 speculation (mixed form): when the predictor says rank 0,
-    // dense fill columns are scaled in FP32 only, and the rank is certified 0
-    // if the fill block's squared norm is at most eps^2 / 2; otherwise they
-    // are gathered again and scaled in FP64 and the column-pivoted QR decides
-    // as usual
+    // dense fill columns are scaled in FP32 only, and the rank is 0 if the
+    // FP32 result with its forward-error bound proves ||G^-1 A_sw||_F <= eps;
+    // otherwise they are gathered again and scaled in FP64 and the
+    // column-pivoted QR decides as usual
     bool spec0 = false;
     if (predict) {
         const float y = predict_fraction(g, model, fsh, fsh + kFeat, G32, red);
@@ -688,7 +688,9 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     }
     // pass 2: dense columns by forward substitution from their first nonzero
     // row (zeros above stay zero); speculated fill columns in FP32 (values in
-    // the first float of each slot)
+    // the first float of each slot), with the terms of their error bound:
+    // the squared norms of the FP32 inputs (lb) and of |G| |x| (lz)
+    float lb = 0.f, lz = 0.f;
     for (int j = tid; j < W; j += NT) {
         if (!dense[j]) continue;
         int i0 = 0;
@@ -697,8 +699,17 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             float* Mf = reinterpret_cast<float*>(M);
             for (int i = i0; i < s; i++) {
                 float acc = (float)M[(int64_t)i * Wt + j];
-                for (int k = i0; k < i; k++) acc -= G32[i * s + k] * Mf[2 * ((int64_t)k * Wt + j)];
-                Mf[2 * ((int64_t)i * Wt + j)] = acc * (float)rdiag[i];
+                lb = fmaf(acc, acc, lb);
+                float za = 0.f;
+                for (int k = i0; k < i; k++) {
+                    const float gk = G32[i * s + k], xk = Mf[2 * ((int64_t)k * Wt + j)];
+                    acc -= gk * xk;
+                    za = fmaf(fabsf(gk), fabsf(xk), za);
+                }
+                const float xi = acc * (float)rdiag[i];
+                Mf[2 * ((int64_t)i * Wt + j)] = xi;
+                za = fmaf(fabsf(G32[i * s + i]), fabsf(xi), za);
+                lz = fmaf(za, za, lz);
             }
             for (int i = 0; i < i0; i++) Mf[2 * ((int64_t)i * Wt + j)] = 0.f;
         } else {
@@ -728,7 +739,28 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                 }
             }
         }
-        rank0 = g.sum(ld + (double)lf, red) <= 0.5 * eps2;
+        // Certificate that the exact scaled block B = G^-1 A_sw has
+        // ||B||_F <= eps (rank 0 by the rank rule): the FP32 result B' of the
+        // substitution solves (G + E) B' = fl32(A_sw) with |E| <= gamma |G|,
+        // gamma = (s + 2) u / (1 - (s + 2) u), u = 2^-24 (rounding of G and of
+        // the reciprocal pivots, s - 1 products and sums), so
+        // ||B - B'||_F <= ||G^-1||_2 (u ||A_sw||_F + gamma || |G| |B'| ||_F)
+        // (standard forward-error analysis of triangular substitution).
+        // ||G^-1||_2 <= ||X||_F for the FP64 inverse X already formed (doubled
+        // to cover X's own error; the FP64 Cholesky is meaningless before
+        // that bound is).  Sums of squares in FP32 carry at most a 1e-4
+        // relative error here.  Rank 0 only if ||B'||_F + bound <= eps.
+        double lx = 0.0;
+        for (int idx = tid; idx < s * s; idx += NT) {
+            const double x = M[(int64_t)(idx / s) * Wt + W + idx % s];
+            lx = fma(x, x, lx);
+        }
+        const double nb = sqrt(g.sum(ld + (double)lf, red)) * (1.0 + 1e-4);
+        const double nin = sqrt(g.sum((double)lb, red)), nz = sqrt(g.sum((double)lz, red));
+        const double nx = 2.0 * sqrt(g.sum(lx, red));
+        const double u = 5.9604644775390625e-8, gam = (s + 2) * u / (1.0 - (s + 2) * u);
+        const double bound = nx * (u * nin + gam * nz) * (1.0 + 1e-4);
+        rank0 = (nb + bound) * (nb + bound) <= eps2;
         if (!rank0) {
             // fallback: the fill columns again from the blocks, scaled in FP64
             for (int e = T.nn + tid; e < L; e += NT)

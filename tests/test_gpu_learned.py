@@ -4,7 +4,8 @@ library's own kernels; on held-out problems it must beat the best constant
 predictor clearly, and the learned mixed form (the prediction gates the
 precision of each cluster's compression) must keep the mixed form's bars
 against FP64: iterations within 1, true residual <= 1e-8, at most 5% of
-ranks differing.  The same bars hold on the 512x512x20 workload."""
+ranks differing; no cluster the rank-0 certificate accepts has a nonzero
+rank in FP64.  The same bars hold on the 512x512x20 workload."""
 import numpy as np
 import pytest
 
@@ -69,6 +70,11 @@ def test_learned_mixed_form(trained):
     assert res <= 1e-8 and ilr.rel_resid <= 1e-8
     assert abs(ilr.iters - i64.iters) <= 1
     assert np.sum(rlr != r64) <= 0.05 * len(r64)
+    # the rank-0 certificate proves ||G^-1 A_sw||_F <= eps: a cluster it
+    # certifies (rank 0 here, above 0 without the predictor) has rank 0 in FP64
+    certified = (rlr == 0) & (rmx > 0)
+    print(f"certified rank 0 where the mixed form's QR found a rank: {int(certified.sum())}")
+    assert np.sum(certified & (r64 > 0)) == 0
 
 
 @pytest.mark.slow
@@ -101,6 +107,11 @@ def test_learned_form_at_512x512x20(trained):
         res[name] = (h.kernel_stats()["factor"]["ms"], info.iters, info.rel_resid, ranks)
         h.close()
     print("factor ms and iterations:", {k: v[:3] for k, v in res.items()})
+    # clusters certified rank 0 where the mixed form's FP32 QR found a rank:
+    # only threshold cases (the FP32 QR rounding a norm just below eps above it)
+    cert = int(np.sum((res["learned"][3] == 0) & (res["mixed"][3] > 0)))
+    print("certified rank 0 where the mixed form's QR found a rank:", cert)
+    assert cert <= max(2, 1e-4 * len(res["mixed"][3]))
     assert abs(res["learned"][1] - res["mixed"][1]) <= 1
     assert res["learned"][2] <= 1e-8
     assert np.sum(res["learned"][3] != res["mixed"][3]) <= 0.05 * len(res["mixed"][3])
