@@ -48,6 +48,7 @@ enum { HS_MEM_HOST = 0, HS_MEM_DEVICE = 1 };
 enum { HS_PREC_FP64 = 0, HS_PREC_MIXED = 1 };
 enum { HS_KRYLOV_PCG = 0, HS_KRYLOV_GMRES = 1 };
 enum { HS_PRODUCTS_FP32 = 0, HS_PRODUCTS_TF32X3 = 1, HS_PRODUCTS_TF32 = 2, HS_PRODUCTS_BF16 = 3 };
+enum { HS_PART_AUTO = 0, HS_PART_MULTILEVEL = 1 };
 
 /* Partition tree: leaf c owns the DOFs perm[leaf_ptr[c] .. leaf_ptr[c+1]);
  * siblings 2c, 2c+1 merge at the next level (Sec. 4.2, Sec. 5).  n_leaf must
@@ -131,6 +132,11 @@ typedef struct {
                             (tensor cores, BF16 products, about 2^-8); FP32
                             accumulation and an FP64 block store in every
                             case.  Ignored by the FP64 form.                 */
+    int32_t partitioner;  /* when no tree is given: HS_PART_AUTO (default:
+                            coordinate bisection with coords, else BFS
+                            graph growing) or HS_PART_MULTILEVEL (the
+                            multilevel graph bisection of
+                            hs_partition_multilevel; coords ignored)         */
 } hs_options;
 
 typedef struct {
@@ -157,6 +163,18 @@ int hs_default_options(hs_options* opt);
 int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col,
                           const double* val, const double* coords, int32_t leaf_lines,
                           double theta, hs_tree* out);
+
+/* The same partition from the matrix alone (Sec. 4.2 with a graph
+ * partitioner in place of coordinates; Sec. 6 on black-box use): the lines
+ * are found as above, then the weighted line graph (an edge per pair of
+ * lines sharing a nonzero, weight = sum of |a_ij| over those nonzeros) is
+ * bisected recursively by a multilevel method (heavy-edge matching,
+ * graph growing on the coarsest graph, Fiduccia-Mattheyses refinement on
+ * the way back up) into ceil(k/2) and floor(k/2) lines at every split.  The
+ * result depends only on the matrix (not on the thread count).  Arguments,
+ * ownership and errors as for hs_partition_extruded. */
+int hs_partition_multilevel(int64_t n, const int64_t* rowptr, const int32_t* col,
+                            const double* val, int32_t leaf_lines, double theta, hs_tree* out);
 int hs_tree_free(hs_tree* t);
 
 /* Phase plan of one level (host only, no device work; the same code the
@@ -186,7 +204,8 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
 
 /* Hierarchical_Factor (Algorithm 1): scaled low-rank elimination of every
  * cluster, level by level, then dense Cholesky of the top.  tree may be NULL
- * (then hs_partition_extruded runs on options->coords, options->leaf_lines,
+ * (then hs_partition_extruded, or hs_partition_multilevel when
+ * options->partitioner says so, runs on options->coords, options->leaf_lines,
  * options->theta, and options->depth applies).  CSR in options->mem.  On HS_ERR_NOT_SPD the
  * failing (level, cluster) is written to *info when info is not NULL.
  * With device inputs the pattern (and, for the partitioner, the values) is

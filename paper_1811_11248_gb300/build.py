@@ -1,6 +1,6 @@
 """Build the solver's C-ABI shared library for sm_103a (in-tree, nvcc only).
 
-Four translation units compiled in parallel, then linked into
+Five translation units compiled in parallel, then linked into
 paper_1811_11248_gb300/_build/libhsolve.so.  The CUDA runtime is linked
 statically so the library has no dependency beyond the driver.
 """
@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhsolve.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hs_kernels.cu", "hs_mlp.cu", "hs_nodc.cu", "hs_host.cpp"]
+SOURCES = ["hs_kernels.cu", "hs_mlp.cu", "hs_nodc.cu", "hs_host.cpp", "hs_mlpart.cpp"]
 
 
 def _nvcc():

@@ -339,7 +339,10 @@ struct Partitioner {
     int nl = 0;
     std::vector<double> lx, ly;
     bool have_coords = false;
+    bool multilevel = false;
     std::vector<int> gptr, gadj;
+    std::vector<double> gw;       // line-graph edge weights (multilevel only)
+    std::vector<int> own, loc;    // per line: its set in the current round and its place there
     int L = 0;
     std::vector<int> leaf_of;
     int next_leaf = 0;
@@ -383,12 +386,31 @@ struct Partitioner {
     // longer extent, else the first ceil(k/2) lines of a BFS order started
     // from a pseudo-peripheral line; both parts come out ascending.  Only the
     // coordinate rule runs on several sets at once (the BFS reads the marks
-    // of neighbouring lines, which may belong to another set).
-    void bisect(const std::vector<int>& set, std::vector<int>& a, std::vector<int>& b) {
+    // of neighbouring lines, which may belong to another set).  The
+    // multilevel rule bisects the weighted subgraph induced by `set` (its
+    // lines carry own == sid) into ceil(k/2) and floor(k/2) lines.
+    void bisect(const std::vector<int>& set, std::vector<int>& a, std::vector<int>& b, int sid = -1) {
         const size_t k = set.size(), left = (k + 1) / 2;
         a.clear();
         b.clear();
-        if (have_coords) {
+        if (multilevel) {
+            std::vector<int> sp(k + 1, 0), sa;
+            std::vector<double> sw;
+            for (size_t i = 0; i < k; i++) {
+                const int x = set[i];
+                for (int e = gptr[x]; e < gptr[x + 1]; e++)
+                    if (own[gadj[e]] == sid) {
+                        sa.push_back(loc[gadj[e]]);
+                        sw.push_back(gw[e]);
+                    }
+                sp[i + 1] = (int)sa.size();
+            }
+            std::vector<char> part;
+            ml_bisect((int)k, sp.data(), sa.data(), sw.data(), (int)left, part);
+            a.reserve(left);
+            b.reserve(k - left);
+            for (size_t i = 0; i < k; i++) (part[i] == 0 ? a : b).push_back(set[i]);
+        } else if (have_coords) {
             double x0 = lx[set[0]], x1 = x0, y0 = ly[set[0]], y1 = y0;
             for (int x : set) {
                 x0 = std::min(x0, lx[x]); x1 = std::max(x1, lx[x]);
@@ -441,7 +463,7 @@ struct Partitioner {
     // The same leaves; for many lines with coordinates, in L rounds with all
     // sets of a round bisected in parallel.
     void split_all(std::vector<int> all) {
-        if (!(have_coords && nl > (1 << 15) && !tl_serial)) {
+        if (!multilevel && !(have_coords && nl > (1 << 15) && !tl_serial)) {
             split(std::move(all), 0, 0);
             return;
         }
@@ -452,9 +474,17 @@ struct Partitioner {
             const int ns = (int)sets.size(), half = 1 << (L - depth - 1);
             next.assign(2 * (size_t)ns, {});
             nbase.assign(2 * (size_t)ns, 0);
+            if (multilevel)  // each line learns its set of this round before any set is bisected
+                parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
+                    for (int64_t i = lo; i < hi; i++)
+                        for (size_t j = 0; j < sets[i].size(); j++) {
+                            own[sets[i][j]] = (int)i;
+                            loc[sets[i][j]] = (int)j;
+                        }
+                });
             parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
                 for (int64_t i = lo; i < hi; i++) {
-                    bisect(sets[i], next[2 * i], next[2 * i + 1]);
+                    bisect(sets[i], next[2 * i], next[2 * i + 1], (int)i);
                     nbase[2 * i] = base[i];
                     nbase[2 * i + 1] = base[i] + half;
                     std::vector<int>().swap(sets[i]);
@@ -471,7 +501,8 @@ struct Partitioner {
 };
 
 int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const double* val, const double* coords,
-                   int leaf_lines, double theta, std::vector<int32_t>& perm, std::vector<int32_t>& leaf_ptr) {
+                   int leaf_lines, double theta, std::vector<int32_t>& perm, std::vector<int32_t>& leaf_ptr,
+                   int method = kPartAuto) {
     const int n = (int)n64;
     Trace tr;
     // strongly coupled lines: union-find over |a_ij| >= theta * max_{k != i} |a_ik|.
@@ -611,6 +642,40 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
         }
     }
     tr.mark("  partition: line graph");
+    if (method == kPartMultilevel) {
+        // edge weight between two lines: sum of |a_ij| over the nonzeros
+        // joining them (summed in DOF order, then CSR order)
+        P.multilevel = true;
+        P.gw.assign(P.gadj.size(), 0.0);
+        const int nl = P.nl;
+        std::vector<int> lptr(nl + 1, 0), ldof(n);
+        for (int i = 0; i < n; i++) lptr[line_of[i] + 1]++;
+        for (int l = 0; l < nl; l++) lptr[l + 1] += lptr[l];
+        {
+            std::vector<int> pos(lptr.begin(), lptr.end() - 1);
+            for (int i = 0; i < n; i++) ldof[pos[line_of[i]]++] = i;
+        }
+        parallel_ranges(nl, 256, [&](int64_t lo, int64_t hi, int) {
+            std::vector<double> acc(nl, 0.0);
+            for (int64_t l = lo; l < hi; l++) {
+                for (int q = lptr[l]; q < lptr[l + 1]; q++) {
+                    const int i = ldof[q];
+                    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                        const int lj = line_of[col[e]];
+                        if (lj != l) acc[lj] += std::fabs(val[e]);
+                    }
+                }
+                for (int e = P.gptr[l]; e < P.gptr[l + 1]; e++) {
+                    P.gw[e] = acc[P.gadj[e]];
+                    acc[P.gadj[e]] = 0.0;
+                }
+            }
+        });
+        P.own.assign(nl, -1);
+        P.loc.assign(nl, 0);
+        coords = nullptr;
+        tr.mark("  partition: edge weights");
+    }
     if (coords) {
         P.have_coords = true;
         P.lx.resize(P.nl);
@@ -1860,7 +1925,7 @@ void partition_batched(hs_factor_s* h, const int64_t* rp, const int32_t* cl, con
             }
             if (bad) return;
             partition_impl(m, srp.data(), scol.data(), vl + rp[lo], h->opt.coords ? h->opt.coords + 2 * lo : nullptr,
-                           h->opt.leaf_lines, h->opt.theta, perm[p], lp[p]);
+                           h->opt.leaf_lines, h->opt.theta, perm[p], lp[p], h->opt.partitioner);
         }
     };
     run_threads(std::min(hs_threads(), np), [&](int) { work(); });
@@ -1950,7 +2015,8 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         leaf_ptr.assign(tree_in->leaf_ptr, tree_in->leaf_ptr + tree_in->n_leaf + 1);
         depth = tree_in->depth;
     } else {
-        partition_impl(n, rp, cl, vl, h->opt.coords, h->opt.leaf_lines, h->opt.theta, h->perm, leaf_ptr);
+        partition_impl(n, rp, cl, vl, h->opt.coords, h->opt.leaf_lines, h->opt.theta, h->perm, leaf_ptr,
+                       h->opt.partitioner);
         depth = h->opt.depth;
     }
     const int nleaf = (int)leaf_ptr.size() - 1;
@@ -2884,8 +2950,8 @@ int hs_default_options(hs_options* opt) {
     return HS_OK;
 }
 
-int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
-                          const double* coords, int32_t leaf_lines, double theta, hs_tree* out) {
+static int partition_entry(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                           const double* coords, int32_t leaf_lines, double theta, int method, hs_tree* out) {
     if (!out) return HS_ERR_ARG;
     out->n_leaf = 0;
     out->perm = nullptr;
@@ -2894,7 +2960,7 @@ int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col, 
     if (n <= 0 || n > INT32_MAX || !rowptr || !col || !val || leaf_lines <= 0) return HS_ERR_ARG;
     return run_guarded([&] {
         std::vector<int32_t> perm, lp;
-        partition_impl(n, rowptr, col, val, coords, leaf_lines, theta, perm, lp);
+        partition_impl(n, rowptr, col, val, coords, leaf_lines, theta, perm, lp, method);
         const int nleaf = (int)lp.size() - 1;
         out->perm = static_cast<int32_t*>(std::malloc(sizeof(int32_t) * n));
         out->leaf_ptr = static_cast<int32_t*>(std::malloc(sizeof(int32_t) * (nleaf + 1)));
@@ -2912,6 +2978,16 @@ int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col, 
         while ((1 << (Lg + 1)) <= nleaf) Lg++;
         out->depth = std::max(nleaf >= 2 ? 1 : 0, Lg - 2);
     });
+}
+
+int hs_partition_extruded(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                          const double* coords, int32_t leaf_lines, double theta, hs_tree* out) {
+    return partition_entry(n, rowptr, col, val, coords, leaf_lines, theta, kPartAuto, out);
+}
+
+int hs_partition_multilevel(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                            int32_t leaf_lines, double theta, hs_tree* out) {
+    return partition_entry(n, rowptr, col, val, nullptr, leaf_lines, theta, kPartMultilevel, out);
 }
 
 int hs_tree_free(hs_tree* t) {
@@ -3001,6 +3077,7 @@ int hs_plan_level(int32_t nc, const int64_t* adj_ptr, const int32_t* adj, const 
 static int nodc_options_check(const hs_options* opt) {
     if (opt->no_dc != 0 && opt->no_dc != 1) return HS_ERR_ARG;
     if (opt->schur_products < 0 || opt->schur_products > 3) return HS_ERR_ARG;
+    if (opt->partitioner != HS_PART_AUTO && opt->partitioner != HS_PART_MULTILEVEL) return HS_ERR_ARG;
     if (opt->no_dc && (opt->rank_model || opt->record_ranks)) return HS_ERR_UNSUPPORTED;
     return HS_OK;
 }

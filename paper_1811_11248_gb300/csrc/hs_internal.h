@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -234,5 +235,12 @@ constexpr int kNoAllocMaxDevices = 64;
 // device address of the static scratch on the current device (looked up once per device)
 cudaError_t noalloc_scratch(double** ptr);
 constexpr int kFactorMaxSmem = 226 * 1024;  // dynamic part; static shared adds a few bytes
+
+// Multilevel bisection (hs_mlpart.cpp) of a weighted graph: CSR ptr[n+1],
+// adj, w (symmetric, no self loops, w > 0).  part[v] = 0 for exactly na
+// vertices (0 <= na <= n), 1 for the rest, chosen for a small edge cut.
+void ml_bisect(int n, const int* ptr, const int* adj, const double* w, int na, std::vector<char>& part);
+// partitioner methods of partition_impl
+enum { kPartAuto = 0, kPartMultilevel = 1 };
 
 }  // namespace hs

@@ -22,6 +22,7 @@ HS_MEM_HOST, HS_MEM_DEVICE = 0, 1
 HS_PREC_FP64, HS_PREC_MIXED = 0, 1
 HS_KRYLOV_PCG, HS_KRYLOV_GMRES = 0, 1
 HS_PRODUCTS_FP32, HS_PRODUCTS_TF32X3, HS_PRODUCTS_TF32, HS_PRODUCTS_BF16 = 0, 1, 2, 3
+HS_PART_AUTO, HS_PART_MULTILEVEL = 0, 1
 KERNEL_CLASSES = ("factor", "schur", "assembly", "top", "apply", "krylov", "factor_fused", "spmv")
 
 P = ctypes.c_void_p
@@ -38,7 +39,8 @@ class hs_options(ctypes.Structure):
                 ("precision", I32), ("krylov", I32), ("restart", I32), ("rtol", F64),
                 ("maxit", I32), ("mem", I32), ("profile", I32), ("stream", P), ("coords", P),
                 ("coarse_dense", I32), ("fused_levels", I32), ("record_ranks", I32),
-                ("rank_model", P), ("no_dc", I32), ("wait_polls", I32), ("schur_products", I32)]
+                ("rank_model", P), ("no_dc", I32), ("wait_polls", I32), ("schur_products", I32),
+                ("partitioner", I32)]
 
 
 class hs_info(ctypes.Structure):
@@ -70,6 +72,7 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     L.hs_default_options.argtypes = [ctypes.POINTER(hs_options)]
     L.hs_partition_extruded.argtypes = [I64, P, P, P, P, I32, F64, ctypes.POINTER(hs_tree)]
+    L.hs_partition_multilevel.argtypes = [I64, P, P, P, I32, F64, ctypes.POINTER(hs_tree)]
     L.hs_tree_free.argtypes = [ctypes.POINTER(hs_tree)]
     L.hs_plan_level.argtypes = [I32, P, P, P, I32, P, P, P, P, P, I64, P, P, I64]
     L.hs_setup.argtypes = [I64, P, P, P, ctypes.POINTER(hs_tree), ctypes.POINTER(hs_options),
@@ -113,7 +116,7 @@ EXPORTED = ("hs_default_options", "hs_partition_extruded", "hs_tree_free", "hs_s
             "hs_measure_fp64_peak", "hs_launch_count", "hs_status_str", "hs_setup_batched",
             "hs_krylov_batched", "hs_num_problems", "hs_problem_info", "hs_mlp_forward", "hs_mlp_grad",
             "hs_mlp_adam", "hs_mlp_train", "hs_rank_samples", "hs_plan_level", "hs_eval_pivot_reciprocals",
-            "hs_measure_fp32_peak")
+            "hs_measure_fp32_peak", "hs_partition_multilevel")
 MLP_NIN, MLP_NPARAM, MLP_MAX_BATCH = 8, 4801, 256
 
 
@@ -175,6 +178,19 @@ def hs_partition_extruded(n, rowptr, col, val, coords=None, leaf_lines=4, theta=
     _check(lib().hs_partition_extruded(int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(coords),
                                        int(leaf_lines), float(theta), ctypes.byref(t)),
            "hs_partition_extruded")
+    return _take_tree(t, n)
+
+
+def hs_partition_multilevel(n, rowptr, col, val, leaf_lines=4, theta=0.5):
+    """Partition from the matrix alone -> (perm, leaf_ptr, default depth)."""
+    t = hs_tree()
+    _check(lib().hs_partition_multilevel(int(n), _ptr(rowptr), _ptr(col), _ptr(val),
+                                         int(leaf_lines), float(theta), ctypes.byref(t)),
+           "hs_partition_multilevel")
+    return _take_tree(t, n)
+
+
+def _take_tree(t, n):
     try:
         perm = np.ctypeslib.as_array(t.perm, shape=(int(n),)).copy()
         lp = np.ctypeslib.as_array(t.leaf_ptr, shape=(t.n_leaf + 1,)).copy()

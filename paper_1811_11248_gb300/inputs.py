@@ -171,6 +171,107 @@ def vector_operator(nx, ny, nz, ratio, coupling=0.5, sigma=0.0, seed=0,
     return Problem(n, rowptr, col, val, b, coords, meta)
 
 
+def unstructured_operator(mx, my, nz, ratio, sigma=0.0, seed=0, kh=1.0, bc="ice",
+                          shelf=0.25, jitter=0.4, grade=0.5, shuffle=True):
+    """Extruded operator on an unstructured horizontal mesh (Sec. 4: the
+    ice-sheet meshes are unstructured triangulations extruded in layers).
+
+    Horizontal mesh: the mx*my points of a unit lattice, each moved by
+    uniform[-jitter, jitter] in x and y, then graded in x by
+    x <- x - grade * (L/2pi) sin(2pi x/L) (L = mx - 1; the points crowd
+    around x = 0 and x = L and thin out in between), and joined by their
+    Delaunay triangulation (scipy.spatial).  Each triangle edge (u, v) of
+    length l couples the two nodes with kh * hmean(c_u, c_v) / l in every
+    layer; the outermost ring of lattice points carries a lateral Dirichlet
+    term kh * c.  Layers, vertical coupling (ratio), node coefficients
+    c = exp(sigma * xi) and the bottom/top conditions are those of
+    ``grid_operator`` (bc "ice": Neumann top, Robin bottom with beta = 0 for
+    x >= (1 - shelf) * L).  Unshuffled DOF index = node * nz + k;
+    ``shuffle`` renumbers the DOFs by a seeded random permutation, so that
+    neither the lines nor the mesh can be read off the numbering (the
+    partitioner then has only the matrix).  xi, then b, are drawn in the
+    unshuffled order from the seeded generator, the permutation after them.
+    """
+    from scipy.spatial import Delaunay
+
+    mx, my, nz = int(mx), int(my), int(nz)
+    nn = mx * my
+    n = nn * nz
+    rng = np.random.default_rng(seed)
+    c = np.exp(sigma * rng.standard_normal(n)) if sigma > 0.0 else np.ones(n)
+    b = rng.uniform(-1.0, 1.0, n)
+    gi, gj = np.meshgrid(np.arange(mx, dtype=np.float64), np.arange(my, dtype=np.float64))
+    gi, gj = gi.ravel(), gj.ravel()  # node = j * mx + i
+    prng = np.random.default_rng(seed + 500_009)
+    px = gi + prng.uniform(-jitter, jitter, nn)
+    py = gj + prng.uniform(-jitter, jitter, nn)
+    span = max(mx - 1, 1)
+    px = px - grade * span / (2 * np.pi) * np.sin(2 * np.pi * px / span)
+    tri = Delaunay(np.stack([px, py], axis=1)).simplices.astype(np.int64)
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+    e = np.unique(np.sort(e, axis=1), axis=0)  # undirected edges u < v
+    length = np.hypot(px[e[:, 0]] - px[e[:, 1]], py[e[:, 0]] - py[e[:, 1]])
+    ring = (gi == 0) | (gi == mx - 1) | (gj == 0) | (gj == my - 1)
+
+    def hmean(a, bb):
+        return 2.0 * a * bb / (a + bb)
+
+    kk = np.arange(nz, dtype=np.int64)
+    diag = np.zeros(n)
+    rows, cols, vals = [], [], []
+    # horizontal edges in every layer
+    su = (e[:, 0][:, None] * nz + kk[None, :]).ravel()
+    sv = (e[:, 1][:, None] * nz + kk[None, :]).ravel()
+    coef = kh * hmean(c[su], c[sv]) / np.repeat(length, nz)
+    for src, dst in ((su, sv), (sv, su)):
+        rows.append(src)
+        cols.append(dst)
+        vals.append(-coef)
+        np.add.at(diag, src, coef)
+    lat = (np.flatnonzero(ring)[:, None] * nz + kk[None, :]).ravel()
+    np.add.at(diag, lat, kh * c[lat])
+    # vertical couplings and the bottom/top conditions
+    idx = np.arange(n, dtype=np.int64)
+    k = idx % nz
+    node = idx // nz
+    for inside, step in ((k > 0, -1), (k < nz - 1, +1)):
+        src = idx[inside]
+        dst = src + step
+        cv = kh * ratio * hmean(c[src], c[dst])
+        rows.append(src)
+        cols.append(dst)
+        vals.append(-cv)
+        np.add.at(diag, src, cv)
+    bottom, top = idx[k == 0], idx[k == nz - 1]
+    if bc == "ice":
+        bottom = bottom[px[node[bottom]] < (1.0 - shelf) * span]
+        np.add.at(diag, bottom, kh * ratio * c[bottom])
+    else:
+        for out in (bottom, top):
+            np.add.at(diag, out, kh * ratio * c[out])
+    rows.append(idx)
+    cols.append(idx)
+    vals.append(diag)
+    r = np.concatenate(rows)
+    cc = np.concatenate(cols)
+    coords = np.stack([px[node], py[node]], axis=1)
+    if shuffle:
+        q = np.random.default_rng(seed + 900_001).permutation(n)  # old DOF i -> new q[i]
+        r, cc = q[r], q[cc]
+        bn = np.empty(n)
+        bn[q] = b
+        b = bn
+        cn = np.empty_like(coords)
+        cn[q] = coords
+        coords = cn
+    rowptr, col, val = _coo_to_csr(n, r, cc, np.concatenate(vals))
+    meta = dict(kind="unstructured", mx=mx, my=my, nz=nz, nodes=nn, edges=int(len(e)),
+                ratio=float(ratio), sigma=float(sigma), seed=int(seed), kh=float(kh), bc=bc,
+                shelf=float(shelf), jitter=float(jitter), grade=float(grade), shuffle=bool(shuffle),
+                dofs_per_node=1)
+    return Problem(n, rowptr, col, val, b, coords, meta)
+
+
 # ---------------------------------------------------------------------------
 # The named workloads (sizes and seeds fixed here, one place).
 # ---------------------------------------------------------------------------

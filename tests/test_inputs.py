@@ -101,3 +101,39 @@ def test_batched_workload_shapes():
         nx, ny, nz = q.meta["nx"], q.meta["ny"], q.meta["nz"]
         assert 16 <= nx <= 48 and 16 <= ny <= 48 and 4 <= nz <= 12
         assert nx % 2 == 0 and ny % 2 == 0 and q.n == nx * ny * nz
+
+
+@pytest.mark.parametrize("bc", ["ice", "dirichlet"])
+def test_unstructured_operator_structure(bc):
+    """The unstructured extruded operator: symmetric positive definite; its
+    horizontal graph is a triangulation (Euler: E = 3V - 3 - H for V points,
+    H of them on the convex hull); interior top-layer rows of the ice
+    conditions sum to zero (natural boundary, no lateral term); the shuffled
+    numbering is the documented permutation of the natural one."""
+    from scipy.spatial import ConvexHull
+
+    mx, my, nz, seed = 7, 6, 4, 3
+    a = inputs.unstructured_operator(mx, my, nz, ratio=1e3, sigma=0.5, seed=seed, bc=bc, shuffle=False)
+    A = a.dense()
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A).min() > 0
+    pts = a.coords[::nz]
+    hull = ConvexHull(pts)
+    assert a.meta["edges"] == 3 * mx * my - 3 - len(hull.vertices)
+    off = A - np.diag(np.diag(A))
+    assert off.max() <= 0.0
+    node = np.arange(a.n) // nz
+    k = np.arange(a.n) % nz
+    gi, gj = node % mx, node // mx
+    ring = (gi == 0) | (gi == mx - 1) | (gj == 0) | (gj == my - 1)
+    rs = A.sum(1)
+    if bc == "ice":
+        top_inner = (k == nz - 1) & ~ring
+        np.testing.assert_allclose(rs[top_inner], 0.0, atol=1e-12 * np.abs(A).max())
+    assert np.all(rs[ring] > 0)
+    b = inputs.unstructured_operator(mx, my, nz, ratio=1e3, sigma=0.5, seed=seed, bc=bc, shuffle=True)
+    q = np.random.default_rng(seed + 900_001).permutation(a.n)
+    B = b.dense()
+    np.testing.assert_array_equal(B[np.ix_(q, q)], A)
+    np.testing.assert_array_equal(b.b[q], a.b)
+    np.testing.assert_array_equal(b.coords[q], a.coords)
