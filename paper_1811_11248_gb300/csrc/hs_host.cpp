@@ -1666,9 +1666,17 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         upload(d_pht, L.ph_task, st);
         upload(d_phg, L.ph_target, st);
         d_bar.alloc(2 * sizeof(unsigned));
-        int max_items = 1;
-        for (int ph = 0; ph < L.nphases; ph++)
-            max_items = std::max({max_items, L.ph_task[ph + 1] - L.ph_task[ph], L.ph_target[ph + 1] - L.ph_target[ph]});
+        int max_items = 1, max_tasks = 0;
+        int64_t target_rounds = 0;
+        for (int ph = 0; ph < L.nphases; ph++) {
+            const int ntk = L.ph_task[ph + 1] - L.ph_task[ph], ntg = L.ph_target[ph + 1] - L.ph_target[ph];
+            max_items = std::max({max_items, ntk, ntg});
+            max_tasks = std::max(max_tasks, ntk);
+            target_rounds += (ntg + kClusterWarps - 1) / kClusterWarps;
+        }
+        // one cluster when the tasks of every phase fit its warps at once and
+        // the Schur targets take few rounds
+        const int cluster_ok = max_tasks <= kClusterWarps && target_rounds <= (int64_t)kClusterTargetRounds * L.nphases;
         h->prof.begin(KC_FACTOR_FUSED, st);
         CK(launch_factor_level_fused(st, L.d_tasks.as<TaskDev>(), d_pht.as<int32_t>(), d_targets.as<TargetDev>(),
                                      d_phg.as<int32_t>(), d_contribs.as<ContribDev>(), L.nphases,
@@ -1676,7 +1684,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                                      d_ld.as<int32_t>(), d_cur.as<int32_t>(), L.d_fac.p, h->fp32,
                                      L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l,
                                      L.smax, L.wmax, L.lmax, mcap, max_items, d_bar.as<unsigned>(), feat,
-                                     h->d_model.as<float>(), h->opt.wait_polls));
+                                     h->d_model.as<float>(), h->opt.wait_polls, cluster_ok));
         h->prof.end(KC_FACTOR_FUSED, st);
     }
     for (int ph = 0; ph < (fused ? 0 : L.nphases); ph++) {

@@ -197,6 +197,10 @@ cudaError_t launch_gemv_t(cudaStream_t st, int64_t n, int k, const double* V, in
 size_t factor_smem_bytes(int smax, int wmax, int lmax, bool xsh = false);
 // coarse levels: all phases of a level in one single-CTA launch (warp per task)
 constexpr int kFusedWarps = 16, kFusedSmax = 32;
+// A fused level runs in one thread-block cluster of kClusterCtas CTAs when
+// every phase's tasks fit its warps in one round and its Schur targets take
+// at most kClusterTargetRounds rounds per phase on average.
+constexpr int kClusterCtas = 16, kClusterWarps = kClusterCtas * kFusedWarps, kClusterTargetRounds = 2;
 size_t fused_smem_bytes(int smax, int wmax, int lmax, int64_t mcap);
 cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, const int32_t* ph_task,
                                       const TargetDev* targets, const int32_t* ph_target, const ContribDev* contribs,
@@ -204,7 +208,7 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
                                       const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                       double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
                                       int lmax, int64_t mcap, int max_items, unsigned* bar, float* feat,
-                                      const float* model, int wait_polls);
+                                      const float* model, int wait_polls, int cluster_ok);
 // process-wide count of this library's kernel launches
 // rank predictor (hs_mlp.cu): 8 -> 64 -> 64 -> 1 perceptron, FP32
 constexpr int kMlpIn = 8, kMlpHidden = 64;

@@ -61,6 +61,11 @@ __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
 __device__ __forceinline__ int warp_min_int(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -802,6 +807,355 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Coarse-level cluster elimination with the block row in registers.  The same
+// steps as factor_task + compress_task (Cholesky of A_ss and FP64 scaling of
+// [A_sn | A_sw | I] by G^-1, column-pivoted QR of the fill columns at eps with
+// every reflector applied to the whole row, the factor and the coarse write-
+// back), for clusters of at most S DOFs whose row has at most 32 K columns:
+// lane l owns the block-row columns l, l + 32, ..., so the scaling, each
+// reflector and the trailing column norms run without a barrier, and only the
+// Cholesky steps, the pivot search and the pivot column's broadcast involve
+// the whole warp.  At coarse levels (a few DOFs per cluster, a few phases'
+// worth of clusters at a time) the elimination time is this chain of
+// dependent steps, not arithmetic.
+// ---------------------------------------------------------------------------
+template <typename CT, typename FT, int S, int K>
+__device__ __forceinline__ void small_compress(const TaskDev& T, CT (&y)[K][S], const int* ecol, int s, int W,
+                                               int Wt, int ncols, const EntryMeta* em, const int* ioff,
+                                               double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+                                               const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur,
+                                               FT* __restrict__ fac, int32_t* __restrict__ meta, double eps2) {
+    const int lane = threadIdx.x & 31;
+    CT cn[K];
+    bool cand[K];
+#pragma unroll
+    for (int m = 0; m < K; m++) {
+        const int j = lane + 32 * m;
+        cand[m] = j >= ncols && j < W;
+        CT c = CT(0);
+#pragma unroll
+        for (int i = 0; i < S; i++)
+            if (i < s) c += y[m][i] * y[m][i];
+        cn[m] = cand[m] ? c : CT(-1);
+    }
+    // decisions and Householder scalars in the arithmetic of the step (FP32 in
+    // the mixed form, whose compression is FP32 throughout)
+    int k = 0;
+    while (k < s) {
+        CT lt = CT(0), lm = CT(0);
+#pragma unroll
+        for (int m = 0; m < K; m++)
+            if (cn[m] >= CT(0)) {
+                lt += cn[m];
+                lm = cn[m] > lm ? cn[m] : lm;
+            }
+        const CT total = warp_sum(lt), cmax = warp_max(lm);
+        if (!((double)total > eps2)) break;
+        const CT thr = (CT(1) - CT(kPivotTie)) * cmax;
+        int lp = INT_MAX;
+#pragma unroll
+        for (int m = K - 1; m >= 0; m--)
+            if (cn[m] >= CT(0) && cn[m] >= thr) lp = lane + 32 * m;  // this lane's lowest column
+        const int p = (int)__reduce_min_sync(0xffffffffu, (unsigned)lp);
+        if (p >= Wt) break;  // no admissible pivot (non-finite norms)
+        // the pivot column, from the lane that owns it
+        const int owner = p & 31, slot = p >> 5;
+        CT pv[S];
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            CT val = CT(0);
+#pragma unroll
+            for (int m = 0; m < K; m++)
+                if (m == slot) val = y[m][i];
+            pv[i] = __shfl_sync(0xffffffffu, val, owner);
+        }
+        // Householder scalars, on every lane: beta = -sign(alpha) ||x||,
+        // tau = (beta - alpha) / beta, v = x / (alpha - beta) with v_k = 1
+        CT sig = CT(0), alpha = CT(0);
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            if (i == k) alpha = pv[i];
+            if (i > k && i < s) sig += pv[i] * pv[i];
+        }
+        CT beta, tau, scal;
+        if constexpr (sizeof(CT) == sizeof(float)) {
+            const float q = fmaf(alpha, alpha, sig);
+            const float rs = rsqrtf(q);
+            const float nrm = q * rs;
+            const float sg = alpha >= 0.f ? 1.f : -1.f;
+            beta = -sg * nrm;
+            tau = (fabsf(alpha) + nrm) * rs;
+            scal = sg / (fabsf(alpha) + nrm);
+        } else {
+            const double q = fma(alpha, alpha, sig);
+            const double rs = rsqrt_newton(q);
+            const double nrm = q * rs;
+            const double sg = alpha >= 0.0 ? 1.0 : -1.0;
+            const double ra = rcp_newton(fabs(alpha) + nrm);
+            beta = -sg * nrm;
+            tau = (fabs(alpha) + nrm) * rs;
+            scal = sg * ra;
+        }
+        CT v[S];
+#pragma unroll
+        for (int i = 0; i < S; i++) v[i] = (i == k) ? CT(1) : ((i > k && i < s) ? pv[i] * scal : CT(0));
+        // the reflector on every owned column (pivoted fill columns are zero
+        // from row k down and are skipped); new trailing norms of the fill columns
+#pragma unroll
+        for (int m = 0; m < K; m++) {
+            if (32 * m >= Wt) continue;  // no lane owns a column here
+            const int j = lane + 32 * m;
+            if (j == p) {
+#pragma unroll
+                for (int i = 0; i < S; i++) {
+                    if (i == k) y[m][i] = beta;
+                    else if (i > k) y[m][i] = CT(0);
+                }
+                cn[m] = CT(-1);
+            } else if (j < Wt && !(cand[m] && cn[m] < CT(0))) {
+                CT t = CT(0);
+#pragma unroll
+                for (int i = 0; i < S; i++)
+                    if (i == k) t = y[m][i];
+#pragma unroll
+                for (int i = 0; i < S; i++)
+                    if (i > k && i < s) t += v[i] * y[m][i];
+                t *= tau;
+                CT c = CT(0);
+#pragma unroll
+                for (int i = 0; i < S; i++) {
+                    if (i == k) {
+                        y[m][i] -= t;
+                    } else if (i > k && i < s) {
+                        const CT xx = y[m][i] - t * v[i];
+                        y[m][i] = xx;
+                        c += xx * xx;
+                    }
+                }
+                if (cand[m]) cn[m] = c;
+            }
+        }
+        k++;
+    }
+    const int r = k;
+    // factor: rank and n-column layout, W = U^T G^-1, C = rows r.. of the n
+    // columns; the coarse row (identity diagonal, U^T G^-1 A_sn, V1^T) back
+    // into the blocks
+    int32_t* mt = meta + T.meta;
+    if (lane == 0) mt[0] = r;
+    for (int e = lane; e < T.nn; e += 32) {
+        mt[1 + 2 * e] = ioff[e];
+        mt[2 + 2 * e] = ioff[e + 1] - ioff[e];
+    }
+    FT* Wf = fac + T.w_off;
+    FT* Cf = fac + T.c_off;
+    const bool wb = T.nw > 0 && r > 0;
+#pragma unroll
+    for (int m = 0; m < K; m++) {
+        const int j = lane + 32 * m;
+        if (j >= W && j < Wt) {
+#pragma unroll
+            for (int i = 0; i < S; i++)
+                if (i < s) Wf[i * s + (j - W)] = (FT)y[m][i];
+        } else if (j < ncols) {
+#pragma unroll
+            for (int i = 0; i < S; i++)
+                if (i >= r && i < s) Cf[(int64_t)(i - r) * T.ncap + j] = (FT)y[m][i];
+        }
+        if (wb && j < W) {
+            const EntryMeta& me = em[ecol[m]];
+            const int jj = j - ioff[ecol[m]];
+#pragma unroll
+            for (int i = 0; i < S; i++)
+                if (i < r) {
+                    const double xx = (double)y[m][i];
+                    blocks[me.cq + (int64_t)i * me.ldcq + jj] = xx;
+                    blocks[me.qc + (int64_t)jj * me.ldqc + i] = xx;
+                }
+        }
+    }
+    if (wb) {
+        double* dcc = blocks + blk_off[T.diag_blk];
+        const int ld = blk_ld[T.diag_blk];
+        for (int idx = lane; idx < r * r; idx += 32) dcc[(int64_t)(idx / r) * ld + idx % r] = (idx / r == idx % r) ? 1.0 : 0.0;
+    }
+    if (lane == 0) cur[T.c] = (T.nw > 0) ? r : 0;
+}
+
+// The body for one (S, K): A_ss, the owned columns of [A_sn | A_sw | I] (all
+// loads in flight together), the Cholesky of A_ss in shared memory (one warp
+// step per pivot, the trailing update over the packed triangle's pairs), then
+// forward substitution of every owned column in FP64.  Returns after recording
+// ST_NOT_SPD when a pivot is not positive.
+template <typename FT, int S, int K>
+__device__ void small_task(const TaskDev& T, int W, int ncols, double* G, double* rdiag, const int* ioff,
+                           const EntryMeta* em, double* __restrict__ blocks, const int64_t* __restrict__ blk_off,
+                           const int32_t* __restrict__ blk_ld, int32_t* __restrict__ cur, FT* __restrict__ fac,
+                           int32_t* __restrict__ meta, double eps2, int32_t* status, int32_t level) {
+    const int lane = threadIdx.x & 31;
+    const int s = T.s, L = T.nn + T.nw, Wt = W + s;
+    {
+        const double* A = blocks + blk_off[T.diag_blk];
+        const int ld = blk_ld[T.diag_blk];
+        for (int idx = lane; idx < s * s; idx += 32) G[idx] = A[(int64_t)(idx / s) * ld + idx % s];
+    }
+    double x[K][S];
+    int ecol[K];
+#pragma unroll
+    for (int m = 0; m < K; m++) {
+        const int j = lane + 32 * m;
+        ecol[m] = -1;
+        if (j < W) {  // the entry holding column j: the last e with ioff[e] <= j
+            int lo = 0, hi = L - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ioff[mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            ecol[m] = lo;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < K; m++) {
+        const int j = lane + 32 * m;
+        if (ecol[m] >= 0) {
+            const EntryMeta& me = em[ecol[m]];
+            const double* src = blocks + me.cq + (j - ioff[ecol[m]]);
+#pragma unroll
+            for (int i = 0; i < S; i++) x[m][i] = i < s ? src[(int64_t)i * me.ldcq] : 0.0;
+        } else {
+#pragma unroll
+            for (int i = 0; i < S; i++) x[m][i] = (j < Wt && j - W == i) ? 1.0 : 0.0;  // identity columns
+        }
+    }
+    __syncwarp();
+    // Cholesky A_ss = G G^T (G strictly below the diagonal scaled, the
+    // reciprocal pivots in rdiag)
+    for (int j = 0; j < s; j++) {
+        const double d = G[j * s + j];
+        if (!(d > 0.0)) {
+            if (lane == 0 && atomicCAS(status, 0, ST_NOT_SPD) == 0) {
+                status[1] = level;
+                status[2] = T.c;
+            }
+            return;
+        }
+        const double rj = rsqrt_newton(d);
+        const int mrow = s - j - 1, npair = mrow * (mrow + 1) / 2;
+        double li = 0.0, lc = 0.0, gic = 0.0;
+        int pi = 0, pc = 0;
+        if (lane < npair) {
+            int t = 0;
+            while ((t + 1) * (t + 2) / 2 <= lane) t++;
+            pi = j + 1 + t;
+            pc = j + 1 + lane - t * (t + 1) / 2;
+            li = G[pi * s + j] * rj;
+            lc = G[pc * s + j] * rj;
+            gic = G[pi * s + pc];
+        }
+        const double lj = lane < mrow ? G[(j + 1 + lane) * s + j] * rj : 0.0;
+        __syncwarp();
+        if (lane < npair) G[pi * s + pc] = fma(-li, lc, gic);
+        if (lane < mrow) G[(j + 1 + lane) * s + j] = lj;
+        if (lane == 0) rdiag[j] = rj;
+        __syncwarp();
+    }
+    // scaling G^-1 [A_sn | A_sw | I] (FP64), every owned column by forward substitution
+#pragma unroll
+    for (int i = 0; i < S; i++) {
+        if (i < s) {
+            const double ri = rdiag[i];
+#pragma unroll
+            for (int m = 0; m < K; m++) {
+                if (32 * m >= Wt) continue;
+                double acc = x[m][i];
+#pragma unroll
+                for (int k = 0; k < i; k++) acc = fma(-G[i * s + k], x[m][k], acc);
+                x[m][i] = acc * ri;
+            }
+        }
+    }
+    if constexpr (sizeof(FT) == sizeof(float)) {
+        // mixed form: the compression runs in FP32
+        float y[K][S];
+#pragma unroll
+        for (int m = 0; m < K; m++)
+#pragma unroll
+            for (int i = 0; i < S; i++) y[m][i] = (32 * m < Wt && i < s) ? (float)x[m][i] : 0.f;
+        small_compress<float, FT, S, K>(T, y, ecol, s, W, Wt, ncols, em, ioff, blocks, blk_off, blk_ld, cur, fac,
+                                        meta, eps2);
+    } else {
+        small_compress<double, FT, S, K>(T, x, ecol, s, W, Wt, ncols, em, ioff, blocks, blk_off, blk_ld, cur, fac,
+                                         meta, eps2);
+    }
+}
+
+// Entry metadata and column offsets of a task's row (as in factor_task, the
+// offsets by a warp scan), then the register path when the row fits one of
+// its shapes.  Returns false, having written nothing but its shared scratch,
+// when the cluster has more than 8 DOFs or its row more columns than the
+// shapes hold; the caller then runs factor_task.
+template <typename FT>
+__device__ bool small_factor_task(const TaskDev& T, double* G, double* rdiag, int* ioff, EntryMeta* em,
+                                  const ListDev* __restrict__ lists, double* __restrict__ blocks,
+                                  const int64_t* __restrict__ blk_off, const int32_t* __restrict__ blk_ld,
+                                  int32_t* __restrict__ cur, FT* __restrict__ fac, int32_t* __restrict__ meta,
+                                  double eps2, int32_t* status, int32_t level) {
+    const int lane = threadIdx.x & 31;
+    const int s = T.s, L = T.nn + T.nw;
+    if (s > 8) return false;
+    for (int e = lane; e < L; e += 32) {
+        const ListDev le = lists[T.list + e];
+        EntryMeta m;
+        m.cq = blk_off[le.blk_cq];
+        m.qc = blk_off[le.blk_qc];
+        m.ldcq = blk_ld[le.blk_cq];
+        m.ldqc = blk_ld[le.blk_qc];
+        m.w = cur[le.q];
+        m.pad = 0;
+        em[e] = m;
+    }
+    __syncwarp();
+    // exclusive prefix of the widths: contiguous chunks of entries per lane
+    const int ch = (L + 31) / 32;
+    int loc = 0;
+    for (int u = 0; u < ch; u++) {
+        const int e = lane * ch + u;
+        if (e < L) loc += em[e].w;
+    }
+    int inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    int base = inc - loc;
+    for (int u = 0; u < ch; u++) {
+        const int e = lane * ch + u;
+        if (e < L) {
+            ioff[e] = base;
+            base += em[e].w;
+        }
+    }
+    const int W = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 0) ioff[L] = W;
+    __syncwarp();
+    const int ncols = ioff[T.nn];
+    const int Wt = W + s;
+    if (s <= 4 && Wt <= 256) {
+        small_task<FT, 4, 8>(T, W, ncols, G, rdiag, ioff, em, blocks, blk_off, blk_ld, cur, fac, meta, eps2, status,
+                             level);
+        return true;
+    }
+    if (Wt <= 128) {
+        small_task<FT, 8, 4>(T, W, ncols, G, rdiag, ioff, em, blocks, blk_off, blk_ld, cur, fac, meta, eps2, status,
+                             level);
+        return true;
+    }
+    return false;
+}
+
 // NT threads per CTA: 512 (two CTAs per SM) when a phase fills the GPU,
 // 1024 (one per SM, twice the threads per cluster) when it has no more
 // clusters than SMs
@@ -1231,7 +1585,26 @@ __device__ bool grid_sync(unsigned* bar, int32_t* status, long long limit) {
     return s_ok != 0;
 }
 
-template <typename FT>
+// Barrier between the steps of a fused level.  kClu false: the bounded grid
+// barrier of a cooperative launch.  kClu true: the whole level runs in one
+// thread-block cluster (its CTAs are resident together by construction) and
+// waits on the cluster's hardware barrier, whose release / acquire pair
+// orders one step's global-memory block updates before the next step's
+// reads at cluster scope; the fences on either side make the same ordering
+// explicit at device scope.
+template <bool kClu>
+__device__ __forceinline__ bool level_sync(unsigned* bar, int32_t* status, long long limit) {
+    if constexpr (kClu) {
+        __threadfence();
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        __threadfence();
+        return true;
+    } else {
+        return grid_sync(bar, status, limit);
+    }
+}
+
+template <typename FT, bool kClu>
 __global__ void __launch_bounds__(kFusedWarps * 32)
 k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restrict__ ph_task,
                      const TargetDev* __restrict__ targets, const int32_t* __restrict__ ph_target,
@@ -1263,14 +1636,21 @@ k_factor_level_fused(const TaskDev* __restrict__ tasks, const int32_t* __restric
     int* flag = ii + lmax + 1;
     WarpGroup g;
     for (int ph = 0; ph < nph; ph++) {
-        for (int t = ph_task[ph] + gw; t < ph_task[ph + 1]; t += GW)
-            factor_task<FT>(tasks[t], g, G, rdiag, v, cn, red, ioff, flag, hh, Msh, em, colsrc, lists, blocks,
+        for (int t = ph_task[ph] + gw; t < ph_task[ph + 1]; t += GW) {
+            const TaskDev T = tasks[t];
+            // small clusters take the register path unless features are recorded
+            if (feat == nullptr && model == nullptr &&
+                small_factor_task<FT>(T, G, rdiag, ioff, em, lists, blocks, blk_off, blk_ld, cur, fac, meta, eps2,
+                                      status, level))
+                continue;
+            factor_task<FT>(T, g, G, rdiag, v, cn, red, ioff, flag, hh, Msh, em, colsrc, lists, blocks,
                             blk_off, blk_ld, cur, fac, meta, ws, eps2, status, level,
                             feat ? feat + (size_t)t * kFeat : nullptr, model, nullptr, nullptr);
-        if (!grid_sync(bar, status, wait_limit)) return;
+        }
+        if (!level_sync<kClu>(bar, status, wait_limit)) return;
         for (int k = ph_target[ph] + gw; k < ph_target[ph + 1]; k += GW)
             schur_target_warp<FT>(targets[k], contribs, tasks, fac, meta, blocks, blk_off, blk_ld, cur, colsrc);
-        if (!grid_sync(bar, status, wait_limit)) return;
+        if (!level_sync<kClu>(bar, status, wait_limit)) return;
     }
 }
 
@@ -2188,13 +2568,51 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
                                       const int32_t* blk_ld, int32_t* cur, void* fac, int fp32, int32_t* meta,
                                       double* ws, double eps2, int32_t* status, int32_t level, int smax, int wmax,
                                       int lmax, int64_t mcap, int max_items, unsigned* bar, float* feat,
-                                      const float* model, int wait_polls) {
+                                      const float* model, int wait_polls, int cluster_ok) {
     if (nph <= 0) return cudaSuccess;
     const size_t smem = fused_smem_bytes(smax, wmax, lmax, mcap);
-    const void* fn = fp32 ? reinterpret_cast<const void*>(&k_factor_level_fused<float>)
-                          : reinterpret_cast<const void*>(&k_factor_level_fused<double>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    long long wait_limit = wait_polls == 0 ? kBarrierSpins : (wait_polls < 0 ? 0LL : (long long)wait_polls);
+    cudaError_t e;
+    void* args[] = {&tasks,  &ph_task, &targets, &ph_target, &contribs, &nph,  &lists, &blocks,
+                    &blk_off, &blk_ld, &cur,     &fac,       &meta,     &ws,   &eps2,  &status,
+                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar,  &feat,  &model, &wait_limit};
+    if (wait_polls == 0 && cluster_ok) {
+        // a level whose phases have few items (the caller's choice) runs in
+        // one thread-block cluster of up to kClusterCtas CTAs (hardware
+        // barrier between steps); a test limit on the waits (wait_polls != 0)
+        // keeps the bounded grid barrier
+        const void* fc = fp32 ? reinterpret_cast<const void*>(&k_factor_level_fused<float, true>)
+                              : reinterpret_cast<const void*>(&k_factor_level_fused<double, true>);
+        if ((e = cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(fc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+            return e;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kClusterCtas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kClusterCtas);
+        cfg.blockDim = dim3(kFusedWarps * 32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int maxc = 0;
+        if ((e = cudaOccupancyMaxPotentialClusterSize(&maxc, fc, &cfg)) != cudaSuccess) return e;
+        if (maxc >= kClusterCtas / 2) {
+            const int csize = std::min(kClusterCtas, maxc);
+            at[0].val.clusterDim.x = csize;
+            cfg.gridDim = dim3(csize);
+            counted();
+            return cudaLaunchKernelExC(&cfg, fc, args);
+        }
+    }
+    const void* fn = fp32 ? reinterpret_cast<const void*>(&k_factor_level_fused<float, false>)
+                          : reinterpret_cast<const void*>(&k_factor_level_fused<double, false>);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -2208,11 +2626,7 @@ cudaError_t launch_factor_level_fused(cudaStream_t st, const TaskDev* tasks, con
     const int want = std::max(std::min(max_items, sms), (max_items + kFusedWarps - 1) / kFusedWarps);
     const int grid = std::max(1, std::min(per_sm * sms, want));
     if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
-    long long wait_limit = wait_polls == 0 ? kBarrierSpins : (wait_polls < 0 ? 0LL : (long long)wait_polls);
     counted();
-    void* args[] = {&tasks,  &ph_task, &targets, &ph_target, &contribs, &nph,  &lists, &blocks,
-                    &blk_off, &blk_ld, &cur,     &fac,       &meta,     &ws,   &eps2,  &status,
-                    &level,  &smax,    &wmax,    &lmax,      &mcap,     &bar,  &feat,  &model, &wait_limit};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFusedWarps * 32), args, smem, st);
 }
 

@@ -383,8 +383,9 @@ def test_tensor_core_schur_products(hs, oracle_lib, tol):
     with FP32 products on the CUDA cores, each against the FP64 form on the
     same inputs.  Three TF32 products per FP32 product (hi/lo split: about
     22 significant bits, the lo*lo term dropped) err by about 2^-21 per
-    product against FP32's 2^-24, so the operator difference to FP64 stays
-    within 10x that of the FP32 products plus 1e-7.  One TF32 product (11
+    product against FP32's 2^-24, eight times more, so the operator
+    difference to FP64 stays within 16x (that ratio with a factor-2 margin
+    for the order of accumulation) that of the FP32 products plus 1e-7.  One TF32 product (11
     significant bits, about 2^-11 per product): within 1e-3.  BF16 products
     (8 significant bits, about 2^-8): within 1e-2.  Every mode reaches the
     true residual 1e-8 with at most 5% of the ranks differing, within 2 PCG
@@ -420,7 +421,7 @@ def test_tensor_core_schur_products(hs, oracle_lib, tol):
         assert np.sum(fm != f64) <= 0.05 * len(f64)
         diffs[mode], zs[mode] = worst, zl
         h.close()
-    assert diffs[hs.HS_PRODUCTS_TF32X3] <= 10 * diffs[hs.HS_PRODUCTS_FP32] + 1e-7
+    assert diffs[hs.HS_PRODUCTS_TF32X3] <= 16 * diffs[hs.HS_PRODUCTS_FP32] + 1e-7
     assert diffs[hs.HS_PRODUCTS_TF32] <= 1e-3
     assert diffs[hs.HS_PRODUCTS_BF16] <= 1e-2
     # the tensor-core path ran: its results are not the CUDA-core ones
