@@ -212,9 +212,13 @@ int hs_threads() {
 thread_local bool tl_serial = false;
 
 // Persistent worker threads for the host planner (created on first use):
-// run(T, fn) hands fn(1) .. fn(T-1) to the workers, runs fn(0) on the
-// caller and returns when all are done.  A call from a worker, or while
-// another call is running, runs serially on its thread.
+// run(T, fn) runs fn(0) .. fn(T-1), fn(0) on the caller, the rest on whichever
+// thread (worker or caller) takes them first, and returns when all are done.
+// A call from a worker, or while another call is running, runs serially on
+// its thread.  Between jobs a worker polls for the next one for a while
+// (HS_SPIN_US microseconds, default 2000) before it sleeps: the planner's
+// parallel loops come in bursts a few hundred microseconds apart, and waking a
+// sleeping thread costs tens of microseconds per job.
 thread_local bool tl_in_pool = false;
 
 class Pool {
@@ -229,17 +233,30 @@ class Pool {
         std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
         if (!busy.owns_lock()) return false;
         {
-            std::lock_guard<std::mutex> lk(mu_);
+            // workers join a job under mu_; a worker still inside the
+            // previous job (it took no task, or its last one) leaves first
+            std::unique_lock<std::mutex> lk(mu_);
+            while (inside_.load(std::memory_order_acquire) > 0) {
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            }
             job_ = &fn;
             njob_ = T;
-            next_ = 1;
-            pending_ = T - 1;
+            next_.store(1, std::memory_order_relaxed);
+            pending_.store(T - 1, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         fn(0);
-        std::unique_lock<std::mutex> lk(mu_);
-        done_.wait(lk, [&] { return pending_ == 0; });
-        job_ = nullptr;
+        for (;;) {  // the caller takes tasks no worker has taken yet
+            const int t = next_.fetch_add(1, std::memory_order_acq_rel);
+            if (t >= T) break;
+            fn(t);
+            pending_.fetch_sub(1, std::memory_order_acq_rel);
+        }
+        for (int k = 0; pending_.load(std::memory_order_acquire) != 0; k++)
+            if (k > 4096) std::this_thread::yield();
         return true;
     }
     ~Pool() {
@@ -250,6 +267,7 @@ class Pool {
         {
             std::lock_guard<std::mutex> lk(mu_);
             stop_ = true;
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         for (auto& t : th_) t.join();
@@ -257,30 +275,50 @@ class Pool {
 
   private:
     explicit Pool(int n) : pid_(getpid()) {
+        const char* e = std::getenv("HS_SPIN_US");
+        spin_us_ = e ? std::max(0, std::atoi(e)) : 2000;
         for (int i = 0; i < n; i++) th_.emplace_back([this] { loop(); });
     }
     void loop() {
         tl_in_pool = true;
+        unsigned seen = gen_.load(std::memory_order_acquire);
         for (;;) {
-            const std::function<void(int)>* f;
-            int t;
-            {
-                std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [&] { return stop_ || (job_ && next_ < njob_); });
-                if (stop_) return;
-                f = job_;
-                t = next_++;
+            // poll for the next job (the clock read every 64 polls), then sleep
+            const auto t0 = std::chrono::steady_clock::now();
+            for (int k = 1; gen_.load(std::memory_order_acquire) == seen; k++) {
+                if ((k & 63) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(spin_us_)) {
+                    std::unique_lock<std::mutex> lk(mu_);
+                    cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
+                    break;
+                }
             }
-            (*f)(t);
-            std::lock_guard<std::mutex> lk(mu_);
-            if (--pending_ == 0) done_.notify_all();
+            const std::function<void(int)>* f;
+            int n;
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                if (stop_) return;
+                seen = gen_.load(std::memory_order_acquire);
+                f = job_;
+                n = njob_;
+                inside_.fetch_add(1, std::memory_order_acq_rel);
+            }
+            for (;;) {
+                const int t = next_.fetch_add(1, std::memory_order_acq_rel);
+                if (t >= n) break;
+                (*f)(t);
+                pending_.fetch_sub(1, std::memory_order_acq_rel);
+            }
+            inside_.fetch_sub(1, std::memory_order_acq_rel);
         }
     }
     std::vector<std::thread> th_;
     std::mutex mu_, run_mu_;
-    std::condition_variable cv_, done_;
+    std::condition_variable cv_;
+    std::atomic<unsigned> gen_{0};
+    std::atomic<int> next_{0}, pending_{0}, inside_{0};
     const std::function<void(int)>* job_ = nullptr;
-    int njob_ = 0, next_ = 0, pending_ = 0;
+    int njob_ = 0;
+    int spin_us_ = 2000;
     bool stop_ = false;
     pid_t pid_;
 };
@@ -1333,9 +1371,9 @@ struct hs_factor_s {
 
 namespace {
 
-void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
-    std::vector<int32_t> st;
-    download(st, d_status.p, 3, h->st);
+// Raises the error a status word (status, level, cluster) read back from the
+// kernels stands for.
+void raise_status(hs_factor_s* h, const int32_t* st, hs_info* info) {
     if (st[0] == ST_NOT_SPD) {
         if (info) {
             // a dense top fails as (depth of its problem, problem index)
@@ -1350,9 +1388,16 @@ void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
     if (st[0] != ST_OK) throw HsError{HS_ERR_UNSUPPORTED};
 }
 
+void check_status(hs_factor_s* h, DBuf& d_status, hs_info* info) {
+    std::vector<int32_t> st;
+    download(st, d_status.p, 3, h->st);
+    raise_status(h, st.data(), info);
+}
+
 // Block table of a level: CSR over clusters of the blocks in `all`.
 struct BlockTable {
     std::vector<int32_t> ptr, col, ld;
+    std::vector<int32_t> tpos;  // tpos[b]: index of the transposed block (q, p) of block b = (p, q)
     std::vector<int64_t> off;
     int64_t total = 0;
     int find(int p, int q) const {
@@ -1360,6 +1405,18 @@ struct BlockTable {
         auto it = std::lower_bound(b, e, q);
         if (it == e || *it != q) throw HsError{HS_ERR_ARG};  // planner invariant broken
         return (int)(it - col.begin());
+    }
+    // find(p, q) for lookups of ascending q in one row: `cur` (the previous
+    // result, or any value) is a hint; a short forward scan from it, else a
+    // binary search.  Same result as find.
+    int find_from(int p, int q, int& cur) const {
+        const int b = ptr[p], e = ptr[p + 1];
+        int k = (cur >= b && cur < e && col[cur] <= q) ? cur : b;
+        for (int step = 0; step < 8 && k < e && col[k] < q; step++) k++;
+        if (k < e && col[k] < q) k = (int)(std::lower_bound(col.begin() + k, col.begin() + e, q) - col.begin());
+        if (k >= e || col[k] != q) throw HsError{HS_ERR_ARG};  // planner invariant broken
+        cur = k;
+        return k;
     }
 };
 
@@ -1393,6 +1450,33 @@ BlockTable make_table(const LevelPlan& P) {
         }
     });
     T.total = rowsz[nc];
+    // transposed positions (the block pattern is symmetric): small tables by
+    // one sweep of row cursors (row q lists its p in ascending order), large
+    // ones by parallel lookups; checked either way
+    T.tpos.resize(nb);
+    if (nb < (1 << 17)) {
+        std::vector<int32_t> cursor(T.ptr.begin(), T.ptr.end() - 1);
+        for (int p = 0; p < nc; p++)
+            for (int b = T.ptr[p]; b < T.ptr[p + 1]; b++) {
+                const int q = T.col[b];
+                const int t = cursor[q]++;
+                if (t >= T.ptr[q + 1] || T.col[t] != p) throw HsError{HS_ERR_ARG};  // planner invariant broken
+                T.tpos[b] = t;
+            }
+    } else {
+        std::atomic<int> bad{0};
+        parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t p = lo; p < hi; p++)
+                for (int b = T.ptr[p]; b < T.ptr[p + 1]; b++) {
+                    const int q = T.col[b];
+                    auto e = T.col.begin() + T.ptr[q + 1];
+                    auto it = std::lower_bound(T.col.begin() + T.ptr[q], e, (int32_t)p);
+                    if (it == e || *it != p) bad = 1;
+                    else T.tpos[b] = (int32_t)(it - T.col.begin());
+                }
+        });
+        if (bad) throw HsError{HS_ERR_ARG};
+    }
     return T;
 }
 
@@ -1479,13 +1563,14 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             TaskDev& t = L.tasks[ti];
             const int c = t.c;
             t.diag_blk = T.find(c, c);
+            int cur = -1;
             for (int k = 0; k < t.nn + t.nw; k++) {
                 const int q = k < t.nn ? P.nl[c][k] : P.wl[c][k - t.nn];
                 ListDev& le = L.lists[t.list + k];
                 le = ListDev{};
                 le.q = q;
-                le.blk_cq = T.find(c, q);
-                le.blk_qc = T.find(q, c);
+                le.blk_cq = T.find_from(c, q, cur);
+                le.blk_qc = T.tpos[le.blk_cq];
             }
         }
     });
@@ -1539,13 +1624,14 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                     }
                     auto& tg = rt[k][ph];
                     auto& ct = rc[k][ph];
+                    int cur = -1;  // targets come in (p, q) order
                     for (size_t i = 0; i < tcs.size();) {
                         size_t j = i;
                         TargetDev g{};
                         g.p = tcs[i].p;
                         g.q = tcs[i].q;
-                        g.blk_pq = T.find(g.p, g.q);
-                        g.blk_qp = T.find(g.q, g.p);
+                        g.blk_pq = T.find_from(g.p, g.q, cur);
+                        g.blk_qp = T.tpos[g.blk_pq];
                         g.c_begin = (int)ct.size();
                         while (j < tcs.size() && tcs[j].p == g.p && tcs[j].q == g.q) ct.push_back(tcs[j++].c);
                         g.c_end = (int)ct.size();
@@ -1661,7 +1747,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     for (const TaskDev& t : L.tasks) mcap = std::max<int64_t>(mcap, (int64_t)t.s * (t.wcap + t.s));
     const bool fused = !nodc && h->opt.fused_levels && L.smax <= kFusedSmax &&
                        fused_smem_bytes(L.smax, L.wmax, L.lmax, mcap) <= (size_t)kFactorMaxSmem;
-    if (fused) {
+    if (fused && nt > 0) {
         DBuf d_pht, d_phg, d_bar;
         upload(d_pht, L.ph_task, st);
         upload(d_phg, L.ph_target, st);
@@ -1713,15 +1799,27 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
     }
     tr.mark("  launches");
-    check_status(h, d_status, info);
-    tr.mark("  kernels (sync)");
-    {
-        std::vector<int32_t> fin;
-        download(fin, d_cur.p, P.nc, st);
-        L.fin.assign(fin.begin(), fin.end());
+    // the level's results in one read-back: status word, final cluster sizes
+    // and the tasks' rank / column layout
+    std::vector<int32_t> hmeta(meta);
+    if (nt == 0) {
+        // nothing to eliminate (every cluster empty): no kernel ran, sizes stay
+        L.fin.assign(P.size0.begin(), P.size0.end());
+    } else {
+        const size_t b_st = sizeof(int32_t) * 3, b_fin = sizeof(int32_t) * P.nc, b_meta = sizeof(int32_t) * meta;
+        const size_t o_fin = 256, o_meta = o_fin + ((b_fin + 255) & ~(size_t)255);
+        char* pin = g_stage.take(o_meta + b_meta, st);
+        CK(cudaMemcpyAsync(pin, d_status.p, b_st, cudaMemcpyDeviceToHost, st));
+        if (b_fin) CK(cudaMemcpyAsync(pin + o_fin, d_cur.p, b_fin, cudaMemcpyDeviceToHost, st));
+        if (b_meta) CK(cudaMemcpyAsync(pin + o_meta, L.d_meta.p, b_meta, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        tr.mark("  kernels (sync)");
+        raise_status(h, reinterpret_cast<const int32_t*>(pin), info);
+        const int32_t* fin = reinterpret_cast<const int32_t*>(pin + o_fin);
+        L.fin.assign(fin, fin + P.nc);
+        if (b_meta) std::memcpy(hmeta.data(), pin + o_meta, b_meta);
+        g_stage.synced(st);
     }
-    std::vector<int32_t> hmeta;
-    download(hmeta, L.d_meta.p, meta, st);
     tr.mark("  downloads");
     // solve-phase records with resolved offsets
     {
@@ -1881,14 +1979,15 @@ std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& f
     return parallel_collect<CopyDev>(P.nc, 1024, [&](int64_t a, std::vector<CopyDev>& cps) {
         if (fin[a] <= 0) return;
         if ((par[a] < 0) != to_tops) return;
+        int cur = -1, curn = -1;
         for (int b : P.endp[a]) {
             if (fin[b] <= 0) continue;
             CopyDev c{};
-            const int sb = T.find((int)a, b);
+            const int sb = T.find_from((int)a, b, cur);
             c.src = T.off[sb];
             c.src_ld = T.ld[sb];
             if (!to_tops) {
-                const int db = Tn->find(par[a], par[b]);
+                const int db = Tn->find_from(par[a], par[b], curn);
                 c.dst = Tn->off[db] + (int64_t)poff[a] * nsize[par[b]] + poff[b];
                 c.dst_ld = nsize[par[b]];
             } else {
@@ -1979,14 +2078,25 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         g_pattern_stage.drain();
         const size_t b_rp = sizeof(int64_t) * (n + 1), b_col = sizeof(int32_t) * nnz0;
         const size_t b_val = tree_in ? 0 : sizeof(double) * nnz0;
-        char* pin = g_pattern_stage.take(b_rp + b_col + b_val + 512, st);
+        const size_t o_col = (b_rp + 255) & ~(size_t)255, o_val = o_col + ((b_col + 255) & ~(size_t)255);
+        const size_t o_flag = o_val + ((b_val + 255) & ~(size_t)255);
+        char* pin = g_pattern_stage.take(o_flag + 256, st);
         int64_t* prp = reinterpret_cast<int64_t*>(pin);
-        int32_t* pcol = reinterpret_cast<int32_t*>(pin + ((b_rp + 255) & ~(size_t)255));
-        double* pval = reinterpret_cast<double*>(pin + ((b_rp + 255) & ~(size_t)255) + ((b_col + 255) & ~(size_t)255));
+        int32_t* pcol = reinterpret_cast<int32_t*>(pin + o_col);
+        double* pval = reinterpret_cast<double*>(pin + o_val);
+        int32_t* pbad = reinterpret_cast<int32_t*>(pin + o_flag);
+        // the pattern is validated where it lies, by a kernel, while it is
+        // copied down (the flag comes back with it)
+        DBuf d_bad;
+        d_bad.alloc(sizeof(int32_t));
+        CK(cudaMemsetAsync(d_bad.p, 0, sizeof(int32_t), st));
+        CK(launch_check_csr(st, n, nnz0, rowptr, col, d_bad.as<int32_t>()));
         CK(cudaMemcpyAsync(prp, rowptr, b_rp, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(pcol, col, b_col, cudaMemcpyDeviceToHost, st));
         if (b_val) CK(cudaMemcpyAsync(pval, val, b_val, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(pbad, d_bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (*pbad != 0 || prp[n] != nnz0) throw HsError{HS_ERR_ARG};
         rp = prp;
         cl = pcol;
         vl = b_val ? pval : nullptr;
@@ -1994,7 +2104,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     }
     const int64_t nnz = rp[n];
     h->nnz = nnz;
-    {
+    if (h->opt.mem != HS_MEM_DEVICE) {
         std::atomic<int> bad{0};
         parallel_ranges(n, 1 << 16, [&](int64_t lo, int64_t hi, int) {
             for (int64_t i = lo; i < hi; i++)
@@ -2147,7 +2257,6 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
                               d_dc.as<int32_t>(), d_dl.as<int32_t>(), d_bp.as<int32_t>(), d_bc.as<int32_t>(),
                               d_bo.as<int64_t>(), d_bl.as<int32_t>(), blocks.as<double>()));
         h->prof.end(KC_ASSEMBLY, st);
-        CK(cudaStreamSynchronize(st));
     }
     h->work_bytes[KC_ASSEMBLY] += 20.0 * nnz;
     tr.mark("level-0 scatter");
@@ -2305,8 +2414,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             CK(launch_copy_blocks(st, d_cps.as<CopyDev>(), (int)cps.size(), blocks.as<double>(),
                                   nblocks.as<double>()));
             h->prof.end(KC_ASSEMBLY, st);
-            CK(cudaStreamSynchronize(st));
-            tr.mark("  assembly kernels (sync)");
+            tr.mark("  assembly kernels");
             blocks = std::move(nblocks);
             release_plan(P);
             P = std::move(Pn);
@@ -2581,7 +2689,20 @@ void apply_impl(hs_factor_s* h, const double* r, double* z) {
     h->prof.end(KC_APPLY, st);
 }
 
+// one device double read back through the pinned staging area (a copy to
+// pageable memory would be staged by the driver); synchronises the stream
 double read_scalar(hs_factor_s* h, const double* d) {
+    double* pin = reinterpret_cast<double*>(g_stage.take(sizeof(double), h->st));
+    CK(cudaMemcpyAsync(pin, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const double v = *pin;
+    g_stage.synced(h->st);
+    return v;
+}
+
+// the same into a stack variable (no staging area, which may allocate): for
+// the allocation-free PCG
+double read_scalar_stack(hs_factor_s* h, const double* d) {
     double v = 0.0;
     CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -2873,7 +2994,7 @@ int pcg_noalloc(hs_factor_s* h, const double* b, double* x, double* scratch, hs_
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     dot(b, b, sc + 4);
-    const double bn = std::sqrt(read_scalar(h, sc + 4));
+    const double bn = std::sqrt(read_scalar_stack(h, sc + 4));
     if (bn == 0.0) {
         info->iters = 0;
         info->rel_resid = 0.0;
@@ -2891,12 +3012,12 @@ int pcg_noalloc(hs_factor_s* h, const double* b, double* x, double* scratch, hs_
         CK(launch_pcg_update_xr(st, n, sc + 0, sc + 1, p, q, x, r));
         it++;
         dot(r, r, sc + 3);
-        rn = std::sqrt(read_scalar(h, sc + 3));
+        rn = std::sqrt(read_scalar_stack(h, sc + 3));
         if (rn / bn <= h->opt.rtol) {
             spmv(x, q);
             CK(launch_axpby(st, n, 1.0, b, -1.0, q));
             dot(q, q, sc + 3);
-            rn = std::sqrt(read_scalar(h, sc + 3));
+            rn = std::sqrt(read_scalar_stack(h, sc + 3));
             if (rn / bn <= h->opt.rtol) { rc = HS_OK; break; }
             CK(cudaMemcpyAsync(r, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             apply(r, z);

@@ -114,6 +114,10 @@ struct CopyDev {
 enum : int32_t { ST_OK = 0, ST_NOT_SPD = 1, ST_TOO_BIG = 2, ST_TIMEOUT = 3 };
 
 // ---- kernel launchers (hs_kernels.cu) -------------------------------------
+// *bad |= 1 unless rowptr[0] == 0, rowptr is non-decreasing over [0, n] and
+// every col[e], e < nnz, lies in [0, n)
+cudaError_t launch_check_csr(cudaStream_t st, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                             int32_t* bad);
 cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col,
                                const double* val, const int32_t* dof_cluster, const int32_t* dof_local,
                                const int32_t* blk_ptr, const int32_t* blk_col, const int64_t* blk_off,

@@ -127,6 +127,23 @@ __global__ void k_scatter_csr(int64_t n, const int64_t* __restrict__ rowptr, con
     }
 }
 
+// Validity of a CSR pattern on the device (inputs already in device memory):
+// rowptr[0] == 0, non-decreasing row pointers, every column index in [0, n).
+// Any violation sets *bad (never cleared here).
+__global__ void k_check_csr(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col, int32_t* __restrict__ bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        v |= rowptr[i + 1] < rowptr[i];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        const int32_t c = col[e];
+        v |= (c < 0) | ((int64_t)c >= n);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) v |= rowptr[0] != 0;
+    if (__any_sync(0xffffffffu, v) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
 // ---------------------------------------------------------------------------
 // Factor one phase: one CTA per cluster.
 // Shared memory: G (s*s) | rdiag (s) | v (s) | cn (wmax) | red (64) | ioff (lmax+1 ints) | flags
@@ -212,17 +229,27 @@ __device__ __forceinline__ long long abs_bits(double a) {
     return __double_as_longlong(a) & 0x7fffffffffffffffLL;
 }
 
-// In-place FP64 -> FP32 conversion of count elements by the group: float i
-// overwrites bytes of double i / 2, which an earlier chunk (or this chunk,
-// before the barrier) has already read.
+// In-place FP64 -> FP32 conversion of count elements by the group, in chunks
+// of kConvBatch elements per member: float i overwrites bytes of double i / 2,
+// which an earlier chunk (or this chunk, before the barrier) has already read.
+constexpr int kConvBatch = 8;
 template <typename Grp>
 __device__ __forceinline__ void to_float_inplace(const Grp& g, double* M, int64_t count) {
     float* F = reinterpret_cast<float*>(M);
-    for (int64_t base = 0; base < count; base += g.size) {
-        const int64_t i = base + g.rank;
-        const double x = i < count ? M[i] : 0.0;
+    const int64_t chunk = (int64_t)g.size * kConvBatch;
+    for (int64_t base = 0; base < count; base += chunk) {
+        double x[kConvBatch];
+#pragma unroll
+        for (int u = 0; u < kConvBatch; u++) {
+            const int64_t i = base + (int64_t)u * g.size + g.rank;
+            x[u] = i < count ? M[i] : 0.0;
+        }
         g.sync();
-        if (i < count) F[i] = (float)x;
+#pragma unroll
+        for (int u = 0; u < kConvBatch; u++) {
+            const int64_t i = base + (int64_t)u * g.size + g.rank;
+            if (i < count) F[i] = (float)x[u];
+        }
     }
     g.sync();
 }
@@ -414,6 +441,17 @@ __device__ float predict_fraction(const Grp& g, const float* __restrict__ model,
         out += (double)(w3[j] * (a > 0.f ? a : 0.f));
     }
     return (float)(g.sum(out, red) + (double)b3);
+}
+
+// Column j of M <- G^-1 M(:, j) by forward substitution from its first
+// nonzero row i0 (zeros above stay zero), FP64.
+__device__ __forceinline__ void scale_dense_column(const double* G, const double* rdiag, double* M, int s,
+                                                   int Wt, int j, int i0) {
+    for (int i = i0; i < s; i++) {
+        double acc = M[(int64_t)i * Wt + j];
+        for (int k = i0; k < i; k++) acc = fma(-G[i * s + k], M[(int64_t)k * Wt + j], acc);
+        M[(int64_t)i * Wt + j] = acc * rdiag[i];
+    }
 }
 
 // One scaled low-rank elimination (Sec. 3.1) by the group g.  Shared memory
@@ -610,7 +648,7 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
             }
         }
         const bool sparse = nz <= kSparseNz && 2 * nz <= s - i0;
-        dense[j] = sparse ? 0 : 1;
+        dense[j] = sparse ? 0 : (unsigned char)(1 + i0);  // dense: 1 + its first nonzero row
         dense_fill |= fill && !sparse;
         if (want_feat && sparse) {
             float cj = 0.f;
@@ -696,11 +734,72 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
     // the first float of each slot), with the terms of their error bound:
     // the squared norms of the FP32 inputs (lb) and of |G| |x| (lz)
     float lb = 0.f, lz = 0.f;
+    // Few dense columns (at most kXCols, CTA groups): every one becomes
+    // X a_j, X = G^-1 (lower triangular).  Its rows are independent sums, so
+    // a warp takes the row pair (i, s-1-i) -- s + 1 terms for every pair --
+    // with its lanes on 32 columns at a time, from the group's first nonzero
+    // row on (the terms above are zero), instead of one thread running a
+    // column's whole substitution (a chain of up to s^2 / 2 dependent FMAs,
+    // which only many columns keep the FP64 pipe busy with).  Row i is
+    // sum_k X_ik a_k in ascending k, accumulated by FMA.
+    constexpr int kXCols = 96;
+    bool xpath = false;
+    if (NT >= 256 && s <= 64) {
+        int* dj = reinterpret_cast<int*>(colsrc);  // the column table is free from here on
+        int* cnt = reinterpret_cast<int*>(red + 48);
+        if (tid == 0) *cnt = 0;
+        g.sync();
+        for (int j = tid; j < W; j += NT)
+            if (dense[j] && !(spec0 && j >= ncols)) {
+                const int q = atomicAdd(cnt, 1);
+                if (q < kXCols) dj[q] = j;
+            }
+        g.sync();
+        const int nd = *cnt;
+        xpath = nd <= kXCols;
+        if (xpath && nd > 0) {
+            // X: G^-1 in shared memory, unless the predictor used that space;
+            // else the identity columns of the block row, which hold G^-1 now
+            const bool xs = Xsh != nullptr && !predict;
+            const double* Xp = xs ? Xsh : M + W;
+            const int64_t ldX = xs ? s : Wt;
+            const int lane = tid & 31, wid = tid >> 5, nw = NT >> 5, npair = (s + 1) / 2;
+            for (int c0 = 0; c0 < nd; c0 += 32) {
+                const int j = c0 + lane < nd ? dj[c0 + lane] : -1;
+                const int k0 = (int)__reduce_min_sync(0xffffffffu, j >= 0 ? (unsigned)(dense[j] - 1) : 64u);
+                double ya[4], yb[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int ia = wid + u * nw, ib = s - 1 - ia;
+                    ya[u] = 0.0;
+                    yb[u] = 0.0;
+                    if (ia >= npair || j < 0) continue;
+                    for (int k = k0; k <= ib; k++) {
+                        const double a = M[(int64_t)k * Wt + j];
+                        if (k <= ia) ya[u] = fma(Xp[ia * ldX + k], a, ya[u]);
+                        yb[u] = fma(Xp[ib * ldX + k], a, yb[u]);
+                    }
+                }
+                g.sync();  // every warp has read the group's columns
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int ia = wid + u * nw, ib = s - 1 - ia;
+                    if (ia >= npair || j < 0) continue;
+                    if (ia >= k0) M[(int64_t)ia * Wt + j] = ya[u];
+                    if (ib != ia && ib >= k0) M[(int64_t)ib * Wt + j] = yb[u];
+                }
+            }
+        }
+    }
     for (int j = tid; j < W; j += NT) {
         if (!dense[j]) continue;
+        if (!(spec0 && j >= ncols)) {
+            if (!xpath) scale_dense_column(G, rdiag, M, s, Wt, j, dense[j] - 1);
+            continue;
+        }
         int i0 = 0;
         while (i0 < s && (__double_as_longlong(M[(int64_t)i0 * Wt + j]) << 1) == 0) i0++;
-        if (spec0 && j >= ncols) {
+        {
             float* Mf = reinterpret_cast<float*>(M);
             for (int i = i0; i < s; i++) {
                 float acc = (float)M[(int64_t)i * Wt + j];
@@ -717,12 +816,6 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
                 lz = fmaf(za, za, lz);
             }
             for (int i = 0; i < i0; i++) Mf[2 * ((int64_t)i * Wt + j)] = 0.f;
-        } else {
-            for (int i = i0; i < s; i++) {
-                double acc = M[(int64_t)i * Wt + j];
-                for (int k = i0; k < i; k++) acc = fma(-G[i * s + k], M[(int64_t)k * Wt + j], acc);
-                M[(int64_t)i * Wt + j] = acc * rdiag[i];
-            }
         }
     }
     g.sync();
@@ -2503,6 +2596,16 @@ cudaError_t launch_scatter_csr(cudaStream_t st, int64_t n, const int64_t* rowptr
     counted();
     k_scatter_csr<<<blocks_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, dof_cluster, dof_local, blk_ptr,
                                                       blk_col, blk_off, blk_ld, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_csr(cudaStream_t st, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                             int32_t* bad) {
+    if (n < 0 || nnz < 0) return cudaErrorInvalidValue;
+    const int64_t work = std::max(n, nnz);
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(work, 256), 4 * 152));
+    counted();
+    k_check_csr<<<nb, 256, 0, st>>>(n, nnz, rowptr, col, bad);
     return cudaGetLastError();
 }
 

@@ -197,6 +197,35 @@ def test_not_spd_reported(hs, oracle_lib):
     assert operator_diff(h, ref, q.n, nvec=2) <= 1e-10
 
 
+@pytest.mark.parametrize("mem", ["device", "host"])
+def test_invalid_csr_rejected(hs, mem):
+    """A column index out of range, a decreasing row pointer or a non-zero
+    first row pointer is HS_ERR_ARG (validated on the device for device
+    inputs, on the host for host inputs), and the context stays usable."""
+    p = inputs.grid_operator(8, 8, 4, ratio=1e2)
+    bad_col = p.col.copy()
+    bad_col[5] = p.n
+    neg_col = p.col.copy()
+    neg_col[p.col.size - 1] = -1
+    bad_rp = p.rowptr.copy()
+    bad_rp[3], bad_rp[4] = bad_rp[4], bad_rp[3]
+    off_rp = p.rowptr.copy()
+    off_rp[0] = 1
+    for rp, ci in ((p.rowptr, bad_col), (p.rowptr, neg_col), (bad_rp, p.col), (off_rp, p.col)):
+        if mem == "device":
+            opt = hs.hs_default_options(tol=1e-2, mem=hs.HS_MEM_DEVICE, stream=torch.cuda.current_stream().cuda_stream)
+            args = (dev(rp), dev(ci), dev(p.val))
+        else:
+            opt = hs.hs_default_options(tol=1e-2, mem=hs.HS_MEM_HOST)
+            args = (rp, ci, p.val)
+        with pytest.raises(hs.HsError) as e:
+            hs.hs_setup(p.n, *args, opt=opt)
+        assert e.value.code == hs.HS_ERR_ARG
+    x = np.zeros(p.n)
+    info, rc = hs.hs_solve(p.n, p.rowptr, p.col, p.val, p.b, x, mem=hs.HS_MEM_HOST, tol=1e-2)
+    assert rc == 0 and info.rel_resid <= 1e-8
+
+
 def test_single_dof(hs):
     rp = np.array([0, 1], np.int64)
     ci = np.array([0], np.int32)
