@@ -191,8 +191,9 @@ constexpr int kNB = 16;  // Cholesky panel width
 // error: 2^-22 -> 2^-44 -> below FP64 rounding); outside the FP32 range the
 // FP64 square root and division.
 __device__ __forceinline__ double rsqrt_newton(double d) {
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
+    const float f = (float)d;  // the range test in FP32 (no FP64 compare on the chain)
+    if (!(f > 1e-30f && f < 1e30f)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf(f);
     double h = fma(-d * y, y, 1.0);
     y = fma(0.5 * y, h, y);
     h = fma(-d * y, y, 1.0);
@@ -561,22 +562,29 @@ __device__ void factor_task(const TaskDev& T, const Grp& g, double* G, double* r
         // rows below j: X part (columns c <= j) and G part (j < c <= i), each
         // as one flat index space so that every FP64 instruction is full
         const int nx = m * (j + 1), ngt = m * (m + 1) / 2;
-        for (int idx = tid; idx < nx; idx += NT) {
-            const int t = idx / (j + 1), i = j + 1 + t, c0 = idx - t * (j + 1);
-            X[i * ldx + c0] = fma(-lcol[i], X[j * ldx + c0], X[i * ldx + c0]);
+        // with a CTA, the first thread of the last warp takes entry 0 of the
+        // triangle, (j+1, j+1), and the next pivot at once, while the other
+        // warps update the rest; with a warp, lane 0 takes the pivot after
+        // its share of the updates
+        const bool pw = NT >= 256;
+        const int nup = pw ? NT - 32 : NT;
+        if (tid < nup) {
+            for (int idx = tid; idx < nx; idx += nup) {
+                const int t = idx / (j + 1), i = j + 1 + t, c0 = idx - t * (j + 1);
+                X[i * ldx + c0] = fma(-lcol[i], X[j * ldx + c0], X[i * ldx + c0]);
+            }
+            for (int idx = tid + (pw ? 1 : 0); idx < ngt; idx += nup) {
+                // entry idx of the packed trailing triangle: row t has t + 1 entries
+                int t = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+                while (t * (t + 1) / 2 > idx) t--;
+                while ((t + 1) * (t + 2) / 2 <= idx) t++;
+                const int i = j + 1 + t, c0 = j + 1 + idx - t * (t + 1) / 2;
+                G[i * s + c0] = fma(-lcol[i], lcol[c0], G[i * s + c0]);
+            }
         }
-        for (int idx = tid; idx < ngt; idx += NT) {
-            // entry idx of the packed trailing triangle: row t has t + 1 entries
-            int t = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
-            while (t * (t + 1) / 2 > idx) t--;
-            while ((t + 1) * (t + 2) / 2 <= idx) t++;
-            const int i = j + 1 + t, c0 = j + 1 + idx - t * (t + 1) / 2;
-            G[i * s + c0] = fma(-lcol[i], lcol[c0], G[i * s + c0]);
-        }
-        // the next pivot: entry 0 of the triangle, updated by this thread only
-        if (tid == 0 && j + 1 < s) {
+        if (tid == (pw ? nup : 0) && j + 1 < s) {
             const int i = j + 1;
-            const double d = G[i * s + i];
+            const double d = pw ? fma(-lcol[i], lcol[i], G[i * s + i]) : G[i * s + i];
             if (!(d > 0.0)) {
                 *s_flag = 1;
             } else {
