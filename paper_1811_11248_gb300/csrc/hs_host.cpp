@@ -228,6 +228,24 @@ class Pool {
         return p;
     }
     int workers() const { return (int)th_.size(); }
+    // Starts the workers polling (they find no task) so that the next job
+    // does not wait for them to wake: for a caller about to run a burst of
+    // parallel loops.
+    void wake() {
+        if (getpid() != pid_ || th_.empty()) return;
+        std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
+        if (!busy.owns_lock()) return;
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            if (inside_.load(std::memory_order_acquire) > 0) return;
+            job_ = nullptr;
+            njob_ = 0;
+            next_.store(1, std::memory_order_relaxed);
+            pending_.store(0, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_release);
+        }
+        cv_.notify_all();
+    }
     bool try_run(int T, const std::function<void(int)>& fn) {
         if (getpid() != pid_) return false;  // a forked child has no workers
         std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
@@ -1436,7 +1454,7 @@ BlockTable make_table(const LevelPlan& P) {
     T.col.resize(nb);
     T.off.resize(nb);
     T.ld.resize(nb);
-    parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nc, 256, [&](int64_t lo, int64_t hi, int) {
         for (int64_t c = lo; c < hi; c++) {
             int64_t o = rowsz[c];
             int b = T.ptr[c];
@@ -1465,7 +1483,7 @@ BlockTable make_table(const LevelPlan& P) {
             }
     } else {
         std::atomic<int> bad{0};
-        parallel_ranges(nc, 1024, [&](int64_t lo, int64_t hi, int) {
+        parallel_ranges(nc, 256, [&](int64_t lo, int64_t hi, int) {
             for (int64_t p = lo; p < hi; p++)
                 for (int b = T.ptr[p]; b < T.ptr[p + 1]; b++) {
                     const int q = T.col[b];
@@ -1511,7 +1529,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     }
     const int nt = (int)order.size();
     std::vector<int32_t> t_ncap(nt), t_wcap(nt);
-    parallel_ranges(nt, 1024, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nt, 256, [&](int64_t lo, int64_t hi, int) {
         for (int64_t ti = lo; ti < hi; ti++) {
             const int c = (int)order[ti];
             int ncap = 0, wcap = 0;
@@ -1558,7 +1576,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     }
     tr0.mark("  tasks: sizes and offsets");
     L.lists.resize(list_off[nt]);
-    parallel_ranges(nt, 1024, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nt, 128, [&](int64_t lo, int64_t hi, int) {
         for (int64_t ti = lo; ti < hi; ti++) {
             TaskDev& t = L.tasks[ti];
             const int c = t.c;
@@ -1644,7 +1662,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         // threads only when there are enough pairs to pay for waking them
         int64_t npairs = 0;
         for (int ti = 0; ti < nt; ti++) npairs += (int64_t)L.tasks[ti].nn * L.tasks[ti].nn;
-        run_threads(npairs < (1 << 16) ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
+        run_threads(npairs < (1 << 11) ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
         tr0.mark("  targets: pairs");
         // concatenation in (phase, range) order: offsets first, then the
         // copies item by item in parallel
@@ -1663,7 +1681,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         char* pin = g_stage.take(tb_al + cb, st);
         TargetDev* targets = reinterpret_cast<TargetDev*>(pin);
         ContribDev* contribs = reinterpret_cast<ContribDev*>(pin + tb_al);
-        parallel_ranges(nitems, 8, [&](int64_t lo, int64_t hi, int) {
+        parallel_ranges(nitems, 2, [&](int64_t lo, int64_t hi, int) {
             for (int64_t it = lo; it < hi; it++) {
                 const int ph = (int)(it / nr), k = (int)(it % nr);
                 const int base = (int)coff[it];
@@ -1836,7 +1854,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             const int c = L.tasks[ti].c;
             pull_off[ti + 1] = pull_off[ti] + (L.early_ptr[c + 1] - L.early_ptr[c]);
         }
-        parallel_ranges(nt, 1024, [&](int64_t lo, int64_t hi, int) {
+        parallel_ranges(nt, 256, [&](int64_t lo, int64_t hi, int) {
             for (int64_t ti = lo; ti < hi; ti++) {
                 const TaskDev& t = L.tasks[ti];
                 const int32_t* mt = hmeta.data() + t.meta;
@@ -1976,7 +1994,7 @@ std::vector<CopyDev> make_assembly(const LevelPlan& P, const std::vector<int>& f
                                    const BlockTable* Tn, const std::vector<int>& nsize, const std::vector<int>& par,
                                    const std::vector<int>& poff, const std::vector<int64_t>& tmat,
                                    const std::vector<int64_t>& tpos, const std::vector<int>& tn, bool to_tops) {
-    return parallel_collect<CopyDev>(P.nc, 1024, [&](int64_t a, std::vector<CopyDev>& cps) {
+    return parallel_collect<CopyDev>(P.nc, 128, [&](int64_t a, std::vector<CopyDev>& cps) {
         if (fin[a] <= 0) return;
         if ((par[a] < 0) != to_tops) return;
         int cur = -1, curn = -1;
@@ -2061,6 +2079,7 @@ void partition_batched(hs_factor_s* h, const int64_t* rp, const int32_t* cl, con
 void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const double* val,
                 const hs_tree* tree_in, hs_info* info) {
     cudaStream_t st = h->st;
+    if (!tl_in_pool && !tl_serial) Pool::get().wake();  // the planner's loops follow
     const int64_t n = h->n;
     Trace tr;
     // host copy of the pattern (the symbolic analysis runs on the host)
@@ -2386,7 +2405,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             std::vector<int> kid0(nn, -1);  // first child of every parent (children are consecutive)
             for (int a = nc - 1; a >= 0; a--)
                 if (par[a] >= 0) kid0[par[a]] = a;
-            Pn.adj0 = build_lists(nn, 512, [&](int64_t k, std::vector<int32_t>& v, int) {
+            Pn.adj0 = build_lists(nn, 128, [&](int64_t k, std::vector<int32_t>& v, int) {
                 const size_t b0 = v.size();
                 for (int a = kid0[k]; a < nc && par[a] == k; a++) {
                     if (fin[a] <= 0) continue;
