@@ -2746,14 +2746,17 @@ int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
     double* z = r + n;
     double* p = z + n;
     double* q = p + n;
-    h->d_part.ensure(sizeof(double) * kDotParts);
+    // block partials, then the fused kernels' arrival counter
+    h->d_part.ensure(sizeof(double) * (kDotParts + 2));
     h->d_scal.ensure(sizeof(double) * 8);
     double* part = h->d_part.as<double>();
-    double* sc = h->d_scal.as<double>();  // 0 rz, 1 pq, 2 rz_new, 3 rr, 4 bb
+    unsigned* cnt = reinterpret_cast<unsigned*>(part + kDotParts);
+    double* sc = h->d_scal.as<double>();  // 0, 2: rz (alternating), 1 pq, 3 rr, 4 bb
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned), st));
     auto spmv = [&](const double* xx, double* yy) { spmv_prof(h, xx, yy); };
     auto dot = [&](const double* a, const double* bb, double* out) {
         h->prof.begin(KC_KRYLOV, st);
-        CK(launch_dot(st, n, a, bb, part, out));
+        CK(launch_dot_fused(st, n, a, bb, part, cnt, out));
         h->prof.end(KC_KRYLOV, st);
     };
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
@@ -2765,20 +2768,24 @@ int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
         info->rel_resid = 0.0;
         return HS_OK;
     }
+    int rz = 0;  // slot of the current r^T z; the next one goes to the other
     apply_impl(h, r, z);
     CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    dot(r, z, sc + 0);
+    dot(r, z, sc + rz);
     int it = 0;
     double rn = bn;
     int rc = HS_ERR_NOCONV;
     while (it < h->opt.maxit) {
-        spmv(p, q);
-        dot(p, q, sc + 1);
+        // q = A p with pq = p^T q; then x, r and rr = r^T r (one pass each)
+        h->prof.begin(KC_SPMV, st);
+        CK(launch_spmv_dot(st, n, h->d_rowptr.as<int64_t>(), h->d_col.as<int32_t>(), h->d_val.as<double>(), p, q,
+                           part, cnt, sc + 1));
+        h->prof.end(KC_SPMV, st);
+        h->work_bytes[KC_SPMV] += 12.0 * (double)h->nnz + 32.0 * (double)n;
         h->prof.begin(KC_KRYLOV, st);
-        CK(launch_pcg_update_xr(st, n, sc + 0, sc + 1, p, q, x, r));
+        CK(launch_pcg_xr_dot(st, n, sc + rz, sc + 1, p, q, x, r, part, cnt, sc + 3));
         h->prof.end(KC_KRYLOV, st);
         it++;
-        dot(r, r, sc + 3);
         rn = std::sqrt(read_scalar(h, sc + 3));
         if (rn / bn <= h->opt.rtol) {
             spmv(x, q);
@@ -2791,15 +2798,16 @@ int pcg_impl(hs_factor_s* h, const double* b, double* x, hs_info* info) {
             CK(cudaMemcpyAsync(r, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             apply_impl(h, r, z);
             CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-            dot(r, z, sc + 0);
+            dot(r, z, sc + rz);
             continue;
         }
         apply_impl(h, r, z);
-        dot(r, z, sc + 2);
+        const int rzn = 2 - rz;
+        dot(r, z, sc + rzn);
         h->prof.begin(KC_KRYLOV, st);
-        CK(launch_pcg_update_p(st, n, sc + 2, sc + 0, z, p));
+        CK(launch_pcg_update_p(st, n, sc + rzn, sc + rz, z, p));
         h->prof.end(KC_KRYLOV, st);
-        CK(cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        rz = rzn;
     }
     info->iters = it;
     info->rel_resid = rn / bn;

@@ -174,6 +174,13 @@ cudaError_t launch_spmv(cudaStream_t st, int64_t n, const int64_t* rowptr, const
 cudaError_t launch_dot(cudaStream_t st, int64_t n, const double* a, const double* b, double* partial,
                        double* out);
 // y = a*x + y with device scalar alpha = num/den (sign), etc.
+// fused PCG steps (*count: a zeroed counter, left zeroed; partial: kDotParts doubles)
+cudaError_t launch_spmv_dot(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                            const double* x, double* y, double* partial, unsigned* count, double* out);
+cudaError_t launch_pcg_xr_dot(cudaStream_t st, int64_t n, const double* rz, const double* pq, const double* p,
+                              const double* q, double* x, double* r, double* partial, unsigned* count, double* out);
+cudaError_t launch_dot_fused(cudaStream_t st, int64_t n, const double* a, const double* b, double* partial,
+                             unsigned* count, double* out);
 cudaError_t launch_pcg_update_xr(cudaStream_t st, int64_t n, const double* rz, const double* pq,
                                  const double* p, const double* q, double* x, double* r);
 cudaError_t launch_pcg_update_p(cudaStream_t st, int64_t n, const double* rz_new, const double* rz_old,

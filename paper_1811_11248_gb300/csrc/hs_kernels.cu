@@ -2391,6 +2391,76 @@ __global__ void k_pcg_p(int64_t n, const double* __restrict__ rzn, const double*
     p[i] = z[i] + beta * p[i];
 }
 
+// ---- fused PCG steps: each adds a dot product to its vector pass ----
+// The blocks' partial sums go to partial[block]; the last block to arrive
+// (counted in *count, which it resets to zero) adds them in index order into
+// *out, so the value depends only on the grid, not on the arrival order.
+__device__ __forceinline__ void dot_finish(double v, double* __restrict__ partial, unsigned* __restrict__ count,
+                                           double* __restrict__ out) {
+    __shared__ double red[32];
+    __shared__ int last;
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = v;
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double t = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + i);
+        t = block_sum(t, red);
+        if (threadIdx.x == 0) {
+            *out = t;
+            *count = 0;
+        }
+    }
+}
+
+// y = A x and *out = x^T y (the SpMV and p^T A p of a PCG step)
+__global__ void __launch_bounds__(256) k_spmv_dot(int64_t n, const int64_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                  const double* __restrict__ x, double* __restrict__ y,
+                                                  double* __restrict__ partial, unsigned* __restrict__ count,
+                                                  double* __restrict__ out) {
+    double d = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) t += val[e] * x[col[e]];
+        y[i] = t;
+        d += x[i] * t;
+    }
+    dot_finish(d, partial, count, out);
+}
+
+// x += alpha p, r -= alpha q with alpha = rz / pq, and *out = r^T r
+__global__ void __launch_bounds__(256) k_pcg_xr_dot(int64_t n, const double* __restrict__ rz,
+                                                    const double* __restrict__ pq, const double* __restrict__ p,
+                                                    const double* __restrict__ q, double* __restrict__ x,
+                                                    double* __restrict__ r, double* __restrict__ partial,
+                                                    unsigned* __restrict__ count, double* __restrict__ out) {
+    const double alpha = *rz / *pq;
+    double d = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        d += ri * ri;
+    }
+    dot_finish(d, partial, count, out);
+}
+
+// *out = a^T b in one launch
+__global__ void __launch_bounds__(256) k_dot_fused(int64_t n, const double* __restrict__ a,
+                                                   const double* __restrict__ b, double* __restrict__ partial,
+                                                   unsigned* __restrict__ count, double* __restrict__ out) {
+    double d = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d += a[i] * b[i];
+    dot_finish(d, partial, count, out);
+}
+
 // ---- batched PCG: independent problems on one block-diagonal system ----
 // Problem p owns entries pp[p] .. pp[p+1] of every vector; its scalars are
 // sc[p * kBScal + slot] and its flags fl[p * kBFlag + slot] (BF_* slots).
@@ -2905,6 +2975,32 @@ cudaError_t launch_dot(cudaStream_t st, int64_t n, const double* a, const double
     k_dot_partial<<<kDotParts, 256, 0, st>>>(n, a, b, partial);
     counted();
     k_sum_partials<<<1, 1024, 0, st>>>(partial, kDotParts, out);
+    return cudaGetLastError();
+}
+
+// grid of the fused PCG kernels: one thread per entry up to kDotParts blocks
+inline unsigned fused_grid(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n, 256), kDotParts));
+}
+
+cudaError_t launch_spmv_dot(cudaStream_t st, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                            const double* x, double* y, double* partial, unsigned* count, double* out) {
+    counted();
+    k_spmv_dot<<<fused_grid(n), 256, 0, st>>>(n, rowptr, col, val, x, y, partial, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_xr_dot(cudaStream_t st, int64_t n, const double* rz, const double* pq, const double* p,
+                              const double* q, double* x, double* r, double* partial, unsigned* count, double* out) {
+    counted();
+    k_pcg_xr_dot<<<fused_grid(n), 256, 0, st>>>(n, rz, pq, p, q, x, r, partial, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_fused(cudaStream_t st, int64_t n, const double* a, const double* b, double* partial,
+                             unsigned* count, double* out) {
+    counted();
+    k_dot_fused<<<fused_grid(n), 256, 0, st>>>(n, a, b, partial, count, out);
     return cudaGetLastError();
 }
 
