@@ -150,6 +150,41 @@ __global__ void k_check_csr(int64_t n, int64_t nnz, const int64_t* __restrict__ 
 // ---------------------------------------------------------------------------
 constexpr int kFactorThreads = 512;
 
+// Block-wide sum and maximum for the factor kernels (scratch holds >= 33
+// doubles), with the same reduction tree as block_sum / block_max and so the
+// same results, built for GB300's small FP64 rate: a warp whose values are
+// all zero skips its shuffle tree (its partial is exactly 0, which a sum or a
+// maximum over such partials takes as the tree would), and the second level
+// runs on warp 0 alone and is broadcast through scratch[32].  In the
+// factorization most warps hold no column at a given step, and every FP64
+// add of a tree run by all 32 warps competes for the same pipe.
+__device__ double block_sum_sparse(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const double t = warp_sum((lane < nw) ? scratch[lane] : 0.0);
+        if (lane == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    return scratch[32];
+}
+__device__ double block_max_sparse(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (__any_sync(0xffffffffu, v != 0.0)) v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const double t = warp_max((lane < nw) ? scratch[lane] : -DBL_MAX);
+        if (lane == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    return scratch[32];
+}
+
 // Thread groups that run one cluster elimination: a whole CTA (fine levels)
 // or one warp (coarse levels).  Reductions return the same value to every
 // member and use a fixed tree (deterministic).
@@ -157,8 +192,8 @@ struct CtaGroup {
     int rank, size;
     __device__ CtaGroup() : rank(threadIdx.x), size(blockDim.x) {}
     __device__ void sync() const { __syncthreads(); }
-    __device__ double sum(double v, double* red) const { return block_sum(v, red); }
-    __device__ double max(double v, double* red) const { return block_max(v, red); }
+    __device__ double sum(double v, double* red) const { return block_sum_sparse(v, red); }
+    __device__ double max(double v, double* red) const { return block_max_sparse(v, red); }
     __device__ int minint(int v, double* red) const { return block_min_int(v, reinterpret_cast<int*>(red)); }
     __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
 };
@@ -269,12 +304,19 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
     const int s = T.s, tid = g.rank, NT = g.size;
     const int L = T.nn + T.nw, Wn = W - ncols;
     // column-pivoted QR of the fill columns, reflectors applied to the whole row
-    // rank0: the rank is already known to be 0 (no reflector)
+    // rank0: the rank is already known to be 0 (no reflector).  A thread's
+    // column is read kRowBatch rows at a time, all loads of a batch issued
+    // before any is used (the sums keep their row order).
+    constexpr int kRowBatch = 8;
     for (int j = tid; j < (rank0 ? 0 : Wn); j += NT) {
         CT c = 0;
-        for (int i = 0; i < s; i++) {
-            const CT x = M[(int64_t)i * Wt + ncols + j];
-            c += x * x;
+        for (int i0 = 0; i0 < s; i0 += kRowBatch) {
+            CT a[kRowBatch];
+#pragma unroll
+            for (int u = 0; u < kRowBatch; u++) a[u] = i0 + u < s ? M[(int64_t)(i0 + u) * Wt + ncols + j] : CT(0);
+#pragma unroll
+            for (int u = 0; u < kRowBatch; u++)
+                if (i0 + u < s) c += a[u] * a[u];
         }
         cn[j] = c;
     }
@@ -336,15 +378,32 @@ __device__ __forceinline__ void compress_task(const TaskDev& T, const Grp& g, CT
             if (j == pc) continue;
             const bool cand = (j >= ncols && j < W);
             if (cand && cn[j - ncols] < (CT)0) continue;  // pivoted: zero below its row
+            // t = v^T M(k:, j) (rows in order), then M(k:, j) -= tau t v with the
+            // new trailing squared norm; loads of a batch before its stores
+            // (distinct rows of the thread's own column)
             CT t = M[(int64_t)k * Wt + j];
-            for (int i = k + 1; i < s; i++) t += v[i] * M[(int64_t)i * Wt + j];
+            for (int i0 = k + 1; i0 < s; i0 += kRowBatch) {
+                CT a[kRowBatch];
+#pragma unroll
+                for (int u = 0; u < kRowBatch; u++) a[u] = i0 + u < s ? M[(int64_t)(i0 + u) * Wt + j] : CT(0);
+#pragma unroll
+                for (int u = 0; u < kRowBatch; u++)
+                    if (i0 + u < s) t += v[i0 + u] * a[u];
+            }
             t *= tau;
             M[(int64_t)k * Wt + j] -= t;
             CT c = 0;
-            for (int i = k + 1; i < s; i++) {
-                const CT x = M[(int64_t)i * Wt + j] - t * v[i];
-                M[(int64_t)i * Wt + j] = x;
-                if (cand) c += x * x;
+            for (int i0 = k + 1; i0 < s; i0 += kRowBatch) {
+                CT a[kRowBatch];
+#pragma unroll
+                for (int u = 0; u < kRowBatch; u++) a[u] = i0 + u < s ? M[(int64_t)(i0 + u) * Wt + j] : CT(0);
+#pragma unroll
+                for (int u = 0; u < kRowBatch; u++) {
+                    if (i0 + u >= s) break;
+                    const CT x = a[u] - t * v[i0 + u];
+                    M[(int64_t)(i0 + u) * Wt + j] = x;
+                    if (cand) c += x * x;
+                }
             }
             if (cand) cn[j - ncols] = c;
         }
