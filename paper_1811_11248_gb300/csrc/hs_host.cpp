@@ -754,7 +754,7 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     // many DOFs over contiguous chunks: counts per leaf and chunk, offsets
     // leaf by leaf with the chunks in order, then every chunk places its DOFs)
     const int nleaf = 1 << L;
-    const int nch = tl_serial ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / 65536));
+    const int nch = tl_serial ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(hs_threads(), n / 8192));
     leaf_ptr.assign(nleaf + 1, 0);
     perm.assign(n, 0);
     if (nch == 1) {
