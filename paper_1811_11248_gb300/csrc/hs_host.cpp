@@ -1293,6 +1293,7 @@ struct Level {
     DBuf d_tasks, d_lists, d_meta, d_fac, d_slot, d_vcopy, d_y, d_stage;
     DBuf d_ap_tasks, d_ap_pulls, d_ap_nbs, d_ap_fins, d_ph;
     int nvcopy = 0, nfin = 0;
+    bool fused = false;                // factored by the fused coarse-level kernel
     int64_t fac_doubles = 0;
     // algorithmic work of the level (filled after it ran)
     double flops_factor = 0, flops_compress = 0, flops_schur = 0;
@@ -1501,7 +1502,8 @@ BlockTable make_table(const LevelPlan& P) {
 // Factor one level: plan, device records, phases.  `blocks` holds the level's
 // assembled matrix (layout T).  Returns the final sizes.
 void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf& blocks, DBuf& d_cur,
-                  DBuf& d_status, hs_info* info, const std::vector<std::pair<int, int>>& ranges) {
+                  DBuf& d_status, hs_info* info, const std::vector<std::pair<int, int>>& ranges,
+                  const std::function<void()>& overlap) {
     Level& L = *h->lev[l];
     cudaStream_t st = h->st;
     Trace tr0;
@@ -1817,6 +1819,8 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
     }
     tr.mark("  launches");
+    overlap();  // host work of earlier levels while these kernels run
+    L.fused = fused;
     // the level's results in one read-back: status word, final cluster sizes
     // and the tasks' rank / column layout
     std::vector<int32_t> hmeta(meta);
@@ -1839,6 +1843,19 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         g_stage.synced(st);
     }
     tr.mark("  downloads");
+    L.hmeta = std::move(hmeta);
+}
+
+// The level's solve-phase records (tasks, pulls, neighbour records, stages)
+// and its algorithmic work, from its readback; run by the setup while the
+// next level's kernels execute.
+void level_records(hs_factor_s* h, int l) {
+    Level& L = *h->lev[l];
+    cudaStream_t st = h->st;
+    Trace tr;
+    const int nt = (int)L.tasks.size();
+    const bool fused = L.fused, nodc = h->opt.no_dc != 0;
+    const std::vector<int32_t>& hmeta = L.hmeta;
     // solve-phase records with resolved offsets
     {
         std::vector<ApTask> at(nt);
@@ -1917,7 +1934,6 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         upload(L.d_ap_tasks, ats, st);
         upload(L.d_ap_nbs, nbs, st);
         upload(L.d_ph, L.ap_stage, st);
-        L.hmeta = std::move(hmeta);
         L.early.clear();
         L.early_ptr.clear();
     }
@@ -1931,7 +1947,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         double ncol = 0, wcol = 0;
         for (int k = 0; k < t.nn + t.nw; k++) {
             const int q = L.lists[t.list + k].q;
-            const int w = (P.phase[q] >= 0 && P.phase[q] < P.phase[t.c]) ? L.fin[q] : P.size0[q];
+            const int w = (L.phase[q] >= 0 && L.phase[q] < L.phase[t.c]) ? L.fin[q] : L.size0[q];
             (k < t.nn ? ncol : wcol) += w;
         }
         const double s = t.s;
@@ -2198,7 +2214,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
 
     // level 0 pattern
     std::vector<int32_t> dof_cluster(n), dof_local(n);
-    parallel_ranges(nleaf, 256, [&](int64_t lo, int64_t hi, int) {
+    parallel_ranges(nleaf, 64, [&](int64_t lo, int64_t hi, int) {
         for (int64_t c = lo; c < hi; c++)
             for (int k = leaf_ptr[c]; k < leaf_ptr[c + 1]; k++) {
                 dof_cluster[h->perm[k]] = (int32_t)c;
@@ -2212,7 +2228,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
     {
         // block pattern of level 0, kept symmetric even if the CSR pattern is not
         std::vector<std::vector<int>> stamp(hs_threads());
-        P.adj0 = build_lists(nleaf, 256, [&](int64_t c, std::vector<int32_t>& out, int t) {
+        P.adj0 = build_lists(nleaf, 64, [&](int64_t c, std::vector<int32_t>& out, int t) {
             auto& st = stamp[t];
             if (st.empty()) st.assign(nleaf, -1);
             const size_t b0 = out.size();
@@ -2325,13 +2341,23 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         h->tops.push_back(TopDev{h->top_bufs.back().as<double>(), 0, nt, 0});
         ntop_total = nt;
     }
+    // the previous level's solve records and vector copies, built while
+    // the next level's kernels run
+    std::function<void()> deferred;
+    auto run_deferred = [&] {
+        if (deferred) {
+            auto f = std::move(deferred);
+            deferred = nullptr;
+            f();
+        }
+    };
     for (int l = 0; !act.empty(); l++) {
         h->lev.emplace_back(new Level());
         DBuf d_cur;
         upload(d_cur, P.size0, st);
         ranges.clear();
         for (const Active& a : act) ranges.push_back({a.lo, a.hi});
-        factor_level(h, l, P, T, blocks, d_cur, d_status, info, ranges);
+        factor_level(h, l, P, T, blocks, d_cur, d_status, info, ranges, run_deferred);
         tr.mark("level factor (records+kernels)");
         Level& L = *h->lev[l];
         const std::vector<int>& fin = L.fin;
@@ -2383,7 +2409,10 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         for (int k = 0; k < nn; k++) nslot[k + 1] = nslot[k] + nsize[k];
         for (int cc = 0; cc < nc; cc++)
             if (par[cc] >= 0) dst[cc] = nslot[par[cc]] + poff[cc];
-        make_vcopies(h, L, dst, to_top);
+        deferred = [h, l, dst = std::move(dst), to_top = std::move(to_top)] {
+            level_records(h, l);
+            make_vcopies(h, *h->lev[l], dst, to_top);
+        };
         if (!ending.empty()) {
             // dense tops of the problems that end here
             h->top_bufs.emplace_back();
@@ -2442,6 +2471,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         act = std::move(nact);
         tr.mark("next-level plan+assembly");
     }
+    run_deferred();
     // factor every dense top (one CTA per problem)
     h->ntop = (int)ntop_total;
     h->d_ytop.alloc(sizeof(double) * std::max<int64_t>(ntop_total, 1));
@@ -2455,7 +2485,6 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         else
             CK(launch_tops_cholesky(st, h->d_tops.as<TopDev>(), (int)h->tops.size(), d_status.as<int32_t>()));
         h->prof.end(KC_TOP, st);
-        check_status(h, d_status, info);
     }
     blocks.release();
     // level vectors for the solve phase
@@ -2466,10 +2495,13 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         fb += Lp->fac_doubles * (h->fp32 ? 4 : 8);
     }
     h->factor_bytes = fb;
-    CK(cudaStreamSynchronize(st));
     tr.mark("top");
+    // the dense coarse operator is formed and the solve graph captured while
+    // the tops' Cholesky runs; then one synchronisation reads the status of
+    // both (and of everything the setup enqueued)
     build_apply_graph(h);
     h->apply_bytes = apply_work_bytes(h);
+    check_status(h, d_status, info);
     tr.mark("apply graph");
 }
 
@@ -2662,11 +2694,9 @@ void build_apply_graph(hs_factor_s* h) {
         CK(launch_ap_coarse_batch(h->st, d_al.as<ApLevel>(), (int)al.size(), h->ntop, h->top_L, ytop0,
                                   yin0, n, stride, h->d_coarse.as<double>(), h->fp32));
         h->prof.end(KC_TOP, h->st);
-        CK(cudaStreamSynchronize(h->st));
     } else {
         std::vector<ApLevel> al = make_levels(nullptr, nullptr, nullptr, nullptr);
         upload(h->d_aplevels, al, h->st);
-        CK(cudaStreamSynchronize(h->st));
     }
     h->apply_out = (h->coarse_dense && ld == 0) ? h->d_ycout.as<double>() : nullptr;
     cudaStream_t cap;
