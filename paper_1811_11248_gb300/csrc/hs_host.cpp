@@ -1595,144 +1595,120 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
         }
     });
     tr0.mark("  tasks: lists");
-    // Schur targets of every phase: (p, q), p <= q, contributions in
-    // ascending task order (sort by target, stable in task order).  The
-    // independent cluster ranges are handled on their own threads and
-    // concatenated (targets of a range lie in that range).
-    {
-        struct TC {
-            int p, q;
-            ContribDev c;
-        };
-        const int nr = std::max<int>(1, (int)ranges.size());
-        std::vector<std::vector<std::vector<TargetDev>>> rt(nr, std::vector<std::vector<TargetDev>>(L.nphases));
-        std::vector<std::vector<std::vector<ContribDev>>> rc(nr, std::vector<std::vector<ContribDev>>(L.nphases));
-        std::atomic<int> next{0};
-        // work items: (range, phase) pairs, independent of each other
-        const int nitems = nr * L.nphases;
-        auto work = [&] {
-            std::vector<TC> tcs, tmp;
-            std::vector<int> cntv;
-            for (int item = next++; item < nitems; item = next++) {
-                const int k = item / L.nphases;
-                const int lo = ranges.empty() ? 0 : ranges[k].first, hi = ranges.empty() ? P.nc : ranges[k].second;
-                {
-                    const int ph = item % L.nphases;
-                    const auto& cs = P.phases[ph];
-                    auto b0 = std::lower_bound(cs.begin(), cs.end(), lo), b1 = std::lower_bound(cs.begin(), cs.end(), hi);
-                    tcs.clear();
-                    for (auto it = b0; it != b1; ++it) {
-                        const int c = *it, ti = task_of[c];
-                        const auto& nlc = P.nl[c];
-                        for (int a = 0; a < (int)nlc.size(); a++)
-                            for (int b = 0; b < (int)nlc.size(); b++)
-                                if (nlc[a] <= nlc[b]) tcs.push_back(TC{nlc[a], nlc[b], ContribDev{ti, a, b}});
-                    }
-                    // stable order by (p, q): counting sort on q, then on p
-                    // (keys are cluster ids in [lo, hi))
-                    if (!tcs.empty()) {
-                        const int span = hi - lo;
-                        cntv.assign(span + 1, 0);
-                        tmp.resize(tcs.size());
-                        for (const TC& x : tcs) cntv[x.q - lo + 1]++;
-                        for (int u = 0; u < span; u++) cntv[u + 1] += cntv[u];
-                        for (const TC& x : tcs) tmp[cntv[x.q - lo]++] = x;
-                        cntv.assign(span + 1, 0);
-                        for (const TC& x : tmp) cntv[x.p - lo + 1]++;
-                        for (int u = 0; u < span; u++) cntv[u + 1] += cntv[u];
-                        for (const TC& x : tmp) tcs[cntv[x.p - lo]++] = x;
-                    }
-                    auto& tg = rt[k][ph];
-                    auto& ct = rc[k][ph];
-                    int cur = -1;  // targets come in (p, q) order
-                    for (size_t i = 0; i < tcs.size();) {
-                        size_t j = i;
-                        TargetDev g{};
-                        g.p = tcs[i].p;
-                        g.q = tcs[i].q;
-                        g.blk_pq = T.find_from(g.p, g.q, cur);
-                        g.blk_qp = T.tpos[g.blk_pq];
-                        g.c_begin = (int)ct.size();
-                        while (j < tcs.size() && tcs[j].p == g.p && tcs[j].q == g.q) ct.push_back(tcs[j++].c);
-                        g.c_end = (int)ct.size();
-                        tg.push_back(g);
-                        i = j;
+    // Schur targets of every phase (built before the launch of a fused
+    // level; with per-phase launches, while the first phase runs)
+    auto build_targets = [&] {
+        // Schur targets of every phase: (p, q), p <= q, contributions in
+        // ascending task order (sort by target, stable in task order).  The
+        // independent cluster ranges are handled on their own threads and
+        // concatenated (targets of a range lie in that range).
+        {
+            struct TC {
+                int p, q;
+                ContribDev c;
+            };
+            const int nr = std::max<int>(1, (int)ranges.size());
+            std::vector<std::vector<std::vector<TargetDev>>> rt(nr, std::vector<std::vector<TargetDev>>(L.nphases));
+            std::vector<std::vector<std::vector<ContribDev>>> rc(nr, std::vector<std::vector<ContribDev>>(L.nphases));
+            std::atomic<int> next{0};
+            // work items: (range, phase) pairs, independent of each other
+            const int nitems = nr * L.nphases;
+            auto work = [&] {
+                std::vector<TC> tcs, tmp;
+                std::vector<int> cntv;
+                for (int item = next++; item < nitems; item = next++) {
+                    const int k = item / L.nphases;
+                    const int lo = ranges.empty() ? 0 : ranges[k].first, hi = ranges.empty() ? P.nc : ranges[k].second;
+                    {
+                        const int ph = item % L.nphases;
+                        const auto& cs = P.phases[ph];
+                        auto b0 = std::lower_bound(cs.begin(), cs.end(), lo), b1 = std::lower_bound(cs.begin(), cs.end(), hi);
+                        tcs.clear();
+                        for (auto it = b0; it != b1; ++it) {
+                            const int c = *it, ti = task_of[c];
+                            const auto& nlc = P.nl[c];
+                            for (int a = 0; a < (int)nlc.size(); a++)
+                                for (int b = 0; b < (int)nlc.size(); b++)
+                                    if (nlc[a] <= nlc[b]) tcs.push_back(TC{nlc[a], nlc[b], ContribDev{ti, a, b}});
+                        }
+                        // stable order by (p, q): counting sort on q, then on p
+                        // (keys are cluster ids in [lo, hi))
+                        if (!tcs.empty()) {
+                            const int span = hi - lo;
+                            cntv.assign(span + 1, 0);
+                            tmp.resize(tcs.size());
+                            for (const TC& x : tcs) cntv[x.q - lo + 1]++;
+                            for (int u = 0; u < span; u++) cntv[u + 1] += cntv[u];
+                            for (const TC& x : tcs) tmp[cntv[x.q - lo]++] = x;
+                            cntv.assign(span + 1, 0);
+                            for (const TC& x : tmp) cntv[x.p - lo + 1]++;
+                            for (int u = 0; u < span; u++) cntv[u + 1] += cntv[u];
+                            for (const TC& x : tmp) tcs[cntv[x.p - lo]++] = x;
+                        }
+                        auto& tg = rt[k][ph];
+                        auto& ct = rc[k][ph];
+                        int cur = -1;  // targets come in (p, q) order
+                        for (size_t i = 0; i < tcs.size();) {
+                            size_t j = i;
+                            TargetDev g{};
+                            g.p = tcs[i].p;
+                            g.q = tcs[i].q;
+                            g.blk_pq = T.find_from(g.p, g.q, cur);
+                            g.blk_qp = T.tpos[g.blk_pq];
+                            g.c_begin = (int)ct.size();
+                            while (j < tcs.size() && tcs[j].p == g.p && tcs[j].q == g.q) ct.push_back(tcs[j++].c);
+                            g.c_end = (int)ct.size();
+                            tg.push_back(g);
+                            i = j;
+                        }
                     }
                 }
-            }
-        };
-        // threads only when there are enough pairs to pay for waking them
-        int64_t npairs = 0;
-        for (int ti = 0; ti < nt; ti++) npairs += (int64_t)L.tasks[ti].nn * L.tasks[ti].nn;
-        run_threads(npairs < (1 << 11) ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
-        tr0.mark("  targets: pairs");
-        // concatenation in (phase, range) order: offsets first, then the
-        // copies item by item in parallel
-        std::vector<int64_t> toff(nitems + 1, 0), coff(nitems + 1, 0);
-        for (int ph = 0, it = 0; ph < L.nphases; ph++) {
-            for (int k = 0; k < nr; k++, it++) {
-                toff[it + 1] = toff[it] + (int64_t)rt[k][ph].size();
-                coff[it + 1] = coff[it] + (int64_t)rc[k][ph].size();
-            }
-            L.ph_target.push_back((int)toff[it]);
-        }
-        // written straight into pinned staging (one area for both) and
-        // copied to the device from there
-        const size_t tb = sizeof(TargetDev) * (size_t)toff[nitems], cb = sizeof(ContribDev) * (size_t)coff[nitems];
-        const size_t tb_al = (tb + 255) & ~(size_t)255;
-        char* pin = g_stage.take(tb_al + cb, st);
-        TargetDev* targets = reinterpret_cast<TargetDev*>(pin);
-        ContribDev* contribs = reinterpret_cast<ContribDev*>(pin + tb_al);
-        parallel_ranges(nitems, 2, [&](int64_t lo, int64_t hi, int) {
-            for (int64_t it = lo; it < hi; it++) {
-                const int ph = (int)(it / nr), k = (int)(it % nr);
-                const int base = (int)coff[it];
-                int64_t o = toff[it];
-                for (TargetDev g : rt[k][ph]) {
-                    g.c_begin += base;
-                    g.c_end += base;
-                    targets[o++] = g;
+            };
+            // threads only when there are enough pairs to pay for waking them
+            int64_t npairs = 0;
+            for (int ti = 0; ti < nt; ti++) npairs += (int64_t)L.tasks[ti].nn * L.tasks[ti].nn;
+            run_threads(npairs < (1 << 11) ? 1 : std::min<int>(hs_threads(), std::max(nitems, 1)), [&](int) { work(); });
+            tr0.mark("  targets: pairs");
+            // concatenation in (phase, range) order: offsets first, then the
+            // copies item by item in parallel
+            std::vector<int64_t> toff(nitems + 1, 0), coff(nitems + 1, 0);
+            for (int ph = 0, it = 0; ph < L.nphases; ph++) {
+                for (int k = 0; k < nr; k++, it++) {
+                    toff[it + 1] = toff[it] + (int64_t)rt[k][ph].size();
+                    coff[it + 1] = coff[it] + (int64_t)rc[k][ph].size();
                 }
-                std::copy(rc[k][ph].begin(), rc[k][ph].end(), contribs + coff[it]);
-                // freed here, in parallel (a worker allocated them)
-                std::vector<TargetDev>().swap(rt[k][ph]);
-                std::vector<ContribDev>().swap(rc[k][ph]);
+                L.ph_target.push_back((int)toff[it]);
             }
-        });
-        d_targets.alloc(std::max<size_t>(tb, 16));
-        d_contribs.alloc(std::max<size_t>(cb, 16));
-        if (tb) CK(cudaMemcpyAsync(d_targets.p, targets, tb, cudaMemcpyHostToDevice, st));
-        if (cb) CK(cudaMemcpyAsync(d_contribs.p, contribs, cb, cudaMemcpyHostToDevice, st));
-    }
-    tr0.mark("  targets");
-    // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
-    // before its own transform (q in a later phase) or at level end (earlier)
-    {
-        L.early_ptr.assign(P.nc + 1, 0);
-        L.late_ptr.assign(P.nc + 1, 0);
-        for (int ti = 0; ti < nt; ti++) {
-            const TaskDev& t = L.tasks[ti];
-            for (int k = 0; k < t.nn; k++) {
-                const int q = L.lists[t.list + k].q;
-                (P.phase[q] > P.phase[t.c] ? L.early_ptr : L.late_ptr)[q + 1]++;
-            }
+            // written straight into pinned staging (one area for both) and
+            // copied to the device from there
+            const size_t tb = sizeof(TargetDev) * (size_t)toff[nitems], cb = sizeof(ContribDev) * (size_t)coff[nitems];
+            const size_t tb_al = (tb + 255) & ~(size_t)255;
+            char* pin = g_stage.take(tb_al + cb, st);
+            TargetDev* targets = reinterpret_cast<TargetDev*>(pin);
+            ContribDev* contribs = reinterpret_cast<ContribDev*>(pin + tb_al);
+            parallel_ranges(nitems, 2, [&](int64_t lo, int64_t hi, int) {
+                for (int64_t it = lo; it < hi; it++) {
+                    const int ph = (int)(it / nr), k = (int)(it % nr);
+                    const int base = (int)coff[it];
+                    int64_t o = toff[it];
+                    for (TargetDev g : rt[k][ph]) {
+                        g.c_begin += base;
+                        g.c_end += base;
+                        targets[o++] = g;
+                    }
+                    std::copy(rc[k][ph].begin(), rc[k][ph].end(), contribs + coff[it]);
+                    // freed here, in parallel (a worker allocated them)
+                    std::vector<TargetDev>().swap(rt[k][ph]);
+                    std::vector<ContribDev>().swap(rc[k][ph]);
+                }
+            });
+            d_targets.alloc(std::max<size_t>(tb, 16));
+            d_contribs.alloc(std::max<size_t>(cb, 16));
+            if (tb) CK(cudaMemcpyAsync(d_targets.p, targets, tb, cudaMemcpyHostToDevice, st));
+            if (cb) CK(cudaMemcpyAsync(d_contribs.p, contribs, cb, cudaMemcpyHostToDevice, st));
         }
-        for (int q = 0; q < P.nc; q++) {
-            L.early_ptr[q + 1] += L.early_ptr[q];
-            L.late_ptr[q + 1] += L.late_ptr[q];
-        }
-        L.early.resize(L.early_ptr[P.nc]);
-        L.late.resize(L.late_ptr[P.nc]);
-        std::vector<int32_t> fe(L.early_ptr.begin(), L.early_ptr.end() - 1), fl(L.late_ptr.begin(), L.late_ptr.end() - 1);
-        for (int ti = 0; ti < nt; ti++) {
-            const TaskDev& t = L.tasks[ti];
-            for (int k = 0; k < t.nn; k++) {
-                const int q = L.lists[t.list + k].q;
-                if (P.phase[q] > P.phase[t.c]) L.early[fe[q]++] = {ti, k};
-                else L.late[fl[q]++] = {ti, k};
-            }
-        }
-    }
+        tr0.mark("  targets");
+    };
     L.wmax = std::max(L.wmax, 64);  // the fused kernel's Schur step stages 32 x 4 int64 in the column table
     const bool nodc = h->opt.no_dc != 0;
     if ((nodc ? factor_nodc_smem_bytes(L.smax, L.wmax, L.lmax) : factor_smem_bytes(L.smax, L.wmax, L.lmax)) >
@@ -1767,6 +1743,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
     for (const TaskDev& t : L.tasks) mcap = std::max<int64_t>(mcap, (int64_t)t.s * (t.wcap + t.s));
     const bool fused = !nodc && h->opt.fused_levels && L.smax <= kFusedSmax &&
                        fused_smem_bytes(L.smax, L.wmax, L.lmax, mcap) <= (size_t)kFactorMaxSmem;
+    if (fused) build_targets();
     if (fused && nt > 0) {
         DBuf d_pht, d_phg, d_bar;
         upload(d_pht, L.ph_task, st);
@@ -1808,6 +1785,7 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
                                    L.d_meta.as<int32_t>(), d_ws.as<double>(), eps2, d_status.as<int32_t>(), l, feat,
                                    h->d_model.as<float>()));
         h->prof.end(KC_FACTOR, st);
+        if (ph == 0) build_targets();
         const int g0 = L.ph_target[ph], ng = L.ph_target[ph + 1] - g0;
         if (ng > 0) {
             h->prof.begin(KC_SCHUR, st);
@@ -1818,7 +1796,36 @@ void factor_level(hs_factor_s* h, int l, LevelPlan& P, const BlockTable& T, DBuf
             h->prof.end(KC_SCHUR, st);
         }
     }
+    if (!fused && L.nphases == 0) build_targets();
     tr.mark("  launches");
+    // solve-phase updates: neighbour q of task t receives C_t(:, q)^T y_t(fine)
+    // before its own transform (q in a later phase) or at level end (earlier)
+    {
+        L.early_ptr.assign(P.nc + 1, 0);
+        L.late_ptr.assign(P.nc + 1, 0);
+        for (int ti = 0; ti < nt; ti++) {
+            const TaskDev& t = L.tasks[ti];
+            for (int k = 0; k < t.nn; k++) {
+                const int q = L.lists[t.list + k].q;
+                (P.phase[q] > P.phase[t.c] ? L.early_ptr : L.late_ptr)[q + 1]++;
+            }
+        }
+        for (int q = 0; q < P.nc; q++) {
+            L.early_ptr[q + 1] += L.early_ptr[q];
+            L.late_ptr[q + 1] += L.late_ptr[q];
+        }
+        L.early.resize(L.early_ptr[P.nc]);
+        L.late.resize(L.late_ptr[P.nc]);
+        std::vector<int32_t> fe(L.early_ptr.begin(), L.early_ptr.end() - 1), fl(L.late_ptr.begin(), L.late_ptr.end() - 1);
+        for (int ti = 0; ti < nt; ti++) {
+            const TaskDev& t = L.tasks[ti];
+            for (int k = 0; k < t.nn; k++) {
+                const int q = L.lists[t.list + k].q;
+                if (P.phase[q] > P.phase[t.c]) L.early[fe[q]++] = {ti, k};
+                else L.late[fl[q]++] = {ti, k};
+            }
+        }
+    }
     overlap();  // host work of earlier levels while these kernels run
     L.fused = fused;
     // the level's results in one read-back: status word, final cluster sizes
