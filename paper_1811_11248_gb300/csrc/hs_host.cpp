@@ -198,11 +198,14 @@ bool sorted_has(const std::vector<int>& v, int x) { return std::binary_search(v.
 
 // Run f(lo, hi, t) over [0, n) split into contiguous ranges on up to
 // hs_threads() host threads (the results never depend on the split).
+// Default: up to 16, leaving two of the machine's cores to other threads
+// (the workers poll between jobs, and a polling worker that shares a core
+// with the caller or a driver thread would slow them).
 int hs_threads() {
     static const int t = [] {
         const unsigned h = std::thread::hardware_concurrency();
         const char* e = std::getenv("HS_THREADS");
-        int v = e ? std::atoi(e) : (int)std::min(16u, std::max(1u, h));
+        int v = e ? std::atoi(e) : (int)std::min(16u, h > 3 ? h - 2 : 1u);
         return std::max(1, v);
     }();
     return t;
@@ -301,9 +304,11 @@ class Pool {
         tl_in_pool = true;
         unsigned seen = gen_.load(std::memory_order_acquire);
         for (;;) {
-            // poll for the next job (the clock read every 64 polls), then sleep
+            // poll for the next job (the clock read every 64 polls, the core
+            // offered to other threads every 256), then sleep
             const auto t0 = std::chrono::steady_clock::now();
             for (int k = 1; gen_.load(std::memory_order_acquire) == seen; k++) {
+                if ((k & 255) == 0) std::this_thread::yield();
                 if ((k & 63) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(spin_us_)) {
                     std::unique_lock<std::mutex> lk(mu_);
                     cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
@@ -2160,6 +2165,18 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
         if (bad) throw HsError{HS_ERR_ARG};
     }
     tr.mark("  pattern checks");
+    // device copies of A (SpMV), in flight during the partition
+    h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));
+    h->d_col.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    h->d_val.alloc(sizeof(double) * std::max<int64_t>(nnz, 1));
+    {
+        const cudaMemcpyKind kind = h->opt.mem == HS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpyAsync(h->d_rowptr.p, rowptr, sizeof(int64_t) * (n + 1), kind, st));
+        if (nnz) {
+            CK(cudaMemcpyAsync(h->d_col.p, col, sizeof(int32_t) * nnz, kind, st));
+            CK(cudaMemcpyAsync(h->d_val.p, val, sizeof(double) * nnz, kind, st));
+        }
+    }
 
     // partition tree
     std::vector<int32_t> leaf_ptr;
@@ -2207,16 +2224,7 @@ void setup_impl(hs_factor_s* h, const int64_t* rowptr, const int32_t* col, const
             for (int j = 0; j < kMlpHidden; j++) mdl.push_back(W2[j * kMlpHidden + k]);
         upload(h->d_model, mdl, st);
     }
-    // device copies of A (SpMV) and of the permutation
-    h->d_rowptr.alloc(sizeof(int64_t) * (n + 1));
-    h->d_col.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1));
-    h->d_val.alloc(sizeof(double) * std::max<int64_t>(nnz, 1));
-    const cudaMemcpyKind kind = h->opt.mem == HS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(h->d_rowptr.p, rowptr, sizeof(int64_t) * (n + 1), kind, st));
-    if (nnz) {
-        CK(cudaMemcpyAsync(h->d_col.p, col, sizeof(int32_t) * nnz, kind, st));
-        CK(cudaMemcpyAsync(h->d_val.p, val, sizeof(double) * nnz, kind, st));
-    }
+    // device copy of the permutation
     upload(h->d_perm, h->perm, st);
 
     // level 0 pattern
