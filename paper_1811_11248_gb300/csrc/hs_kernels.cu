@@ -46,6 +46,17 @@ namespace {
 
 constexpr double kPivotTie = 1e-6;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may be scheduled while its predecessor in the stream is still
+// running.  griddep_wait() blocks until every predecessor grid has completed
+// and its memory writes are visible; griddep_release() lets the successor's
+// CTAs be scheduled once every CTA of this grid has issued it or exited.
+// Without the launch attribute both are no-ops.  Every kernel launched
+// through launch_chained calls griddep_wait() before its first global access,
+// so it is ordered after the whole chain before it.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1885,6 +1896,8 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
     extern __shared__ double sh[];
     FT* ys = reinterpret_cast<FT*>(sh);
     FT* yn = ys + smax;
+    griddep_wait();
+    griddep_release();
     const ApTask T = tasks[t0 + blockIdx.x];
     const int s = T.s, tid = threadIdx.x, NT = blockDim.x;
     double* yg = y + T.y;
@@ -1966,6 +1979,8 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
 __global__ void __launch_bounds__(kApplyThreads)
 k_ap_fin(const ApFin* __restrict__ fins, const ApPull* __restrict__ pulls, const double* __restrict__ stage,
          double* __restrict__ y, double* __restrict__ ynext, double* __restrict__ ytop) {
+    griddep_wait();
+    griddep_release();
     const ApFin F = fins[blockIdx.x];
     double* dst = (F.to_top ? ytop : ynext) + F.dst;
     for (int j = threadIdx.x; j < F.len; j += blockDim.x) {
@@ -1988,6 +2003,8 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
     double* part = sh + smax;
     FT* xnf = reinterpret_cast<FT*>(part + blockDim.x);
     FT* xsf = xnf + nmax;
+    griddep_wait();
+    griddep_release();
     const ApTask T = tasks[t0 + blockIdx.x];
     const int s = T.s, r = T.r, f = s - r, tid = threadIdx.x, NT = blockDim.x;
     double* yg = y + T.y;
@@ -2262,6 +2279,8 @@ template <typename FT>
 __global__ void __launch_bounds__(kCoarseThreads)
 k_ap_coarse(const ApLevel* __restrict__ lvl, int nlev, int ntop, const double* __restrict__ Ltop,
             double* __restrict__ ytop) {
+    griddep_wait();
+    griddep_release();
     coarse_chain<FT>(lvl, nlev, ntop, Ltop, ytop, 0);
 }
 
@@ -2285,6 +2304,8 @@ k_ap_coarse_batch(const ApLevel* __restrict__ lvl, int nlev, int ntop, const dou
 // y = Mc x (n x n, row-major): one warp per row, lanes over columns.
 __global__ void __launch_bounds__(256) k_dense_gemv(int n, const double* __restrict__ Mc,
                                                     const double* __restrict__ x, double* __restrict__ y) {
+    griddep_wait();
+    griddep_release();
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= n) return;
@@ -2303,6 +2324,8 @@ __global__ void __launch_bounds__(256) k_dense_gemv(int n, const double* __restr
 // reverse: y_level[src] <- (to_top ? ytop : y_next)[dst]; forward the other way
 __global__ void k_vcopy(const VCopyDev* __restrict__ cps, int ncps, const double* __restrict__ src,
                         double* __restrict__ dst, int reverse, const double* __restrict__ ytop) {
+    griddep_wait();
+    griddep_release();
     const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (c >= ncps) return;
     const VCopyDev v = cps[c];
@@ -2354,6 +2377,8 @@ __global__ void __launch_bounds__(256) k_tops_cholesky(const TopDev* __restrict_
 
 // y <- L^-T L^-1 y for every top (one CTA per problem).
 __global__ void __launch_bounds__(256) k_tops_solve(const TopDev* __restrict__ tops, double* __restrict__ ytop) {
+    griddep_wait();
+    griddep_release();
     const TopDev tp = tops[blockIdx.x];
     const int n = tp.n, tid = threadIdx.x, NT = blockDim.x;
     const double* L = tp.L;
@@ -2908,26 +2933,42 @@ cudaError_t launch_dense_cholesky(cudaStream_t st, int n, double* a, int32_t* st
     return cudaGetLastError();
 }
 
+// Launch on st with programmatic stream serialisation (the kernel must call
+// griddep_wait() before its first global access).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                           Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, args...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax,
                           const ApPull* pulls, const void* fac, int fp32, double* stage, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
     const size_t smem = sizeof(double) * 2 * smax;
     if (fp32)
-        k_ap_fwd<float><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, pulls, static_cast<const float*>(fac), stage, y,
-                                                             smax);
-    else
-        k_ap_fwd<double><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, pulls, static_cast<const double*>(fac), stage,
-                                                              y, smax);
-    return cudaGetLastError();
+        return launch_chained(k_ap_fwd<float>, ntasks, kApplyThreads, smem, st, tasks, t0, pulls,
+                              static_cast<const float*>(fac), stage, y, smax);
+    return launch_chained(k_ap_fwd<double>, ntasks, kApplyThreads, smem, st, tasks, t0, pulls,
+                          static_cast<const double*>(fac), stage, y, smax);
 }
 
 cudaError_t launch_ap_fin(cudaStream_t st, const ApFin* fins, int nfin, const ApPull* pulls, const double* stage,
                           double* y, double* ynext, double* ytop) {
     if (nfin <= 0) return cudaSuccess;
     counted();
-    k_ap_fin<<<nfin, kApplyThreads, 0, st>>>(fins, pulls, stage, y, ynext, ytop);
-    return cudaGetLastError();
+    return launch_chained(k_ap_fin, nfin, kApplyThreads, 0, st, fins, pulls, stage, y, ynext, ytop);
 }
 
 cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntasks, int smax, int nmax,
@@ -2936,12 +2977,10 @@ cudaError_t launch_ap_bwd(cudaStream_t st, const ApTask* tasks, int t0, int ntas
     counted();
     const size_t smem = sizeof(double) * (2 * (size_t)smax + kApplyThreads + nmax);
     if (fp32)
-        k_ap_bwd<float><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const float*>(fac), y, smax,
-                                                             nmax);
-    else
-        k_ap_bwd<double><<<ntasks, kApplyThreads, smem, st>>>(tasks, t0, nbs, static_cast<const double*>(fac), y,
-                                                              smax, nmax);
-    return cudaGetLastError();
+        return launch_chained(k_ap_bwd<float>, ntasks, kApplyThreads, smem, st, tasks, t0, nbs,
+                              static_cast<const float*>(fac), y, smax, nmax);
+    return launch_chained(k_ap_bwd<double>, ntasks, kApplyThreads, smem, st, tasks, t0, nbs,
+                          static_cast<const double*>(fac), y, smax, nmax);
 }
 
 cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L,
@@ -2965,8 +3004,7 @@ cudaError_t launch_ap_coarse_batch(cudaStream_t st, const ApLevel* lvl, int nlev
 cudaError_t launch_dense_gemv(cudaStream_t st, int n, const double* Mc, const double* x, double* y) {
     if (n <= 0) return cudaSuccess;
     counted();
-    k_dense_gemv<<<(n + 7) / 8, 256, 0, st>>>(n, Mc, x, y);
-    return cudaGetLastError();
+    return launch_chained(k_dense_gemv, (n + 7) / 8, 256, 0, st, n, Mc, x, y);
 }
 
 cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int ntop, const double* L, double* ytop,
@@ -2979,17 +3017,15 @@ cudaError_t launch_ap_coarse(cudaStream_t st, const ApLevel* lvl, int nlev, int 
                          : cudaFuncSetAttribute(k_ap_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)smem);
     if (e != cudaSuccess) return e;
-    if (fp32) k_ap_coarse<float><<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
-    else k_ap_coarse<double><<<1, kCoarseThreads, smem, st>>>(lvl, nlev, ntop, L, ytop);
-    return cudaGetLastError();
+    if (fp32) return launch_chained(k_ap_coarse<float>, 1, kCoarseThreads, smem, st, lvl, nlev, ntop, L, ytop);
+    return launch_chained(k_ap_coarse<double>, 1, kCoarseThreads, smem, st, lvl, nlev, ntop, L, ytop);
 }
 
 cudaError_t launch_vcopy(cudaStream_t st, const VCopyDev* cps, int ncps, const double* src, double* dst,
                          int reverse, const double* ytop) {
     if (ncps <= 0) return cudaSuccess;
     counted();
-    k_vcopy<<<blocks_for(ncps, 8), 256, 0, st>>>(cps, ncps, src, dst, reverse, ytop);
-    return cudaGetLastError();
+    return launch_chained(k_vcopy, blocks_for(ncps, 8), 256, 0, st, cps, ncps, src, dst, reverse, ytop);
 }
 
 cudaError_t launch_tops_cholesky(cudaStream_t st, const TopDev* tops, int ntops, int32_t* status) {
@@ -3002,8 +3038,7 @@ cudaError_t launch_tops_cholesky(cudaStream_t st, const TopDev* tops, int ntops,
 cudaError_t launch_tops_solve(cudaStream_t st, const TopDev* tops, int ntops, double* ytop) {
     if (ntops <= 0) return cudaSuccess;
     counted();
-    k_tops_solve<<<ntops, 256, 0, st>>>(tops, ytop);
-    return cudaGetLastError();
+    return launch_chained(k_tops_solve, ntops, 256, 0, st, tops, ytop);
 }
 
 cudaError_t launch_top_solve(cudaStream_t st, int n, const double* L, double* y) {
