@@ -14,6 +14,7 @@
 // input; eliminating a cluster's fine part creates a block between every pair
 // of its neighbours; a cluster with no fill block has rank 0 and leaves.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -442,14 +443,13 @@ struct Partitioner {
         return out;
     }
 
-    // One bisection of `set` (ascending): with coordinates the left part is
-    // the ceil(k/2) smallest lines in (coordinate, index) order along the
-    // longer extent, else the first ceil(k/2) lines of a BFS order started
-    // from a pseudo-peripheral line; both parts come out ascending.  Only the
-    // coordinate rule runs on several sets at once (the BFS reads the marks
-    // of neighbouring lines, which may belong to another set).  The
-    // multilevel rule bisects the weighted subgraph induced by `set` (its
-    // lines carry own == sid) into ceil(k/2) and floor(k/2) lines.
+    // One bisection of `set` (ascending) without coordinates: the first
+    // ceil(k/2) lines of a BFS order started from a pseudo-peripheral line;
+    // both parts come out ascending.  The BFS reads the marks of neighbouring
+    // lines, which may belong to another set, so it runs on one set at a
+    // time.  The multilevel rule bisects the weighted subgraph induced by
+    // `set` (its lines carry own == sid) into ceil(k/2) and floor(k/2) lines.
+    // With coordinates, bisect_coords below.
     void bisect(const std::vector<int>& set, std::vector<int>& a, std::vector<int>& b, int sid = -1) {
         const size_t k = set.size(), left = (k + 1) / 2;
         a.clear();
@@ -471,20 +471,6 @@ struct Partitioner {
             a.reserve(left);
             b.reserve(k - left);
             for (size_t i = 0; i < k; i++) (part[i] == 0 ? a : b).push_back(set[i]);
-        } else if (have_coords) {
-            double x0 = lx[set[0]], x1 = x0, y0 = ly[set[0]], y1 = y0;
-            for (int x : set) {
-                x0 = std::min(x0, lx[x]); x1 = std::max(x1, lx[x]);
-                y0 = std::min(y0, ly[x]); y1 = std::max(y1, ly[x]);
-            }
-            const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? lx : ly;
-            auto less = [&](int u, int v) { return key[u] < key[v] || (key[u] == key[v] && u < v); };
-            std::vector<int> tmp(set);
-            std::nth_element(tmp.begin(), tmp.begin() + (left - 1), tmp.end(), less);
-            const int piv = tmp[left - 1];
-            a.reserve(left);
-            b.reserve(k - left);
-            for (int x : set) (less(x, piv) || x == piv ? a : b).push_back(x);
         } else {
             const int lo = *std::min_element(set.begin(), set.end());
             std::vector<int> first = bfs(set, lo);
@@ -498,8 +484,7 @@ struct Partitioner {
 
     // Leaf ids follow the depth-first order: the left half of the set below
     // leaf offset `base` at depth d keeps `base`, the right half starts
-    // 2^(L-d-1) further.  Depth-first recursion, the top on two threads with
-    // coordinates.
+    // 2^(L-d-1) further.  Depth-first recursion (the BFS rule).
     void split(std::vector<int> set, int depth, int base) {
         if (depth == L) {
             for (int x : set) leaf_of[x] = base;
@@ -507,24 +492,90 @@ struct Partitioner {
         }
         std::vector<int> a, b;
         bisect(set, a, b);
-        const size_t k = set.size();
         std::vector<int>().swap(set);
         const int half = 1 << (L - depth - 1);
-        if (have_coords && depth < 3 && k > 4096 && !tl_serial) {
+        split(std::move(a), depth + 1, base);
+        split(std::move(b), depth + 1, base + half);
+    }
+
+    // The coordinate rule on v[0, k) (ascending) in place: the left part is
+    // the ceil(k/2) smallest lines in (coordinate, index) order along the
+    // longer extent; the pivot is selected by nth_element on a copy in tmp
+    // (at least k ints), then both parts are written back ascending.
+    void bisect_coords(int* v, int k, int* tmp) {
+        const int left = (k + 1) / 2;
+        double x0 = lx[v[0]], x1 = x0, y0 = ly[v[0]], y1 = y0;
+        for (int i = 0; i < k; i++) {
+            const int x = v[i];
+            x0 = std::min(x0, lx[x]); x1 = std::max(x1, lx[x]);
+            y0 = std::min(y0, ly[x]); y1 = std::max(y1, ly[x]);
+        }
+        const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? lx : ly;
+        auto less = [&](int u, int w) { return key[u] < key[w] || (key[u] == key[w] && u < w); };
+        std::copy(v, v + k, tmp);
+        std::nth_element(tmp, tmp + (left - 1), tmp + k, less);
+        const int piv = tmp[left - 1];
+        int na = 0, nb = 0;
+        for (int i = 0; i < k; i++) {
+            const int x = v[i];
+            if (less(x, piv) || x == piv) v[na++] = x;
+            else tmp[nb++] = x;
+        }
+        std::copy(tmp, tmp + nb, v + na);
+    }
+    void split_coords(int* v, int k, int depth, int base, int* tmp) {
+        if (depth == L || k <= 0) {
+            for (int i = 0; i < k; i++) leaf_of[v[i]] = base;
+            return;
+        }
+        bisect_coords(v, k, tmp);
+        const int left = (k + 1) / 2, half = 1 << (L - depth - 1);
+        if (depth < 3 && k > 4096 && !tl_serial) {  // the two halves' scratch is disjoint too
             run_threads(2, [&](int t) {
-                if (t == 1) split(std::move(a), depth + 1, base);
-                else split(std::move(b), depth + 1, base + half);
+                if (t == 1) split_coords(v, left, depth + 1, base, tmp);
+                else split_coords(v + left, k - left, depth + 1, base + half, tmp + left);
             });
         } else {
-            split(std::move(a), depth + 1, base);
-            split(std::move(b), depth + 1, base + half);
+            split_coords(v, left, depth + 1, base, tmp);
+            split_coords(v + left, k - left, depth + 1, base + half, tmp);
         }
     }
 
-    // The same leaves; for many lines with coordinates, in L rounds with all
-    // sets of a round bisected in parallel.
+    // The same leaves; with coordinates in place on one array (for many
+    // lines in L rounds, the sets of a round bisected in parallel), for the
+    // multilevel rule in L rounds of parallel bisections.
     void split_all(std::vector<int> all) {
-        if (!multilevel && !(have_coords && nl > (1 << 15) && !tl_serial)) {
+        if (have_coords && !multilevel) {
+            const int k = (int)all.size();
+            std::vector<int> tmp(std::max(k, 1));  // scratch: a set's copy sits at the set's offset
+            if (nl <= (1 << 15) || tl_serial) {
+                split_coords(all.data(), k, 0, 0, tmp.data());
+                return;
+            }
+            // sets of a round: (offset, size, leaf base), contiguous in `all`
+            std::vector<std::array<int, 3>> sets{{0, k, 0}}, next;
+            for (int depth = 0; depth < L; depth++) {
+                const int half = 1 << (L - depth - 1);
+                parallel_ranges((int64_t)sets.size(), 1, [&](int64_t lo, int64_t hi, int) {
+                    for (int64_t i = lo; i < hi; i++)
+                        if (sets[i][1] > 0)
+                            bisect_coords(all.data() + sets[i][0], sets[i][1], tmp.data() + sets[i][0]);
+                });
+                next.clear();
+                for (const auto& st : sets) {
+                    const int left = (st[1] + 1) / 2;
+                    next.push_back({st[0], left, st[2]});
+                    next.push_back({st[0] + left, st[1] - left, st[2] + half});
+                }
+                sets.swap(next);
+            }
+            parallel_ranges((int64_t)sets.size(), 64, [&](int64_t lo, int64_t hi, int) {
+                for (int64_t i = lo; i < hi; i++)
+                    for (int j = 0; j < sets[i][1]; j++) leaf_of[all[sets[i][0] + j]] = sets[i][2];
+            });
+            return;
+        }
+        if (!multilevel) {
             split(std::move(all), 0, 0);
             return;
         }
@@ -535,14 +586,14 @@ struct Partitioner {
             const int ns = (int)sets.size(), half = 1 << (L - depth - 1);
             next.assign(2 * (size_t)ns, {});
             nbase.assign(2 * (size_t)ns, 0);
-            if (multilevel)  // each line learns its set of this round before any set is bisected
-                parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
-                    for (int64_t i = lo; i < hi; i++)
-                        for (size_t j = 0; j < sets[i].size(); j++) {
-                            own[sets[i][j]] = (int)i;
-                            loc[sets[i][j]] = (int)j;
-                        }
-                });
+            // each line learns its set of this round before any set is bisected
+            parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
+                for (int64_t i = lo; i < hi; i++)
+                    for (size_t j = 0; j < sets[i].size(); j++) {
+                        own[sets[i][j]] = (int)i;
+                        loc[sets[i][j]] = (int)j;
+                    }
+            });
             parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
                 for (int64_t i = lo; i < hi; i++) {
                     bisect(sets[i], next[2 * i], next[2 * i + 1], (int)i);

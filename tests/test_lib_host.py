@@ -43,6 +43,8 @@ def test_default_options_and_status(hs):
     lambda: inputs.vector_operator(8, 6, 3, ratio=1e6),
     lambda: inputs.grid_operator(4, 4, 4, ratio=1e-3),
     lambda: inputs.batched_problem(3),
+    # 10,000 lines: the top bisections of the coordinate rule on two threads
+    lambda: inputs.grid_operator(100, 100, 2, ratio=1e4, sigma=1.0, seed=2, bc="ice"),
 ])
 def test_partition_matches_oracle(hs, oracle_lib, make, use_coords):
     p = make()
