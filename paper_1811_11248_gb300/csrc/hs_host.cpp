@@ -1085,9 +1085,17 @@ constexpr int kBitsMax = 2048;
 
 void plan_range_bits(LevelPlan& P, int lo, int hi, std::vector<std::vector<int>>& phases, RangeLists& out) {
     const int m = hi - lo, W = (m + 63) / 64;
-    std::vector<uint64_t> cur((size_t)m * W, 0), in((size_t)m * W, 0), gone((size_t)m * W, 0);
+    // the three bit matrices in one buffer kept by the thread (a fresh
+    // allocation of this size costs more in page faults than the planning)
+    static thread_local std::vector<uint64_t> bits;
+    const size_t mw = (size_t)m * W;
+    if (bits.size() < 3 * mw) bits.resize(3 * mw);
+    std::memset(bits.data(), 0, sizeof(uint64_t) * 3 * mw);
+    uint64_t* const cur = bits.data();
+    uint64_t* const in = cur + mw;
+    uint64_t* const gone = in + mw;
     std::vector<uint64_t> blocked(W), nlb((size_t)W);
-    auto row = [&](std::vector<uint64_t>& b, int c) { return b.data() + (size_t)(c - lo) * W; };
+    auto row = [&](uint64_t* b, int c) { return b + (size_t)(c - lo) * W; };
     auto set = [&](uint64_t* r, int q) { r[(q - lo) >> 6] |= 1ull << ((q - lo) & 63); };
     auto has = [&](const uint64_t* r, int q) { return (r[(q - lo) >> 6] >> ((q - lo) & 63)) & 1ull; };
     // appends the set bits of r, ascending; returns their number
@@ -1169,6 +1177,24 @@ void plan_range_bits(LevelPlan& P, int lo, int hi, std::vector<std::vector<int>>
         phases.push_back(sel);
     }
     for (int k = 0; k < LS_N; k++) out.cnt[k].assign(m, 0);
+    {
+        // exact sizes of the four lists first, so that none of them grows
+        size_t tot_all = 0, tot_end = 0;
+        for (int c = lo; c < hi; c++) {
+            const uint64_t *rc = row(cur, c), *gc = row(gone, c);
+            size_t a = 0, e = 0;
+            for (int w = 0; w < W; w++) {
+                a += (size_t)__builtin_popcountll(gc[w] | rc[w]);
+                e += (size_t)__builtin_popcountll(rc[w]);
+            }
+            tot_all += a + 1;
+            tot_end += e + 1;
+        }
+        out.data[LS_NL].reserve(out.data[LS_NL].size() + nw.size());
+        out.data[LS_WL].reserve(out.data[LS_WL].size() + nw.size());
+        out.data[LS_ALL].reserve(out.data[LS_ALL].size() + tot_all);
+        out.data[LS_END].reserve(out.data[LS_END].size() + tot_end);
+    }
     for (int c = lo; c < hi; c++) {
         const int i = c - lo;
         out.cnt[LS_NL][i] = cnt_n[i];
