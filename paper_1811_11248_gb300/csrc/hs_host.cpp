@@ -661,7 +661,7 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     tr.mark("  partition: union-find");
     Partitioner P;
     std::vector<int> line_of(n), first;
-    if (n <= (1 << 15) || tl_serial) {
+    if (n <= (1 << 18) || tl_serial) {
         std::vector<int> id(n, -1);
         for (int i = 0; i < n; i++) {
             const int r = find(i);  // roots are final: no link is running
