@@ -1931,33 +1931,82 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
     int jv = 0;  // columns below jv done with vector loads
     if constexpr (sizeof(FT) == sizeof(float)) {
         // four columns per thread, one aligned float4 per row (C and its
-        // leading dimension are multiples of 4 floats), four rows in flight
+        // leading dimension are multiples of 4 floats)
         jv = T.ncols & ~3;
-        for (int j4 = 4 * tid; j4 < jv; j4 += 4 * NT) {
+        const int ncg = jv >> 2;
+        int P = 32;  // threads per row chunk: a power of two >= the column groups
+        while (P < ncg) P <<= 1;
+        if (P <= NT / 2 && f >= 16) {
+            // the rows in R = NT / P chunks, eight rows in flight per thread;
+            // the chunks' partial sums are added in chunk order through
+            // shared memory (behind the two vectors)
+            const int R = NT / P, q = tid / P, cg = tid % P;
+            const int i0 = q * f / R, i1 = (q + 1) * f / R;
             float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
-            const float* cj = reinterpret_cast<const float*>(C) + j4;
-            int i = 0;
-            for (; i + 3 < f; i += 4) {
-                const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
-                const float4 c1 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 1) * T.ncap);
-                const float4 c2 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 2) * T.ncap);
-                const float4 c3 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 3) * T.ncap);
-                const float y0 = yf[i], y1 = yf[i + 1], y2 = yf[i + 2], y3 = yf[i + 3];
-                p0.x += c0.x * y0 + c2.x * y2; p0.y += c0.y * y0 + c2.y * y2;
-                p0.z += c0.z * y0 + c2.z * y2; p0.w += c0.w * y0 + c2.w * y2;
-                p1.x += c1.x * y1 + c3.x * y3; p1.y += c1.y * y1 + c3.y * y3;
-                p1.z += c1.z * y1 + c3.z * y3; p1.w += c1.w * y1 + c3.w * y3;
+            if (cg < ncg) {
+                const float* cj = reinterpret_cast<const float*>(C) + 4 * cg;
+                int i = i0;
+                for (; i + 7 < i1; i += 8) {
+                    float4 c[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) c[u] = *reinterpret_cast<const float4*>(cj + (int64_t)(i + u) * T.ncap);
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        const float ya = yf[i + u], yb = yf[i + u + 1];
+                        p0.x += c[u].x * ya; p0.y += c[u].y * ya; p0.z += c[u].z * ya; p0.w += c[u].w * ya;
+                        p1.x += c[u + 1].x * yb; p1.y += c[u + 1].y * yb;
+                        p1.z += c[u + 1].z * yb; p1.w += c[u + 1].w * yb;
+                    }
+                }
+                for (; i < i1; i++) {
+                    const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
+                    const float y0 = yf[i];
+                    p0.x += c0.x * y0; p0.y += c0.y * y0; p0.z += c0.z * y0; p0.w += c0.w * y0;
+                }
             }
-            for (; i < f; i++) {
-                const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
-                const float y0 = yf[i];
-                p0.x += c0.x * y0; p0.y += c0.y * y0; p0.z += c0.z * y0; p0.w += c0.w * y0;
+            float4* red = reinterpret_cast<float4*>(sh + 2 * smax);
+            red[tid] = make_float4(p0.x + p1.x, p0.y + p1.y, p0.z + p1.z, p0.w + p1.w);
+            __syncthreads();
+            if (q == 0 && cg < ncg) {
+                float4 a = red[cg];
+                for (int k = 1; k < R; k++) {
+                    const float4 b = red[k * P + cg];
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                }
+                double* st = stage + T.stg + 4 * cg;
+                st[0] = (double)a.x;
+                st[1] = (double)a.y;
+                st[2] = (double)a.z;
+                st[3] = (double)a.w;
             }
-            double* st = stage + T.stg + j4;
-            st[0] = (double)(p0.x + p1.x);
-            st[1] = (double)(p0.y + p1.y);
-            st[2] = (double)(p0.z + p1.z);
-            st[3] = (double)(p0.w + p1.w);
+        } else {
+            // more column groups than half the threads: one thread per group
+            for (int j4 = 4 * tid; j4 < jv; j4 += 4 * NT) {
+                float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+                const float* cj = reinterpret_cast<const float*>(C) + j4;
+                int i = 0;
+                for (; i + 3 < f; i += 4) {
+                    const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
+                    const float4 c1 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 1) * T.ncap);
+                    const float4 c2 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 2) * T.ncap);
+                    const float4 c3 = *reinterpret_cast<const float4*>(cj + (int64_t)(i + 3) * T.ncap);
+                    const float y0 = yf[i], y1 = yf[i + 1], y2 = yf[i + 2], y3 = yf[i + 3];
+                    p0.x += c0.x * y0 + c2.x * y2; p0.y += c0.y * y0 + c2.y * y2;
+                    p0.z += c0.z * y0 + c2.z * y2; p0.w += c0.w * y0 + c2.w * y2;
+                    p1.x += c1.x * y1 + c3.x * y3; p1.y += c1.y * y1 + c3.y * y3;
+                    p1.z += c1.z * y1 + c3.z * y3; p1.w += c1.w * y1 + c3.w * y3;
+                }
+                for (; i < f; i++) {
+                    const float4 c0 = *reinterpret_cast<const float4*>(cj + (int64_t)i * T.ncap);
+                    const float y0 = yf[i];
+                    p0.x += c0.x * y0; p0.y += c0.y * y0; p0.z += c0.z * y0; p0.w += c0.w * y0;
+                }
+                double* st = stage + T.stg + j4;
+                st[0] = (double)(p0.x + p1.x);
+                st[1] = (double)(p0.y + p1.y);
+                st[2] = (double)(p0.z + p1.z);
+                st[3] = (double)(p0.w + p1.w);
+            }
         }
     }
     for (int j = jv + tid; j < T.ncols; j += NT) {
@@ -2956,7 +3005,9 @@ cudaError_t launch_ap_fwd(cudaStream_t st, const ApTask* tasks, int t0, int ntas
                           const ApPull* pulls, const void* fac, int fp32, double* stage, double* y) {
     if (ntasks <= 0) return cudaSuccess;
     counted();
-    const size_t smem = sizeof(double) * 2 * smax;
+    // the two vectors, then (FP32 factor) one float4 per thread for the
+    // row-chunk partial sums
+    const size_t smem = sizeof(double) * 2 * smax + (fp32 ? sizeof(float) * 4 * kApplyThreads : 0);
     if (fp32)
         return launch_chained(k_ap_fwd<float>, ntasks, kApplyThreads, smem, st, tasks, t0, pulls,
                               static_cast<const float*>(fac), stage, y, smax);
