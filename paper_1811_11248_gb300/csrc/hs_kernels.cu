@@ -11,17 +11,25 @@
 //                          offdiag_new, Eq. sparse; FP32 in the mixed form),
 //                          write-back of the coarse row (Eq. perm) and of the
 //                          factor {W = U^T G^-1, C, r}.
-//   k_factor_level_fused : all phases of a coarse level in one cooperative
-//                          launch, one warp per cluster, bounded grid barrier.
-//   k_schur_phase        : one CTA per target block: X_nn = A_nn - C^T C (Eq.
-//                          elim), contributions summed in ascending cluster order.
+//   k_factor_level_fused : all phases of a coarse level in one launch, one
+//                          warp per cluster (clusters of at most 8 DOFs with
+//                          the block row in registers): one thread-block
+//                          cluster with the hardware cluster barrier between
+//                          phases, else a cooperative launch with a bounded
+//                          grid barrier.
+//   k_schur_phase(_tc)   : one CTA per target block: X_nn = A_nn - C^T C (Eq.
+//                          elim), contributions summed in ascending cluster
+//                          order; the mixed form's products on the tensor
+//                          cores (mma.sync, TF32 x3 split or BF16).
 //   k_dense_cholesky / k_tops_cholesky : the dense top(s).
 // Solve (Algorithm 2): k_ap_fwd / k_ap_bwd per stage with the explicit
 // per-cluster operator W = U^T G^-1, k_ap_fin / k_vcopy between levels,
 // k_ap_coarse (single-CTA chain) or k_dense_gemv (explicit coarse operator
-// formed by k_ap_coarse_batch), k_tops_solve for batched tops.
-// Krylov: CSR SpMV, deterministic two-stage dot products, vector updates,
-// per-problem (segmented) PCG kernels for batched handles.
+// formed by k_ap_coarse_batch), k_tops_solve for batched tops; captured in
+// one CUDA graph, each kernel launched with programmatic dependent launch.
+// Krylov: CSR SpMV fused with p^T q, the x/r update fused with r^T r, dot
+// products in one launch (block partials added in index order by the last
+// block), per-problem (segmented) PCG kernels for batched handles.
 //
 // Decisions that must agree with any other implementation of the method:
 // rank = smallest k with sum of squared trailing column norms <= eps^2;
