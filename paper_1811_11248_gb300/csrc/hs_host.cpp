@@ -703,17 +703,17 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
     }
     P.nl = (int)first.size();
     tr.mark("  partition: line ids");
+    // DOFs grouped by line (counting sort), ascending within a line
+    std::vector<int> lptr(P.nl + 1, 0), ldof(n);
+    for (int i = 0; i < n; i++) lptr[line_of[i] + 1]++;
+    for (int l = 0; l < P.nl; l++) lptr[l + 1] += lptr[l];
     {
-        // DOFs grouped by line (counting sort), then each line's neighbour
-        // lines collected with a visit stamp and sorted
+        std::vector<int> pos(lptr.begin(), lptr.end() - 1);
+        for (int i = 0; i < n; i++) ldof[pos[line_of[i]]++] = i;
+    }
+    {
+        // each line's neighbour lines collected with a visit stamp and sorted
         const int nl = P.nl;
-        std::vector<int> lptr(nl + 1, 0), ldof(n);
-        for (int i = 0; i < n; i++) lptr[line_of[i] + 1]++;
-        for (int l = 0; l < nl; l++) lptr[l + 1] += lptr[l];
-        {
-            std::vector<int> pos(lptr.begin(), lptr.end() - 1);
-            for (int i = 0; i < n; i++) ldof[pos[line_of[i]]++] = i;
-        }
         // neighbour lines of each line, ranges of lines on separate threads
         const int T = hs_threads();
         std::vector<std::vector<int>> adj(T), cnt(T);
@@ -760,13 +760,6 @@ int partition_impl(int64_t n64, const int64_t* rowptr, const int32_t* col, const
         P.multilevel = true;
         P.gw.assign(P.gadj.size(), 0.0);
         const int nl = P.nl;
-        std::vector<int> lptr(nl + 1, 0), ldof(n);
-        for (int i = 0; i < n; i++) lptr[line_of[i] + 1]++;
-        for (int l = 0; l < nl; l++) lptr[l + 1] += lptr[l];
-        {
-            std::vector<int> pos(lptr.begin(), lptr.end() - 1);
-            for (int i = 0; i < n; i++) ldof[pos[line_of[i]]++] = i;
-        }
         parallel_ranges(nl, 256, [&](int64_t lo, int64_t hi, int) {
             std::vector<double> acc(nl, 0.0);
             for (int64_t l = lo; l < hi; l++) {
