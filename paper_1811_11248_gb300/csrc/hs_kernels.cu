@@ -1887,6 +1887,48 @@ __global__ void __launch_bounds__(1024) k_dense_cholesky(int n, double* a, int32
 // ---------------------------------------------------------------------------
 constexpr int kApplyThreads = 128;
 
+// v - sum of stage[pulls[pi].off + j] over pi in [p0, p1), subtracted in
+// ascending pi.  The offsets and values are fetched eight pulls at a time, so
+// a task with P pulls waits for 2 ceil(P/8) rounds of loads instead of 2P.
+__device__ __forceinline__ double sub_pulls(double v, const ApPull* __restrict__ pulls, int p0, int p1,
+                                            const double* __restrict__ stage, int j) {
+    constexpr int kB = 8;
+    for (int pi = p0; pi < p1; pi += kB) {
+        int64_t o[kB];
+        double u[kB];
+#pragma unroll
+        for (int k = 0; k < kB; k++) o[k] = pi + k < p1 ? pulls[pi + k].off : -1;
+#pragma unroll
+        for (int k = 0; k < kB; k++) u[k] = o[k] >= 0 ? stage[o[k] + j] : 0.0;
+#pragma unroll
+        for (int k = 0; k < kB; k++)
+            if (pi + k < p1) v -= u[k];
+    }
+    return v;
+}
+
+// Gathers the neighbour slices nbs[e0, e1) of y into xnf (converted to FT):
+// xnf[nb.col + j] = y[nb.y + j] for j < nb.m, by threads g, g + gs, ...
+// Four descriptors, then their first values, are fetched per round of loads.
+template <typename FT>
+__device__ __forceinline__ void gather_nbs(const ApNb* __restrict__ nbs, int e0, int e1,
+                                           const double* __restrict__ y, FT* xnf, int g, int gs) {
+    constexpr int kB = 4;
+    for (int e = e0; e < e1; e += kB) {
+        ApNb nb[kB];
+        double u[kB];
+#pragma unroll
+        for (int k = 0; k < kB; k++) nb[k] = e + k < e1 ? nbs[e + k] : ApNb{0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kB; k++) u[k] = g < nb[k].m ? y[nb[k].y + g] : 0.0;
+#pragma unroll
+        for (int k = 0; k < kB; k++) {
+            if (g < nb[k].m) xnf[nb[k].col + g] = (FT)u[k];
+            for (int j = g + gs; j < nb[k].m; j += gs) xnf[nb[k].col + j] = (FT)y[nb[k].y + j];
+        }
+    }
+}
+
 // ----- solve phase, fine levels: one CTA per task, one launch per phase -----
 
 // Forward step of one phase:
@@ -1911,7 +1953,7 @@ k_ap_fwd(const ApTask* __restrict__ tasks, int t0, const ApPull* __restrict__ pu
     double* yg = y + T.y;
     for (int j = tid; j < s; j += NT) {
         double v = yg[j];
-        for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
+        v = sub_pulls(v, pulls, T.pull0, T.pull1, stage, j);
         ys[j] = (FT)v;
     }
     __syncthreads();
@@ -2042,7 +2084,7 @@ k_ap_fin(const ApFin* __restrict__ fins, const ApPull* __restrict__ pulls, const
     double* dst = (F.to_top ? ytop : ynext) + F.dst;
     for (int j = threadIdx.x; j < F.len; j += blockDim.x) {
         double v = y[F.y + j];
-        for (int pi = F.pull0; pi < F.pull1; pi++) v -= stage[pulls[pi].off + j];
+        v = sub_pulls(v, pulls, F.pull0, F.pull1, stage, j);
         y[F.y + j] = v;
         dst[j] = v;
     }
@@ -2066,10 +2108,7 @@ k_ap_bwd(const ApTask* __restrict__ tasks, int t0, const ApNb* __restrict__ nbs,
     const int s = T.s, r = T.r, f = s - r, tid = threadIdx.x, NT = blockDim.x;
     double* yg = y + T.y;
     for (int i = tid; i < s; i += NT) xs[i] = yg[i];
-    for (int e = T.nb0; e < T.nb1; e++) {
-        const ApNb nb = nbs[e];
-        for (int j = tid; j < nb.m; j += NT) xnf[nb.col + j] = (FT)y[nb.y + j];
-    }
+    gather_nbs<FT>(nbs, T.nb0, T.nb1, y, xnf, tid, NT);
     __syncthreads();
     const FT* C = fac + T.cm;
     const int lane = tid & 31, wid = tid >> 5, nwarp = NT >> 5;
@@ -2168,7 +2207,7 @@ __device__ void group_fwd(bool act, const ApTask& T, int gl, int gs, const ApPul
     const int s = act ? T.s : 0;
     for (int j = gl; j < s; j += gs) {
         double v = y[T.y + j];
-        for (int pi = T.pull0; pi < T.pull1; pi++) v -= stage[pulls[pi].off + j];
+        v = sub_pulls(v, pulls, T.pull0, T.pull1, stage, j);
         ysf[j] = (FT)v;
     }
     __syncwarp();
@@ -2222,10 +2261,7 @@ __device__ void group_bwd(bool act, const ApTask& T, int gl, int gs, const ApNb*
     const int s = act ? T.s : 0, r = T.r, f = s - r;
     for (int i = gl; i < s; i += gs) xs[i] = y[T.y + i];
     const int ncols = act ? T.ncols : 0;
-    for (int e = act ? T.nb0 : 0; e < (act ? T.nb1 : 0); e++) {
-        const ApNb nb = nbs[e];
-        for (int j = gl; j < nb.m; j += gs) xnf[nb.col + j] = (FT)y[nb.y + j];
-    }
+    if (act) gather_nbs<FT>(nbs, T.nb0, T.nb1, y, xnf, gl, gs);
     __syncwarp();
     if (act) {
         const FT* C = fac + T.cm;
@@ -2292,7 +2328,7 @@ __device__ void coarse_chain(const ApLevel* __restrict__ lvl, int nlev, int ntop
             const ApFin F = V.fins[k];
             for (int j = lane; j < F.len; j += 32) {
                 double v = yv[F.y + j];
-                for (int pi = F.pull0; pi < F.pull1; pi++) v -= stg[V.pulls[pi].off + j];
+                v = sub_pulls(v, V.pulls, F.pull0, F.pull1, stg, j);
                 yv[F.y + j] = v;
                 ynx[F.dst + j] = v;
             }
