@@ -404,7 +404,7 @@ struct Partitioner {
     bool multilevel = false;
     std::vector<int> gptr, gadj;
     std::vector<double> gw;       // line-graph edge weights (multilevel only)
-    std::vector<int> own, loc;    // per line: its set in the current round and its place there
+    std::vector<int> own, loc;    // per line: its set at the current depth and its place there
     int L = 0;
     std::vector<int> leaf_of;
     int next_leaf = 0;
@@ -586,7 +586,7 @@ struct Partitioner {
             const int ns = (int)sets.size(), half = 1 << (L - depth - 1);
             next.assign(2 * (size_t)ns, {});
             nbase.assign(2 * (size_t)ns, 0);
-            // each line learns its set of this round before any set is bisected
+            // each line learns its set at this depth before any set is bisected
             parallel_ranges(ns, 1, [&](int64_t lo, int64_t hi, int) {
                 for (int64_t i = lo; i < hi; i++)
                     for (size_t j = 0; j < sets[i].size(); j++) {
