@@ -127,6 +127,18 @@ def test_level_plan_matches_oracle_on_a_large_grid(hs, oracle_lib):
     assert ph.max() >= 2 and van.sum() > 0
 
 
+@pytest.mark.parametrize("nx,ny,diag", [(32, 32, True), (45, 40, False), (64, 32, True)])
+def test_level_plan_matches_oracle_bit_planner(hs, oracle_lib, nx, ny, diag):
+    """One range of at most 2,048 clusters (the bit-row planner, as at level
+    0 of the 64x64x16 workload), planned twice in a row on the same thread so
+    that its reused buffers start from the previous plan's contents."""
+    ptr, adj = _grid_graph(nx, ny, diag=diag)
+    size0 = np.random.default_rng(nx + ny).integers(1, 9, nx * ny)
+    first = _compare_plans(hs, oracle_lib, ptr, adj, size0)
+    again = _compare_plans(hs, oracle_lib, ptr, adj, size0)
+    assert all(np.array_equal(a, b) for a, b in zip(first, again))
+
+
 def test_level_plan_matches_oracle_on_random_graphs(hs, oracle_lib):
     rng = np.random.default_rng(1)
     for nc, deg in ((3000, 5.0), (20000, 7.0)):
